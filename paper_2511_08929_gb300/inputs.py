@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs: particle beams, laser parameters and the named workloads.
+
+This module holds no arithmetic of the QED method: it only draws initial particle
+states (positions, momenta, spins, polarizations, weights, ids) with numpy's
+seeded generator and records workload parameters.  Both the CUDA path and the
+CPU oracle start from these arrays.  The random numbers the method itself draws
+(optical depths, energy fractions, collapses, daughter ids) are not made here:
+each side derives them from its own Philox4x32-10 keyed by (id, step).
+
+Units: time 1/omega, length c/omega, momentum m c, fields m c omega / e.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+ME_EV = 510998.95  # electron rest energy, eV
+HC_EV_NM = 1239.841984  # h c, eV nm
+
+
+def eta0_for_wavelength(wavelength_um: float) -> float:
+    """hbar omega / (m c^2) of a laser of the given wavelength."""
+    return HC_EV_NM / (wavelength_um * 1000.0) / ME_EV
+
+
+def _unit_vectors(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def lepton_beam(n: int, gamma: float, *, rel_spread: float = 0.0, ang_sigma: float = 0.0,
+                direction=(0.0, 0.0, -1.0), z_range=(0.0, 0.0), transverse=0.0, spin="random",
+                spin_dir=(0.0, 0.0, 1.0), degree: float = 1.0, seed: int = 0, id_offset: int = 0,
+                weight: float = 1.0) -> dict:
+    """A beam of n leptons with mean Lorentz factor `gamma`.
+
+    spin: "random"  -- independent uniformly distributed unit vectors (unpolarized ensemble)
+          "fixed"   -- all along spin_dir
+          "degree"  -- +-spin_dir with P(+) = (1 + degree)/2 (partially polarized, pure states)
+          "zero"    -- s = 0 (mixed, unpolarized macro-particles)
+    """
+    rng = np.random.default_rng(seed)
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    g = gamma * (1.0 + rel_spread * rng.normal(size=n)) if rel_spread > 0 else np.full(n, float(gamma))
+    g = np.maximum(g, 1.0 + 1e-9)
+    pmag = np.sqrt(g * g - 1.0)
+    # two unit vectors orthogonal to d
+    a = np.array([1.0, 0.0, 0.0]) if abs(d[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(d, a)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    th1 = ang_sigma * rng.normal(size=n) if ang_sigma > 0 else np.zeros(n)
+    th2 = ang_sigma * rng.normal(size=n) if ang_sigma > 0 else np.zeros(n)
+    dirs = d[None, :] + th1[:, None] * e1[None, :] + th2[:, None] * e2[None, :]
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    mom = dirs * pmag[:, None]
+    pos = np.zeros((n, 3))
+    pos[:, 2] = rng.uniform(z_range[0], z_range[1], size=n) if z_range[1] > z_range[0] else z_range[0]
+    if transverse > 0:
+        pos[:, 0] = rng.uniform(-transverse, transverse, size=n)
+        pos[:, 1] = rng.uniform(-transverse, transverse, size=n)
+    sd = np.asarray(spin_dir, dtype=np.float64)
+    sd = sd / np.linalg.norm(sd)
+    if spin == "random":
+        s = _unit_vectors(rng, n)
+    elif spin == "fixed":
+        s = np.tile(sd, (n, 1))
+    elif spin == "degree":
+        sign = np.where(rng.uniform(size=n) < 0.5 * (1.0 + degree), 1.0, -1.0)
+        s = sign[:, None] * sd[None, :]
+    elif spin == "zero":
+        s = np.zeros((n, 3))
+    else:
+        raise ValueError(spin)
+    ids = np.arange(id_offset, id_offset + n, dtype=np.uint64)
+    return {"pos": pos, "mom": mom, "spin": s, "w": np.full(n, float(weight)), "id": ids}
+
+
+def photon_beam(n: int, energy: float, *, direction=(1.0, 0.0, 0.0), P=(0.0, 1.0, 0.0), seed: int = 0,
+                id_offset: int = 0, weight: float = 1.0, P_list=None) -> dict:
+    """n photons of energy `energy` (units of m c^2) along `direction`, polarization vector P
+    (or P_list, cycled over the photons)."""
+    rng = np.random.default_rng(seed)
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    mom = np.tile(d * energy, (n, 1))
+    pos = np.zeros((n, 3))
+    pos[:, 0] = rng.uniform(-1.0, 1.0, size=n) * 0.0
+    if P_list is not None:
+        Ps = np.asarray(P_list, dtype=np.float64)
+        pol = Ps[np.arange(n) % len(Ps)]
+    else:
+        pol = np.tile(np.asarray(P, dtype=np.float64), (n, 1))
+    ids = np.arange(id_offset, id_offset + n, dtype=np.uint64)
+    return {"pos": pos, "mom": mom, "spin": pol, "w": np.full(n, float(weight)), "id": ids}
+
+
+def random_states(n: int, *, seed: int, gamma_range=(50.0, 5000.0), field_region=(-30.0, 30.0)) -> dict:
+    """Generic lepton states scattered over a collision region (used to exercise every branch in
+    one step): log-uniform gamma, random directions near -z, random pure/mixed spins."""
+    rng = np.random.default_rng(seed)
+    g = np.exp(rng.uniform(math.log(gamma_range[0]), math.log(gamma_range[1]), size=n))
+    pm = np.sqrt(g * g - 1.0)
+    d = np.column_stack([rng.normal(0, 0.05, n), rng.normal(0, 0.05, n), -np.ones(n)])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    mom = d * pm[:, None]
+    pos = np.column_stack([rng.uniform(-5, 5, n), rng.uniform(-5, 5, n), rng.uniform(*field_region, n)])
+    s = _unit_vectors(rng, n) * np.where(rng.uniform(size=n) < 0.7, 1.0, rng.uniform(size=n))[:, None]
+    return {"pos": pos, "mom": mom, "spin": s, "w": rng.uniform(0.5, 2.0, n), "id": np.arange(n, dtype=np.uint64) * 7919 + 13}
+
+
+# ----------------------------------------------------------------------------------------------
+# Named workloads (synthetic stand-ins for the paper's laser-beam collisions)
+# ----------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Laser:
+    kind: str  # "LP", "CP", "CP_COUNTER", "CONST"
+    a0: float
+    wavelength_um: float
+    n_cycles: float
+    phase: float = 0.0
+
+    @property
+    def eta0(self) -> float:
+        return eta0_for_wavelength(self.wavelength_um)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    n_electrons: int
+    gamma: float
+    laser: Laser
+    steps: int
+    dt: float = 2.0 * math.pi / 100.0  # lambda / (100 c)
+    rel_spread: float = 0.0
+    ang_sigma: float = 0.0
+    spin: str = "random"
+    spin_dir: tuple = (0.0, 0.0, 1.0)
+    pairs: bool = False
+    capacity_factor: float = 4.0
+    n_chi: int = 256
+    n_r: int = 256
+    seed: int = 1
+    photon_store_min: float = 0.0
+
+    def beam(self, n=None, seed=None):
+        n = self.n_electrons if n is None else n
+        lam = 2.0 * math.pi  # wavelength in c/omega
+        return lepton_beam(n, self.gamma, rel_spread=self.rel_spread, ang_sigma=self.ang_sigma,
+                           direction=(0.0, 0.0, -1.0), z_range=(lam, 11.0 * lam), spin=self.spin,
+                           spin_dir=self.spin_dir, seed=self.seed if seed is None else seed)
+
+
+# 1e4 electrons, gamma 2000 (1 % spread, 1 mrad), random unit spins, LP a0=50, 0.8 um, 10 cycles,
+# 2000 steps, emission only, tables 256 x 256, seed 1.
+HEADON_LP_SMALL = Workload("headon_lp_a50_g2000_n1e4", 10_000, 2000.0, Laser("LP", 50.0, 0.8, 10.0), 2000,
+                           rel_spread=0.01, ang_sigma=1e-3, spin="random", seed=1)
+# 1e7 electrons, gamma 4000, s = +z, CP a0=150, 20 cycles, 4000 steps, NLC + NBW, buffers 4x.
+HEADON_CP_LARGE = Workload("headon_cp_a150_g4000_n1e7", 10_000_000, 4000.0, Laser("CP", 150.0, 0.8, 20.0), 4000,
+                           spin="fixed", spin_dir=(0.0, 0.0, 1.0), pairs=True, capacity_factor=4.0, seed=2)
+
+
+def batched_instances(n_inst: int = 96, seed: int = 3, n_min: float = 1e3, n_max: float = 2e6):
+    """Independent collisions of uneven sizes: N log-uniform in [n_min, n_max], a0 ~ U[10, 300],
+    gamma ~ U[500, 8000], spins +-n_i with P(+) = (1 + d_i)/2, d_i ~ U[0, 1]; LP and CP alternate."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        a0 = float(rng.uniform(10.0, 300.0))
+        g = float(rng.uniform(500.0, 8000.0))
+        nd = rng.normal(size=3)
+        nd /= np.linalg.norm(nd)
+        deg = float(rng.uniform(0.0, 1.0))
+        out.append({"n": n, "a0": a0, "gamma": g, "spin_dir": tuple(nd), "degree": deg,
+                    "kind": "LP" if i % 2 == 0 else "CP", "seed": int(rng.integers(1 << 31))})
+    return out

@@ -1,0 +1,20 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: longer CPU-only statistical test")
+
+
+@pytest.fixture(scope="session")
+def small_tables():
+    """Oracle tables on a small grid (fast to build); the parity tests use the same grid on both sides."""
+    import oracle as O
+    return O.tables(1e-3, 1e2, 24, 64)
