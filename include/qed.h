@@ -1,0 +1,256 @@
+/*
+ * qed.h -- C ABI of libqedgb, a GB300 (sm_103a) implementation of the per-particle,
+ * per-time-step spin- and polarization-resolved strong-field QED step of
+ * Qian, Seipt, Vranic, Grismayer, Ridgers and Thomas, "A Fully Spin and
+ * Polarization Resolved Strong Field QED Algorithm for Particle-in-Cell Codes"
+ * (arXiv:2511.08929).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units: time 1/omega, length c/omega, momentum m c, fields m c omega / e,
+ *    photon energy m c^2.  eta0 = hbar omega / (m c^2); the Schwinger field is 1/eta0.
+ *  - Pointers named *_dev, and every array reached through qed_particles and
+ *    qed_counters, are DEVICE pointers (cudaMalloc / PyTorch CUDA tensors) owned by
+ *    the caller.  Pointers named host_* are host memory owned by the caller.  The
+ *    table handle owns its device memory and is freed by qed_tables_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call only enqueues work on it and returns, except where "synchronizes"
+ *    is written.  Calls are graph-capturable unless stated otherwise: particle
+ *    counts live in device memory and are read and updated by the kernels.
+ *  - Argument errors are returned synchronously (QED_ERR_ARG) and nothing is
+ *    enqueued.  Errors found on the device (capacity exhausted, non-finite input,
+ *    chi beyond the table) never trap: they are counted in qed_counters and the
+ *    first one sets qed_counters.status / first_bad, read back by qed_counters_read.
+ *  - All random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *    key = id ^ seed, counter = (step_lo, step_hi, slot, 0), so results do not
+ *    depend on launch configuration, and daughters get ids from the same stream.
+ *  - Thread safety: calls on different streams may run concurrently when they touch
+ *    disjoint particle buffers and counters; the table handle is read-only after build.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QED_ABI_VERSION 1
+
+typedef enum {
+    QED_OK = 0,
+    QED_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, misaligned buffer) */
+    QED_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    QED_ERR_CAPACITY = -3, /* device: a daughter did not fit in its buffer (counted, not applied) */
+    QED_ERR_RANGE = -4,    /* device: chi above the table range (clamped and counted) */
+    QED_ERR_NAN = -5,      /* device: a particle with non-finite state was skipped */
+    QED_ERR_TIMEOUT = -6,  /* device: a bounded wait gave up */
+    QED_ERR_STATE = -7,    /* handle used after destroy, or library not initialised */
+    QED_ERR_NOMEM = -8     /* device allocation failed */
+} qed_status;
+
+/* Particle buffer layouts = the two arithmetic paths. */
+enum {
+    QED_FP64 = 0, /* plain path: eleven double planes, all arithmetic in FP64 */
+    QED_FP32 = 1  /* fast path: three float4 planes; push, rates and sampling in FP32,
+                     optical depth and spin renormalisation in FP64 */
+};
+
+/* Species charge (qed_particles.charge). */
+enum { QED_ELECTRON = -1, QED_PHOTON = 0, QED_POSITRON = 1 };
+
+/* Physics switches (qed_step_desc.flags); the paper's "flexible switch" of Sec. 7.4.1. */
+enum {
+    QED_F_TAU = 1u << 0,           /* optical-depth event decision (Sec. 3.1); else r1 < W dt per step */
+    QED_F_RECOIL = 1u << 1,        /* radiation reaction p_f = (1 - lambda) p_i (Sec. 4.1) */
+    QED_F_SPIN_COLLAPSE = 1u << 2, /* s_f = +-S_SQA (Sec. 4.1, 4.2); else the expectation value */
+    QED_F_POL_COLLAPSE = 1u << 3,  /* xi = +-Xi_PQA (Sec. 4.1); else xi = F/F0 */
+    QED_F_NONTRANSITION = 1u << 4, /* spin / polarization update without an event (Sec. 5) */
+    QED_F_PUSH = 1u << 5,          /* Boris momentum push */
+    QED_F_TBMT = 1u << 6,          /* T-BMT spin precession (Sec. 7.3) */
+    QED_F_TBMT_PAPER = 1u << 7,    /* T-BMT v x E coefficient as printed, (a + 1/gamma) */
+    QED_F_EMIT = 1u << 8,          /* QED events: NLC for leptons, NBW for photons */
+    QED_F_RESOLVED = 1u << 9,      /* rates and sampling depend on s.beta / xi3 (Sec. 4.1, 4.2) */
+    QED_F_MOVE = 1u << 10,         /* position advance */
+    QED_F_SPIN_EVENT = 1u << 11,   /* lepton spin changes at emission; pair daughters get spins */
+    QED_F_POL_EVENT = 1u << 12     /* emitted photons carry the Stokes vector of F (else unpolarized) */
+};
+#define QED_F_FULL                                                                                     \
+    (QED_F_TAU | QED_F_RECOIL | QED_F_SPIN_COLLAPSE | QED_F_POL_COLLAPSE | QED_F_NONTRANSITION |       \
+     QED_F_PUSH | QED_F_TBMT | QED_F_EMIT | QED_F_RESOLVED | QED_F_MOVE | QED_F_SPIN_EVENT | QED_F_POL_EVENT)
+
+/* Analytic fields that stand in for the PIC grid fields (Sec. 3). */
+enum {
+    QED_FIELD_CONST = 0,     /* E = E0, B = B0 */
+    QED_FIELD_LP = 1,        /* E = a0 g(phi) cos(phi) x, B = z x E, phi = t - z + phase */
+    QED_FIELD_CP = 2,        /* E = a0 g(phi) (cos phi, sin phi, 0), B = z x E */
+    QED_FIELD_CP_COUNTER = 3 /* CP plus a CP wave along -z with phi2 = t + z + phase, B2 = -z x E2 */
+};
+
+typedef struct {
+    int32_t kind;
+    int32_t pad;
+    double a0;       /* peak amplitude per component, units of m c omega / e */
+    double n_cycles; /* envelope g = sin^2(phi / (2 n_cycles)) on 0 <= phi <= 2 pi n_cycles, else 0 */
+    double phase;    /* added to t - z (and to t + z for the counter-propagating wave) */
+    double E0[3], B0[3];
+    double eta0;     /* hbar omega / (m c^2) of the laser that sets the units */
+} qed_field;
+
+/* Rate and inverse-CDF tables (Sec. 4.1: W_up/W_down and IntF^-1_up/down;
+ * Sec. 4.2: W_+/W_- and IntG^-1_+/-).
+ *   chi_i = exp(ln chi_min + i dlnchi), i < n_chi; y_m = y_lo + m dy, m < n_r, r_m = 1/(1 + e^-y_m).
+ *   NLC rate  ln I_s(chi_i),  I_s = int_0^1 [-IntK13(u') + kappa K23(u') + s lambda K13(u')] d lambda
+ *   NBW rate  ln(J_s(chi_i) e^{8/(3 chi_i)}),  J_s = int_0^1 [IntK13 + rho K23 - s K23](u~') d lambda
+ *   NLC ICDF  ln u'(chi_i, r_m),  the u' = 2 lambda / (3 chi (1 - lambda)) below which a fraction r_m
+ *             of the spectrum lies
+ *   NBW ICDF  ln x(chi_i, r_m),   x = u~' - 8/(3 chi) of the spectrum folded about lambda = 1/2,
+ *             counted from the centre
+ * Lookups interpolate linearly in (ln chi, value) between rows and by 4-point Lagrange in y along a row;
+ * below y_lo the asymptote (u' ~ r^3, x ~ r^2), above y_hi the last entry. */
+typedef struct {
+    double chi_min, chi_max;
+    int32_t n_chi; /* >= 2 */
+    int32_t n_r;   /* >= 4 */
+    double y_lo, y_hi;
+} qed_table_desc;
+
+typedef struct qed_tables_s *qed_tables_t;
+
+/* One particle species in structure-of-arrays form.  For photons, (px, py, pz) is the
+ * momentum hbar k and (sx, sy, sz) the polarization vector P of Sec. 2.2.
+ *   layout QED_FP64: x..w are eleven double arrays of `capacity` entries.
+ *   layout QED_FP32: q0 = (x, y, z, px), q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi) are float4
+ *                    arrays of `capacity` entries (16-byte aligned); tau is the FP64 optical depth stored
+ *                    as the low and high 32-bit words of its bit pattern.
+ * id: uint64 array; the Philox key of each particle.  count: device int64, the live count, advanced
+ * by the kernels that append daughters.  begin: optional device int64; when set, a step call processes
+ * particles [0, *begin) instead of [0, *count at launch), so that daughters appended during the current
+ * step by another call are not stepped until the next one (qed_snapshot_counts sets it).
+ * dead / n_dead (photons only): device list of the indices that converted to pairs, consumed by
+ * qed_compact; converted photons keep momentum 0 and weight 0 until then. */
+typedef struct {
+    int32_t layout;
+    int32_t charge;
+    int64_t capacity;
+    int64_t *count;
+    int64_t *begin;
+    double *x, *y, *z, *px, *py, *pz, *sx, *sy, *sz, *tau, *w;
+    float *q0, *q1, *q2;
+    uint64_t *id;
+    int64_t *dead;
+    int64_t *n_dead;
+} qed_particles;
+
+/* Per-step parameters. */
+typedef struct {
+    double dt;        /* step length */
+    double t;         /* time at the start of the step (fields are taken at t and the pre-push position) */
+    uint64_t step;    /* step index: the Philox counter */
+    uint64_t seed;    /* xored into the Philox key */
+    uint32_t flags;   /* QED_F_* */
+    uint32_t pad;
+    double photon_store_min; /* emitted photons with |k| below this are not stored (Sec. 3.2); 0 keeps all */
+    double chi_floor;        /* no QED event is considered below this chi */
+} qed_step_desc;
+
+/* Device-resident counters, accumulated by every step call (zero them with cudaMemset). */
+typedef struct {
+    unsigned long long events;           /* emissions (push step) or pair conversions (pair step) */
+    unsigned long long stored;           /* daughters written */
+    unsigned long long dropped_capacity; /* daughters that did not fit */
+    unsigned long long chi_clamped;      /* particle-steps with chi above chi_max */
+    unsigned long long renormalised;     /* spin / Stokes vectors rescaled to unit length */
+    unsigned long long below_store;      /* photons not stored because |k| < photon_store_min */
+    unsigned long long nonfinite;        /* particles skipped because their state was not finite */
+    int32_t status;                      /* first device-side error (qed_status), 0 if none */
+    int32_t pad;
+    int64_t first_bad;                   /* particle index of the first device-side error, -1 if none */
+} qed_counters;
+
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Version of this header the library was built from. */
+int32_t qed_abi_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *qed_status_string(int32_t status);
+
+/* Build the FP64 tables on the current device (Sec. 4.1 and 4.2 rate and ICDF tables, from the
+ * Bessel-function forms of App. A).  All integrals are evaluated in FP64 to full precision; the FP32
+ * path uses a float copy made here too.  Synchronizes `stream` before returning.
+ * Errors: QED_ERR_ARG (bad desc or null out), QED_ERR_NOMEM, QED_ERR_CUDA. */
+qed_status qed_tables_build(const qed_table_desc *desc, qed_tables_t *out, void *stream);
+
+/* Copy the FP64 tables to host arrays: rates [2][n_chi] (index 0 = up / xi3 = +1, 1 = down / xi3 = -1),
+ * ICDFs [2][n_chi][n_r].  Any pointer may be NULL to skip it.  Synchronous. */
+qed_status qed_tables_export(qed_tables_t t, double *host_nlc_rate, double *host_nbw_rate, double *host_nlc_icdf,
+                             double *host_nbw_icdf);
+
+/* Free the tables.  Synchronizes the device. */
+qed_status qed_tables_destroy(qed_tables_t t);
+
+/* Evaluate the device implementations of e^x K_{1/3}(x), e^x K_{2/3}(x), e^x int_x^inf K_{1/3} (App. A
+ * Bessel forms) for n arguments: precision QED_FP64 (table + series, FP64) or QED_FP32 (float table).
+ * x_dev: double[n]; out_dev: double[3 n] (k13, k23, intk13 interleaved).  For tests of the special
+ * functions used by the step kernels. */
+qed_status qed_bessel_eval(qed_tables_t t, int32_t precision, const double *x_dev, double *out_dev, int64_t n,
+                           void *stream);
+
+/* Look up the tables for n values of chi and r exactly as the step kernels do (FP64 or FP32 arithmetic):
+ * out_dev: double[6 n] = (I_up, I_down, ln u'_up(r), ln u'_down(r), J_+ e^{..}..) -- see qed_lookup_layout
+ * below.  For tests of the interpolation rules. */
+qed_status qed_tables_lookup(qed_tables_t t, int32_t precision, const double *chi_dev, const double *r_dev,
+                             double *out_dev, int64_t n, void *stream);
+/* out_dev row layout of qed_tables_lookup: [0] I_up(chi), [1] I_down(chi), [2] J_+(chi), [3] J_-(chi)
+ * (unscaled), [4] ln u' from the up ICDF, [5] ln u' from the down ICDF, [6] ln x from the + ICDF,
+ * [7] ln x from the - ICDF (NBW rows take r as the folded coordinate). */
+#define QED_LOOKUP_COLS 8
+
+/* Optical depth at birth for particles [begin, *count): tau = -ln u(id, step = 2^64 - 1, slot 0)
+ * (Sec. 3.1, optical-depth method). */
+qed_status qed_init_tau(qed_particles *p, uint64_t seed, int64_t begin, void *stream);
+
+/* One lepton step (Sec. 4.1 and its flow chart; Sec. 5 non-emission update): for every lepton in
+ * [0, *count at launch): fields at (x, t), Boris push, T-BMT precession, position advance, chi and the
+ * (eps, beta, k) basis, W_s, optical depth; on emission lambda from the ICDF, recoil, SQA collapse of
+ * the spin, PQA collapse of the photon Stokes vector, and a photon appended to `photons` (its P vector
+ * in the emission basis); without emission the non-emission spin update.  leptons->charge must be
+ * QED_ELECTRON or QED_POSITRON.  Photons appended this step are not stepped until the next call.
+ * photons may be NULL (emitted photons are then counted as dropped).  leptons and photons must have the
+ * same layout.  counters_dev: device qed_counters (accumulated). */
+qed_status qed_push_step(qed_tables_t t, const qed_field *field, const qed_step_desc *step, qed_particles *leptons,
+                         qed_particles *photons, qed_counters *counters_dev, void *stream);
+
+/* One photon step (Sec. 4.2 and its flow chart; Sec. 5 non-pair update): ballistic move, chi_gamma,
+ * basis, Stokes from P, W_xi, optical depth; on conversion lambda from the folded ICDF, the four
+ * correlated spin states of the pair, an electron and a positron appended (both at the photon's
+ * position), and the photon flagged dead (appended to photons->dead); otherwise the non-pair update of
+ * the Stokes vector.  A pair that does not fit leaves the photon alive (it retries next step). */
+qed_status qed_pair_step(qed_tables_t t, const qed_field *field, const qed_step_desc *step, qed_particles *photons,
+                         qed_particles *electrons, qed_particles *positrons, qed_counters *counters_dev,
+                         void *stream);
+
+/* Remove the photons listed in photons->dead (Sec. 3.3: converted photons leave the simulation) by
+ * moving live photons from the tail into the holes; the order of the survivors changes, their set does
+ * not.  Resets *n_dead to 0.  workspace: device memory of at least qed_compact_workspace_bytes(capacity)
+ * bytes (16-byte aligned), owned by the caller, zeroed (cudaMemset) before its first use; every call
+ * leaves it ready for the next one.  Calls that share a workspace must not overlap on the device. */
+qed_status qed_compact(qed_particles *photons, void *workspace, size_t workspace_bytes, void *stream);
+size_t qed_compact_workspace_bytes(int64_t capacity);
+
+/* *begin = *count for each of the n buffers (device-side copy; graph-capturable).  Call it at the start
+ * of a time step that runs several step calls, so each call processes only the particles alive when the
+ * step began (Sec. 3.3: an event's daughters join the simulation from the next step).  Buffers whose
+ * begin is NULL are skipped. */
+qed_status qed_snapshot_counts(qed_particles *const *buffers, int32_t n, void *stream);
+
+/* Copy the device counters to host and synchronize `stream` (the only blocking call of a step loop). */
+qed_status qed_counters_read(const qed_counters *counters_dev, qed_counters *host_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QED_H */

@@ -1,0 +1,189 @@
+"""Device memory for the C ABI: particle buffers as PyTorch CUDA tensors, the table handle, and the
+field / step descriptors.  PyTorch only allocates memory and provides streams here; every step of the
+method runs in libqedgb's kernels (see binding.py)."""
+from __future__ import annotations
+
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+PLANES64 = ("x", "y", "z", "px", "py", "pz", "sx", "sy", "sz", "tau", "w")
+
+
+class ParticleBuffer:
+    """One species in the layout qed.h describes: QED_FP64 (eleven double planes) or QED_FP32
+    (q0 = (x, y, z, px), q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi) float4 planes)."""
+
+    def __init__(self, capacity: int, layout: int, charge: int, device="cuda", photons: bool = False,
+                 use_begin: bool = False):
+        self.capacity = int(capacity)
+        self.layout = layout
+        self.charge = charge
+        cap = max(self.capacity, 1)
+        dev = torch.device(device)
+        self.device = dev
+        self.s = B.QedParticles()
+        self.s.layout = layout
+        self.s.charge = charge
+        self.s.capacity = self.capacity
+        if layout == B.QED_FP64:
+            self.planes = torch.zeros((11, cap), dtype=torch.float64, device=dev)
+            for i, n in enumerate(PLANES64):
+                setattr(self.s, n, self.planes[i].data_ptr())
+        else:
+            self.q = torch.zeros((3, cap, 4), dtype=torch.float32, device=dev)
+            for i in range(3):
+                setattr(self.s, f"q{i}", self.q[i].data_ptr())
+        self.ids = torch.zeros(cap, dtype=torch.int64, device=dev)
+        self.s.id = self.ids.data_ptr()
+        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)  # [count, begin]
+        self.s.count = self.counts.data_ptr()
+        # begin is opt-in: a caller that sets it must refresh it each step (qed_snapshot_counts)
+        self.s.begin = self.counts[1:].data_ptr() if use_begin else None
+        if photons:
+            self.dead = torch.zeros(cap, dtype=torch.int64, device=dev)
+            self.n_dead = torch.zeros(1, dtype=torch.int64, device=dev)
+            self.s.dead = self.dead.data_ptr()
+            self.s.n_dead = self.n_dead.data_ptr()
+
+    # ---- host <-> device marshalling -----------------------------------------------------
+    def load(self, pos, mom, spin, w, ids, tau=None):
+        """Copy host arrays (n, 3), (n, 3), (n, 3), (n,), (n,) [and tau (n,)] into [0, n) and set the count."""
+        n = len(ids)
+        if n > self.capacity:
+            raise ValueError("capacity")
+        pos, mom, spin = (np.asarray(a, dtype=np.float64).reshape(n, 3) for a in (pos, mom, spin))
+        w = np.asarray(w, dtype=np.float64).reshape(n)
+        tau = np.zeros(n) if tau is None else np.asarray(tau, dtype=np.float64).reshape(n)
+        if self.layout == B.QED_FP64:
+            host = np.empty((11, n))
+            host[0:3] = pos.T
+            host[3:6] = mom.T
+            host[6:9] = spin.T
+            host[9] = tau
+            host[10] = w
+            self.planes[:, :n].copy_(torch.from_numpy(host))
+        else:
+            host = np.zeros((3, n, 4), dtype=np.float32)
+            host[0, :, 0:3] = pos
+            host[0, :, 3] = mom[:, 0]
+            host[1, :, 0:2] = mom[:, 1:3]
+            host[1, :, 2:4] = spin[:, 0:2]
+            host[2, :, 0] = spin[:, 2]
+            host[2, :, 1] = w
+            host[2, :, 2:4] = tau.astype(np.float64).view(np.uint32).reshape(n, 2).view(np.float32)
+            self.q[:, :n].copy_(torch.from_numpy(host))
+        self.ids[:n].copy_(torch.from_numpy(np.asarray(ids, dtype=np.uint64).view(np.int64)))
+        self.counts.copy_(torch.tensor([n, n], dtype=torch.int64))
+        if hasattr(self, "n_dead"):
+            self.n_dead.zero_()
+
+    def count(self) -> int:
+        return int(self.counts[0].item())
+
+    def read(self) -> dict:
+        """Host copy of [0, count) as FP64 arrays (pos, mom, spin, tau, w, id)."""
+        n = self.count()
+        if self.layout == B.QED_FP64:
+            h = self.planes[:, :n].cpu().numpy()
+            pos, mom, spin, tau, w = h[0:3].T.copy(), h[3:6].T.copy(), h[6:9].T.copy(), h[9].copy(), h[10].copy()
+        else:
+            h = self.q[:, :n].cpu().numpy()
+            pos = h[0, :, 0:3].astype(np.float64)
+            mom = np.column_stack([h[0, :, 3], h[1, :, 0], h[1, :, 1]]).astype(np.float64)
+            spin = np.column_stack([h[1, :, 2], h[1, :, 3], h[2, :, 0]]).astype(np.float64)
+            w = h[2, :, 1].astype(np.float64)
+            tau = np.ascontiguousarray(h[2, :, 2:4]).view(np.uint32).reshape(n, 2).copy().view(np.float64).reshape(n)
+        ids = self.ids[:n].cpu().numpy().view(np.uint64).copy()
+        return {"pos": pos, "mom": mom, "spin": spin, "tau": tau, "w": w, "id": ids}
+
+    def init_tau(self, seed: int, begin: int = 0, stream: int = 0):
+        B.qed_init_tau(self.s, seed, begin, stream)
+
+    def bytes_per_particle(self) -> int:
+        return (88 if self.layout == B.QED_FP64 else 48) + 8
+
+
+class Tables:
+    """Owner of a qed_tables_t handle."""
+
+    def __init__(self, chi_min=1e-4, chi_max=1e3, n_chi=256, n_r=256, y_lo=-20.0, y_hi=20.0, stream: int = 0):
+        self.desc = B.QedTableDesc(chi_min, chi_max, n_chi, n_r, y_lo, y_hi)
+        self.handle = B.qed_tables_build(self.desc, stream)
+
+    def export(self):
+        return B.qed_tables_export(self.handle, self.desc)
+
+    def close(self):
+        if self.handle:
+            B.qed_tables_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def field(kind=B.QED_FIELD_LP, a0=0.0, n_cycles=10.0, phase=0.0, E0=(0, 0, 0), B0=(0, 0, 0),
+          eta0=3.0329e-6) -> B.QedField:
+    f = B.QedField()
+    f.kind = kind
+    f.a0 = a0
+    f.n_cycles = n_cycles
+    f.phase = phase
+    for i in range(3):
+        f.E0[i] = E0[i]
+        f.B0[i] = B0[i]
+    f.eta0 = eta0
+    return f
+
+
+def step_desc(dt, t, step, seed, flags=None, photon_store_min=0.0, chi_floor=0.0) -> B.QedStepDesc:
+    s = B.QedStepDesc()
+    s.dt = dt
+    s.t = t
+    s.step = step
+    s.seed = seed
+    s.flags = B.QED_F_FULL if flags is None else flags
+    s.photon_store_min = photon_store_min
+    s.chi_floor = chi_floor
+    return s
+
+
+class Counters:
+    """Device-resident qed_counters."""
+
+    def __init__(self, device="cuda"):
+        self.t = torch.zeros(16, dtype=torch.int64, device=device)  # 128 bytes >= sizeof(qed_counters)
+        self.ptr = self.t.data_ptr()
+
+    def zero(self):
+        self.t.zero_()
+
+    def read(self, stream: int = 0) -> B.QedCounters:
+        return B.qed_counters_read(self.ptr, stream)
+
+
+class CompactWorkspace:
+    def __init__(self, capacity: int, device="cuda"):
+        self.bytes = B.qed_compact_workspace_bytes(capacity)
+        self.t = torch.zeros((self.bytes + 15) // 16 * 2, dtype=torch.int64, device=device)
+        self.ptr = self.t.data_ptr()
+
+
+def laser_field(laser, kind_map=None) -> B.QedField:
+    """qed_field of an inputs.Laser."""
+    kinds = {"LP": B.QED_FIELD_LP, "CP": B.QED_FIELD_CP, "CP_COUNTER": B.QED_FIELD_CP_COUNTER}
+    return field(kinds[laser.kind], a0=laser.a0, n_cycles=laser.n_cycles, phase=laser.phase, eta0=laser.eta0)
+
+
+def sizeof_counters() -> int:
+    import ctypes
+    return ctypes.sizeof(B.QedCounters)
+
+
+assert sizeof_counters() <= 128

@@ -1,0 +1,222 @@
+// qed_bessel.cuh -- modified Bessel functions of the App. A spectra and the table lookups
+// (Sec. 4.1, 4.2).  All Bessel values are scaled: e^x K_{1/3}(x), e^x K_{2/3}(x),
+// e^x int_x^inf K_{1/3} -- the factor cancels in every ratio the event sampling takes, and the
+// rate/CDF integrands put it back explicitly.
+//
+//  * direct evaluation (table build, and x beyond the table): trapezoid rule on
+//    e^x K_nu(x) = int_0^inf exp(-x (cosh t - 1)) cosh(nu t) dt  (DLMF 10.32.9), and
+//    e^x IntK13(x) = int_0^inf exp(-x (cosh t - 1)) cosh(t/3)/cosh t dt, with step
+//    h = min(0.2, 0.6/sqrt x) (error ~ exp(-pi^2/h) for small x, exp(-2 pi^2/(h^2 x)) for large x);
+//  * x < kBesLo: two terms of each ascending series of I_{+-nu} (K_nu = pi (I_-nu - I_nu)/(2 sin nu pi));
+//  * otherwise a table on a uniform grid in ln x (spacing 0.02), interpolated by 8-point Lagrange
+//    (FP64 path, ~2e-15) or 4-point Lagrange (FP32 path, ~1e-9).
+#pragma once
+#include "qed_device.cuh"
+
+namespace qed {
+
+constexpr double kBesLo = 1e-4;   // table start
+constexpr double kBesH = 0.02;    // spacing in ln x
+constexpr int kBesN = 977;        // nodes: ln x in [ln 1e-4, ln 1e-4 + 976 * 0.02] (x up to 2.97e4)
+constexpr double kGamma13 = 2.6789385347077476337;  // Gamma(1/3)
+constexpr double kGamma23 = 1.3541179394264004169;  // Gamma(2/3)
+
+// --------------------------------------------------------------------------------------------
+// direct trapezoid (FP64)
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ void bessel_trapezoid(double x, double out[3]) {
+    double T = acosh(1.0 + 46.0 / x);
+    T = acosh(1.0 + (46.0 + (2.0 / 3.0) * T) / x);
+    const double h = fmin(0.2, 0.6 * rsqrt(x));
+    const int n = (int)ceil(T / h);
+    double s0 = 0.5, s1 = 0.5, s2 = 0.5;  // t = 0: exp(0) * cosh(0) terms, weight 1/2
+    for (int m = 1; m <= n; ++m) {
+        const double t = m * h;
+        const double sh = sinh(0.5 * t);
+        const double e = exp(-x * (2.0 * sh * sh));  // cosh t - 1 = 2 sinh^2(t/2)
+        const double c3 = cosh(t / 3.0);
+        s0 += e * c3;
+        s1 += e * (2.0 * c3 * c3 - 1.0);
+        s2 += e * c3 / cosh(t);
+    }
+    out[0] = s0 * h;
+    out[1] = s1 * h;
+    out[2] = s2 * h;
+}
+
+// --------------------------------------------------------------------------------------------
+// small-argument series (any precision)
+// --------------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void bessel_series(R x, R out[3]) {
+    const R a = R(0.5) * x, a2 = a * a;
+    const R pi3 = R(kPi / kSqrt3);
+    const R g13 = R(kGamma13), g23 = R(kGamma23);
+    const R c1 = cbrt(a);   // a^{1/3}
+    const R c2 = c1 * c1;   // a^{2/3}
+    const R ex = exp_(x);
+    // K13 = pi/sqrt3 [a^-1/3/Gamma(2/3) (1 + a^2/(2/3)) - a^1/3/Gamma(4/3) (1 + a^2/(4/3))]
+    out[0] = pi3 * ((R(1) / (c1 * g23)) * (R(1) + R(1.5) * a2) - (R(3) * c1 / g13) * (R(1) + R(0.75) * a2)) * ex;
+    // K23 = pi/sqrt3 [a^-2/3/Gamma(1/3) (1 + a^2/(1/3)) - a^2/3/Gamma(5/3) (1 + a^2/(5/3))]
+    out[1] = pi3 * ((R(1) / (c2 * g13)) * (R(1) + R(3) * a2) - (R(1.5) * c2 / g23) * (R(1) + R(0.6) * a2)) * ex;
+    // IntK13 = pi/sqrt3 - int_0^x K13 = pi/sqrt3 [1 - 3 a^2/3/Gamma(2/3) (1 + 3 a^2/8) + 1.5 a^4/3/Gamma(4/3) (1 + 3 a^2/10)]
+    out[2] = pi3 * (R(1) - (R(3) * c2 / g23) * (R(1) + R(0.375) * a2) + (R(4.5) * c2 * c2 / g13) * (R(1) + R(0.3) * a2)) * ex;
+}
+
+// --------------------------------------------------------------------------------------------
+// table interpolation
+// --------------------------------------------------------------------------------------------
+// FP64: tab[3][kBesN] of scaled values.
+__device__ __forceinline__ void bessel64(const double* __restrict__ tab, double x, double out[3]) {
+    if (x < kBesLo) {
+        bessel_series<double>(x, out);
+        return;
+    }
+    const double t = (log(x) - log(kBesLo)) / kBesH;
+    if (t > kBesN - 1) {
+        bessel_trapezoid(x, out);
+        return;
+    }
+    int j0 = (int)floor(t);
+    if (j0 < 3) j0 = 3;
+    if (j0 > kBesN - 5) j0 = kBesN - 5;
+    const double tau = t - j0;
+    // Lagrange weights on nodes m = -3..4: L_k = prod_{m != k} (tau - m)/(k - m)
+    double d[8], pre[8], suf[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = tau - (i - 3);
+    pre[0] = 1.0;
+#pragma unroll
+    for (int i = 1; i < 8; ++i) pre[i] = pre[i - 1] * d[i - 1];
+    suf[7] = 1.0;
+#pragma unroll
+    for (int i = 6; i >= 0; --i) suf[i] = suf[i + 1] * d[i + 1];
+    // 1 / prod_{m != k}(k - m) for k = -3..4
+    const double c[8] = {-1.0 / 5040.0, 1.0 / 720.0, -1.0 / 240.0, 1.0 / 144.0, -1.0 / 144.0, 1.0 / 240.0, -1.0 / 720.0,
+                         1.0 / 5040.0};
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const double L = pre[i] * suf[i] * c[i];
+        const int j = j0 - 3 + i;
+        v0 += L * tab[j];
+        v1 += L * tab[kBesN + j];
+        v2 += L * tab[2 * kBesN + j];
+    }
+    out[0] = v0;
+    out[1] = v1;
+    out[2] = v2;
+}
+
+// FP32: tab[3][kBesN] floats (shared memory in the step kernels); beyond the table the leading
+// large-x asymptotics sqrt(pi/(2x)) (1 + c/x).
+__device__ __forceinline__ void bessel32(const float* tab, float x, float out[3]) {
+    if (x < float(kBesLo)) {
+        bessel_series<float>(x, out);
+        return;
+    }
+    const float t = (__logf(x) - float(-9.210340371976182)) * float(1.0 / kBesH);  // ln(1e-4)
+    if (t > float(kBesN - 1)) {
+        const float a = sqrtf(float(kPi / 2.0) / x), ix = 1.0f / x;
+        out[0] = a * (1.0f - (5.0f / 72.0f) * ix);   // (4 nu^2 - 1)/8 with nu = 1/3
+        out[1] = a * (1.0f + (7.0f / 72.0f) * ix);   // nu = 2/3
+        out[2] = a * (1.0f - (41.0f / 72.0f) * ix);  // int_x^inf: (4 nu^2 - 5)/8
+        return;
+    }
+    int j0 = (int)t;
+    if (j0 < 1) j0 = 1;
+    if (j0 > kBesN - 3) j0 = kBesN - 3;
+    const float tau = t - (float)j0;
+    const float wm1 = -tau * (tau - 1.0f) * (tau - 2.0f) * (1.0f / 6.0f);
+    const float w0 = (tau + 1.0f) * (tau - 1.0f) * (tau - 2.0f) * 0.5f;
+    const float w1 = -(tau + 1.0f) * tau * (tau - 2.0f) * 0.5f;
+    const float w2 = (tau + 1.0f) * tau * (tau - 1.0f) * (1.0f / 6.0f);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const float* r = tab + f * kBesN + j0;
+        out[f] = wm1 * r[-1] + w0 * r[0] + w1 * r[1] + w2 * r[2];
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// rate / ICDF lookups (the interpolation rules are part of the tables' definition, see qed.h)
+// --------------------------------------------------------------------------------------------
+template <class R>
+struct TabP {
+    const R* nlc_rate;  // [2][n_chi]
+    const R* nbw_rate;  // [2][n_chi]
+    const R* nlc_icdf;  // [2][n_chi][n_r]
+    const R* nbw_icdf;  // [2][n_chi][n_r]
+    R lnchi_min, inv_dlnchi, chi_min, chi_max;
+    R y_lo, inv_dy;
+    int n_chi, n_r;
+};
+
+// chi row coordinate (i, f): linear in ln chi, clamped to the grid
+template <class R>
+__device__ __forceinline__ void chi_coord(const TabP<R>& T, R lnchi, int& i, R& f) {
+    const R s = (lnchi - T.lnchi_min) * T.inv_dlnchi;
+    if (!(s > R(0))) { i = 0; f = R(0); return; }
+    if (s >= R(T.n_chi - 1)) { i = T.n_chi - 2; f = R(1); return; }
+    i = (int)s;
+    if (i > T.n_chi - 2) i = T.n_chi - 2;
+    f = s - R(i);
+}
+
+// NLC rate integrals I_up, I_down at chi (classical chi-proportional below chi_min, clamped above chi_max)
+template <class R>
+__device__ __forceinline__ void nlc_rates(const TabP<R>& T, R chi, R lnchi, R& Iu, R& Id) {
+    if (chi < T.chi_min) {
+        const R sc = chi / T.chi_min;
+        Iu = exp_(T.nlc_rate[0]) * sc;
+        Id = exp_(T.nlc_rate[T.n_chi]) * sc;
+        return;
+    }
+    int i; R f;
+    chi_coord(T, lnchi, i, f);
+    Iu = exp_((R(1) - f) * T.nlc_rate[i] + f * T.nlc_rate[i + 1]);
+    Id = exp_((R(1) - f) * T.nlc_rate[T.n_chi + i] + f * T.nlc_rate[T.n_chi + i + 1]);
+}
+
+// NBW rate integrals J_+, J_- at chi (zero below chi_min)
+template <class R>
+__device__ __forceinline__ void nbw_rates(const TabP<R>& T, R chi, R lnchi, R& Jp, R& Jm) {
+    if (chi < T.chi_min) { Jp = R(0); Jm = R(0); return; }
+    int i; R f;
+    chi_coord(T, lnchi, i, f);
+    const R chic = chi > T.chi_max ? T.chi_max : chi;
+    const R sub = R(8.0 / 3.0) / chic;
+    Jp = exp_((R(1) - f) * T.nbw_rate[i] + f * T.nbw_rate[i + 1] - sub);
+    Jm = exp_((R(1) - f) * T.nbw_rate[T.n_chi + i] + f * T.nbw_rate[T.n_chi + i + 1] - sub);
+}
+
+// one ICDF row at logit y: 4-point Lagrange inside the grid, asymptote below, last entry above
+template <class R>
+__device__ __forceinline__ R icdf_row(const R* __restrict__ row, const TabP<R>& T, R slope, R y) {
+    const R tt = (y - T.y_lo) * T.inv_dy;
+    if (!(tt > R(0))) return row[0] + slope * (y - T.y_lo);
+    if (tt >= R(T.n_r - 1)) return row[T.n_r - 1];
+    int m = (int)tt;
+    if (m < 1) m = 1;
+    if (m > T.n_r - 3) m = T.n_r - 3;
+    const R x = tt - R(m);
+    const R wm1 = -x * (x - R(1)) * (x - R(2)) / R(6);
+    const R w0 = (x + R(1)) * (x - R(1)) * (x - R(2)) / R(2);
+    const R w1 = -(x + R(1)) * x * (x - R(2)) / R(2);
+    const R w2 = (x + R(1)) * x * (x - R(1)) / R(6);
+    return wm1 * row[m - 1] + w0 * row[m] + w1 * row[m + 1] + w2 * row[m + 2];
+}
+
+// ln of the sampled variable (NLC: u'; NBW: x) for chi and the uniform r; rows blended in ln chi
+template <class R>
+__device__ __forceinline__ R icdf_lookup(const TabP<R>& T, bool nbw, int s, R lnchi, R y) {
+    const R* base = (nbw ? T.nbw_icdf : T.nlc_icdf) + (size_t)s * T.n_chi * T.n_r;
+    int i; R f;
+    chi_coord(T, lnchi, i, f);
+    const R slope = nbw ? R(2) : R(3);
+    const R v0 = icdf_row(base + (size_t)i * T.n_r, T, slope, y);
+    const R v1 = icdf_row(base + (size_t)(i + 1) * T.n_r, T, slope, y);
+    return (R(1) - f) * v0 + f * v1;
+}
+
+}  // namespace qed

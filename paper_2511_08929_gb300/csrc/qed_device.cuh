@@ -1,0 +1,349 @@
+// qed_device.cuh -- device building blocks of the spin/polarization-resolved QED step
+// (Qian et al., arXiv:2511.08929): counter-based random numbers, analytic fields, the Boris and
+// T-BMT pushers, chi and the (eps, beta, k) basis, and the App. A spectra.  Templated on the
+// arithmetic type R (double for the plain path, float for the fast path).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qed.h"
+
+namespace qed {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kAlpha = 7.2973525693e-3;  // fine-structure constant (CODATA 2018)
+constexpr double kSqrt3 = 1.73205080756887729353;
+constexpr uint64_t kStepBirth = 0xFFFFFFFFFFFFFFFFull;  // reserved Philox step of a particle's first draw
+// Philox counter slot of each draw (counter = (step_lo, step_hi, slot, 0)).
+constexpr uint32_t kSlotTauBranch = 0;  // u0: optical depth (or r1 in probability mode), u1: branch r_b
+constexpr uint32_t kSlotLambdaSpin = 1; // u0: r2 (energy fraction), u1: r3 (spin collapse)
+constexpr uint32_t kSlotStokes = 2;     // u0: r4 (Stokes collapse)
+constexpr uint32_t kSlotChild = 3;      // words 0,1 / 2,3: daughter ids
+
+// ---------------------------------------------------------------------------------------------
+// small vectors
+// ---------------------------------------------------------------------------------------------
+template <class R>
+struct V3 {
+    R x, y, z;
+};
+template <class R>
+__device__ __forceinline__ V3<R> v3(R a, R b, R c) { return V3<R>{a, b, c}; }
+template <class R>
+__device__ __forceinline__ R dot(const V3<R>& a, const V3<R>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class R>
+__device__ __forceinline__ V3<R> cross(const V3<R>& a, const V3<R>& b) {
+    return V3<R>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class R>
+__device__ __forceinline__ V3<R> operator+(const V3<R>& a, const V3<R>& b) { return V3<R>{a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R>
+__device__ __forceinline__ V3<R> operator-(const V3<R>& a, const V3<R>& b) { return V3<R>{a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class R>
+__device__ __forceinline__ V3<R> operator*(R s, const V3<R>& a) { return V3<R>{s * a.x, s * a.y, s * a.z}; }
+
+__device__ __forceinline__ double rsqrt_(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ double exp_(double v) { return exp(v); }
+__device__ __forceinline__ float exp_(float v) { return expf(v); }
+__device__ __forceinline__ double log_(double v) { return log(v); }
+__device__ __forceinline__ float log_(float v) { return logf(v); }
+__device__ __forceinline__ void sincos_(double v, double* s, double* c) { sincos(v, s, c); }
+__device__ __forceinline__ void sincos_(float v, float* s, float* c) { sincosf(v, s, c); }
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t id, uint64_t seed, uint64_t step, uint32_t slot) {
+    const uint64_t k = id ^ seed;
+    return philox(make_uint4((uint32_t)step, (uint32_t)(step >> 32), slot, 0u), make_uint2((uint32_t)k, (uint32_t)(k >> 32)));
+}
+
+// 52 random bits -> (m + 1/2) 2^-52, exactly representable, strictly inside (0, 1).
+__device__ __forceinline__ double uniform52(uint32_t hi, uint32_t lo) {
+    const uint64_t m = ((uint64_t)(hi >> 12) << 32) | (uint64_t)lo;
+    return ((double)m + 0.5) * 0x1.0p-52;
+}
+
+__device__ __forceinline__ double birth_tau(uint64_t id, uint64_t seed) {
+    const uint4 w = draw(id, seed, kStepBirth, kSlotTauBranch);
+    return -log(uniform52(w.x, w.y));
+}
+
+// ---------------------------------------------------------------------------------------------
+// analytic plane-wave fields (stand-in for the grid fields of Sec. 3)
+// ---------------------------------------------------------------------------------------------
+template <class R>
+struct FieldP {
+    int kind;
+    R a0, inv2n, phimax;  // envelope sin^2(phi * inv2n) on [0, phimax]
+    R E0x, E0y, E0z, B0x, B0y, B0z;
+    R eta0;
+};
+
+template <class R>
+__device__ __forceinline__ R envelope(R phi, const FieldP<R>& f) {
+    if (phi < R(0) || phi > f.phimax) return R(0);
+    R s, c;
+    sincos_(phi * f.inv2n, &s, &c);
+    return s * s;
+}
+
+// phase_t = t + phase (split by the caller for the FP32 path as hi + lo)
+template <class R>
+__device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x, V3<R>& E, V3<R>& B) {
+    if (f.kind == QED_FIELD_CONST) {
+        E = v3(f.E0x, f.E0y, f.E0z);
+        B = v3(f.B0x, f.B0y, f.B0z);
+        return;
+    }
+    const R phi = (ph_hi - x.z) + ph_lo;
+    const R a = f.a0 * envelope(phi, f);
+    R s, c;
+    sincos_(phi, &s, &c);
+    const R ex = a * c, ey = f.kind == QED_FIELD_LP ? R(0) : a * s;
+    E = v3(ex, ey, R(0));
+    B = v3(-ey, ex, R(0));  // forward wave: B = z x E
+    if (f.kind == QED_FIELD_CP_COUNTER) {
+        const R phi2 = (ph_hi + x.z) + ph_lo;
+        const R a2 = f.a0 * envelope(phi2, f);
+        R s2, c2;
+        sincos_(phi2, &s2, &c2);
+        const R ex2 = a2 * c2, ey2 = a2 * s2;
+        E.x += ex2;
+        E.y += ey2;
+        B.x += ey2;  // backward wave: B = -z x E
+        B.y += -ex2;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// classical pushers
+// ---------------------------------------------------------------------------------------------
+// Boris push of momentum p through dt with charge q (fields E, B).
+template <class R>
+__device__ __forceinline__ V3<R> boris(const V3<R>& p, const V3<R>& E, const V3<R>& B, R q, R dt) {
+    const R h = R(0.5) * q * dt;
+    const V3<R> pm = p + h * E;
+    const R ig = rsqrt_(R(1) + dot(pm, pm));
+    const V3<R> t = (h * ig) * B;
+    const R sfac = R(2) / (R(1) + dot(t, t));
+    const V3<R> pp = pm + cross(pm, t);
+    const V3<R> pl = pm + cross(pp, sfac * t);
+    return pl + h * E;
+}
+
+// T-BMT precession vector Omega (ds/dt = Omega x s) with the time-centred momentum pb.
+template <class R>
+__device__ __forceinline__ V3<R> tbmt_omega(const V3<R>& pb, const V3<R>& E, const V3<R>& B, R q, bool paper_form) {
+    const R ae = R(kAlpha / (2.0 * kPi));
+    const R gb = sqrt_(R(1) + dot(pb, pb));
+    const R ig = R(1) / gb;
+    const V3<R> bb = ig * pb;
+    const R bB = dot(bb, B);
+    const V3<R> bxE = cross(bb, E);
+    const R c1 = ae + ig, c2 = ae * gb / (gb + R(1));
+    if (paper_form)  // (a + 1/gamma)(B - v x E) - (a gamma/(gamma+1))(v.B) v, as printed in Sec. 7.3
+        return (-q) * (c1 * (B - bxE) - (c2 * bB) * bb);
+    // standard form: (a + 1/gamma) B - (a gamma/(gamma+1))(beta.B) beta - (a + 1/(gamma+1)) beta x E
+    const R c3 = ae + R(1) / (gb + R(1));
+    return (-q) * (c1 * B - (c2 * bB) * bb - c3 * bxE);
+}
+
+// rotate s about Omega by |Omega| dt (Rodrigues)
+template <class R>
+__device__ __forceinline__ V3<R> rotate(const V3<R>& s, const V3<R>& Om, R dt) {
+    const R o2 = dot(Om, Om);
+    if (!(o2 > R(0))) return s;
+    const R io = rsqrt_(o2);
+    const V3<R> n = io * Om;
+    R sn, c;
+    sincos_(o2 * io * dt, &sn, &c);
+    const V3<R> nxs = cross(n, s);
+    const R ns = dot(n, s);
+    return c * s + sn * nxs + (ns * (R(1) - c)) * n;
+}
+
+// chi = eta0 sqrt((e E + p x B)^2 - (p.E)^2)
+template <class R>
+__device__ __forceinline__ R chi_of(R eta0, R e, const V3<R>& p, const V3<R>& E, const V3<R>& B) {
+    const V3<R> a = e * E + cross(p, B);
+    const R pe = dot(p, E);
+    const R v = dot(a, a) - pe * pe;
+    return eta0 * sqrt_(v > R(0) ? v : R(0));
+}
+
+// (eps, beta): eps along the part of f = E + v x B perpendicular to khat, times `sign`;
+// beta = khat x eps (right-handed basis).  Returns false if undefined.
+template <class R>
+__device__ __forceinline__ bool make_basis(const V3<R>& E, const V3<R>& B, const V3<R>& v, const V3<R>& khat, R sign,
+                                           V3<R>& eps, V3<R>& beta) {
+    const V3<R> f = E + cross(v, B);
+    const R fk = dot(f, khat);
+    const V3<R> fp = f - fk * khat;
+    const R n2 = dot(fp, fp);
+    if (!(n2 > R(0))) return false;
+    eps = (sign * rsqrt_(n2)) * fp;
+    beta = cross(khat, eps);
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// spectra of App. A (Bessel forms); bes = (K13, K23, IntK13) at the event's u' (any common scale)
+// ---------------------------------------------------------------------------------------------
+// NLC: w = -IntK13 + kappa K23 + lambda (s_i.beta) K13 ;
+//      g = u K13 beta + (-IntK13 + 2 K23) s_i + lambda u (-IntK13 + K23)(s_i.k) k
+template <class R>
+__device__ __forceinline__ void nlc_wg(R lam, R one_m, const R bes[3], const V3<R>& si, const V3<R>& beta,
+                                       const V3<R>& k, R& w, V3<R>& g) {
+    const R u = lam / one_m;
+    const R kappa = R(1) / one_m + one_m;
+    const R K13 = bes[0], K23 = bes[1], IK = bes[2];
+    w = -IK + kappa * K23 + lam * dot(si, beta) * K13;
+    g = (u * K13) * beta + (-IK + R(2) * K23) * si + (lam * u * (-IK + K23) * dot(si, k)) * k;
+}
+
+// NLC photon Stokes spectrum F = (F0, F1, F2, F3), App. A.1 Eqs. F0-F3.
+template <class R>
+__device__ __forceinline__ void nlc_stokes(R lam, R one_m, const R bes[3], const V3<R>& si, const V3<R>& sf, R w,
+                                           const V3<R>& g, const V3<R>& eps, const V3<R>& beta, const V3<R>& k,
+                                           R F[4]) {
+    const R u = lam / one_m;
+    const R kappa = R(1) / one_m + one_m;
+    const R kappat = R(1) / one_m - one_m;
+    const R K13 = bes[0], K23 = bes[1], IK = bes[2];
+    const R sie = dot(si, eps), sib = dot(si, beta), sik = dot(si, k);
+    const R sfe = dot(sf, eps), sfb = dot(sf, beta), sfk = dot(sf, k);
+    const V3<R> fxi = cross(sf, si);
+    const R lu2 = R(0.5) * lam * u;
+    F[0] = w + dot(sf, g);
+    F[1] = -K13 * (u * sie + lam * sfe) - lu2 * IK * (sfe * sib + sfb * sie) + R(0.5) * kappat * K23 * dot(fxi, k);
+    F[2] = R(0.5) * kappat * K13 * dot(fxi, eps) - (lam * IK - kappat * K23) * sik - (u * IK - kappat * K23) * sfk +
+           lu2 * K13 * (sfk * sib + sfb * sik);
+    F[3] = K23 + (u * sib + lam * sfb) * K13 - lu2 * IK * (sfe * sie - sfb * sib) + R(0.5) * kappa * K23 * dot(sf, si) -
+           lu2 * K23 * sfk * sik;
+}
+
+// NBW expected daughter spins (App. A.2): w0, j_e, j_p for positron fraction lam.
+template <class R>
+__device__ __forceinline__ void nbw_j(R lam, R one_m, const R bes[3], const R xi[3], const V3<R>& eps, const V3<R>& beta,
+                                      const V3<R>& k, R& w0, V3<R>& je, V3<R>& jp) {
+    const R il = R(1) / lam, im = R(1) / one_m;
+    const R rho = one_m * il + lam * im;
+    const R rhot = one_m * il - lam * im;
+    const R K13 = bes[0], K23 = bes[1], IK = bes[2];
+    w0 = IK + rho * K23 - xi[2] * K23;
+    je = ((im - xi[2] * il) * K13) * beta + (xi[0] * il * K13) * eps + (xi[1] * (im * IK + rhot * K23)) * k;
+    jp = ((-il + xi[2] * im) * K13) * beta + (-xi[0] * im * K13) * eps + (xi[1] * (il * IK - rhot * K23)) * k;
+}
+
+// NBW full spectrum contracted with xi: G0 + xi . (G1, G2, G3) (App. A.2 Eqs. G0-G3; the last term of G3
+// with the sign of its Airy form).
+template <class R>
+__device__ __forceinline__ R nbw_G(R lam, R one_m, const R bes[3], const R xi[3], const V3<R>& sp, const V3<R>& se,
+                                   const V3<R>& eps, const V3<R>& beta, const V3<R>& k) {
+    const R il = R(1) / lam, im = R(1) / one_m;
+    const R rho = one_m * il + lam * im;
+    const R rhot = one_m * il - lam * im;
+    const R ut = il + im;
+    const R K13 = bes[0], K23 = bes[1], IK = bes[2];
+    const R spe = dot(sp, eps), spb = dot(sp, beta), spk = dot(sp, k);
+    const R see = dot(se, eps), seb = dot(se, beta), sek = dot(se, k);
+    const V3<R> pxe = cross(sp, se);
+    const R sps = dot(sp, se);
+    const R G0 = IK + rho * K23 + im * seb * K13 - il * spb * K13 + (IK - R(2) * K23) * sps +
+                 (rho * IK - (rho - R(2)) * K23) * spk * sek;
+    const R G1 = K13 * (il * see - im * spe) - R(0.5) * ut * IK * (spe * seb + spb * see) + R(0.5) * rhot * K23 * dot(pxe, k);
+    const R G2 = -R(0.5) * ut * K13 * dot(pxe, eps) + (im * IK + rhot * K23) * sek + (il * IK - rhot * K23) * spk -
+                 R(0.5) * rhot * K13 * (spk * seb + spb * sek);
+    const R G3 = -K23 + (-il * seb + im * spb) * K13 - R(0.5) * ut * IK * (spe * see - spb * seb) + R(0.5) * rho * K23 * sps +
+                 (R(1) - R(0.5) * rho) * K23 * spk * sek;
+    return G0 + xi[0] * G1 + xi[1] * G2 + xi[2] * G3;
+}
+
+// Stokes -> P (Sec. 2.2): P = xi2 k + l (cos dth eps + sin dth beta), l = |(xi1, xi3)|, 2 dth = atan2(xi1, xi3),
+// written with half-angle identities: l cos dth = sqrt(l (l + xi3)/2), l sin dth = sign(xi1) sqrt(l (l - xi3)/2).
+template <class R>
+__device__ __forceinline__ V3<R> stokes_to_P(const R xi[3], const V3<R>& eps, const V3<R>& beta, const V3<R>& k) {
+    const R l = sqrt_(xi[0] * xi[0] + xi[2] * xi[2]);
+    const R a = R(0.5) * l * (l + xi[2]), b = R(0.5) * l * (l - xi[2]);
+    const R c = sqrt_(a > R(0) ? a : R(0));
+    R s = sqrt_(b > R(0) ? b : R(0));
+    if (xi[0] < R(0)) s = -s;
+    return xi[1] * k + c * eps + s * beta;
+}
+
+// P -> Stokes in the basis (eps, beta, k): xi1 = 2 P1 P2 / l, xi2 = P.k, xi3 = (P1^2 - P2^2)/l.
+template <class R>
+__device__ __forceinline__ void P_to_stokes(const V3<R>& P, const V3<R>& eps, const V3<R>& beta, const V3<R>& k, R xi[3]) {
+    const R P1 = dot(P, eps), P2 = dot(P, beta);
+    const R l2 = P1 * P1 + P2 * P2;
+    xi[1] = dot(P, k);
+    if (l2 > R(0)) {
+        const R il = rsqrt_(l2);
+        xi[0] = R(2) * P1 * P2 * il;
+        xi[2] = (P1 * P1 - P2 * P2) * il;
+    } else {
+        xi[0] = R(0);
+        xi[2] = R(0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// block-level counter reduction: one atomic per block and counter
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int N>
+__device__ __forceinline__ void flush_counters(unsigned long long (&c)[N], unsigned long long* dst) {
+    __shared__ unsigned long long red[32][N];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) c[i] = warp_sum(c[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[wid][i] = c[i];
+    __syncthreads();
+    if (threadIdx.x < N) {
+        unsigned long long s = 0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        if (s) atomicAdd(dst + threadIdx.x, s);
+    }
+}
+
+__device__ __forceinline__ void record_error(qed_counters* ctr, int32_t status, int64_t idx) {
+    if (atomicCAS(&ctr->status, 0, status) == 0) ctr->first_bad = idx;
+}
+
+// warp-aggregated slot reservation on a device counter: returns the slot of this lane (valid if want)
+__device__ __forceinline__ long long reserve_slots(int64_t* counter, bool want, int per) {
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (mask == 0) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    long long base = 0;
+    if (lane == leader) base = (long long)atomicAdd((unsigned long long*)counter, (unsigned long long)(__popc(mask) * per));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + (long long)(__popc(mask & ((1u << lane) - 1u)) * per);
+}
+
+}  // namespace qed
