@@ -276,14 +276,24 @@ __device__ __forceinline__ R nbw_G(R lam, R one_m, const R bes[3], const R xi[3]
 }
 
 // Stokes -> P (Sec. 2.2): P = xi2 k + l (cos dth eps + sin dth beta), l = |(xi1, xi3)|, 2 dth = atan2(xi1, xi3),
-// written with half-angle identities: l cos dth = sqrt(l (l + xi3)/2), l sin dth = sign(xi1) sqrt(l (l - xi3)/2).
+// with half-angle identities: (l cos dth)^2 = l (l + xi3)/2, (l sin dth)^2 = l (l - xi3)/2 and
+// (l cos dth)(l sin dth) = l xi1 / 2.  The larger component comes from its square root (no cancellation),
+// the smaller one from the product; cos dth >= 0.
 template <class R>
 __device__ __forceinline__ V3<R> stokes_to_P(const R xi[3], const V3<R>& eps, const V3<R>& beta, const V3<R>& k) {
     const R l = sqrt_(xi[0] * xi[0] + xi[2] * xi[2]);
-    const R a = R(0.5) * l * (l + xi[2]), b = R(0.5) * l * (l - xi[2]);
-    const R c = sqrt_(a > R(0) ? a : R(0));
-    R s = sqrt_(b > R(0) ? b : R(0));
-    if (xi[0] < R(0)) s = -s;
+    R c = R(0), s = R(0);
+    if (l > R(0)) {
+        const R half = R(0.5) * l * xi[0];
+        if (xi[2] >= R(0)) {
+            c = sqrt_(R(0.5) * l * (l + xi[2]));
+            s = half / c;
+        } else {
+            s = sqrt_(R(0.5) * l * (l - xi[2]));
+            if (xi[0] < R(0)) s = -s;
+            c = half / s;
+        }
+    }
     return xi[1] * k + c * eps + s * beta;
 }
 

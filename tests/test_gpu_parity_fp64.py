@@ -81,7 +81,14 @@ def test_lookups_match_oracle(gpu_tables, ora_tables):
     for i in range(n):
         ref = [ora_tables.nlc_rate_lookup(0, chi[i]), ora_tables.nlc_rate_lookup(1, chi[i]),
                ora_tables.nbw_rate_lookup(0, chi[i]), ora_tables.nbw_rate_lookup(1, chi[i])]
-        np.testing.assert_allclose(g[i, :4], ref, rtol=1e-13, atol=1e-300)
+        np.testing.assert_allclose(g[i, :2], ref[:2], rtol=1e-13, atol=1e-300)
+        # NBW rates are exp(L - 8/(3 chi)): compare logs; a 1e-16 relative error in a large exponent is
+        # an absolute error |exponent| * 1e-16 in the log
+        if ref[2] > 0:
+            lg, lr = np.log(g[i, 2:4]), np.log(ref[2:4])
+            assert np.all(np.abs(lg - lr) <= 1e-13 + 4e-16 * np.abs(lr)), (chi[i], lg, lr)
+        else:
+            assert g[i, 2] == 0 and g[i, 3] == 0
         ic = [ora_tables.icdf(False, 0, chi[i], r[i]), ora_tables.icdf(False, 1, chi[i], r[i]),
               ora_tables.icdf(True, 0, chi[i], r[i]), ora_tables.icdf(True, 1, chi[i], r[i])]
         np.testing.assert_allclose(g[i, 4:], ic, rtol=0, atol=1e-12 * max(1.0, np.abs(ic).max()))
@@ -117,7 +124,9 @@ def test_lepton_single_step_scattered_states(gpu_tables, ora_tables, n):
         gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 1, q=q, dt=0.2, t0=10.0)
         compare_sets(gL.read(), oL.view(), 1e-12, "leptons")
         compare_sets(gG.read(), oG.view(), 1e-12, "photons", P_headless=True)
-        assert c.events == oc.events and c.stored == oc.stored and c.renormalised == oc.renormalised
+        assert c.events == oc.events and c.stored == oc.stored
+        # |s|^2 can sit within rounding of 1: whether it is rescaled then changes s by ~1e-16 only
+        assert abs(c.renormalised - oc.renormalised) <= 2 + oc.renormalised // 200
         assert c.status == 0
 
 
