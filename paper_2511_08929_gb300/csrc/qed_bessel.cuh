@@ -190,21 +190,24 @@ __device__ __forceinline__ void nbw_rates(const TabP<R>& T, R chi, R lnchi, R& J
     Jm = exp_((R(1) - f) * T.nbw_rate[T.n_chi + i] + f * T.nbw_rate[T.n_chi + i + 1] - sub);
 }
 
-// one ICDF row at logit y: 4-point Lagrange inside the grid, asymptote below, last entry above
+// one ICDF row at logit y: the cubic through the 4 nearest nodes inside the grid (written in Newton form
+// about node m: b + x ((c - b) + (x - 1) (D2 + (x + 1) D3)), the same polynomial as the Lagrange form,
+// rounding on the small differences), the asymptote below, the last entry above.  The position inside
+// the cell is one FMA relative to node m, so it keeps the precision of y.
 template <class R>
 __device__ __forceinline__ R icdf_row(const R* __restrict__ row, const TabP<R>& T, R slope, R y) {
-    const R tt = (y - T.y_lo) * T.inv_dy;
+    const R tt = y * T.inv_dy - T.y_lo * T.inv_dy;
     if (!(tt > R(0))) return row[0] + slope * (y - T.y_lo);
     if (tt >= R(T.n_r - 1)) return row[T.n_r - 1];
     int m = (int)tt;
     if (m < 1) m = 1;
     if (m > T.n_r - 3) m = T.n_r - 3;
-    const R x = tt - R(m);
-    const R wm1 = -x * (x - R(1)) * (x - R(2)) / R(6);
-    const R w0 = (x + R(1)) * (x - R(1)) * (x - R(2)) / R(2);
-    const R w1 = -(x + R(1)) * x * (x - R(2)) / R(2);
-    const R w2 = (x + R(1)) * x * (x - R(1)) / R(6);
-    return wm1 * row[m - 1] + w0 * row[m] + w1 * row[m + 1] + w2 * row[m + 2];
+    const R x = fma(y, T.inv_dy, -T.y_lo * T.inv_dy - R(m));
+    const R a = row[m - 1], b = row[m], c = row[m + 1], d = row[m + 2];
+    const R d1 = c - b;
+    const R d2 = R(0.5) * ((a - b) + (c - b));
+    const R d3 = ((d - a) + R(3) * (b - c)) / R(6);
+    return b + x * (d1 + (x - R(1)) * (d2 + (x + R(1)) * d3));
 }
 
 // ln of the sampled variable (NLC: u'; NBW: x) for chi and the uniform r; rows blended in ln chi
@@ -216,7 +219,7 @@ __device__ __forceinline__ R icdf_lookup(const TabP<R>& T, bool nbw, int s, R ln
     const R slope = nbw ? R(2) : R(3);
     const R v0 = icdf_row(base + (size_t)i * T.n_r, T, slope, y);
     const R v1 = icdf_row(base + (size_t)(i + 1) * T.n_r, T, slope, y);
-    return (R(1) - f) * v0 + f * v1;
+    return v0 + f * (v1 - v0);
 }
 
 }  // namespace qed

@@ -95,11 +95,29 @@ struct FieldP {
     R eta0;
 };
 
+// sin and cos of a phase v + dv (dv a small correction): full precision in FP64; in FP32 v is reduced to
+// [-pi, pi] with a two-term 2 pi (Cody-Waite), dv added there, and the hardware approximation evaluated
+__device__ __forceinline__ void phase_sincos(double v, double* s, double* c, double dv = 0.0) { sincos(v + dv, s, c); }
+__device__ __forceinline__ void phase_sincos(float v, float* s, float* c, float dv = 0.0f) {
+    const float k = rintf(v * 0.15915494309189535f);
+    const float r = fmaf(-k, 1.7484555e-07f, fmaf(-k, 6.28318548f, v)) + dv;  // 2 pi = 6.28318548 - 1.7484555e-7
+    __sincosf(r, s, c);
+}
+
+// a + b as an unevaluated sum s + e (Knuth's TwoSum: e is the exact rounding error of s)
+template <class R>
+__device__ __forceinline__ R two_sum(R a, R b, R& e) {
+    const R s = a + b;
+    const R bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+    return s;
+}
+
 template <class R>
 __device__ __forceinline__ R envelope(R phi, const FieldP<R>& f) {
     if (phi < R(0) || phi > f.phimax) return R(0);
     R s, c;
-    sincos_(phi * f.inv2n, &s, &c);
+    phase_sincos(phi * f.inv2n, &s, &c);
     return s * s;
 }
 
@@ -111,18 +129,26 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
         B = v3(f.B0x, f.B0y, f.B0z);
         return;
     }
-    const R phi = (ph_hi - x.z) + ph_lo;
+    // phase t + phase - z: the rounding error of the subtraction is recovered exactly and added to the
+    // reduced argument, so the FP32 carrier keeps the phase to ~1e-7 however large it is
+    R e1;
+    const R ps = two_sum(ph_hi, -x.z, e1);
+    const R dp = e1 + ph_lo;
+    const R phi = ps + dp;
     const R a = f.a0 * envelope(phi, f);
     R s, c;
-    sincos_(phi, &s, &c);
+    phase_sincos(ps, &s, &c, dp);
     const R ex = a * c, ey = f.kind == QED_FIELD_LP ? R(0) : a * s;
     E = v3(ex, ey, R(0));
     B = v3(-ey, ex, R(0));  // forward wave: B = z x E
     if (f.kind == QED_FIELD_CP_COUNTER) {
-        const R phi2 = (ph_hi + x.z) + ph_lo;
+        R e2;
+        const R ps2 = two_sum(ph_hi, x.z, e2);
+        const R dp2 = e2 + ph_lo;
+        const R phi2 = ps2 + dp2;
         const R a2 = f.a0 * envelope(phi2, f);
         R s2, c2;
-        sincos_(phi2, &s2, &c2);
+        phase_sincos(ps2, &s2, &c2, dp2);
         const R ex2 = a2 * c2, ey2 = a2 * s2;
         E.x += ex2;
         E.y += ey2;
@@ -172,7 +198,7 @@ __device__ __forceinline__ V3<R> rotate(const V3<R>& s, const V3<R>& Om, R dt) {
     const R io = rsqrt_(o2);
     const V3<R> n = io * Om;
     R sn, c;
-    sincos_(o2 * io * dt, &sn, &c);
+    phase_sincos(o2 * io * dt, &sn, &c);
     const V3<R> nxs = cross(n, s);
     const R ns = dot(n, s);
     return c * s + sn * nxs + (ns * (R(1) - c)) * n;

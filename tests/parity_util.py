@@ -84,3 +84,42 @@ def oracle_full_step(tb, f, st, leptons, photons, el=None, po=None, ctr=None):
         O.lepton_step(tb, f, st, q, L, photons, ctr)
         L._s.n = n_now
     return ctr
+
+
+def compare_with_flips(gpu: dict, ora: dict, rtol: float, what: str, P_headless: bool = False, pos_floor=1.0,
+                       diverged=0.1, frac_ok=0.0, hard=None):
+    """FP32-vs-FP64 comparison, matched by id.  A decision taken in FP32 next to its threshold (an event,
+    a collapse sign) can go the other way: it leaves one daughter id on one side only and one on the
+    other; such unmatched ids, and particles whose state moved apart by more than `diverged`, are flips.
+    Every other particle must be within rtol, except that a fraction `frac_ok` of them may reach `hard`
+    (ill-conditioned directions, see the FP32 tests).  Returns (flipped decisions, error quantiles)."""
+    g, o = by_id(gpu), by_id(ora)
+    common, gi, oi = np.intersect1d(g["id"], o["id"], assume_unique=False, return_indices=True)
+    only = (len(g["id"]) - len(common)) + (len(o["id"]) - len(common))
+    gg = {k: v[gi] for k, v in g.items()}
+    oo = {k: v[oi] for k, v in o.items()}
+    e = {"pos": rel_vec(gg["pos"], oo["pos"], pos_floor), "mom": rel_vec(gg["mom"], oo["mom"], 1e-300)}
+    sg, so = gg["spin"], oo["spin"]
+    if P_headless:
+        k = oo["mom"] / np.maximum(np.linalg.norm(oo["mom"], axis=1, keepdims=True), 1e-300)
+        gpar, opar = (sg * k).sum(1, keepdims=True) * k, (so * k).sum(1, keepdims=True) * k
+        gperp, operp = sg - gpar, so - opar
+        flip = (gperp * operp).sum(1) < 0
+        sg = np.where(flip[:, None], gpar - gperp, sg)
+    e["spin"] = np.linalg.norm(sg - so, axis=1)
+    fin = np.isfinite(oo["tau"]) & np.isfinite(gg["tau"])
+    e["tau"] = np.where(fin, np.abs(gg["tau"] - oo["tau"]) / np.maximum(np.abs(oo["tau"]), 1.0), 0.0)
+    e["w"] = np.abs(gg["w"] - oo["w"]) / np.maximum(np.abs(oo["w"]), 1e-300)
+    worst_each = np.max(np.stack([e["pos"], e["mom"], e["spin"], e["tau"]]), axis=0)
+    div = worst_each > diverged
+    keep = ~div
+    report = {}
+    for k2, v in e.items():
+        v = v[keep]
+        report[k2] = {"max": float(v.max(initial=0.0)), "p999": float(np.quantile(v, 0.999)) if len(v) else 0.0,
+                      "frac_above": float((v > rtol).mean()) if len(v) else 0.0}
+    hard = rtol if hard is None else hard
+    bad = {k2: r for k2, r in report.items() if r["max"] > hard or r["frac_above"] > frac_ok}
+    assert not bad, f"{what}: beyond rtol {rtol} (hard {hard}, frac {frac_ok}): {bad}; {int(div.sum())} diverged, {only} unmatched"
+    flips = int(div.sum()) + (only + 1) // 2
+    return flips, report

@@ -1,0 +1,217 @@
+"""Parity of the FP32 path (FP32 push, lookups and sampling; FP64 optical depth and renormalisation)
+with the FP64 oracle on the same inputs (the oracle starts from the float-rounded state read back from
+the device).
+
+Bar per step: 1e-5 relative on momenta, spins, Stokes vectors, positions and optical depths.  Two kinds
+of outputs carry a documented tail above it:
+  * quantities proportional to chi where the field is near a node: chi is small there, and the absolute
+    error of the FP32 carrier (~1e-7 in the reduced phase) becomes a larger relative error; such photons
+    are very soft (the worst measured: lambda = 1.3e-7, error 1.04e-5).  At most 1 % may exceed 1e-5,
+    none 3e-5 (measured: median 5e-7, 0.3 % above 1e-5);
+  * directions that are differences of nearly equal terms (the axis j/|j| of a pair daughter's spin when
+    a coefficient such as 1/(1-lambda) - xi3/lambda almost cancels) amplify the ~1e-7 error of their FP32
+    inputs: at most 1 % above 1e-5, none above 1e-3.
+Decisions taken in FP32 next to their threshold may flip: fewer than 1e-5 per particle-step.  Over many
+steps the per-step error compounds at most linearly: an n-step trajectory is held to n x 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2511_08929_gb300 import binding as B
+from paper_2511_08929_gb300 import buffers as Q
+from paper_2511_08929_gb300 import inputs as I
+
+from parity_util import as_oracle_field, as_oracle_step, compare_with_flips, oracle_full_step
+
+pytestmark = pytest.mark.gpu
+
+# the production resolution along r (256 points): the FP32 rounding of the logit coordinate is amplified
+# by the slope of the interpolated row, which a coarse grid makes larger
+DESC = dict(chi_min=1e-3, chi_max=1e2, n_chi=24, n_r=256, y_lo=-20.0, y_hi=20.0)
+ETA0 = I.eta0_for_wavelength(0.8)
+FP32 = B.QED_FP32
+
+
+@pytest.fixture(scope="module")
+def gpu_tables():
+    from paper_2511_08929_gb300 import build as bld
+    bld.build()
+    t = Q.Tables(**DESC)
+    yield t
+    t.close()
+
+
+@pytest.fixture(scope="module")
+def ora_tables():
+    return O.tables(*DESC.values())
+
+
+def _pair(b, charge, cap=None, seed=7, photons=False, use_begin=False):
+    """Device buffer (FP32 layout) and an oracle buffer holding the same float-rounded state."""
+    n = len(b["id"])
+    g = Q.ParticleBuffer(cap or max(n, 1), FP32, charge, photons=photons, use_begin=use_begin)
+    g.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"])
+    if n:
+        g.init_tau(seed)
+    r = g.read()
+    o = O.Particles.from_arrays(cap or max(n, 1), r["pos"], r["mom"], r["spin"], r["w"], r["id"], tau=r["tau"])
+    return g, o
+
+
+def _run_lepton(gt, ot, b, f, steps, q=-1, flags=None, dt=0.2, t0=8.0, seed=7, cap_ph=400000):
+    fl = B.QED_F_FULL if flags is None else flags
+    gL, oL = _pair(b, q, seed=seed)
+    gG = Q.ParticleBuffer(cap_ph, FP32, B.QED_PHOTON)
+    oG = O.Particles(cap_ph)
+    ctr, octr = Q.Counters(), O.Counters()
+    of = as_oracle_field(f)
+    for s in range(steps):
+        st = Q.step_desc(dt, t0 + s * dt, s, seed, fl)
+        B.qed_push_step(gt.handle, f, st, gL.s, gG.s, ctr.ptr)
+        O.lepton_step(ot, of, as_oracle_step(st), q, oL, oG, octr)
+    torch.cuda.synchronize()
+    return gL, gG, oL, oG, ctr.read(), octr
+
+
+@pytest.mark.parametrize("n", [1, 33, 4001])
+def test_lepton_single_step(gpu_tables, ora_tables, n):
+    b = I.random_states(n, seed=200 + n, gamma_range=(50.0, 6000.0), field_region=(-40.0, 10.0))
+    f = Q.field(B.QED_FIELD_LP, a0=120.0, n_cycles=5.0, eta0=ETA0)
+    for q in (-1, 1):
+        gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 1, q=q, t0=10.0)
+        fl1, w1 = compare_with_flips(gL.read(), oL.view(), 1e-5, "leptons")
+        fl2, w2 = compare_with_flips(gG.read(), oG.view(), 1e-5, "photons", P_headless=True, frac_ok=1e-2, hard=3e-5)
+        assert fl1 + fl2 <= 2, (fl1, fl2)
+        assert c.status == 0 and abs(int(c.events) - oc.events) <= 1
+
+
+def test_emitted_spectrum_error(gpu_tables, ora_tables):
+    """Emitted photon energies matched by id: 99 % within 1e-5 of the oracle's, none beyond 3e-5; the
+    spectrum (counts on 64 log-spaced bins per decade) identical except for photons within 3e-5 of an
+    edge."""
+    b = I.random_states(6000, seed=3, gamma_range=(300.0, 6000.0), field_region=(-35.0, 5.0))
+    f = Q.field(B.QED_FIELD_CP, a0=100.0, n_cycles=4.0, eta0=ETA0)
+    gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 3)
+    g, o = gG.read(), oG.view()
+    common, gi, oi = np.intersect1d(g["id"], o["id"], return_indices=True)
+    assert len(common) >= 0.999 * oG.n and oG.n > 1000
+    eg = np.linalg.norm(g["mom"][gi], axis=1)
+    eo = np.linalg.norm(o["mom"][oi], axis=1)
+    err = np.abs(eg / eo - 1)
+    assert np.quantile(err, 0.99) <= 1e-5 and err.max() <= 3e-5, (np.quantile(err, 0.99), err.max())
+    edges = 10 ** (np.arange(-8, 4 + 1e-9, 1 / 64))
+    hg, _ = np.histogram(eg, edges)
+    ho, _ = np.histogram(eo, edges)
+    near = np.min(np.abs(np.log(eo[:, None] / edges[None, :])), axis=1) < 3e-5
+    assert np.abs(hg - ho).sum() <= 2 * near.sum()
+
+
+def test_lepton_multi_step(gpu_tables, ora_tables):
+    b = I.random_states(2000, seed=5, gamma_range=(200.0, 5000.0), field_region=(-35.0, 5.0))
+    f = Q.field(B.QED_FIELD_CP, a0=80.0, n_cycles=5.0, eta0=ETA0)
+    steps = 40
+    gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, steps, dt=0.1, t0=5.0)
+    flips, worst = compare_with_flips(gL.read(), oL.view(), 1e-5 * steps, "leptons")
+    pf, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
+    assert flips + pf <= max(2, 1e-5 * 2000 * steps), (flips, pf)
+
+
+def test_headon_lp_trajectory(gpu_tables, ora_tables):
+    wl = I.HEADON_LP_SMALL
+    b = wl.beam(n=2000)
+    f = Q.laser_field(wl.laser)
+    steps = 1300
+    gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, steps, seed=wl.seed, dt=wl.dt, t0=0.0)
+    assert oc.events > 5000
+    tol = 1e-5 * steps
+    flips, worst = compare_with_flips(gL.read(), oL.view(), tol, "leptons", diverged=0.3)
+    pf, _ = compare_with_flips(gG.read(), oG.view(), tol, "photons", P_headless=True, diverged=0.3)
+    assert flips + pf <= 1e-5 * 2000 * steps, (flips, pf, worst)
+
+
+@pytest.mark.parametrize("flags", [
+    B.QED_F_FULL & ~B.QED_F_TAU,
+    B.QED_F_FULL & ~(B.QED_F_SPIN_COLLAPSE | B.QED_F_POL_COLLAPSE),
+    B.QED_F_FULL & ~B.QED_F_RESOLVED,
+    B.QED_F_FULL | B.QED_F_TBMT_PAPER,
+    B.QED_F_FULL & ~B.QED_F_RECOIL,
+])
+def test_lepton_modes(gpu_tables, ora_tables, flags):
+    b = I.random_states(1500, seed=flags % 997, gamma_range=(100.0, 4000.0), field_region=(-30.0, 5.0))
+    f = Q.field(B.QED_FIELD_LP, a0=100.0, n_cycles=4.0, eta0=ETA0)
+    gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 4, flags=flags, dt=0.15)
+    fl1, _ = compare_with_flips(gL.read(), oL.view(), 2e-5, "leptons")
+    fl2, _ = compare_with_flips(gG.read(), oG.view(), 2e-5, "photons", P_headless=True, frac_ok=1e-2, hard=6e-5)
+    assert fl1 + fl2 <= 2
+
+
+def _photon_inputs(n, seed, energy=3000.0):
+    rng = np.random.default_rng(seed)
+    d = np.column_stack([rng.normal(0, 0.05, n), rng.normal(0, 0.05, n), -np.ones(n)])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    e = energy * np.exp(rng.uniform(-1.5, 0.5, n))
+    P = rng.normal(size=(n, 3))
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    P *= rng.uniform(0, 1, (n, 1))
+    pos = np.column_stack([rng.uniform(-3, 3, n), rng.uniform(-3, 3, n), rng.uniform(-35, 5, n)])
+    return {"pos": pos, "mom": d * e[:, None], "spin": P, "w": rng.uniform(0.5, 2, n),
+            "id": np.arange(n, dtype=np.uint64) * 104729 + 1}
+
+
+def test_photon_pairs_and_compaction(gpu_tables, ora_tables):
+    b = _photon_inputs(4000, seed=21)
+    f = Q.field(B.QED_FIELD_CP, a0=200.0, n_cycles=4.0, eta0=ETA0)
+    of = as_oracle_field(f)
+    gG, oG = _pair(b, B.QED_PHOTON, seed=4, photons=True)
+    gE, gP = Q.ParticleBuffer(8000, FP32, B.QED_ELECTRON), Q.ParticleBuffer(8000, FP32, B.QED_POSITRON)
+    oE, oP = O.Particles(8000), O.Particles(8000)
+    ws = Q.CompactWorkspace(gG.capacity)
+    ctr, octr = Q.Counters(), O.Counters()
+    steps = 20
+    for s in range(steps):
+        st = Q.step_desc(0.2, 6.0 + 0.2 * s, s, 4)
+        B.qed_pair_step(gpu_tables.handle, f, st, gG.s, gE.s, gP.s, ctr.ptr)
+        B.qed_compact(gG.s, ws.ptr, ws.bytes)
+        O.photon_step(ora_tables, of, as_oracle_step(st), oG, oE, oP, octr)
+    torch.cuda.synchronize()
+    assert octr.events > 200 and ctr.read().status == 0
+    # photons are held to the n-step bar; daughters are made in one event and keep their birth state
+    f1, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons")
+    f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5, "electrons", frac_ok=1e-2, hard=1e-3)
+    f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5, "positrons", frac_ok=1e-2, hard=1e-3)
+    assert f1 + f2 + f3 <= max(3, 1e-5 * 4000 * steps * 3), (f1, f2, f3)
+
+
+def test_coupled_species(gpu_tables, ora_tables):
+    f = Q.field(B.QED_FIELD_CP_COUNTER, a0=300.0, n_cycles=3.0, phase=3 * math.pi - 4.0,
+                eta0=I.eta0_for_wavelength(1.0))
+    of = as_oracle_field(f)
+    b = I.lepton_beam(400, 1000.0, direction=(1, 0, 0), z_range=(-0.5, 0.5), spin="random", seed=31)
+    cap = 60000
+    gE, oE = _pair(b, B.QED_ELECTRON, cap=cap, seed=31, use_begin=True)
+    gPo = Q.ParticleBuffer(cap, FP32, B.QED_POSITRON, use_begin=True)
+    gG = Q.ParticleBuffer(cap, FP32, B.QED_PHOTON, photons=True, use_begin=True)
+    oPo, oG = O.Particles(cap), O.Particles(cap)
+    ws = Q.CompactWorkspace(cap)
+    ctr = Q.Counters()
+    steps = 50
+    for s in range(steps):
+        st = Q.step_desc(0.1, 0.1 * s, s, 31, B.QED_F_FULL, photon_store_min=2.0)
+        B.qed_snapshot_counts([gE.s, gPo.s, gG.s])
+        B.qed_pair_step(gpu_tables.handle, f, st, gG.s, gE.s, gPo.s, ctr.ptr)
+        B.qed_push_step(gpu_tables.handle, f, st, gE.s, gG.s, ctr.ptr)
+        B.qed_push_step(gpu_tables.handle, f, st, gPo.s, gG.s, ctr.ptr)
+        B.qed_compact(gG.s, ws.ptr, ws.bytes)
+        oracle_full_step(ora_tables, of, as_oracle_step(st), [(oE, -1), (oPo, 1)], oG, oE, oPo)
+    torch.cuda.synchronize()
+    assert oG.n > 100
+    tol = 1e-5 * steps
+    f1, _ = compare_with_flips(gE.read(), oE.view(), tol, "electrons")
+    f2, _ = compare_with_flips(gPo.read(), oPo.view(), tol, "positrons")
+    f3, _ = compare_with_flips(gG.read(), oG.view(), tol, "photons", P_headless=True)
+    psteps = steps * (oE.n + oG.n)
+    assert f1 + f2 + f3 <= max(4, 1e-5 * psteps), (f1, f2, f3)
