@@ -48,7 +48,8 @@ typedef enum {
     QED_ERR_NAN = -5,      /* device: a particle with non-finite state was skipped */
     QED_ERR_TIMEOUT = -6,  /* device: a bounded wait gave up */
     QED_ERR_STATE = -7,    /* handle used after destroy, or library not initialised */
-    QED_ERR_NOMEM = -8     /* device allocation failed */
+    QED_ERR_NOMEM = -8,    /* device allocation failed */
+    QED_ERR_TOO_LARGE = -9 /* a size above the fixed limit of the call (qed_compact_noalloc) */
 } qed_status;
 
 /* Particle buffer layouts = the two arithmetic paths. */
@@ -240,6 +241,29 @@ qed_status qed_pair_step(qed_tables_t t, const qed_field *field, const qed_step_
  * leaves it ready for the next one.  Calls that share a workspace must not overlap on the device. */
 qed_status qed_compact(qed_particles *photons, void *workspace, size_t workspace_bytes, void *stream);
 size_t qed_compact_workspace_bytes(int64_t capacity);
+
+/* qed_compact without a workspace argument, and without any allocation (no cudaMalloc or cudaFree,
+ * no allocating library).  The paper has no counterpart: this is bookkeeping of the library, for
+ * callers that cannot allocate or hand over device memory at the call site -- host codes whose device
+ * memory is handed out entirely by their own pool, and step loops that must stay asynchronous
+ * (cudaFree, and cudaMalloc under memory pressure, synchronise the device).
+ *
+ * Scratch: a file-scope device array sized for QED_COMPACT_NOALLOC_MAX_CAPACITY photons (4.25 MiB
+ * per device), zero at module load.  Each call zeroes the tail marks it uses with
+ * cudaMemsetAsync on `stream` and resets the header counters in its first kernel, so nothing has to be
+ * cleared by the caller.  Result: the same as qed_compact (the survivors' set; their order may differ).
+ *
+ * Limits and ordering:
+ *  - photons->capacity above QED_COMPACT_NOALLOC_MAX_CAPACITY returns QED_ERR_TOO_LARGE before any
+ *    device work; use qed_compact with a caller workspace there.
+ *  - All calls on one device share the one scratch: calls that overlap on the device (streams with no
+ *    ordering between them, or several host threads) race on it and corrupt the result.  Order them
+ *    on one stream or with events.
+ *  - The first call on each device looks the scratch up (cudaGetSymbolAddress with that device
+ *    current, which may load the module); make that first call before any stream capture begins.
+ * Errors: QED_ERR_ARG (bad buffer), QED_ERR_TOO_LARGE, QED_ERR_CUDA (lookup or launch failed). */
+#define QED_COMPACT_NOALLOC_MAX_CAPACITY 262144
+qed_status qed_compact_noalloc(qed_particles *photons, void *stream);
 
 /* *begin = *count for each of the n buffers (device-side copy; graph-capturable).  Call it at the start
  * of a time step that runs several step calls, so each call processes only the particles alive when the

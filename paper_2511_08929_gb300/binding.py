@@ -18,11 +18,13 @@ LIB_PATH = os.path.join(HERE, "libqedgb.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "qed.h")
 
 QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_RANGE, QED_ERR_NAN, QED_ERR_TIMEOUT, QED_ERR_STATE, \
-    QED_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6, -7, -8
+    QED_ERR_NOMEM, QED_ERR_TOO_LARGE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 QED_FP64, QED_FP32 = 0, 1
 QED_ELECTRON, QED_PHOTON, QED_POSITRON = -1, 0, 1
 QED_FIELD_CONST, QED_FIELD_LP, QED_FIELD_CP, QED_FIELD_CP_COUNTER = 0, 1, 2, 3
 QED_LOOKUP_COLS = 8
+QED_COMPACT_NOALLOC_MAX_CAPACITY = int(re.search(r"#define QED_COMPACT_NOALLOC_MAX_CAPACITY (\d+)",
+                                                 open(HEADER).read()).group(1))
 
 
 def _flags_from_header():
@@ -106,6 +108,7 @@ def lib():
                                         P(QedParticles), vp, vp]),
                 "qed_compact": (i32, [P(QedParticles), vp, C.c_size_t, vp]),
                 "qed_compact_workspace_bytes": (C.c_size_t, [i64]),
+                "qed_compact_noalloc": (i32, [P(QedParticles), vp]),
                 "qed_snapshot_counts": (i32, [P(P(QedParticles)), i32, vp]),
                 "qed_counters_read": (i32, [vp, P(QedCounters), vp]),
             }
@@ -186,6 +189,14 @@ def qed_compact_workspace_bytes(capacity: int) -> int:
 
 def qed_compact(photons: QedParticles, workspace_dev: int, workspace_bytes: int, stream: int = 0):
     _check(lib().qed_compact(C.byref(photons), workspace_dev, workspace_bytes, stream or None), "qed_compact")
+
+
+def qed_compact_noalloc(photons: QedParticles, stream: int = 0):
+    st = lib().qed_compact_noalloc(C.byref(photons), stream or None)
+    if st == QED_ERR_TOO_LARGE:
+        raise QedError(st, f"qed_compact_noalloc: capacity {photons.capacity} is above the fixed scratch limit "
+                           f"of {QED_COMPACT_NOALLOC_MAX_CAPACITY} photons (use qed_compact with a workspace)")
+    _check(st, "qed_compact_noalloc")
 
 
 def qed_snapshot_counts(buffers, stream: int = 0):

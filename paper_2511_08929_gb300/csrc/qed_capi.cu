@@ -1,5 +1,6 @@
 // qed_capi.cu -- the C ABI of include/qed.h: argument checks, dispatch by buffer layout, and the small
 // bookkeeping kernels (birth optical depths, count snapshots and clamps, photon compaction).
+#include <atomic>
 #include <cstring>
 
 #include "qed_device.cuh"
@@ -21,6 +22,7 @@ extern "C" const char* qed_status_string(int32_t s) {
         case QED_ERR_TIMEOUT: return "bounded device wait gave up";
         case QED_ERR_STATE: return "invalid handle";
         case QED_ERR_NOMEM: return "device allocation failed";
+        case QED_ERR_TOO_LARGE: return "size above the fixed limit of the call";
         default: return "unknown status";
     }
 }
@@ -231,4 +233,64 @@ extern "C" qed_status qed_counters_read(const qed_counters* dev, qed_counters* h
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(host, dev, sizeof(qed_counters), cudaMemcpyDeviceToHost, st) != cudaSuccess) return QED_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+// ---- photon compaction without any allocation ----
+// qed_compact_noalloc runs the four compaction kernels above on a scratch area that is a file-scope
+// device array, sized for QED_COMPACT_NOALLOC_MAX_CAPACITY photons and carved like a caller workspace
+// of that capacity.  It serves callers that cannot allocate or hand over device memory at the call
+// site: host codes whose device memory is handed out entirely by their own pool, and step loops that
+// must stay asynchronous (cudaFree, and cudaMalloc under memory pressure, synchronise the device).
+namespace qed {
+
+constexpr size_t kNoAllocScratchBytes =
+    64 + 2 * ((sizeof(int64_t) * (size_t)QED_COMPACT_NOALLOC_MAX_CAPACITY + 15) & ~size_t(15)) +
+    (((size_t)QED_COMPACT_NOALLOC_MAX_CAPACITY + 15) & ~size_t(15));
+
+// Zero-initialised at module load like every static device object; each call zeroes the marks it
+// uses again (the header slots are written by compact_head_kernel), so no call depends on how the
+// previous one ended.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocDevices = 64;
+static std::atomic<void*> g_noalloc_addr[kNoAllocDevices];
+
+// Device address of the scratch on the current device, looked up once per device.
+static cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kNoAllocDevices) {
+        void* p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+        if (p) {
+            *out = p;
+            return cudaSuccess;
+        }
+    }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kNoAllocDevices) g_noalloc_addr[dev].store(p, std::memory_order_release);
+    *out = p;
+    return cudaSuccess;
+}
+
+}  // namespace qed
+
+extern "C" qed_status qed_compact_noalloc(qed_particles* photons, void* stream) {
+    if (check_particles(photons, true) != QED_OK) return QED_ERR_ARG;
+    if (photons->capacity > QED_COMPACT_NOALLOC_MAX_CAPACITY) return QED_ERR_TOO_LARGE;
+    void* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return QED_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const CompactWs w = carve(scratch, QED_COMPACT_NOALLOC_MAX_CAPACITY);
+    if (photons->capacity > 0 && cudaMemsetAsync(w.mark, 0, (size_t)photons->capacity, st) != cudaSuccess)
+        return QED_ERR_CUDA;
+    const PartDev g = part_dev(photons);
+    const int blocks = launch_blocks(photons->capacity, 256);
+    compact_head_kernel<<<1, 32, 0, st>>>(g, w);
+    compact_classify_kernel<<<blocks, 256, 0, st>>>(g, w);
+    compact_tail_kernel<<<blocks, 256, 0, st>>>(w);
+    compact_move_kernel<<<blocks, 256, 0, st>>>(g, photons->layout, w);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
