@@ -1,18 +1,23 @@
 """Throughput of the spin/polarization-resolved QED step on GB300.
 
-Workload (default): 1e7 electrons, gamma 4000, spin +z, head-on with a circularly polarized plane wave
-(a0 = 150 per component, 0.8 um, 20-cycle sin^2 envelope), NLC + polarization-resolved NBW, daughters
-appended to buffers of 4x the initial count, dt = lambda/(100 c), FP32 path (FP64 optical depth).
-The beam is advanced (untimed) to the middle of the interaction, then W warm-up steps and K timed
-steps run.  One step = snapshot of the counts, the photon (pair) step, the electron and positron
-(emission) steps and the compaction of converted photons; its particle-steps are the photons,
-electrons and positrons alive at the step's start.  The particle state (~2.4 GB) is far larger than
-L2, so no flush is needed between steps.
+Workload (default, --workload batched): 96 independent collisions stepped together, N_i log-uniform in
+[1e3, 2e6] electrons (2.2e7 in all), a0 ~ U[10, 300], gamma ~ U[500, 8000], partially polarized spins
+(+-n_i, P(+) = (1 + d_i)/2), LP and CP alternating, 0.8 um, 10-cycle sin^2 envelopes, NLC + NBW,
+daughters appended to per-instance buffers of 4x the initial count, dt = lambda/(100 c), FP32 path with
+FP64 optical depth.  One step of the batch = the planning kernel, one persistent kernel over every
+instance and species, and the per-instance photon compaction, replayed from a CUDA graph; the launch
+shape comes from the library's autotuner (timed on the run's own steps during the untimed advance).
+The batch is advanced (untimed) into the interaction, then W warm-up steps and K timed steps run as
+one graph launch; particle-steps are the photons, electrons and positrons alive at each step's start,
+counted on the device.  The particle state (several GB) is far larger than L2: no flush is needed.
 
-Multi-GPU (torchrun): every rank runs an independent replica of the workload with its own seed
-(particles never interact across ranks; there is no data-path collective): weak scaling.
+--workload headon: the single-buffer entry points on one collision (1e7 electrons, gamma 4000, spin +z,
+CP a0 = 150, 20 cycles).
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+Multi-GPU (torchrun): every rank runs an independent replica with its own seeds (particles never
+interact across ranks; there is no data-path collective): weak scaling.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload batched|headon]
 """
 from __future__ import annotations
 
@@ -30,20 +35,26 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "QED particle-steps/s (FP32 path, head-on CP a0=150 collision, NLC + NBW)"
+METRIC = "QED particle-steps/s on 1 GB300 (FP32 batched vs plain FP64) at stated error; % HBM peak"
 UNIT = "particle-steps/s"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--electrons", type=int, default=10_000_000)
-    ap.add_argument("--advance", type=int, default=620, help="untimed steps before warm-up (reach the pulse)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "headon"])
+    ap.add_argument("--electrons", type=int, default=10_000_000, help="headon workload only")
+    ap.add_argument("--advance", type=int, default=None,
+                    help="untimed steps before warm-up (into the interaction; default 450 batched, 620 headon)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU-baseline legs")
-    return ap.parse_args()
+    ap.add_argument("--no-tune", action="store_true", help="batched: keep the default launch shape")
+    a = ap.parse_args()
+    if a.advance is None:
+        a.advance = 450 if a.workload == "batched" else 620
+    return a
 
 
 # ------------------------------------------------------------------------------------------------
@@ -160,8 +171,8 @@ class Sim:
 def main():
     args = parse()
     if args.impl == "reference":
-        return reference_arm(args)
-    out = native(args)
+        return reference_arm(args) if args.workload == "headon" else reference_arm_batch(args)
+    out = native(args) if args.workload == "headon" else native_batch(args)
     if out is not None:
         print(json.dumps(out))
 
@@ -289,6 +300,381 @@ def native(args):
     if rank != 0:
         return None
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# the batched workload
+# ------------------------------------------------------------------------------------------------
+def batch_setup(Q, B, I, tables, rank, device):
+    wl = I.BATCHED_96
+    insts = wl.instances()
+    fields = [Q.laser_field(wl.laser(x)) for x in insts]
+    seeds = [x["seed"] + 1000 * rank for x in insts]
+    caps = [tuple(max(4096, int(wl.capacity_factor * x["n"])) for _ in range(3)) for x in insts]
+    bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
+                 device=device)
+    for k, (x, (e, p, g)) in enumerate(zip(insts, bt.buffers())):
+        b = wl.beam(k, x)
+        if rank:
+            b["id"] = b["id"] + np.uint64(rank << 48)
+        e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"])
+        e.init_tau(seeds[k])
+    return wl, insts, fields, seeds, caps, bt
+
+
+def native_batch(args):
+    import torch
+    from paper_2511_08929_gb300 import binding as B
+    from paper_2511_08929_gb300 import build as bld
+    from paper_2511_08929_gb300 import buffers as Q
+    from paper_2511_08929_gb300 import inputs as I
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = f"cuda:{local if world > 1 else 0}"
+    bld.build()
+    t0 = time.time()
+    tables = Q.Tables(1e-4, 1e3, 256, 256)
+    torch.cuda.synchronize()
+    t_tables = time.time() - t0
+    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    # untimed advance into the interaction; the autotuner times its candidates on real steps mid-way
+    half = args.advance // 2
+    bt.step(half, stream)
+    tuning = bt.tuning()
+    tune_s = 0.0
+    if not args.no_tune:
+        cache = os.environ.get("QED_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qedgb",
+                                                              "autotune.jsonl"))
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        t0 = time.time()
+        tuning = bt.tune(1, cache, stream)
+        tune_s = time.time() - t0
+    st = bt.stats(stream)
+    if st.step < args.advance:
+        bt.step(int(args.advance - st.step), stream)
+    bt.step(args.warmup, stream)
+    torch.cuda.synchronize()
+
+    # the timed region is one launch of a graph of K steps with event pairs around each persistent kernel
+    K = args.steps
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    B.qed_batch_set_tuning(bt.handle, B.QedBatchTuning(tuning.variant, tuning.blocks_per_sm, tuning.chunk, K))
+    bt.set_kernel_events(kev)
+    bt.step(0, stream)  # capture and instantiate outside the timed region
+    bt.ctr.zero()
+    torch.cuda.synchronize()
+    s0 = bt.stats(stream)
+    stop = threading.Event()
+    clock_lines = []
+    th = threading.Thread(target=clocks_sampler, args=(stop, clock_lines, local), daemon=True)
+    th.start()
+    time.sleep(0.5)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    bt.step(K, stream)
+    end.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stop.set()
+    th.join(timeout=5)
+    ms = start.elapsed_time(end)
+    s1 = bt.stats(stream)
+    ctr = bt.ctr.read()
+    try:
+        t_kern = [a.elapsed_time(b) for a, b in kev]
+    except RuntimeError:
+        t_kern = None
+    psteps = float(s1.particle_steps - s0.particle_steps)
+    d_sp = [float(s1.species_steps[i] - s0.species_steps[i]) for i in range(3)]
+    tmax, psteps_all = ms, psteps
+    if dist is not None:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+        p = torch.tensor([psteps], device=device, dtype=torch.float64)
+        dist.all_reduce(p)
+        psteps_all = float(p.item())
+    value = psteps_all / (tmax / 1e3)
+
+    # roofline of the persistent kernel: algorithmic bytes per launch / its event-timed duration
+    # 88 B per lepton-step, 76 B per photon-step, 8 B (id) per event, 52 B per stored daughter
+    peak, peak_kind = measured_peaks()
+    alg = 88.0 * (d_sp[0] + d_sp[1]) + 76.0 * d_sp[2] + 8.0 * ctr.events + 52.0 * ctr.stored
+    roof = {"kernel": "batch_step_kernel", "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
+            "frac": None, "traffic": None, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": alg / K}
+    if t_kern:
+        tk = sum(t_kern)
+        achieved = alg / (tk / 1e3) / 1e9
+        roof.update({"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+                     "ms_per_launch": round(tk / K, 4), "share_of_step": round(tk / ms, 4)})
+    clocks = summarize_clocks(clock_lines)
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, torch, stream)
+    n_el = sum(x["n"] for x in insts)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "instances": len(insts), "electrons_per_gpu": n_el,
+                   "laser": "LP/CP alternating 0.8um 10 cycles, a0 U[10,300]", "gamma": "U[500,8000]",
+                   "buffers": "4x initial per species and instance", "layout": "FP32 float4 SoA",
+                   "timed_from_step": int(s0.step), "parallelism": f"replicas x{world}",
+                   "launch": {"graph_steps": K, "tuning": tuning.as_dict(), "autotune_s": round(tune_s, 2)},
+                   "l2": "state > L2 (no flush needed)", "tables": "256 chi x 256 r, FP64-built"},
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": 6 * K,
+        "particles_at_start": {"electrons": int(s0.alive[0]), "positrons": int(s0.alive[1]),
+                               "photons": int(s0.alive[2])},
+        "particle_steps_timed": {"electrons": d_sp[0], "positrons": d_sp[1], "photons": d_sp[2]},
+        "counters": {k: int(v) for k, v in ctr.as_dict().items()},
+        "table_build_s": round(t_tables, 2),
+    }
+    out.update(extras)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return out
+
+
+def _to_fp64(b32, b64, torch):
+    """Copy an FP32 buffer's [0, count) into an FP64 buffer (device-side repacking)."""
+    n = b32.count()
+    q = b32.q[:, :n]
+    P = b64.planes
+    P[0:3, :n] = q[0, :, 0:3].T.double()
+    P[3, :n] = q[0, :, 3].double()
+    P[4:6, :n] = q[1, :, 0:2].T.double()
+    P[6:8, :n] = q[1, :, 2:4].T.double()
+    P[8, :n] = q[2, :, 0].double()
+    P[10, :n] = q[2, :, 1].double()
+    P[9, :n] = q[2, :, 2:4].contiguous().view(torch.float64).reshape(n)
+    b64.ids[:n] = b32.ids[:n]
+    b64.counts[:] = n
+
+
+def batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, torch, stream):
+    """The plain FP64 path on the same state (instance by instance through the single-buffer entry
+    points), e2e through the C ABI with host-resident state, and the oracle on a bounded sample."""
+    out = {}
+    st = bt.stats(stream)
+    step0 = int(st.step)
+    # ---- plain FP64 path on the same state ----
+    bufs64, cnt = [], 0.0
+    for (e, p, g), cap in zip(bt.buffers(), caps):
+        e64 = Q.ParticleBuffer(cap[0], B.QED_FP64, B.QED_ELECTRON, use_begin=True)
+        p64 = Q.ParticleBuffer(cap[1], B.QED_FP64, B.QED_POSITRON, use_begin=True)
+        g64 = Q.ParticleBuffer(cap[2], B.QED_FP64, B.QED_PHOTON, photons=True, use_begin=True)
+        for a, b in ((e, e64), (p, p64), (g, g64)):
+            _to_fp64(a, b, torch)
+        bufs64.append((e64, p64, g64, Q.CompactWorkspace(cap[2])))
+    ctr64 = Q.Counters()
+    torch.cuda.synchronize()
+
+    def step64(s):
+        n = 0
+        for (e64, p64, g64, ws), f, sd in zip(bufs64, fields, seeds):
+            d = Q.step_desc(wl.dt, float(s) * wl.dt, s, sd, B.QED_F_FULL, wl.photon_store_min)
+            B.qed_snapshot_counts([e64.s, p64.s, g64.s], stream)
+            B.qed_pair_step(tables.handle, f, d, g64.s, e64.s, p64.s, ctr64.ptr, stream)
+            B.qed_push_step(tables.handle, f, d, e64.s, g64.s, ctr64.ptr, stream)
+            B.qed_push_step(tables.handle, f, d, p64.s, g64.s, ctr64.ptr, stream)
+            B.qed_compact(g64.s, ws.ptr, ws.bytes, stream)
+    K64 = 3
+    alive = [torch.stack([b.counts[0] for b in (x[0], x[1], x[2])]).sum() for x in bufs64]
+    n_before = float(sum(a.item() for a in alive))
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    counts = []
+    s_.record()
+    for k in range(K64):
+        counts.append(torch.stack([torch.stack([b.counts[0] for b in x[:3]]).sum() for x in bufs64]).sum())
+        step64(step0 + k)
+    e_.record()
+    torch.cuda.synchronize()
+    ps64 = float(sum(c.item() for c in counts))
+    out["fp64_plain"] = {"value": ps64 / (s_.elapsed_time(e_) / 1e3), "unit": UNIT, "steps": K64,
+                         "ms_per_step": s_.elapsed_time(e_) / K64,
+                         "note": "single-buffer FP64 entry points, instance by instance, same state"}
+    del bufs64
+    torch.cuda.empty_cache()
+    bt.step(K64, stream)  # keep the FP32 batch at the same step as the FP64 copy went (not needed after)
+
+    # ---- e2e: host-resident particle state, copied in and out through pinned memory every step ----
+    Ke = 3
+    host = []
+    for x in bt.buffers():
+        host.append([(torch.empty_like(b.q, device="cpu").pin_memory(), torch.empty_like(b.ids, device="cpu").pin_memory())
+                     for b in x])
+    for hx, x in zip(host, bt.buffers()):
+        for (hq, hi), b in zip(hx, x):
+            hq.copy_(b.q)
+            hi.copy_(b.ids)
+    counts_dev = torch.stack([b.counts[0] for x in bt.buffers() for b in x])
+    h_counts = torch.empty(counts_dev.numel(), dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    n_now = [b.count() for x in bt.buffers() for b in x]
+    t0 = time.perf_counter()
+    ps_e, bi, bo = 0.0, 0, 0
+    for _ in range(Ke):
+        k = 0
+        for hx, x in zip(host, bt.buffers()):
+            for (hq, hi), b in zip(hx, x):
+                nn = n_now[k]
+                b.q[:, :nn].copy_(hq[:, :nn], non_blocking=True)
+                b.ids[:nn].copy_(hi[:nn], non_blocking=True)
+                bi += 3 * nn * 16 + 8 * nn
+                k += 1
+        ps_e += sum(n_now)
+        bt.step(1, stream)
+        h_counts.copy_(torch.stack([b.counts[0] for x in bt.buffers() for b in x]), non_blocking=True)
+        torch.cuda.synchronize()
+        n_now = h_counts.tolist()
+        k = 0
+        for hx, x in zip(host, bt.buffers()):
+            for (hq, hi), b in zip(hx, x):
+                nn = n_now[k]
+                hq[:, :nn].copy_(b.q[:, :nn], non_blocking=True)
+                hi[:nn].copy_(b.ids[:nn], non_blocking=True)
+                bo += 3 * nn * 16 + 8 * nn
+                k += 1
+        bo += 8 * len(n_now)
+        torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    out["e2e"] = {"value": ps_e / te, "unit": UNIT, "h2d_bytes_per_step": bi // Ke, "d2h_bytes_per_step": bo // Ke,
+                  "note": "all instances' particle state host-resident, copied in and out through pinned memory "
+                          "every step around one qed_batch_step"}
+    del host
+
+    # ---- CPU baseline: the oracle on a bounded sample of the same state ----
+    out["cpu_baseline"] = batch_cpu_baseline(bt, wl, insts, fields, seeds, int(bt.stats(stream).step))
+    return out
+
+
+def _oracle_batch_step(O, tb, f, st, E, P, G):
+    """One time step of one instance on the oracle, with the begin-snapshot semantics of the batch:
+    photons first (pairs appended to E, P), then each lepton species over its particles present at the
+    step's start (lepton steps append photons only)."""
+    nE, nP = E.n, P.n
+    O.photon_step(tb, f, st, G, E, P)
+    for L, q, n0 in ((E, -1, nE), (P, 1, nP)):
+        n_now = L.n
+        L._s.n = n0
+        O.lepton_step(tb, f, st, q, L, G)
+        L._s.n = n_now
+
+
+def _oracle_field(O, f):
+    return O.field(f.kind, a0=f.a0, n_cycles=f.n_cycles, phase=f.phase, E0=tuple(f.E0), B0=tuple(f.B0), eta0=f.eta0)
+
+
+def batch_cpu_baseline(bt, wl, insts, fields, seeds, step0, seconds=15.0, frac=0.02, max_steps=40):
+    """The oracle on a bounded sample of the batch's current state: from every instance the first
+    `frac` of its electrons, positrons and photons (at least one of each where present), stepped with
+    the instance's own laser and seed for at most max_steps steps and about `seconds` of CPU work."""
+    import oracle as O
+    tb = O.tables(1e-4, 1e3, 256, 256)
+    sample = []
+    n_e = n_g = 0
+    for (e, p, g), f, sd in zip(bt.buffers(), fields, seeds):
+        parts = []
+        ms = [max(1, int(frac * b.count())) for b in (e, p, g)]
+        caps = (2 * (ms[0] + ms[2]) + 64, 2 * (ms[1] + ms[2]) + 64, ms[2] + 40 * (ms[0] + ms[1]) + 256)
+        for b, m, cap in zip((e, p, g), ms, caps):
+            d = b.read(m)
+            parts.append(O.Particles.from_arrays(cap, d["pos"], d["mom"], d["spin"], d["w"], d["id"], tau=d["tau"]))
+        n_e += parts[0].n
+        n_g += parts[2].n
+        sample.append((parts, _oracle_field(O, f), sd))
+    ps, dt, steps = 0, 0.0, 0
+    while steps < max_steps and dt < seconds:
+        s = step0 + steps
+        for (E, P, G), f, sd in sample:
+            st = O.step_desc(wl.dt, float(s) * wl.dt, s, sd, O.F_FULL, wl.photon_store_min)
+            c = E.n + P.n + G.n
+            t0 = time.perf_counter()
+            _oracle_batch_step(O, tb, f, st, E, P, G)
+            dt += time.perf_counter() - t0
+            ps += c
+        steps += 1
+    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{frac:.0%} of every instance's particles at step {step0} ({n_e} electrons, {n_g} photons), "
+                      f"{steps} steps, {dt:.1f} s"}
+
+
+def reference_arm_batch(args):
+    """The oracle, as it stands, on the host cores: the batched workload with every instance reduced
+    to a bounded sample of its electrons, advanced to the same window, then W + K timed steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2511_08929_gb300 import inputs as I
+    wl = I.BATCHED_96
+    insts = wl.instances()
+    tb = O.tables(1e-4, 1e3, 256, 256)
+    scale = 2e-3
+    sample = []
+    n_tot = 0
+    for k, x in enumerate(insts):
+        n = max(1, int(scale * x["n"]))
+        b = wl.beam(k, x, n=n)
+        L = O.Particles.from_arrays(40 * n + 64, b["pos"], b["mom"], b["spin"], b["w"], b["id"])
+        L.init_tau(x["seed"])
+        lz = wl.laser(x)
+        f = O.field(O.FIELD_LP if lz.kind == "LP" else O.FIELD_CP, a0=lz.a0, n_cycles=lz.n_cycles, phase=lz.phase,
+                    eta0=lz.eta0)
+        sample.append((L, O.Particles(40 * n + 64), O.Particles(400 * n + 256), f, x["seed"]))
+        n_tot += n
+    s = 0
+
+    def one():
+        nonlocal s
+        c = 0
+        for E, P, G, f, sd in sample:
+            st = O.step_desc(wl.dt, float(s) * wl.dt, s, sd, O.F_FULL, wl.photon_store_min)
+            c += E.n + P.n + G.n
+            _oracle_batch_step(O, tb, f, st, E, P, G)
+        s += 1
+        return c
+    while s < args.advance:
+        one()
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    ps = 0
+    for _ in range(args.steps):
+        ps += one()
+    dt = time.perf_counter() - t0
+    v = ps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "instances": len(insts), "sample_electrons": n_tot,
+                      "sample": f"{scale:g} of every instance's electrons (at least 1)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": O.num_threads(),
+                            "sample": f"{n_tot} electrons over {len(insts)} instances ({scale:g} of each), "
+                                      f"steps {args.advance + args.warmup}..{s - 1}"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
 
 
 def extra_legs(args, sim, Q, B, I, wl, tables, device, torch):

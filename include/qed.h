@@ -265,6 +265,84 @@ size_t qed_compact_workspace_bytes(int64_t capacity);
 #define QED_COMPACT_NOALLOC_MAX_CAPACITY 262144
 qed_status qed_compact_noalloc(qed_particles *photons, void *stream);
 
+/* ---- Batched collisions: many independent instances stepped together ----
+ * A batch is a set of independent collision instances (each its own laser, seed and three FP32 species
+ * buffers) advanced in lockstep.  One time step of the whole batch is: a planning kernel (alive counts
+ * at step start, the tile list over all instances and species), one persistent kernel that streams every
+ * tile of 32 particles of every instance (the lepton step of Sec. 4.1 for electrons and positrons, the
+ * photon step of Sec. 4.2 for photons, each as qed_push_step / qed_pair_step do), and the photon
+ * compaction of every instance.  The step index and time live in device memory and advance on the
+ * device, so a captured CUDA graph of one or more steps is replayed unchanged.  Results are the ones
+ * qed_push_step, qed_pair_step and qed_compact give per instance with begin snapshots (the same
+ * arithmetic and random draws; appended daughters may sit in another order), whatever the tuning. */
+#define QED_BATCH_MAX_INSTANCES 1024
+#define QED_BATCH_VARIANTS 4
+
+typedef struct qed_batch_s *qed_batch_t;
+
+typedef struct {
+    qed_field field; /* the instance's laser */
+    uint64_t seed;   /* the instance's Philox seed */
+    qed_particles electrons, positrons, photons; /* layout QED_FP32; photons with a dead list; begin unused */
+} qed_instance;
+
+typedef struct {
+    double dt;       /* time step of every instance */
+    double t0;       /* time of step step0; step k is at t0 + (k - step0) dt (rounded as a product, then a sum) */
+    uint64_t step0;  /* Philox step index of the first step */
+    uint32_t flags;  /* QED_F_* */
+    int32_t pad;
+    double photon_store_min, chi_floor; /* as in qed_step_desc */
+} qed_batch_desc;
+
+/* Launch shape of the batch step (no effect on results).
+ *   variant       kernel build: 0 = 256 threads, 3-stage copies, registers for 3 blocks/SM;
+ *                 1 = 256 threads, 3 stages, 2 blocks/SM; 2 = 128 threads, 4 stages, 5 blocks/SM;
+ *                 3 = 512 threads, 2 stages, 1 block/SM
+ *   blocks_per_sm resident blocks per SM of the persistent grid (0: the occupancy maximum)
+ *   chunk         consecutive tiles of 32 particles a warp takes before moving on by the grid's width
+ *   graph_steps   time steps captured per CUDA graph (0: launch the kernels directly every step) */
+typedef struct {
+    int32_t variant, blocks_per_sm, chunk, graph_steps;
+} qed_batch_tuning;
+
+typedef struct {
+    uint64_t step;              /* Philox index of the next step */
+    uint64_t particle_steps;    /* particles processed since creation (all instances and species) */
+    uint64_t species_steps[3];  /* the same split into electrons, positrons, photons */
+    int64_t alive[3];           /* electrons, positrons, photons processed by the last step */
+} qed_batch_stats;
+
+/* Create a batch of n_inst (1 .. QED_BATCH_MAX_INSTANCES) instances.  The instance array is copied; the
+ * particle buffers stay the caller's and must outlive the batch.  The batch owns its device planning
+ * state and the compaction workspace (17 B per photon of capacity), and writes its counters to
+ * counters_dev.  Errors: QED_ERR_ARG, QED_ERR_STATE (tables), QED_ERR_NOMEM, QED_ERR_CUDA. */
+qed_status qed_batch_create(qed_tables_t t, const qed_instance *instances, int32_t n_inst, const qed_batch_desc *desc,
+                            qed_counters *counters_dev, qed_batch_t *out);
+/* Set / read the launch shape; setting it discards any captured graph. */
+qed_status qed_batch_set_tuning(qed_batch_t b, const qed_batch_tuning *tuning);
+qed_status qed_batch_get_tuning(qed_batch_t b, qed_batch_tuning *out);
+/* Advance every instance n_steps time steps on `stream` (asynchronous).  With graph_steps > 0 the steps
+ * run as launches of a CUDA graph of graph_steps steps, captured on first use; the rest directly.
+ * n_steps = 0 only captures the graph (if graph_steps > 0 and none is held), so that the capture and
+ * instantiation can be kept out of a timed region. */
+qed_status qed_batch_step(qed_batch_t b, int32_t n_steps, void *stream);
+/* Kernel timing: events[2k], events[2k+1] (cudaEvent_t, created by the caller with timing enabled) are
+ * recorded around the persistent kernel of the k-th step (k modulo n_pairs) of every CUDA graph captured
+ * from now on (step k of the graph) and of directly launched steps (counted from this call).  n_pairs = 0
+ * switches it off.  Discards any captured graph. */
+qed_status qed_batch_set_kernel_events(qed_batch_t b, void *const *events, int32_t n_pairs);
+/* Autotuner: times the persistent kernel of every launch shape it considers on the batch's own next
+ * steps (they are real steps: results do not depend on the shape), picks the one with the least time
+ * per particle-step and sets it.  steps_per_candidate >= 1.  cache_path (may be NULL): a text file of
+ * one JSON object per line, keyed by device, SM count and workload size; a matching line is used
+ * without timing, a new result is appended.  Synchronizes `stream`. */
+qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate, const char *cache_path, qed_batch_tuning *out,
+                          void *stream);
+/* Step index and processed particle-steps (synchronizes `stream`). */
+qed_status qed_batch_stats_read(qed_batch_t b, qed_batch_stats *out, void *stream);
+void qed_batch_destroy(qed_batch_t b);
+
 /* *begin = *count for each of the n buffers (device-side copy; graph-capturable).  Call it at the start
  * of a time step that runs several step calls, so each call processes only the particles alive when the
  * step began (Sec. 3.3: an event's daughters join the simulation from the next step).  Buffers whose

@@ -72,6 +72,28 @@ class QedStepDesc(C.Structure):
                 ("chi_floor", C.c_double)]
 
 
+class QedInstance(C.Structure):
+    _fields_ = [("field", QedField), ("seed", C.c_uint64), ("electrons", QedParticles), ("positrons", QedParticles),
+                ("photons", QedParticles)]
+
+
+class QedBatchDesc(C.Structure):
+    _fields_ = [("dt", C.c_double), ("t0", C.c_double), ("step0", C.c_uint64), ("flags", C.c_uint32),
+                ("pad", C.c_int32), ("photon_store_min", C.c_double), ("chi_floor", C.c_double)]
+
+
+class QedBatchTuning(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32), ("graph_steps", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class QedBatchStats(C.Structure):
+    _fields_ = [("step", C.c_uint64), ("particle_steps", C.c_uint64), ("species_steps", C.c_uint64 * 3),
+                ("alive", C.c_int64 * 3)]
+
+
 class QedCounters(C.Structure):
     _fields_ = [("events", C.c_ulonglong), ("stored", C.c_ulonglong), ("dropped_capacity", C.c_ulonglong),
                 ("chi_clamped", C.c_ulonglong), ("renormalised", C.c_ulonglong), ("below_store", C.c_ulonglong),
@@ -111,6 +133,14 @@ def lib():
                 "qed_compact_noalloc": (i32, [P(QedParticles), vp]),
                 "qed_snapshot_counts": (i32, [P(P(QedParticles)), i32, vp]),
                 "qed_counters_read": (i32, [vp, P(QedCounters), vp]),
+                "qed_batch_create": (i32, [vp, P(QedInstance), i32, P(QedBatchDesc), vp, P(vp)]),
+                "qed_batch_set_tuning": (i32, [vp, P(QedBatchTuning)]),
+                "qed_batch_get_tuning": (i32, [vp, P(QedBatchTuning)]),
+                "qed_batch_step": (i32, [vp, i32, vp]),
+                "qed_batch_set_kernel_events": (i32, [vp, P(vp), i32]),
+                "qed_batch_tune": (i32, [vp, i32, C.c_char_p, P(QedBatchTuning), vp]),
+                "qed_batch_stats_read": (i32, [vp, P(QedBatchStats), vp]),
+                "qed_batch_destroy": (None, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -208,6 +238,53 @@ def qed_counters_read(counters_dev: int, stream: int = 0) -> QedCounters:
     out = QedCounters()
     _check(lib().qed_counters_read(counters_dev, C.byref(out), stream or None), "qed_counters_read")
     return out
+
+
+def qed_batch_create(tables, instances, desc: QedBatchDesc, counters_dev: int) -> int:
+    """instances: a sequence of QedInstance; returns the batch handle."""
+    arr = (QedInstance * len(instances))(*instances)
+    h = C.c_void_p()
+    _check(lib().qed_batch_create(tables, arr, len(instances), C.byref(desc), counters_dev, C.byref(h)),
+           "qed_batch_create")
+    return h.value
+
+
+def qed_batch_set_tuning(batch: int, tuning: QedBatchTuning):
+    _check(lib().qed_batch_set_tuning(batch, C.byref(tuning)), "qed_batch_set_tuning")
+
+
+def qed_batch_get_tuning(batch: int) -> QedBatchTuning:
+    out = QedBatchTuning()
+    _check(lib().qed_batch_get_tuning(batch, C.byref(out)), "qed_batch_get_tuning")
+    return out
+
+
+def qed_batch_step(batch: int, n_steps: int, stream: int = 0):
+    _check(lib().qed_batch_step(batch, n_steps, stream or None), "qed_batch_step")
+
+
+def qed_batch_set_kernel_events(batch: int, events, n_pairs: int):
+    """events: sequence of 2 n_pairs cudaEvent_t handles (integers, e.g. torch.cuda.Event.cuda_event)."""
+    arr = (C.c_void_p * max(1, len(events)))(*events) if events else None
+    _check(lib().qed_batch_set_kernel_events(batch, arr, n_pairs), "qed_batch_set_kernel_events")
+
+
+def qed_batch_tune(batch: int, steps_per_candidate: int = 2, cache_path=None, stream: int = 0) -> QedBatchTuning:
+    out = QedBatchTuning()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().qed_batch_tune(batch, steps_per_candidate, path, C.byref(out), stream or None), "qed_batch_tune")
+    return out
+
+
+def qed_batch_stats_read(batch: int, stream: int = 0) -> QedBatchStats:
+    out = QedBatchStats()
+    _check(lib().qed_batch_stats_read(batch, C.byref(out), stream or None), "qed_batch_stats_read")
+    return out
+
+
+def qed_batch_destroy(batch: int):
+    if batch:
+        lib().qed_batch_destroy(batch)
 
 
 def declared_entry_points():

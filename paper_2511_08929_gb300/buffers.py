@@ -83,9 +83,12 @@ class ParticleBuffer:
     def count(self) -> int:
         return int(self.counts[0].item())
 
-    def read(self) -> dict:
-        """Host copy of [0, count) as FP64 arrays (pos, mom, spin, tau, w, id)."""
+    def read(self, limit=None) -> dict:
+        """Host copy of [0, count) (or of its first `limit` particles) as FP64 arrays (pos, mom, spin,
+        tau, w, id)."""
         n = self.count()
+        if limit is not None:
+            n = min(n, int(limit))
         if self.layout == B.QED_FP64:
             h = self.planes[:, :n].cpu().numpy()
             pos, mom, spin, tau, w = h[0:3].T.copy(), h[3:6].T.copy(), h[6:9].T.copy(), h[9].copy(), h[10].copy()
@@ -173,6 +176,83 @@ class CompactWorkspace:
         self.bytes = B.qed_compact_workspace_bytes(capacity)
         self.t = torch.zeros((self.bytes + 15) // 16 * 2, dtype=torch.int64, device=device)
         self.ptr = self.t.data_ptr()
+
+
+class Batch:
+    """A batch of independent collisions (qed_batch_*): per instance an FP32 electron, positron and
+    photon buffer, a laser and a Philox seed; all instances advance together in one persistent launch
+    per time step."""
+
+    def __init__(self, tables: "Tables", fields, seeds, capacities, dt, t0=0.0, step0=0, flags=None,
+                 photon_store_min=0.0, chi_floor=0.0, device="cuda"):
+        """fields: QedField per instance; seeds: Philox seed per instance; capacities: (electrons,
+        positrons, photons) capacity per instance."""
+        self.device = torch.device(device)
+        self.el, self.po, self.ph = [], [], []
+        insts = []
+        for f, sd, (ce, cp, cg) in zip(fields, seeds, capacities):
+            e = ParticleBuffer(ce, B.QED_FP32, B.QED_ELECTRON, device=device)
+            p = ParticleBuffer(cp, B.QED_FP32, B.QED_POSITRON, device=device)
+            g = ParticleBuffer(cg, B.QED_FP32, B.QED_PHOTON, device=device, photons=True)
+            self.el.append(e)
+            self.po.append(p)
+            self.ph.append(g)
+            inst = B.QedInstance()
+            inst.field = f
+            inst.seed = int(sd)
+            inst.electrons, inst.positrons, inst.photons = e.s, p.s, g.s
+            insts.append(inst)
+        self.desc = B.QedBatchDesc()
+        self.desc.dt, self.desc.t0, self.desc.step0 = dt, t0, step0
+        self.desc.flags = B.QED_F_FULL if flags is None else flags
+        self.desc.photon_store_min, self.desc.chi_floor = photon_store_min, chi_floor
+        self.ctr = Counters(device)
+        self.tables = tables
+        self.handle = B.qed_batch_create(tables.handle, insts, self.desc, self.ctr.ptr)
+
+    def __len__(self):
+        return len(self.el)
+
+    def step(self, n_steps: int = 1, stream: int = 0):
+        B.qed_batch_step(self.handle, n_steps, stream)
+
+    def tune(self, steps_per_candidate: int = 2, cache_path=None, stream: int = 0):
+        return B.qed_batch_tune(self.handle, steps_per_candidate, cache_path, stream)
+
+    def set_tuning(self, variant=0, blocks_per_sm=0, chunk=4, graph_steps=8):
+        t = B.QedBatchTuning(variant, blocks_per_sm, chunk, graph_steps)
+        B.qed_batch_set_tuning(self.handle, t)
+
+    def tuning(self):
+        return B.qed_batch_get_tuning(self.handle)
+
+    def set_kernel_events(self, events):
+        """events: list of (start, end) torch.cuda.Event pairs (timing enabled) recorded around the
+        persistent kernel of successive steps (see qed_batch_set_kernel_events)."""
+        for pair in events:  # torch creates the CUDA event at its first record
+            for e in pair:
+                if not e.cuda_event:
+                    e.record()
+        torch.cuda.synchronize(self.device)
+        flat = [e.cuda_event for pair in events for e in pair]
+        B.qed_batch_set_kernel_events(self.handle, flat, len(events))
+
+    def stats(self, stream: int = 0):
+        return B.qed_batch_stats_read(self.handle, stream)
+
+    def buffers(self):
+        return [(self.el[k], self.po[k], self.ph[k]) for k in range(len(self))]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.qed_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def laser_field(laser, kind_map=None) -> B.QedField:

@@ -17,8 +17,11 @@ LIB = os.path.join(HERE, "libqedgb.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE]
-# the FP32 path: approximate FP32 division and square root, denormals flushed (FP64 is unaffected)
-PER_FILE_FLAGS = {"qed_step32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+# the FP32 path: denormals flushed (FP64 is unaffected); IEEE-rounded division and square root and no
+# implicit contraction of a product and a sum into one FMA (only the explicit fmaf calls fuse), so that a
+# source line rounds the same way wherever it is inlined and results do not depend on the launch shape
+_FP32_FLAGS = ["-ftz=true", "-prec-div=true", "-prec-sqrt=true", "-fmad=false"]
+PER_FILE_FLAGS = {"qed_step32.cu": _FP32_FLAGS, "qed_batch.cu": _FP32_FLAGS}
 
 
 def _nvcc() -> str:

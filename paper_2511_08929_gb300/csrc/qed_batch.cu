@@ -1,0 +1,799 @@
+// qed_batch.cu -- batched collisions: every instance and species of a batch in one persistent launch per
+// time step, the step index and time on the device (so a CUDA graph of whole steps replays unchanged),
+// and an autotuner for the launch shape.
+//
+// One time step of the batch is six launches on one stream:
+//   plan      alive counts at step start (counts clamped to capacity), the tile list over all segments
+//             (segment = one species of one instance, species-major), particle-step accounting;
+//   step      the persistent kernel: every warp walks its share of the tile list (chunks of `chunk`
+//             consecutive tiles, chunk k of warp w at k * warps + w) with the same bulk-copy pipeline,
+//             per-particle arithmetic and per-warp event queue as the single-buffer FP32 kernels; the
+//             event queue is drained when a warp crosses into another segment;
+//   compact   head / classify / tail / move of every instance's photons (converted photons leave,
+//             Sec. 3.3), the last one also advancing the device step counter.
+// Daughters appended during a step sit beyond the counts taken by `plan`, so they are first stepped in
+// the next step (the begin snapshot of the single-buffer path).
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qed_step32.cuh"
+
+namespace qed {
+
+constexpr int kSpecies = 3;  // electrons, positrons, photons
+
+struct InstDev {
+    FieldP<float> F;
+    double phase;
+    uint64_t seed;
+    PartDev sp[kSpecies];
+    int64_t* holes;  // photon compaction scratch of this instance
+    int64_t* live;
+    uint8_t* mark;
+    int64_t* hdr;  // [0] n, [1] D, [2] holes found, [3] live found
+};
+
+struct SegDev {
+    const float4 *q0, *q1, *q2;
+    int64_t n;  // particles processed this step
+};
+
+struct ClockDev {
+    uint64_t step, step0;
+    double t0, dt;
+    unsigned long long psteps;
+    unsigned long long species_steps[kSpecies];
+    long long alive[kSpecies];
+};
+
+struct BatchP {
+    uint32_t flags;
+    float dt_f;
+    double store_min, chi_floor;
+};
+
+// ------------------------------------------------------------------------------------------------
+// plan: one block of kPlanThreads threads, each owning up to 3 consecutive segments
+// ------------------------------------------------------------------------------------------------
+constexpr int kPlanThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev* __restrict__ inst, int n_inst, SegDev* seg,
+                                                                 int64_t* tile0, ClockDev* clk) {
+    __shared__ long long wsum[32];
+    __shared__ unsigned long long tot[kSpecies];
+    const int n_seg = kSpecies * n_inst;
+    const int per = (n_seg + kPlanThreads - 1) / kPlanThreads;  // <= 3
+    const int s0 = threadIdx.x * per;
+    if (threadIdx.x < kSpecies) tot[threadIdx.x] = 0;
+    __syncthreads();
+    long long loc[3] = {0, 0, 0}, mine = 0;
+    for (int k = 0; k < per; ++k) {
+        const int s = s0 + k;
+        if (s >= n_seg) break;
+        const int sp = s / n_inst, i = s - sp * n_inst;
+        const PartDev& P = inst[i].sp[sp];
+        const int64_t c = *P.count;
+        const int64_t n = c < 0 ? 0 : (c > P.capacity ? P.capacity : c);
+        if (c != n) *P.count = n;  // reservations that did not fit
+        seg[s] = SegDev{P.q0, P.q1, P.q2, n};
+        loc[k] = (n + 31) / 32;
+        mine += loc[k];
+        atomicAdd(&tot[sp], (unsigned long long)n);
+    }
+    // block-wide exclusive scan of the per-thread tile counts
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long v = wsum[lane], x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        wsum[lane] = x - v;  // exclusive prefix of the warp totals
+        if (lane == 31) tile0[n_seg] = x;
+    }
+    __syncthreads();
+    long long ex = wsum[wid] + incl - mine;
+    for (int k = 0; k < per; ++k) {
+        const int s = s0 + k;
+        if (s >= n_seg) break;
+        tile0[s] = ex;
+        ex += loc[k];
+    }
+    if (threadIdx.x == 0) {
+        clk->psteps += tot[0] + tot[1] + tot[2];
+        for (int k = 0; k < kSpecies; ++k) {
+            clk->species_steps[k] += tot[k];
+            clk->alive[k] = (long long)tot[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// the persistent step kernel
+// ------------------------------------------------------------------------------------------------
+__host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
+    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4);
+    off += align128((size_t)(n_seg + 1) * 8);
+    off += align128((size_t)warps * sizeof(Ctx));
+    off += (size_t)warps * stages * sizeof(Tile);
+    off += (size_t)warps * stages * 8;
+    off += (size_t)warps * kWQ * 8;
+    return off;
+}
+
+// this warp's walk over the tile list: its i-th tile is tile_of(i)
+template <int STAGES>
+struct BatchStream {
+    Tile* tile;
+    uint64_t* bar;
+    const int64_t* tile0;  // shared memory: first tile of each segment, tile0[n_seg] = total
+    const SegDev* seg;
+    int n_seg;
+    int64_t total, wg, W;
+    int chunk;
+
+    __device__ __forceinline__ int64_t tile_of(int64_t i) const {
+        const int64_t k = i / chunk;
+        return (wg + k * W) * chunk + (i - k * chunk);
+    }
+    // the segment holding tile t (t < total): the last s with tile0[s] <= t
+    __device__ __forceinline__ int find(int64_t t) const {
+        int lo = 0, hi = n_seg;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tile0[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        return lo;
+    }
+    // lane 0: start the copies of this warp's i-th tile into stage i % STAGES
+    __device__ __forceinline__ void issue(int64_t i) const {
+        const int64_t t = tile_of(i);
+        if (t >= total) return;
+        const int s = find(t);
+        const SegDev g = seg[s];
+        const int64_t b = (t - tile0[s]) * 32;
+        const int st = (int)(i % STAGES);
+        const uint32_t bytes = (uint32_t)(min((int64_t)32, g.n - b) * 16);
+        mbar_expect_tx(&bar[st], 3 * bytes);
+        bulk_g2s(tile[st].q0, g.q0 + b, bytes, &bar[st]);
+        bulk_g2s(tile[st].q1, g.q1 + b, bytes, &bar[st]);
+        bulk_g2s(tile[st].q2, g.q2 + b, bytes, &bar[st]);
+    }
+};
+
+template <int WARPS, int STAGES, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+    batch_step_kernel(TabP<float> T, const float* __restrict__ bes_g, const InstDev* __restrict__ inst,
+                      const SegDev* __restrict__ seg, const int64_t* __restrict__ tile0_g, int n_inst,
+                      const ClockDev* __restrict__ clk, BatchP P, int chunk, qed_counters* ctr) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n_seg = kSpecies * n_inst;
+    Shared32 sh;
+    sh.bes = (float*)smem;
+    sh.rates = sh.bes + 3 * kBesN;
+    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * T.n_chi * 4);
+    int64_t* s_tile0 = (int64_t*)(smem + off);
+    off += align128((size_t)(n_seg + 1) * 8);
+    Ctx* s_ctx = (Ctx*)(smem + off);
+    off += align128((size_t)WARPS * sizeof(Ctx));
+    sh.tiles = (Tile*)(smem + off);
+    off += (size_t)WARPS * STAGES * sizeof(Tile);
+    sh.bars = (uint64_t*)(smem + off);
+    off += (size_t)WARPS * STAGES * 8;
+    sh.queue = (int64_t*)(smem + off);
+
+    load_tables32(sh, bes_g, T);
+    for (int i = threadIdx.x; i <= n_seg; i += blockDim.x) s_tile0[i] = tile0_g[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    BatchStream<STAGES> ts;
+    ts.tile = sh.tiles + warp * STAGES;
+    ts.bar = sh.bars + warp * STAGES;
+    ts.tile0 = s_tile0;
+    ts.seg = seg;
+    ts.n_seg = n_seg;
+    ts.wg = (int64_t)blockIdx.x * WARPS + warp;
+    ts.W = (int64_t)gridDim.x * WARPS;
+    ts.chunk = chunk;
+    int64_t* wq = sh.queue + warp * kWQ;
+    Ctx& C = s_ctx[warp];
+    if (lane == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&ts.bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // tables, tile list and barriers ready
+    ts.total = s_tile0[n_seg];
+    const uint64_t step = clk->step;
+    // time of this step: a product then a sum, each rounded (no contraction)
+    const double t_now = __dadd_rn(clk->t0, __dmul_rn((double)(step - clk->step0), clk->dt));
+    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    if (lane == 0)
+        for (int s = 0; s < STAGES; ++s) ts.issue(s);
+    int qn = 0;     // queued event indices of the current segment (warp-uniform)
+    int cur = -1;   // current segment
+    int sp = 0, ii = 0;
+    int64_t i = 0;
+    bool timed_out = false;
+    for (;; ++i) {
+        const int64_t t = ts.tile_of(i);
+        if (t >= ts.total) break;
+        const int st = (int)(i % STAGES);
+        if (!mbar_wait(&ts.bar[st], (uint32_t)((i / STAGES) & 1))) {
+            timed_out = true;
+            break;
+        }
+        const int s = ts.find(t);
+        if (s != cur) {
+            if (qn > 0) {  // the queue holds indices of the previous segment: drain it first
+                const InstDev& I = inst[ii];
+                if (sp == 2) photon_events(C, sh, wq, qn, I.sp[2], I.sp[0], I.sp[1], ctr, c);
+                else lepton_events(C, sh, wq, qn, I.sp[sp], I.sp[2], ctr, c);
+                qn = 0;
+            }
+            cur = s;
+            sp = s / n_inst;
+            ii = s - sp * n_inst;
+            __syncwarp();
+            if (lane == 0) {
+                const InstDev& I = inst[ii];
+                C.T = T;
+                C.T.nlc_rate = sh.rates;
+                C.T.nbw_rate = sh.rates + 2 * T.n_chi;
+                C.bes = sh.bes;
+                C.F = I.F;
+                C.q = sp == 0 ? -1.0f : (sp == 1 ? 1.0f : 0.0f);
+                StepP S;
+                S.dt = clk->dt;
+                S.ph_hi = __dadd_rn(t_now, I.phase);
+                S.ph_hi_f = (float)S.ph_hi;
+                S.ph_lo_f = (float)(S.ph_hi - (double)S.ph_hi_f);
+                S.dt_f = P.dt_f;
+                S.flags = P.flags;
+                S.step = step;
+                S.seed = I.seed;
+                S.store_min = P.store_min;
+                S.chi_floor = P.chi_floor;
+                C.S = S;
+            }
+            __syncwarp();
+        }
+        const int64_t n = ts.seg[s].n;
+        const int64_t j = (t - ts.tile0[s]) * 32 + lane;
+        const bool valid = j < n;
+        float4 a = make_float4(0, 0, 0, 0), b = a, cc = a;
+        if (valid) {
+            a = ts.tile[st].q0[lane];
+            b = ts.tile[st].q1[lane];
+            cc = ts.tile[st].q2[lane];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async();  // this stage's reads happen before the next copy overwrites it
+            ts.issue(i + STAGES);
+        }
+        const InstDev& I = inst[ii];
+        bool event = false;
+        if (valid)
+            event = sp == 2 ? photon_stream_one(C, I.sp[2], j, a, b, cc, ctr, c)
+                            : lepton_stream_one(C, I.sp[sp], j, a, b, cc, ctr, c);
+        const unsigned m = __ballot_sync(0xffffffffu, event);
+        if (event) wq[qn + __popc(m & ((1u << lane) - 1u))] = j;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            if (sp == 2) photon_events(C, sh, wq + (qn - 32), 32, I.sp[2], I.sp[0], I.sp[1], ctr, c);
+            else lepton_events(C, sh, wq + (qn - 32), 32, I.sp[sp], I.sp[2], ctr, c);
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+    if (timed_out) {
+        if (lane == 0) {
+            record_error(ctr, QED_ERR_TIMEOUT, ts.tile_of(i) * 32);
+            for (int64_t u = i; u < i + STAGES && ts.tile_of(u) < ts.total; ++u)  // let the copies in flight land
+                mbar_wait(&ts.bar[u % STAGES], (uint32_t)((u / STAGES) & 1));
+        }
+        __syncwarp();
+    }
+    if (qn > 0) {
+        const InstDev& I = inst[ii];
+        if (sp == 2) photon_events(C, sh, wq, qn, I.sp[2], I.sp[0], I.sp[1], ctr, c);
+        else lepton_events(C, sh, wq, qn, I.sp[sp], I.sp[2], ctr, c);
+    }
+    flush_warp(c, ctr);
+}
+
+// ------------------------------------------------------------------------------------------------
+// photon compaction of every instance (grid.y = instance); the same hole filling as qed_compact
+// ------------------------------------------------------------------------------------------------
+constexpr int kCompactBlocks = 8;  // blocks per instance (grid-stride over the dead list)
+
+__global__ void batch_compact_head(const InstDev* __restrict__ inst, int n_inst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const InstDev& I = inst[i];
+    const PartDev& G = I.sp[2];
+    const int64_t n = max((int64_t)0, min(*G.count, G.capacity));
+    I.hdr[0] = n;
+    I.hdr[1] = max((int64_t)0, min(*G.n_dead, n));
+    I.hdr[2] = 0;
+    I.hdr[3] = 0;
+}
+
+__global__ void batch_compact_classify(const InstDev* __restrict__ inst) {
+    const InstDev& I = inst[blockIdx.y];
+    const int64_t n = I.hdr[0], D = I.hdr[1], lim = n - D;
+    const int64_t* dead = I.sp[2].dead;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < D; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = dead[k];
+        if (d < 0 || d >= n) continue;
+        if (d >= lim) I.mark[d - lim] = 1;
+        else I.holes[atomicAdd((unsigned long long*)&I.hdr[2], 1ull)] = d;
+    }
+}
+
+__global__ void batch_compact_tail(const InstDev* __restrict__ inst) {
+    const InstDev& I = inst[blockIdx.y];
+    const int64_t n = I.hdr[0], D = I.hdr[1], lim = n - D;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < D; k += (int64_t)gridDim.x * blockDim.x) {
+        if (I.mark[k]) I.mark[k] = 0;
+        else I.live[atomicAdd((unsigned long long*)&I.hdr[3], 1ull)] = lim + k;
+    }
+}
+
+__global__ void batch_compact_move(const InstDev* __restrict__ inst, ClockDev* clk) {
+    const InstDev& I = inst[blockIdx.y];
+    const PartDev& G = I.sp[2];
+    const int64_t nh = min(I.hdr[2], I.hdr[3]);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nh; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t src = I.live[k], dst = I.holes[k];
+        G.q0[dst] = G.q0[src];
+        G.q1[dst] = G.q1[src];
+        G.q2[dst] = G.q2[src];
+        G.id[dst] = G.id[src];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *G.count = I.hdr[0] - I.hdr[1];
+        *G.n_dead = 0;
+        if (blockIdx.y == 0) clk->step += 1;  // the step is complete: advance the device clock
+    }
+}
+
+}  // namespace qed
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+using namespace qed;
+
+constexpr uint32_t kBatchMagic = 0x51454442u;  // "QEDB"
+
+struct qed_batch_s;
+typedef void (*batch_launch_fn)(const qed_batch_s* b, int grid, cudaStream_t st);
+
+struct BatchVariant {
+    const void* kern;
+    int warps, stages;
+    batch_launch_fn launch;
+};
+
+struct qed_batch_s {
+    uint32_t magic;
+    int device, sms;
+    const qed_tables_s* tables;
+    int n_inst;
+    qed_batch_desc desc;
+    qed_counters* ctr;
+    InstDev* d_inst;
+    SegDev* d_seg;
+    int64_t* d_tile0;
+    ClockDev* d_clk;
+    int64_t* d_hdr;
+    unsigned char* d_ws;
+    int64_t capacity_total;
+    qed_batch_tuning tuning;
+    int grid;  // persistent grid of the current tuning
+    cudaStream_t cap_stream;
+    cudaGraphExec_t exec;
+    int exec_steps;
+    std::vector<cudaEvent_t> kev;  // caller's event pairs around the persistent kernel (may be empty)
+    long long direct_steps;        // directly launched steps (event pair index of the next one)
+};
+
+template <int WARPS, int STAGES, int MINB>
+static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
+    const qed_tables_s* t = b->tables;
+    const size_t smem = batch_smem_bytes(WARPS, STAGES, t->desc.n_chi, kSpecies * b->n_inst);
+    BatchP P;
+    P.flags = b->desc.flags;
+    P.dt_f = (float)b->desc.dt;
+    P.store_min = b->desc.photon_store_min;
+    P.chi_floor = b->desc.chi_floor;
+    batch_step_kernel<WARPS, STAGES, MINB><<<grid, WARPS * 32, smem, st>>>(
+        tab_params<float>(t), t->bes32, b->d_inst, b->d_seg, b->d_tile0, b->n_inst, b->d_clk, P, b->tuning.chunk, b->ctr);
+}
+
+static const BatchVariant kVariants[QED_BATCH_VARIANTS] = {
+    {(const void*)batch_step_kernel<8, 3, 3>, 8, 3, launch_variant<8, 3, 3>},
+    {(const void*)batch_step_kernel<8, 3, 2>, 8, 3, launch_variant<8, 3, 2>},
+    {(const void*)batch_step_kernel<4, 4, 5>, 4, 4, launch_variant<4, 4, 5>},
+    {(const void*)batch_step_kernel<16, 2, 1>, 16, 2, launch_variant<16, 2, 1>},
+};
+
+static size_t variant_smem(const qed_batch_s* b, int v) {
+    return batch_smem_bytes(kVariants[v].warps, kVariants[v].stages, b->tables->desc.n_chi, kSpecies * b->n_inst);
+}
+
+// resident blocks per SM of variant v for this batch (0 if it does not fit)
+static int variant_occupancy(const qed_batch_s* b, int v) {
+    int per_sm = 0;
+    const size_t smem = variant_smem(b, v);
+    if (cudaFuncSetAttribute(kVariants[v].kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kVariants[v].kern, kVariants[v].warps * 32, smem) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+static bool valid_batch(const qed_batch_s* b) { return b != nullptr && b->magic == kBatchMagic; }
+
+// one time step of the batch on `st`; e0 / e1 (may be null) are recorded around the persistent kernel
+// (as event-record nodes of the graph when `st` is capturing)
+static void launch_batch_step(const qed_batch_s* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                              bool capturing = false) {
+    const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b->d_inst, b->n_inst, b->d_seg, b->d_tile0, b->d_clk);
+    if (e0) cudaEventRecordWithFlags(e0, st, rec);
+    kVariants[b->tuning.variant].launch(b, b->grid, st);
+    if (e1) cudaEventRecordWithFlags(e1, st, rec);
+    batch_compact_head<<<(b->n_inst + 255) / 256, 256, 0, st>>>(b->d_inst, b->n_inst);
+    const dim3 g(kCompactBlocks, b->n_inst);
+    batch_compact_classify<<<g, 256, 0, st>>>(b->d_inst);
+    batch_compact_tail<<<g, 256, 0, st>>>(b->d_inst);
+    batch_compact_move<<<g, 256, 0, st>>>(b->d_inst, b->d_clk);
+}
+
+// the caller's event pair k (modulo their number), or none
+static void kernel_events(const qed_batch_s* b, long long k, cudaEvent_t* e0, cudaEvent_t* e1) {
+    *e0 = *e1 = nullptr;
+    const long long n = (long long)b->kev.size() / 2;
+    if (n == 0) return;
+    const long long i = k % n;
+    *e0 = b->kev[2 * i];
+    *e1 = b->kev[2 * i + 1];
+}
+
+static void drop_graph(qed_batch_s* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->exec_steps = 0;
+}
+
+static bool valid_instance(const qed_instance& in) {
+    const qed_particles* sp[3] = {&in.electrons, &in.positrons, &in.photons};
+    const int32_t charge[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
+    for (int k = 0; k < 3; ++k) {
+        if (check_particles(sp[k], k == 2) != QED_OK || sp[k]->layout != QED_FP32 || sp[k]->charge != charge[k])
+            return false;
+    }
+    return valid_field(&in.field) && in.electrons.count != in.positrons.count && in.electrons.count != in.photons.count &&
+           in.positrons.count != in.photons.count;
+}
+
+static inline size_t r16(size_t v) { return (v + 15) & ~size_t(15); }
+
+extern "C" qed_status qed_batch_set_tuning(qed_batch_t b, const qed_batch_tuning* tn) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (!tn || tn->variant < 0 || tn->variant >= QED_BATCH_VARIANTS || tn->blocks_per_sm < 0 || tn->chunk < 1 ||
+        tn->chunk > (1 << 20) || tn->graph_steps < 0 || tn->graph_steps > 4096)
+        return QED_ERR_ARG;
+    const int occ = variant_occupancy(b, tn->variant);
+    if (occ < 1) return QED_ERR_ARG;  // this variant does not fit this batch (shared memory)
+    const int bps = tn->blocks_per_sm == 0 ? occ : std::min(tn->blocks_per_sm, occ);
+    drop_graph(b);
+    b->tuning = *tn;
+    b->tuning.blocks_per_sm = bps;
+    b->grid = b->sms * bps;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_batch_get_tuning(qed_batch_t b, qed_batch_tuning* out) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (!out) return QED_ERR_ARG;
+    *out = b->tuning;
+    return QED_OK;
+}
+
+extern "C" void qed_batch_destroy(qed_batch_t b) {
+    if (!valid_batch(b)) return;
+    drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_seg);
+    cudaFree(b->d_tile0);
+    cudaFree(b->d_clk);
+    cudaFree(b->d_hdr);
+    cudaFree(b->d_ws);
+    b->magic = 0;
+    delete b;
+}
+
+extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* instances, int32_t n_inst,
+                                       const qed_batch_desc* desc, qed_counters* counters_dev, qed_batch_t* out) {
+    if (!out) return QED_ERR_ARG;
+    *out = nullptr;
+    if (!valid_tables(t)) return QED_ERR_STATE;
+    if (!instances || n_inst < 1 || n_inst > QED_BATCH_MAX_INSTANCES || !desc || !counters_dev) return QED_ERR_ARG;
+    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER;
+    if (!(desc->dt > 0.0) || !std::isfinite(desc->dt) || !std::isfinite(desc->t0) || (desc->flags & ~known) != 0 ||
+        !(desc->photon_store_min >= 0.0) || !(desc->chi_floor >= 0.0))
+        return QED_ERR_ARG;
+    for (int i = 0; i < n_inst; ++i)
+        if (!valid_instance(instances[i])) return QED_ERR_ARG;
+
+    qed_batch_s* b = new qed_batch_s();
+    b->magic = kBatchMagic;
+    b->tables = t;
+    b->n_inst = n_inst;
+    b->desc = *desc;
+    b->ctr = counters_dev;
+    bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
+              cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess;
+    // compaction scratch: per instance holes and live lists (8 B per photon of capacity each) and marks
+    size_t ws = 0;
+    std::vector<size_t> ws_off(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        ws_off[i] = ws;
+        const size_t cap = (size_t)instances[i].photons.capacity;
+        ws += 2 * r16(8 * cap) + r16(cap);
+        b->capacity_total += instances[i].electrons.capacity + instances[i].positrons.capacity + instances[i].photons.capacity;
+    }
+    const int n_seg = kSpecies * n_inst;
+    ok = ok && cudaMalloc(&b->d_inst, sizeof(InstDev) * n_inst) == cudaSuccess &&
+         cudaMalloc(&b->d_seg, sizeof(SegDev) * n_seg) == cudaSuccess &&
+         cudaMalloc(&b->d_tile0, sizeof(int64_t) * (n_seg + 1)) == cudaSuccess &&
+         cudaMalloc(&b->d_clk, sizeof(ClockDev)) == cudaSuccess &&
+         cudaMalloc(&b->d_hdr, sizeof(int64_t) * 4 * n_inst) == cudaSuccess &&
+         cudaMalloc(&b->d_ws, ws < 16 ? 16 : ws) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        qed_batch_destroy(b);
+        return QED_ERR_NOMEM;
+    }
+    std::vector<InstDev> h(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        const qed_instance& in = instances[i];
+        InstDev& d = h[i];
+        d.F = field_params<float>(in.field);
+        d.phase = in.field.phase;
+        d.seed = in.seed;
+        d.sp[0] = part_dev(&in.electrons);
+        d.sp[1] = part_dev(&in.positrons);
+        d.sp[2] = part_dev(&in.photons);
+        const size_t cap = (size_t)in.photons.capacity;
+        unsigned char* base = b->d_ws + ws_off[i];
+        d.holes = (int64_t*)base;
+        d.live = (int64_t*)(base + r16(8 * cap));
+        d.mark = base + 2 * r16(8 * cap);
+        d.hdr = b->d_hdr + 4 * i;
+    }
+    ClockDev clk{};
+    clk.step = desc->step0;
+    clk.step0 = desc->step0;
+    clk.t0 = desc->t0;
+    clk.dt = desc->dt;
+    ok = cudaMemcpy(b->d_inst, h.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_clk, &clk, sizeof(ClockDev), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(b->d_ws, 0, ws < 16 ? 16 : ws) == cudaSuccess &&
+         cudaMemset(b->d_hdr, 0, sizeof(int64_t) * 4 * n_inst) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        qed_batch_destroy(b);
+        return QED_ERR_CUDA;
+    }
+    const qed_batch_tuning def{0, 0, 4, 8};
+    if (qed_batch_set_tuning(b, &def) != QED_OK) {
+        qed_batch_destroy(b);
+        return QED_ERR_CUDA;
+    }
+    *out = b;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_batch_step(qed_batch_t b, int32_t n_steps, void* stream) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (n_steps < 0) return QED_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int done = 0;
+    const int G = b->tuning.graph_steps;
+    if (G > 0 && (n_steps >= G || n_steps == 0)) {
+        if (!b->exec) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QED_ERR_CUDA;
+            for (int k = 0; k < G; ++k) {
+                cudaEvent_t e0, e1;
+                kernel_events(b, k, &e0, &e1);
+                launch_batch_step(b, b->cap_stream, e0, e1, true);
+            }
+            const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+            if (e != cudaSuccess || !g) {
+                cudaGetLastError();
+                return QED_ERR_CUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                b->exec = nullptr;
+                cudaGetLastError();
+                return QED_ERR_CUDA;
+            }
+            b->exec_steps = G;
+        }
+        for (; done + G <= n_steps; done += G)
+            if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return QED_ERR_CUDA;
+    }
+    for (; done < n_steps; ++done) {
+        cudaEvent_t e0, e1;
+        kernel_events(b, b->direct_steps++, &e0, &e1);
+        launch_batch_step(b, st, e0, e1);
+    }
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_batch_set_kernel_events(qed_batch_t b, void* const* events, int32_t n_pairs) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (n_pairs < 0 || n_pairs > (1 << 20) || (n_pairs > 0 && !events)) return QED_ERR_ARG;
+    for (int32_t i = 0; i < 2 * n_pairs; ++i)
+        if (!events[i]) return QED_ERR_ARG;
+    drop_graph(b);
+    b->kev.assign((cudaEvent_t*)events, (cudaEvent_t*)events + 2 * n_pairs);
+    b->direct_steps = 0;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_batch_stats_read(qed_batch_t b, qed_batch_stats* out, void* stream) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (!out) return QED_ERR_ARG;
+    ClockDev c;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&c, b->d_clk, sizeof(ClockDev), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QED_ERR_CUDA;
+    out->step = c.step;
+    out->particle_steps = c.psteps;
+    for (int k = 0; k < kSpecies; ++k) {
+        out->species_steps[k] = c.species_steps[k];
+        out->alive[k] = c.alive[k];
+    }
+    return QED_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------------------------
+static std::string tune_key(const qed_batch_s* b) {
+    cudaDeviceProp p;
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&p, b->device) == cudaSuccess) name = p.name;
+    for (char& ch : name)
+        if (ch == ' ' || ch == '"' || ch == '\\') ch = '_';
+    int lg = 0;
+    while (lg < 62 && (1ll << (lg + 1)) <= b->capacity_total) ++lg;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|sm%d|inst%d|cap2^%d|nchi%d", name.c_str(), b->sms, b->n_inst, lg, b->tables->desc.n_chi);
+    return buf;
+}
+
+static bool json_int(const char* line, const char* field, int* v) {
+    char pat[64];
+    snprintf(pat, sizeof pat, "\"%s\": ", field);
+    const char* p = strstr(line, pat);
+    return p && sscanf(p + strlen(pat), "%d", v) == 1;
+}
+
+static bool cache_lookup(const char* path, const std::string& key, qed_batch_tuning* tn) {
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    const std::string pat = "\"key\": \"" + key + "\"";
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        if (!strstr(line, pat.c_str())) continue;
+        int v, bps, ch;
+        if (json_int(line, "variant", &v) && json_int(line, "blocks_per_sm", &bps) && json_int(line, "chunk", &ch)) {
+            tn->variant = v;
+            tn->blocks_per_sm = bps;
+            tn->chunk = ch;
+            found = true;  // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+extern "C" qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate, const char* cache_path,
+                                     qed_batch_tuning* out, void* stream) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (steps_per_candidate < 1 || steps_per_candidate > 1000) return QED_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int graph_steps = b->tuning.graph_steps;
+    const std::string key = tune_key(b);
+    qed_batch_tuning best = b->tuning;
+    if (cache_path && cache_lookup(cache_path, key, &best)) {
+        best.graph_steps = graph_steps;
+        const qed_status s = qed_batch_set_tuning(b, &best);
+        if (s == QED_OK) {
+            if (out) *out = b->tuning;
+            return QED_OK;
+        }
+    }
+    // candidates: every variant that fits, at its occupancy maximum and one block fewer, three chunk sizes
+    std::vector<qed_batch_tuning> cand;
+    for (int v = 0; v < QED_BATCH_VARIANTS; ++v) {
+        const int occ = variant_occupancy(b, v);
+        for (int bps = occ; bps >= 1 && bps >= occ - 1; --bps)
+            for (int ch : {1, 4, 16}) cand.push_back(qed_batch_tuning{v, bps, ch, 0});
+    }
+    if (cand.empty()) return QED_ERR_CUDA;
+    std::vector<double> score(cand.size(), 1e300);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QED_ERR_CUDA;
+    qed_status status = QED_OK;
+    for (int pass = 0; pass < 2 && status == QED_OK; ++pass) {
+        for (size_t c = 0; c < cand.size() && status == QED_OK; ++c) {
+            const size_t k = pass == 0 ? c : cand.size() - 1 - c;  // second pass in reverse: drift cancels
+            if (qed_batch_set_tuning(b, &cand[k]) != QED_OK) continue;
+            qed_batch_stats s0, s1;
+            if (qed_batch_stats_read(b, &s0, stream) != QED_OK) {
+                status = QED_ERR_CUDA;
+                break;
+            }
+            double ms = 0.0;
+            for (int r = 0; r < steps_per_candidate; ++r) {
+                launch_batch_step(b, st, e0, e1);
+                float x = 0.0f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&x, e0, e1) != cudaSuccess) {
+                    status = QED_ERR_CUDA;
+                    break;
+                }
+                ms += x;
+            }
+            if (status != QED_OK || qed_batch_stats_read(b, &s1, stream) != QED_OK) {
+                status = QED_ERR_CUDA;
+                break;
+            }
+            const double ps = (double)(s1.particle_steps - s0.particle_steps);
+            if (ps > 0) score[k] = std::min(score[k], ms * 1e6 / ps);  // ns per particle-step
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != QED_OK) return status;
+    size_t bi = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+        if (score[c] < score[bi]) bi = c;
+    best = cand[bi];
+    best.graph_steps = graph_steps;
+    const qed_status s = qed_batch_set_tuning(b, &best);
+    if (s != QED_OK) return s;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"blocks_per_sm\": %d, \"chunk\": %d, \"ns_per_particle_step\": %.6g}\n",
+                    key.c_str(), best.variant, best.blocks_per_sm, best.chunk, score[bi]);
+            fclose(f);
+        }
+    }
+    if (out) *out = b->tuning;
+    return QED_OK;
+}

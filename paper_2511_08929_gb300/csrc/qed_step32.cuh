@@ -1,0 +1,594 @@
+// qed_step32.cuh -- the per-particle arithmetic of the FP32 fast path, shared by the single-buffer step
+// kernels (qed_step32.cu) and the batched persistent kernel (qed_batch.cu).
+//
+// Arithmetic split (Sec. 4.1, 4.2, 5): the Boris and T-BMT pushers, chi, the basis, the rate lookups and
+// all event sampling in FP32; the optical depth is accumulated in FP64 and the excess |s|^2 - 1 of a
+// spin / Stokes vector that leaves the unit ball is computed in FP64.  Particles are three float4 planes
+// q0 = (x, y, z, p_x), q1 = (p_y, p_z, s_x, s_y), q2 = (s_z, w, tau_lo, tau_hi).
+#pragma once
+#include "qed_bessel.cuh"
+#include "qed_internal.h"
+#include "qed_steps.h"
+
+namespace qed {
+
+using F3 = V3<float>;
+constexpr int kT32 = 256;  // threads per block
+constexpr int kWarps32 = kT32 / 32;
+constexpr int kStages = 3;  // tiles in flight per warp
+constexpr int kWQ = 64;     // queued event indices per warp (drained 32 at a time)
+constexpr long long kWaitLimit = 1ll << 24;  // bounded mbarrier polling (~0.1 s) before reporting a timeout
+
+struct Tile {  // one tile of 32 particles in shared memory
+    float4 q0[32], q1[32], q2[32];
+};
+
+// ------------------------------------------------------------------------------------------------
+// bulk copies and mbarriers (PTX)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of `parity` to complete (false: gave up)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------------
+// numeric helpers
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double tau_join(float lo, float hi) { return __hiloint2double(__float_as_int(hi), __float_as_int(lo)); }
+__device__ __forceinline__ void tau_split(double t, float& lo, float& hi) {
+    lo = __int_as_float(__double2loint(t));
+    hi = __int_as_float(__double2hiint(t));
+}
+
+// FP32 uniforms from the Philox words.  The method's uniform is u = (m + 1/2) 2^-52 with the 52-bit
+// m = (hi >> 12) 2^32 + lo (exactly as in the FP64 path); here it is rounded to float with two 32-bit
+// integer conversions, and 1 - u is formed from the complementary integer 2^52 - 1 - m, so neither
+// end of (0, 1) loses precision.
+__device__ __forceinline__ float u52f_parts(uint32_t h20, uint32_t lo) {
+    return fmaf((float)h20, 0x1.0p-20f, ((float)lo + 0.5f) * 0x1.0p-52f);
+}
+__device__ __forceinline__ float u52f(uint32_t hi, uint32_t lo) { return u52f_parts(hi >> 12, lo); }
+__device__ __forceinline__ float u52f_comp(uint32_t hi, uint32_t lo) { return u52f_parts(0xFFFFFu - (hi >> 12), ~lo); }
+
+// logit ln(u) - ln(1 - u) of the uniform (full-accuracy logf: it is the ICDF coordinate)
+__device__ __forceinline__ float logit52(uint32_t hi, uint32_t lo) { return logf(u52f(hi, lo)) - logf(u52f_comp(hi, lo)); }
+
+// exponential draw -ln(u) (an optical depth), sampled in FP32 and widened to the FP64 accumulator
+__device__ __forceinline__ double exp_draw(uint32_t hi, uint32_t lo) {
+    const float u = u52f(hi, lo);
+    return (double)(u < 0.5f ? -logf(u) : -log1pf(-u52f_comp(hi, lo)));
+}
+
+__device__ __forceinline__ double birth_tau32(uint64_t id, uint64_t seed) {
+    const uint4 w = draw(id, seed, kStepBirth, kSlotTauBranch);
+    return exp_draw(w.x, w.y);
+}
+
+// Rescale a vector that left the unit ball.  Its excess d = |s|^2 - 1 is computed in FP64 (the
+// products of floats are exact in double, so d is exact to 1e-16); the factor (1 + d)^{-1/2} =
+// 1 - d/2 + 3 d^2/8 (relative error 5 d^3/16 < 1e-11 for d < 2^-10) is then applied in FP32, whose
+// rounding is the precision of the stored state.  Larger excursions take the FP32 reciprocal root.
+__device__ __forceinline__ F3 renorm64(const F3& s) {
+    const double x = s.x, y = s.y, z = s.z;
+    const double d = fma(x, x, fma(y, y, fma(z, z, -1.0)));
+    const float df = (float)d;
+    float f;
+    if (df < 0x1.0p-10f) {
+        f = fmaf(df, fmaf(0.375f, df, -0.5f), 1.0f);
+    } else {
+        const float n2 = 1.0f + df;
+        f = rsqrtf(n2);
+        f = f * (1.5f - 0.5f * n2 * f * f);
+    }
+    return F3{s.x * f, s.y * f, s.z * f};
+}
+
+// optical depth decision tau <= 0 as an integer test on the FP64 bit pattern (+0 and every value
+// with the sign bit set compare <= 0 as signed 64-bit integers)
+__device__ __forceinline__ bool tau_spent(double t) { return __double_as_longlong(t) <= 0ll; }
+
+__device__ __forceinline__ bool finite4(const float4& v) { return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w); }
+
+// ------------------------------------------------------------------------------------------------
+// shared memory
+// ------------------------------------------------------------------------------------------------
+struct Shared32 {
+    float* bes;      // [3][kBesN]
+    float* rates;    // nlc [2][n_chi] then nbw [2][n_chi]
+    Tile* tiles;     // [warps][kStages]
+    uint64_t* bars;  // [warps][kStages]
+    int64_t* queue;  // [warps][kWQ]
+};
+
+__host__ __device__ inline size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
+
+__host__ __device__ inline size_t smem32_bytes(int n_chi) {
+    return align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4) + (size_t)kWarps32 * kStages * sizeof(Tile) +
+           (size_t)kWarps32 * kStages * 8 + (size_t)kWarps32 * kWQ * 8;
+}
+
+__device__ __forceinline__ Shared32 carve32(unsigned char* smem, int n_chi) {
+    Shared32 s;
+    s.bes = (float*)smem;
+    s.rates = s.bes + 3 * kBesN;
+    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4);
+    s.tiles = (Tile*)(smem + off);
+    off += (size_t)kWarps32 * kStages * sizeof(Tile);
+    s.bars = (uint64_t*)(smem + off);
+    off += (size_t)kWarps32 * kStages * 8;
+    s.queue = (int64_t*)(smem + off);
+    return s;
+}
+
+__device__ __forceinline__ void load_tables32(const Shared32& sh, const float* __restrict__ bes_g, const TabP<float>& T) {
+    for (int i = threadIdx.x; i < 3 * kBesN; i += blockDim.x) sh.bes[i] = bes_g[i];
+    for (int i = threadIdx.x; i < 2 * T.n_chi; i += blockDim.x) {
+        sh.rates[i] = T.nlc_rate[i];
+        sh.rates[2 * T.n_chi + i] = T.nbw_rate[i];
+    }
+}
+
+enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_N };
+
+// per-warp counter flush (no block barrier: warps finish at different times)
+__device__ __forceinline__ void flush_warp(unsigned long long (&c)[C_N], qed_counters* ctr) {
+#pragma unroll
+    for (int i = 0; i < C_N; ++i) {
+        const unsigned long long v = warp_sum(c[i]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&ctr->events + i, v);
+    }
+}
+
+// The warp's tile stream: tile t of this warp covers particles [32 g_t, 32 g_t + 32), g_t = g_0 + t G.
+struct TileStream {
+    Tile* tile;      // this warp's kStages tiles
+    uint64_t* bar;   // this warp's kStages mbarriers
+    const float4 *q0, *q1, *q2;
+    int64_t n, g0, G;
+
+    __device__ __forceinline__ int64_t base(int64_t t) const { return (g0 + t * G) * 32; }
+    // lane 0: start the copies of tile t into stage t % kStages
+    __device__ __forceinline__ void issue(int64_t t) const {
+        const int64_t b = base(t);
+        if (b >= n) return;
+        const int s = (int)(t % kStages);
+        const uint32_t bytes = (uint32_t)(min((int64_t)32, n - b) * 16);
+        mbar_expect_tx(&bar[s], 3 * bytes);
+        bulk_g2s(tile[s].q0, q0 + b, bytes, &bar[s]);
+        bulk_g2s(tile[s].q1, q1 + b, bytes, &bar[s]);
+        bulk_g2s(tile[s].q2, q2 + b, bytes, &bar[s]);
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
+// lepton step
+// ------------------------------------------------------------------------------------------------
+struct Ctx {
+    TabP<float> T;  // rates point to shared memory, ICDFs to global
+    const float* bes;
+    FieldP<float> F;
+    StepP S;
+    float q;
+};
+
+// state after the classical part of the step, shared by the streaming pass and the event pass
+struct LState {
+    F3 x, p, s, E, B;
+    float gam, w;
+    bool qed;
+    float chi, lnchi, Wu, Wd, sb, Ws, Wdn;
+    F3 khat, eps, beta;
+};
+
+// fields at x_old, Boris push, T-BMT precession, move, chi, basis and rates
+__device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, LState& st,
+                                                 unsigned long long* c) {
+    const uint32_t fl = C.S.flags;
+    const float dt = C.S.dt_f;
+    const F3 xold{a.x, a.y, a.z};
+    st.p = F3{a.w, b.x, b.y};
+    st.s = F3{b.z, b.w, cc.x};
+    st.w = cc.y;
+    field_eval(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
+    const F3 pold = st.p;
+    if (fl & QED_F_PUSH) st.p = boris(st.p, st.E, st.B, C.q, dt);
+    if (fl & QED_F_TBMT) {
+        const F3 pb = 0.5f * (pold + st.p);
+        st.s = rotate(st.s, tbmt_omega(pb, st.E, st.B, C.q, (fl & QED_F_TBMT_PAPER) != 0), dt);
+    }
+    st.gam = sqrtf(1.0f + dot(st.p, st.p));
+    st.x = xold;
+    if (fl & QED_F_MOVE) {
+        const float ig = dt / st.gam;
+        st.x = F3{xold.x + st.p.x * ig, xold.y + st.p.y * ig, xold.z + st.p.z * ig};
+    }
+    st.qed = false;
+    if (!(fl & QED_F_EMIT)) return;
+    st.chi = chi_of(C.F.eta0, st.gam, st.p, st.E, st.B);
+    const float pn2 = dot(st.p, st.p);
+    if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < (float)C.S.chi_floor) return;
+    st.khat = rsqrtf(pn2) * st.p;
+    const F3 v = (1.0f / st.gam) * st.p;
+    if (!make_basis(st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
+    st.qed = true;
+    st.lnchi = __logf(st.chi);
+    if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
+    nlc_rates(C.T, st.chi, st.lnchi, st.Wu, st.Wd);
+    const float pref = (float)(kAlpha / (kSqrt3 * kPi)) / (C.F.eta0 * st.gam);
+    st.Wu *= pref;
+    st.Wd *= pref;
+    st.sb = (fl & QED_F_RESOLVED) ? dot(st.s, st.beta) : 0.0f;
+    st.Wdn = st.Wd * (1.0f - st.sb) * 0.5f;
+    st.Ws = st.Wu * (1.0f + st.sb) * 0.5f + st.Wdn;
+}
+
+__device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x, const F3& p, const F3& s, float w, double tau) {
+    float lo, hi;
+    tau_split(tau, lo, hi);
+    L.q0[j] = make_float4(x.x, x.y, x.z, p.x);
+    L.q1[j] = make_float4(p.y, p.z, s.x, s.y);
+    L.q2[j] = make_float4(s.z, w, lo, hi);
+}
+
+// the event pass of one warp: lane l takes the particle index q[l] if l < cnt (all 32 lanes call it)
+static __device__ void lepton_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& L, const PartDev& G,
+                              qed_counters* ctr, unsigned long long* c) {
+    const uint32_t fl = C.S.flags;
+    const int e = threadIdx.x & 31;
+    bool want = false;
+    F3 gx{0, 0, 0}, gk{0, 0, 0}, gP{0, 0, 0};
+    float gw = 0.0f;
+    uint64_t gid = 0;
+    int64_t j = -1;
+    if (e < cnt) {
+        j = q[e];
+        const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
+        LState st;
+        lepton_classical(C, a, b, cc, st, nullptr);  // the streaming pass's arithmetic, repeated
+        const uint64_t id = L.id[j];
+        F3 pf = st.p, sf = st.s;
+        double tauf = tau_join(cc.z, cc.w);
+        const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
+        bool down;
+        if (fl & QED_F_TAU) down = u52f(w0.z, w0.w) * st.Ws < st.Wdn;
+        else down = u52f(w0.x, w0.y) < st.Wdn * C.S.dt_f;
+        const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
+        const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
+        const float r3 = u52f(w1.z, w1.w), r4 = u52f(w2.x, w2.y);
+        const float y = logit52(w1.x, w1.y);
+        // the sampled value to full FP32 accuracy: accurate logarithm of chi and exponential
+        const float up = expf(icdf_lookup(C.T, false, down ? 1 : 0, logf(st.chi), y));
+        const float den = 2.0f + 3.0f * st.chi * up;
+        const float lam = 3.0f * st.chi * up / den, one_m = 2.0f / den;
+        const F3 k = lam * st.p;
+        if (fl & QED_F_RECOIL) pf = one_m * st.p;
+        float bb[3];
+        bessel32(sh.bes, up, bb);
+        const bool resolved = (fl & QED_F_RESOLVED) != 0;
+        const F3 si = resolved ? st.s : F3{0, 0, 0};
+        F3 sfu{0, 0, 0};
+        float xi[3] = {0.0f, 0.0f, 0.0f};
+        float wv = 0.0f;
+        F3 g{0, 0, 0};
+        if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, bb, si, st.beta, st.khat, wv, g);
+        if (fl & QED_F_SPIN_EVENT) {
+            const float gn = sqrtf(dot(g, g));
+            if (fl & QED_F_SPIN_COLLAPSE) {
+                const float sg = r3 < (wv - gn) / (2.0f * wv) ? -1.0f : 1.0f;
+                sf = gn > 0.0f ? (sg / gn) * g : F3{0, 0, 0};
+            } else {
+                sf = (1.0f / wv) * g;
+            }
+            sfu = sf;
+        }
+        if (fl & QED_F_POL_EVENT) {
+            float Fv[4];
+            nlc_stokes(lam, one_m, bb, si, sfu, wv, g, st.eps, st.beta, st.khat, Fv);
+            const float Fn = sqrtf(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
+            if (fl & QED_F_POL_COLLAPSE) {
+                const float sg = r4 < (Fv[0] - Fn) / (2.0f * Fv[0]) ? -1.0f : 1.0f;
+                for (int i = 0; i < 3; ++i) xi[i] = Fn > 0.0f ? sg * Fv[i + 1] / Fn : 0.0f;
+            } else {
+                for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] / Fv[0];
+            }
+        }
+        if (fl & QED_F_TAU) tauf = exp_draw(w0.x, w0.y);
+        c[C_EVENTS]++;
+        if (sqrtf(dot(k, k)) >= (float)C.S.store_min) {
+            const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
+            want = true;
+            gx = st.x;
+            gk = k;
+            gP = stokes_to_P(xi, st.eps, st.beta, st.khat);
+            gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
+            gw = st.w;
+        } else {
+            c[C_BELOW]++;
+        }
+        store32(L, j, st.x, pf, sf, st.w, tauf);
+    }
+    if (G.count != nullptr) {
+        const long long slot = reserve_slots(G.count, want, 1);
+        if (want) {
+            if (slot < G.capacity) {
+                store32(G, slot, gx, gk, gP, gw, birth_tau32(gid, C.S.seed));
+                G.id[slot] = gid;
+                c[C_STORED]++;
+            } else {
+                c[C_DROPPED]++;
+                record_error(ctr, QED_ERR_CAPACITY, j);
+            }
+        }
+    } else if (want) {
+        c[C_DROPPED]++;
+    }
+}
+
+// the streaming pass of one particle (no event): non-emission update and store; returns true if the
+// particle's optical depth ran out (it is then left untouched for the event pass)
+__device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L, int64_t j, const float4& a, const float4& b,
+                                                  const float4& cc, qed_counters* ctr, unsigned long long* c) {
+    const uint32_t fl = C.S.flags;
+    const float dt = C.S.dt_f;
+    if (!(finite4(a) && finite4(b) && isfinite(cc.x) && isfinite(cc.y))) {
+        c[C_NONFINITE]++;
+        record_error(ctr, QED_ERR_NAN, j);
+        return false;
+    }
+    LState st;
+    lepton_classical(C, a, b, cc, st, c);
+    const double tau = tau_join(cc.z, cc.w);
+    double tauf = tau;
+    if (st.qed) {
+        if (fl & QED_F_TAU) {
+            tauf = tau - (double)(st.Ws * dt);
+            if (tau_spent(tauf)) return true;
+        } else {
+            const uint4 w0 = draw(L.id[j], C.S.seed, C.S.step, kSlotTauBranch);
+            if (u52f(w0.x, w0.y) < st.Ws * dt) return true;
+        }
+    }
+    F3 sf = st.s;
+    if (st.qed && (fl & QED_F_NONTRANSITION) && (fl & QED_F_RESOLVED)) {
+        // Sec. 5: s <- [s (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . s) dt]
+        const float W0 = 0.5f * (st.Wu + st.Wd), Pi = 0.5f * (st.Wu - st.Wd);
+        const float D = 1.0f - (W0 + Pi * st.sb) * dt;
+        if (D > 0.0f) {
+            const float iD = 1.0f / D, a1 = (1.0f - W0 * dt) * iD, a2 = Pi * dt * iD;
+            sf = F3{st.s.x * a1 - st.beta.x * a2, st.s.y * a1 - st.beta.y * a2, st.s.z * a1 - st.beta.z * a2};
+            if (dot(sf, sf) > 1.0f) {
+                sf = renorm64(sf);
+                c[C_RENORM]++;
+            }
+        }
+    }
+    store32(L, j, st.x, st.p, sf, st.w, tauf);
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------------
+// photon step
+// ------------------------------------------------------------------------------------------------
+struct PState {
+    F3 x, k, P, E, B, khat, eps, beta;
+    float en, w;
+    bool qed;
+    float chi, lnchi, xi[3], Wp, Wm, Wmp, Wx;
+};
+
+__device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, PState& st,
+                                                 unsigned long long* c) {
+    const F3 xold{a.x, a.y, a.z};
+    st.k = F3{a.w, b.x, b.y};
+    st.P = F3{b.z, b.w, cc.x};
+    st.w = cc.y;
+    field_eval(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
+    const float en2 = dot(st.k, st.k);
+    st.en = sqrtf(en2);
+    st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
+    st.x = xold;
+    if (C.S.flags & QED_F_MOVE) st.x = xold + C.S.dt_f * st.khat;
+    st.qed = false;
+    if (!(C.S.flags & QED_F_EMIT) || !(en2 > 0.0f)) return;
+    st.chi = chi_of(C.F.eta0, st.en, st.k, st.E, st.B);
+    if (!(st.chi > 0.0f) || st.chi < (float)C.S.chi_floor) return;
+    if (!make_basis(st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
+    st.qed = true;
+    P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
+    if (!(C.S.flags & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
+    st.lnchi = __logf(st.chi);
+    if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
+    nbw_rates(C.T, st.chi, st.lnchi, st.Wp, st.Wm);
+    const float pref = (float)(kAlpha / (kSqrt3 * kPi)) / (C.F.eta0 * st.en);
+    st.Wp *= pref;
+    st.Wm *= pref;
+    st.Wmp = st.Wm * (1.0f - st.xi[2]) * 0.5f;
+    st.Wx = st.Wp * (1.0f + st.xi[2]) * 0.5f + st.Wmp;
+}
+
+static __device__ void photon_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& G, const PartDev& El,
+                              const PartDev& Po, qed_counters* ctr, unsigned long long* c) {
+    const uint32_t fl = C.S.flags;
+    const bool have = El.count != nullptr && Po.count != nullptr;
+    const int e = threadIdx.x & 31;
+    bool want = false;
+    F3 x{0, 0, 0}, k{0, 0, 0}, P{0, 0, 0}, pe{0, 0, 0}, pp{0, 0, 0}, se{0, 0, 0}, sp{0, 0, 0};
+    float w = 0.0f;
+    double tauf = 0.0;
+    uint64_t ide = 0, idp = 0;
+    int64_t j = -1;
+    if (e < cnt) {
+        j = q[e];
+        const float4 a = __ldcg(G.q0 + j), b = __ldcg(G.q1 + j), cc = __ldcg(G.q2 + j);
+        PState st;
+        photon_classical(C, a, b, cc, st, nullptr);
+        x = st.x;
+        k = st.k;
+        P = st.P;
+        w = st.w;
+        tauf = tau_join(cc.z, cc.w);
+        if (fl & QED_F_TAU) tauf -= (double)(st.Wx * C.S.dt_f);
+        const uint64_t id = G.id[j];
+        const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
+        bool minus;
+        if (fl & QED_F_TAU) minus = u52f(w0.z, w0.w) * st.Wx < st.Wmp;
+        else minus = u52f(w0.x, w0.y) < st.Wmp * C.S.dt_f;
+        const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
+        const float r3 = u52f(w1.z, w1.w);
+        // the folded coordinate rf = |2u - 1| = (2 dm + 1) 2^-52 from the integer bits of u, and 1 - rf
+        const uint64_t m = ((uint64_t)(w1.x >> 12) << 32) | (uint64_t)w1.y;
+        const uint64_t half = 1ull << 51;
+        const bool low = m < half;  // u < 1/2: the positron takes the smaller fraction
+        const uint64_t dm = low ? half - 1ull - m : m - half;
+        const uint64_t dmc = (half - 1ull) - dm;
+        const float rf = fmaf((float)(uint32_t)(dm >> 32), 0x1.0p-19f, ((float)(uint32_t)dm + 0.5f) * 0x1.0p-51f);
+        const float rfc = fmaf((float)(uint32_t)(dmc >> 32), 0x1.0p-19f, ((float)(uint32_t)dmc + 0.5f) * 0x1.0p-51f);
+        const float yf = logf(rf) - logf(rfc);
+        const float xv = expf(icdf_lookup(C.T, true, minus ? 1 : 0, logf(st.chi), yf));
+        const float umin = (8.0f / 3.0f) / st.chi;
+        const float ut = umin + xv;
+        // mu (1 - mu) = q = 2/(3 chi u~'), so 1 - 4q = x/u~' exactly and mu = (1 - sqrt(x/u~'))/2
+        // = u~'_min / (2 u~' (1 + sqrt(x/u~'))), free of cancellation near the centre
+        const float mu = 0.5f * (umin / ut) / (1.0f + sqrtf(xv / ut));
+        const float lam = low ? mu : 1.0f - mu;
+        const float one_m = low ? 1.0f - mu : mu;
+        float bb[3];
+        bessel32(sh.bes, ut, bb);
+        pp = lam * st.k;
+        pe = one_m * st.k;
+        if (fl & QED_F_SPIN_EVENT) {
+            float w0v;
+            F3 je, jp;
+            nbw_j(lam, one_m, bb, st.xi, st.eps, st.beta, st.khat, w0v, je, jp);
+            if (fl & QED_F_SPIN_COLLAPSE) {
+                const float jen = sqrtf(dot(je, je)), jpn = sqrtf(dot(jp, jp));
+                const F3 Se = jen > 0.0f ? (1.0f / jen) * je : F3{0, 0, 0};
+                const F3 Sp = jpn > 0.0f ? (1.0f / jpn) * jp : F3{0, 0, 0};
+                // four correlated states, order (--, -+, +-, ++), first sign = positron
+                float cum = 0.0f;
+                int chosen = 3;
+                const float i4w = 1.0f / (4.0f * w0v);
+                for (int s4 = 0; s4 < 3; ++s4) {
+                    const float sa = (s4 & 2) ? 1.0f : -1.0f, sbb = (s4 & 1) ? 1.0f : -1.0f;
+                    cum += nbw_G(lam, one_m, bb, st.xi, sa * Sp, sbb * Se, st.eps, st.beta, st.khat) * i4w;
+                    if (r3 < cum) {
+                        chosen = s4;
+                        break;
+                    }
+                }
+                const float sa = (chosen & 2) ? 1.0f : -1.0f, sbb = (chosen & 1) ? 1.0f : -1.0f;
+                sp = sa * Sp;
+                se = sbb * Se;
+            } else {
+                se = (1.0f / w0v) * je;
+                sp = (1.0f / w0v) * jp;
+            }
+        }
+        const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
+        ide = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
+        idp = (uint64_t)wc.z | ((uint64_t)wc.w << 32);
+        want = true;
+    }
+    bool ok = false;
+    if (have) {
+        const long long s_e = reserve_slots(El.count, want, 1);
+        const bool e_ok = want && s_e < El.capacity;
+        const long long s_p = reserve_slots(Po.count, e_ok, 1);
+        ok = e_ok && s_p < Po.capacity;
+        if (ok) {
+            store32(El, s_e, x, pe, se, w, birth_tau32(ide, C.S.seed));
+            El.id[s_e] = ide;
+            store32(Po, s_p, x, pp, sp, w, birth_tau32(idp, C.S.seed));
+            Po.id[s_p] = idp;
+        } else if (e_ok) {  // the positron did not fit: the reserved electron slot holds an inert particle
+            store32(El, s_e, x, F3{0, 0, 0}, F3{0, 0, 0}, 0.0f, INFINITY);
+            El.id[s_e] = ide;
+        }
+        const long long s_d = reserve_slots(G.n_dead, ok, 1);
+        if (ok && s_d < G.capacity) G.dead[s_d] = j;
+    }
+    if (want) {
+        if (ok) {
+            c[C_EVENTS]++;
+            c[C_STORED] += 2;
+            store32(G, j, x, F3{0, 0, 0}, P, 0.0f, tauf);  // converted: inert until compaction
+        } else {
+            c[C_DROPPED]++;
+            if (have) record_error(ctr, QED_ERR_CAPACITY, j);
+            store32(G, j, x, k, P, w, tauf);  // survives and retries next step
+        }
+    }
+}
+
+__device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G, int64_t j, const float4& a, const float4& b,
+                                                  const float4& cc, qed_counters* ctr, unsigned long long* c) {
+    const uint32_t fl = C.S.flags;
+    const float dt = C.S.dt_f;
+    if (!(finite4(a) && finite4(b) && isfinite(cc.x) && isfinite(cc.y))) {
+        c[C_NONFINITE]++;
+        record_error(ctr, QED_ERR_NAN, j);
+        return false;
+    }
+    PState st;
+    photon_classical(C, a, b, cc, st, c);
+    const double tau = tau_join(cc.z, cc.w);
+    double tauf = tau;
+    if (st.qed && st.Wx > 0.0f) {
+        if (fl & QED_F_TAU) {
+            tauf = tau - (double)(st.Wx * dt);
+            if (tau_spent(tauf)) return true;
+        } else {
+            const uint4 w0 = draw(G.id[j], C.S.seed, C.S.step, kSlotTauBranch);
+            if (u52f(w0.x, w0.y) < st.Wx * dt) return true;
+        }
+    }
+    F3 Pf = st.P;
+    if (st.qed && (fl & QED_F_NONTRANSITION) && (fl & QED_F_RESOLVED)) {
+        // Sec. 5 with Q = e3: xi <- [xi (1 - <P> dt) - P_i dt e3] / [1 - (<P> + P_i xi3) dt]
+        const float W0 = 0.5f * (st.Wp + st.Wm), Pi = 0.5f * (st.Wp - st.Wm);
+        const float D = 1.0f - (W0 + Pi * st.xi[2]) * dt;
+        if (D > 0.0f) {
+            const float iD = 1.0f / D, a1 = (1.0f - W0 * dt) * iD;
+            float xn[3] = {st.xi[0] * a1, st.xi[1] * a1, st.xi[2] * a1 - Pi * dt * iD};
+            if (xn[0] * xn[0] + xn[1] * xn[1] + xn[2] * xn[2] > 1.0f) {
+                const F3 r = renorm64(F3{xn[0], xn[1], xn[2]});
+                xn[0] = r.x;
+                xn[1] = r.y;
+                xn[2] = r.z;
+                c[C_RENORM]++;
+            }
+            Pf = stokes_to_P(xn, st.eps, st.beta, st.khat);
+        }
+    }
+    store32(G, j, st.x, st.k, Pf, st.w, tauf);
+    return false;
+}
+
+}  // namespace qed

@@ -164,6 +164,38 @@ HEADON_CP_LARGE = Workload("headon_cp_a150_g4000_n1e7", 10_000_000, 4000.0, Lase
                            spin="fixed", spin_dir=(0.0, 0.0, 1.0), pairs=True, capacity_factor=4.0, seed=2)
 
 
+@dataclasses.dataclass
+class BatchWorkload:
+    """Many independent collisions stepped together (see batched_instances for the draws)."""
+    name: str
+    n_inst: int
+    n_min: float
+    n_max: float
+    wavelength_um: float = 0.8
+    n_cycles: float = 10.0
+    steps: int = 2000
+    dt: float = 2.0 * math.pi / 100.0
+    capacity_factor: float = 4.0
+    n_chi: int = 256
+    n_r: int = 256
+    seed: int = 3
+    photon_store_min: float = 0.0
+
+    def instances(self):
+        return batched_instances(self.n_inst, self.seed, self.n_min, self.n_max)
+
+    def laser(self, inst) -> Laser:
+        return Laser(inst["kind"], inst["a0"], self.wavelength_um, self.n_cycles)
+
+    def beam(self, k: int, inst, n=None) -> dict:
+        """Electrons of instance k: counter-propagating along -z, z0 ~ U[lambda, 11 lambda], spins +-n_k
+        with P(+) = (1 + d_k)/2; ids k 2^40 + i."""
+        lam = 2.0 * math.pi
+        return lepton_beam(inst["n"] if n is None else n, inst["gamma"], direction=(0.0, 0.0, -1.0),
+                           z_range=(lam, 11.0 * lam), spin="degree", spin_dir=inst["spin_dir"],
+                           degree=inst["degree"], seed=inst["seed"], id_offset=k << 40)
+
+
 def batched_instances(n_inst: int = 96, seed: int = 3, n_min: float = 1e3, n_max: float = 2e6):
     """Independent collisions of uneven sizes: N log-uniform in [n_min, n_max], a0 ~ U[10, 300],
     gamma ~ U[500, 8000], spins +-n_i with P(+) = (1 + d_i)/2, d_i ~ U[0, 1]; LP and CP alternate."""
@@ -179,3 +211,9 @@ def batched_instances(n_inst: int = 96, seed: int = 3, n_min: float = 1e3, n_max
         out.append({"n": n, "a0": a0, "gamma": g, "spin_dir": tuple(nd), "degree": deg,
                     "kind": "LP" if i % 2 == 0 else "CP", "seed": int(rng.integers(1 << 31))})
     return out
+
+
+# 96 collisions, N log-uniform in [1e3, 2e6] (about 2.5e7 electrons in all), a0 ~ U[10, 300],
+# gamma ~ U[500, 8000], partially polarized spins, LP / CP alternating, 0.8 um, 10 cycles, 2000 steps,
+# NLC + NBW, buffers 4x per species.
+BATCHED_96 = BatchWorkload("batched96_n1e3-2e6_a10-300_g500-8000", 96, 1e3, 2e6)
