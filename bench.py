@@ -51,6 +51,8 @@ def parse():
                     help="untimed steps before warm-up (into the interaction; default 450 batched, 620 headon)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU-baseline legs")
     ap.add_argument("--no-tune", action="store_true", help="batched: keep the default launch shape")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="batched: multiply every instance's electron count (small cases for profiling)")
     a = ap.parse_args()
     if a.advance is None:
         a.advance = 450 if a.workload == "batched" else 620
@@ -132,6 +134,7 @@ class Sim:
         self.stream = torch.cuda.current_stream().cuda_stream
 
     def load_beam(self, beam):
+        beam = z_order(beam)
         self.el.load(beam["pos"], beam["mom"], beam["spin"], beam["w"], beam["id"])
         self.el.init_tau(self.seed)
 
@@ -305,8 +308,18 @@ def native(args):
 # ------------------------------------------------------------------------------------------------
 # the batched workload
 # ------------------------------------------------------------------------------------------------
-def batch_setup(Q, B, I, tables, rank, device):
+def z_order(beam: dict) -> dict:
+    """The same particles (each keeps its id and state) laid out in memory by position along the beam
+    axis, so that the 32 particles of a tile enter and leave the pulse together."""
+    o = np.argsort(beam["pos"][:, 2], kind="stable")
+    return {k: v[o] for k, v in beam.items()}
+
+
+def batch_setup(Q, B, I, tables, rank, device, scale=1.0):
+    import dataclasses
     wl = I.BATCHED_96
+    if scale != 1.0:
+        wl = dataclasses.replace(wl, name=f"{wl.name}_x{scale:g}", n_min=wl.n_min * scale, n_max=wl.n_max * scale)
     insts = wl.instances()
     fields = [Q.laser_field(wl.laser(x)) for x in insts]
     seeds = [x["seed"] + 1000 * rank for x in insts]
@@ -314,7 +327,7 @@ def batch_setup(Q, B, I, tables, rank, device):
     bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
                  device=device)
     for k, (x, (e, p, g)) in enumerate(zip(insts, bt.buffers())):
-        b = wl.beam(k, x)
+        b = z_order(wl.beam(k, x))
         if rank:
             b["id"] = b["id"] + np.uint64(rank << 48)
         e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"])
@@ -345,7 +358,7 @@ def native_batch(args):
     tables = Q.Tables(1e-4, 1e3, 256, 256)
     torch.cuda.synchronize()
     t_tables = time.time() - t0
-    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device)
+    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device, args.scale)
     stream = torch.cuda.current_stream().cuda_stream
 
     # untimed advance into the interaction; the autotuner times its candidates on real steps mid-way

@@ -122,17 +122,9 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev*
 // ------------------------------------------------------------------------------------------------
 // the persistent step kernel
 // ------------------------------------------------------------------------------------------------
-__host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
-    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4);
-    off += align128((size_t)(n_seg + 1) * 8);
-    off += align128((size_t)warps * sizeof(Ctx));
-    off += (size_t)warps * stages * sizeof(Tile);
-    off += (size_t)warps * stages * 8;
-    off += (size_t)warps * kWQ * 8;
-    return off;
-}
 
-// this warp's walk over the tile list: its i-th tile is tile_of(i)
+// this warp's walk over the tile list: its i-th tile is tile_of(i), increasing in i, so the segment of
+// the next tile is found by moving a cursor forward (usually not at all)
 template <int STAGES>
 struct BatchStream {
     Tile* tile;
@@ -142,28 +134,19 @@ struct BatchStream {
     int n_seg;
     int64_t total, wg, W;
     int chunk;
+    int cs;  // the copy cursor (lane 0): segment of the last issued tile
 
     __device__ __forceinline__ int64_t tile_of(int64_t i) const {
         const int64_t k = i / chunk;
         return (wg + k * W) * chunk + (i - k * chunk);
     }
-    // the segment holding tile t (t < total): the last s with tile0[s] <= t
-    __device__ __forceinline__ int find(int64_t t) const {
-        int lo = 0, hi = n_seg;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (tile0[mid] <= t) lo = mid;
-            else hi = mid;
-        }
-        return lo;
-    }
     // lane 0: start the copies of this warp's i-th tile into stage i % STAGES
-    __device__ __forceinline__ void issue(int64_t i) const {
+    __device__ __forceinline__ void issue(int64_t i) {
         const int64_t t = tile_of(i);
         if (t >= total) return;
-        const int s = find(t);
-        const SegDev g = seg[s];
-        const int64_t b = (t - tile0[s]) * 32;
+        while (tile0[cs + 1] <= t) ++cs;
+        const SegDev g = seg[cs];
+        const int64_t b = (t - tile0[cs]) * 32;
         const int st = (int)(i % STAGES);
         const uint32_t bytes = (uint32_t)(min((int64_t)32, g.n - b) * 16);
         mbar_expect_tx(&bar[st], 3 * bytes);
@@ -172,6 +155,23 @@ struct BatchStream {
         bulk_g2s(tile[st].q2, g.q2 + b, bytes, &bar[st]);
     }
 };
+
+// per-warp state of the current segment, in shared memory (written by lane 0 at a segment change)
+struct WarpSeg {
+    Ctx C;      // tables, field, step parameters and charge of the segment's instance and species
+    PartDev L;  // the segment's buffer (planes, ids, count) for the streaming pass
+    int64_t t0, t1, n;  // its tile range and particle count
+};
+
+__host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
+    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4);
+    off += align128((size_t)(n_seg + 1) * 8);
+    off += align128((size_t)warps * sizeof(WarpSeg));
+    off += (size_t)warps * stages * sizeof(Tile);
+    off += (size_t)warps * stages * 8;
+    off += (size_t)warps * kWQ * 8;
+    return off;
+}
 
 template <int WARPS, int STAGES, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * T.n_chi * 4);
     int64_t* s_tile0 = (int64_t*)(smem + off);
     off += align128((size_t)(n_seg + 1) * 8);
-    Ctx* s_ctx = (Ctx*)(smem + off);
-    off += align128((size_t)WARPS * sizeof(Ctx));
+    WarpSeg* s_ws = (WarpSeg*)(smem + off);
+    off += align128((size_t)WARPS * sizeof(WarpSeg));
     sh.tiles = (Tile*)(smem + off);
     off += (size_t)WARPS * STAGES * sizeof(Tile);
     sh.bars = (uint64_t*)(smem + off);
@@ -206,8 +206,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     ts.wg = (int64_t)blockIdx.x * WARPS + warp;
     ts.W = (int64_t)gridDim.x * WARPS;
     ts.chunk = chunk;
+    ts.cs = 0;
     int64_t* wq = sh.queue + warp * kWQ;
-    Ctx& C = s_ctx[warp];
+    WarpSeg& WS = s_ws[warp];
+    Ctx& C = WS.C;
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&ts.bar[s], 1);
         fence_mbar_init();
@@ -220,9 +222,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
     if (lane == 0)
         for (int s = 0; s < STAGES; ++s) ts.issue(s);
-    int qn = 0;     // queued event indices of the current segment (warp-uniform)
-    int cur = -1;   // current segment
+    int qn = 0;    // queued event indices of the current segment (warp-uniform)
+    int cur = -1;  // current segment
     int sp = 0, ii = 0;
+    if (lane == 0) WS.t1 = 0;
+    __syncwarp();
     int64_t i = 0;
     bool timed_out = false;
     for (;; ++i) {
@@ -233,20 +237,24 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             timed_out = true;
             break;
         }
-        const int s = ts.find(t);
-        if (s != cur) {
-            if (qn > 0) {  // the queue holds indices of the previous segment: drain it first
+        if (t >= WS.t1) {  // the tile lies in a later segment
+            if (qn > 0) {    // the queue holds indices of the previous segment: drain it first
                 const InstDev& I = inst[ii];
                 if (sp == 2) photon_events(C, sh, wq, qn, I.sp[2], I.sp[0], I.sp[1], ctr, c);
                 else lepton_events(C, sh, wq, qn, I.sp[sp], I.sp[2], ctr, c);
                 qn = 0;
             }
-            cur = s;
-            sp = s / n_inst;
-            ii = s - sp * n_inst;
+            do ++cur;
+            while (s_tile0[cur + 1] <= t);
+            sp = cur / n_inst;
+            ii = cur - sp * n_inst;
             __syncwarp();
             if (lane == 0) {
                 const InstDev& I = inst[ii];
+                WS.t0 = s_tile0[cur];
+                WS.t1 = s_tile0[cur + 1];
+                WS.n = seg[cur].n;
+                WS.L = I.sp[sp];
                 C.T = T;
                 C.T.nlc_rate = sh.rates;
                 C.T.nbw_rate = sh.rates + 2 * T.n_chi;
@@ -268,9 +276,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             }
             __syncwarp();
         }
-        const int64_t n = ts.seg[s].n;
-        const int64_t j = (t - ts.tile0[s]) * 32 + lane;
-        const bool valid = j < n;
+        const int64_t j = (t - WS.t0) * 32 + lane;
+        const bool valid = j < WS.n;
         float4 a = make_float4(0, 0, 0, 0), b = a, cc = a;
         if (valid) {
             a = ts.tile[st].q0[lane];
@@ -282,16 +289,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             fence_proxy_async();  // this stage's reads happen before the next copy overwrites it
             ts.issue(i + STAGES);
         }
-        const InstDev& I = inst[ii];
         bool event = false;
         if (valid)
-            event = sp == 2 ? photon_stream_one(C, I.sp[2], j, a, b, cc, ctr, c)
-                            : lepton_stream_one(C, I.sp[sp], j, a, b, cc, ctr, c);
+            event = sp == 2 ? photon_stream_one(C, WS.L, j, a, b, cc, ctr, c) : lepton_stream_one(C, WS.L, j, a, b, cc, ctr, c);
         const unsigned m = __ballot_sync(0xffffffffu, event);
         if (event) wq[qn + __popc(m & ((1u << lane) - 1u))] = j;
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
+            const InstDev& I = inst[ii];
             if (sp == 2) photon_events(C, sh, wq + (qn - 32), 32, I.sp[2], I.sp[0], I.sp[1], ctr, c);
             else lepton_events(C, sh, wq + (qn - 32), 32, I.sp[sp], I.sp[2], ctr, c);
             qn -= 32;

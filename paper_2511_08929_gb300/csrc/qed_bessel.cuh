@@ -56,11 +56,11 @@ __device__ __forceinline__ void bessel_series(R x, R out[3]) {
     const R c2 = c1 * c1;   // a^{2/3}
     const R ex = exp_(x);
     // K13 = pi/sqrt3 [a^-1/3/Gamma(2/3) (1 + a^2/(2/3)) - a^1/3/Gamma(4/3) (1 + a^2/(4/3))]
-    out[0] = pi3 * ((R(1) / (c1 * g23)) * (R(1) + R(1.5) * a2) - (R(3) * c1 / g13) * (R(1) + R(0.75) * a2)) * ex;
+    out[0] = pi3 * (rcp_(c1 * g23) * (R(1) + R(1.5) * a2) - div_(R(3) * c1, g13) * (R(1) + R(0.75) * a2)) * ex;
     // K23 = pi/sqrt3 [a^-2/3/Gamma(1/3) (1 + a^2/(1/3)) - a^2/3/Gamma(5/3) (1 + a^2/(5/3))]
-    out[1] = pi3 * ((R(1) / (c2 * g13)) * (R(1) + R(3) * a2) - (R(1.5) * c2 / g23) * (R(1) + R(0.6) * a2)) * ex;
+    out[1] = pi3 * (rcp_(c2 * g13) * (R(1) + R(3) * a2) - div_(R(1.5) * c2, g23) * (R(1) + R(0.6) * a2)) * ex;
     // IntK13 = pi/sqrt3 - int_0^x K13 = pi/sqrt3 [1 - 3 a^2/3/Gamma(2/3) (1 + 3 a^2/8) + 1.5 a^4/3/Gamma(4/3) (1 + 3 a^2/10)]
-    out[2] = pi3 * (R(1) - (R(3) * c2 / g23) * (R(1) + R(0.375) * a2) + (R(4.5) * c2 * c2 / g13) * (R(1) + R(0.3) * a2)) * ex;
+    out[2] = pi3 * (R(1) - div_(R(3) * c2, g23) * (R(1) + R(0.375) * a2) + div_(R(4.5) * c2 * c2, g13) * (R(1) + R(0.3) * a2)) * ex;
 }
 
 // --------------------------------------------------------------------------------------------
@@ -117,7 +117,7 @@ __device__ __forceinline__ void bessel32(const float* tab, float x, float out[3]
     }
     const float t = (__logf(x) - float(-9.210340371976182)) * float(1.0 / kBesH);  // ln(1e-4)
     if (t > float(kBesN - 1)) {
-        const float a = sqrtf(float(kPi / 2.0) / x), ix = 1.0f / x;
+        const float ix = rcp_(x), a = sqrt_(float(kPi / 2.0) * ix);
         out[0] = a * (1.0f - (5.0f / 72.0f) * ix);   // (4 nu^2 - 1)/8 with nu = 1/3
         out[1] = a * (1.0f + (7.0f / 72.0f) * ix);   // nu = 2/3
         out[2] = a * (1.0f - (41.0f / 72.0f) * ix);  // int_x^inf: (4 nu^2 - 5)/8
@@ -167,7 +167,7 @@ __device__ __forceinline__ void chi_coord(const TabP<R>& T, R lnchi, int& i, R& 
 template <class R>
 __device__ __forceinline__ void nlc_rates(const TabP<R>& T, R chi, R lnchi, R& Iu, R& Id) {
     if (chi < T.chi_min) {
-        const R sc = chi / T.chi_min;
+        const R sc = div_(chi, T.chi_min);
         Iu = exp_(T.nlc_rate[0]) * sc;
         Id = exp_(T.nlc_rate[T.n_chi]) * sc;
         return;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void nbw_rates(const TabP<R>& T, R chi, R lnchi, R& J
     int i; R f;
     chi_coord(T, lnchi, i, f);
     const R chic = chi > T.chi_max ? T.chi_max : chi;
-    const R sub = R(8.0 / 3.0) / chic;
+    const R sub = div_(R(8.0 / 3.0), chic);
     Jp = exp_((R(1) - f) * T.nbw_rate[i] + f * T.nbw_rate[i + 1] - sub);
     Jm = exp_((R(1) - f) * T.nbw_rate[T.n_chi + i] + f * T.nbw_rate[T.n_chi + i + 1] - sub);
 }
@@ -206,7 +206,9 @@ __device__ __forceinline__ R icdf_row(const R* __restrict__ row, const TabP<R>& 
     const R a = row[m - 1], b = row[m], c = row[m + 1], d = row[m + 2];
     const R d1 = c - b;
     const R d2 = R(0.5) * ((a - b) + (c - b));
-    const R d3 = ((d - a) + R(3) * (b - c)) / R(6);
+    R d3 = (d - a) + R(3) * (b - c);
+    if constexpr (sizeof(R) == 8) d3 = d3 / R(6);
+    else d3 = d3 * R(1.0 / 6.0);
     return b + x * (d1 + (x - R(1)) * (d2 + (x + R(1)) * d3));
 }
 

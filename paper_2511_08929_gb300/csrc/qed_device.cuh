@@ -42,10 +42,26 @@ __device__ __forceinline__ V3<R> operator-(const V3<R>& a, const V3<R>& b) { ret
 template <class R>
 __device__ __forceinline__ V3<R> operator*(R s, const V3<R>& a) { return V3<R>{s * a.x, s * a.y, s * a.z}; }
 
+// Division, reciprocal and square root.  FP64: IEEE operations.  FP32: the fixed approximate PTX
+// instructions (relative error below 2^-22), written out so that the same source line rounds the same
+// way at every inlining site (the FP32 translation units are built with IEEE division and square root
+// and without contraction, so the compiler has no freedom left that could depend on the context).
 __device__ __forceinline__ double rsqrt_(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
-__device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ float sqrt_(float v) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
+__device__ __forceinline__ float rcp_(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
 __device__ __forceinline__ double exp_(double v) { return exp(v); }
 __device__ __forceinline__ float exp_(float v) { return expf(v); }
 __device__ __forceinline__ double log_(double v) { return log(v); }
@@ -167,7 +183,7 @@ __device__ __forceinline__ V3<R> boris(const V3<R>& p, const V3<R>& E, const V3<
     const V3<R> pm = p + h * E;
     const R ig = rsqrt_(R(1) + dot(pm, pm));
     const V3<R> t = (h * ig) * B;
-    const R sfac = R(2) / (R(1) + dot(t, t));
+    const R sfac = div_(R(2), R(1) + dot(t, t));
     const V3<R> pp = pm + cross(pm, t);
     const V3<R> pl = pm + cross(pp, sfac * t);
     return pl + h * E;
@@ -178,15 +194,15 @@ template <class R>
 __device__ __forceinline__ V3<R> tbmt_omega(const V3<R>& pb, const V3<R>& E, const V3<R>& B, R q, bool paper_form) {
     const R ae = R(kAlpha / (2.0 * kPi));
     const R gb = sqrt_(R(1) + dot(pb, pb));
-    const R ig = R(1) / gb;
+    const R ig = rcp_(gb);
     const V3<R> bb = ig * pb;
     const R bB = dot(bb, B);
     const V3<R> bxE = cross(bb, E);
-    const R c1 = ae + ig, c2 = ae * gb / (gb + R(1));
+    const R c1 = ae + ig, c2 = div_(ae * gb, gb + R(1));
     if (paper_form)  // (a + 1/gamma)(B - v x E) - (a gamma/(gamma+1))(v.B) v, as printed in Sec. 7.3
         return (-q) * (c1 * (B - bxE) - (c2 * bB) * bb);
     // standard form: (a + 1/gamma) B - (a gamma/(gamma+1))(beta.B) beta - (a + 1/(gamma+1)) beta x E
-    const R c3 = ae + R(1) / (gb + R(1));
+    const R c3 = ae + rcp_(gb + R(1));
     return (-q) * (c1 * B - (c2 * bB) * bb - c3 * bxE);
 }
 
@@ -236,8 +252,8 @@ __device__ __forceinline__ bool make_basis(const V3<R>& E, const V3<R>& B, const
 template <class R>
 __device__ __forceinline__ void nlc_wg(R lam, R one_m, const R bes[3], const V3<R>& si, const V3<R>& beta,
                                        const V3<R>& k, R& w, V3<R>& g) {
-    const R u = lam / one_m;
-    const R kappa = R(1) / one_m + one_m;
+    const R u = div_(lam, one_m);
+    const R kappa = rcp_(one_m) + one_m;
     const R K13 = bes[0], K23 = bes[1], IK = bes[2];
     w = -IK + kappa * K23 + lam * dot(si, beta) * K13;
     g = (u * K13) * beta + (-IK + R(2) * K23) * si + (lam * u * (-IK + K23) * dot(si, k)) * k;
@@ -248,9 +264,9 @@ template <class R>
 __device__ __forceinline__ void nlc_stokes(R lam, R one_m, const R bes[3], const V3<R>& si, const V3<R>& sf, R w,
                                            const V3<R>& g, const V3<R>& eps, const V3<R>& beta, const V3<R>& k,
                                            R F[4]) {
-    const R u = lam / one_m;
-    const R kappa = R(1) / one_m + one_m;
-    const R kappat = R(1) / one_m - one_m;
+    const R u = div_(lam, one_m);
+    const R kappa = rcp_(one_m) + one_m;
+    const R kappat = rcp_(one_m) - one_m;
     const R K13 = bes[0], K23 = bes[1], IK = bes[2];
     const R sie = dot(si, eps), sib = dot(si, beta), sik = dot(si, k);
     const R sfe = dot(sf, eps), sfb = dot(sf, beta), sfk = dot(sf, k);
@@ -268,7 +284,7 @@ __device__ __forceinline__ void nlc_stokes(R lam, R one_m, const R bes[3], const
 template <class R>
 __device__ __forceinline__ void nbw_j(R lam, R one_m, const R bes[3], const R xi[3], const V3<R>& eps, const V3<R>& beta,
                                       const V3<R>& k, R& w0, V3<R>& je, V3<R>& jp) {
-    const R il = R(1) / lam, im = R(1) / one_m;
+    const R il = rcp_(lam), im = rcp_(one_m);
     const R rho = one_m * il + lam * im;
     const R rhot = one_m * il - lam * im;
     const R K13 = bes[0], K23 = bes[1], IK = bes[2];
@@ -282,7 +298,7 @@ __device__ __forceinline__ void nbw_j(R lam, R one_m, const R bes[3], const R xi
 template <class R>
 __device__ __forceinline__ R nbw_G(R lam, R one_m, const R bes[3], const R xi[3], const V3<R>& sp, const V3<R>& se,
                                    const V3<R>& eps, const V3<R>& beta, const V3<R>& k) {
-    const R il = R(1) / lam, im = R(1) / one_m;
+    const R il = rcp_(lam), im = rcp_(one_m);
     const R rho = one_m * il + lam * im;
     const R rhot = one_m * il - lam * im;
     const R ut = il + im;
@@ -313,11 +329,11 @@ __device__ __forceinline__ V3<R> stokes_to_P(const R xi[3], const V3<R>& eps, co
         const R half = R(0.5) * l * xi[0];
         if (xi[2] >= R(0)) {
             c = sqrt_(R(0.5) * l * (l + xi[2]));
-            s = half / c;
+            s = div_(half, c);
         } else {
             s = sqrt_(R(0.5) * l * (l - xi[2]));
             if (xi[0] < R(0)) s = -s;
-            c = half / s;
+            c = div_(half, s);
         }
     }
     return xi[1] * k + c * eps + s * beta;

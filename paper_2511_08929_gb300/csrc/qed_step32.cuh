@@ -223,10 +223,11 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
         const F3 pb = 0.5f * (pold + st.p);
         st.s = rotate(st.s, tbmt_omega(pb, st.E, st.B, C.q, (fl & QED_F_TBMT_PAPER) != 0), dt);
     }
-    st.gam = sqrtf(1.0f + dot(st.p, st.p));
+    st.gam = sqrt_(1.0f + dot(st.p, st.p));
+    const float rg = rcp_(st.gam);
     st.x = xold;
     if (fl & QED_F_MOVE) {
-        const float ig = dt / st.gam;
+        const float ig = dt * rg;
         st.x = F3{xold.x + st.p.x * ig, xold.y + st.p.y * ig, xold.z + st.p.z * ig};
     }
     st.qed = false;
@@ -235,13 +236,13 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     const float pn2 = dot(st.p, st.p);
     if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < (float)C.S.chi_floor) return;
     st.khat = rsqrtf(pn2) * st.p;
-    const F3 v = (1.0f / st.gam) * st.p;
+    const F3 v = rg * st.p;
     if (!make_basis(st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
     st.qed = true;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
     nlc_rates(C.T, st.chi, st.lnchi, st.Wu, st.Wd);
-    const float pref = (float)(kAlpha / (kSqrt3 * kPi)) / (C.F.eta0 * st.gam);
+    const float pref = (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0) * rg;
     st.Wu *= pref;
     st.Wd *= pref;
     st.sb = (fl & QED_F_RESOLVED) ? dot(st.s, st.beta) : 0.0f;
@@ -258,7 +259,7 @@ __device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x
 }
 
 // the event pass of one warp: lane l takes the particle index q[l] if l < cnt (all 32 lanes call it)
-static __device__ void lepton_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& L, const PartDev& G,
+static __device__ __noinline__ void lepton_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& L, const PartDev& G,
                               qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = C.S.flags;
     const int e = threadIdx.x & 31;
@@ -286,7 +287,8 @@ static __device__ void lepton_events(const Ctx& C, const Shared32& sh, const int
         // the sampled value to full FP32 accuracy: accurate logarithm of chi and exponential
         const float up = expf(icdf_lookup(C.T, false, down ? 1 : 0, logf(st.chi), y));
         const float den = 2.0f + 3.0f * st.chi * up;
-        const float lam = 3.0f * st.chi * up / den, one_m = 2.0f / den;
+        const float iden = rcp_(den);
+        const float lam = 3.0f * st.chi * up * iden, one_m = 2.0f * iden;
         const F3 k = lam * st.p;
         if (fl & QED_F_RECOIL) pf = one_m * st.p;
         float bb[3];
@@ -299,29 +301,31 @@ static __device__ void lepton_events(const Ctx& C, const Shared32& sh, const int
         F3 g{0, 0, 0};
         if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, bb, si, st.beta, st.khat, wv, g);
         if (fl & QED_F_SPIN_EVENT) {
-            const float gn = sqrtf(dot(g, g));
+            const float gn = sqrt_(dot(g, g));
             if (fl & QED_F_SPIN_COLLAPSE) {
-                const float sg = r3 < (wv - gn) / (2.0f * wv) ? -1.0f : 1.0f;
-                sf = gn > 0.0f ? (sg / gn) * g : F3{0, 0, 0};
+                const float sg = r3 < div_(wv - gn, 2.0f * wv) ? -1.0f : 1.0f;
+                sf = gn > 0.0f ? div_(sg, gn) * g : F3{0, 0, 0};
             } else {
-                sf = (1.0f / wv) * g;
+                sf = rcp_(wv) * g;
             }
             sfu = sf;
         }
         if (fl & QED_F_POL_EVENT) {
             float Fv[4];
             nlc_stokes(lam, one_m, bb, si, sfu, wv, g, st.eps, st.beta, st.khat, Fv);
-            const float Fn = sqrtf(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
+            const float Fn = sqrt_(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
             if (fl & QED_F_POL_COLLAPSE) {
-                const float sg = r4 < (Fv[0] - Fn) / (2.0f * Fv[0]) ? -1.0f : 1.0f;
-                for (int i = 0; i < 3; ++i) xi[i] = Fn > 0.0f ? sg * Fv[i + 1] / Fn : 0.0f;
+                const float sg = r4 < div_(Fv[0] - Fn, 2.0f * Fv[0]) ? -1.0f : 1.0f;
+                const float iF = Fn > 0.0f ? div_(sg, Fn) : 0.0f;
+                for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
             } else {
-                for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] / Fv[0];
+                const float iF = rcp_(Fv[0]);
+                for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
             }
         }
         if (fl & QED_F_TAU) tauf = exp_draw(w0.x, w0.y);
         c[C_EVENTS]++;
-        if (sqrtf(dot(k, k)) >= (float)C.S.store_min) {
+        if (sqrt_(dot(k, k)) >= (float)C.S.store_min) {
             const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
             want = true;
             gx = st.x;
@@ -381,7 +385,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
         const float W0 = 0.5f * (st.Wu + st.Wd), Pi = 0.5f * (st.Wu - st.Wd);
         const float D = 1.0f - (W0 + Pi * st.sb) * dt;
         if (D > 0.0f) {
-            const float iD = 1.0f / D, a1 = (1.0f - W0 * dt) * iD, a2 = Pi * dt * iD;
+            const float iD = rcp_(D), a1 = (1.0f - W0 * dt) * iD, a2 = Pi * dt * iD;
             sf = F3{st.s.x * a1 - st.beta.x * a2, st.s.y * a1 - st.beta.y * a2, st.s.z * a1 - st.beta.z * a2};
             if (dot(sf, sf) > 1.0f) {
                 sf = renorm64(sf);
@@ -411,7 +415,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.w = cc.y;
     field_eval(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const float en2 = dot(st.k, st.k);
-    st.en = sqrtf(en2);
+    st.en = sqrt_(en2);
     st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
     st.x = xold;
     if (C.S.flags & QED_F_MOVE) st.x = xold + C.S.dt_f * st.khat;
@@ -426,14 +430,14 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.lnchi = __logf(st.chi);
     if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
     nbw_rates(C.T, st.chi, st.lnchi, st.Wp, st.Wm);
-    const float pref = (float)(kAlpha / (kSqrt3 * kPi)) / (C.F.eta0 * st.en);
+    const float pref = (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0 * st.en);
     st.Wp *= pref;
     st.Wm *= pref;
     st.Wmp = st.Wm * (1.0f - st.xi[2]) * 0.5f;
     st.Wx = st.Wp * (1.0f + st.xi[2]) * 0.5f + st.Wmp;
 }
 
-static __device__ void photon_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& G, const PartDev& El,
+static __device__ __noinline__ void photon_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& G, const PartDev& El,
                               const PartDev& Po, qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = C.S.flags;
     const bool have = El.count != nullptr && Po.count != nullptr;
@@ -472,11 +476,12 @@ static __device__ void photon_events(const Ctx& C, const Shared32& sh, const int
         const float rfc = fmaf((float)(uint32_t)(dmc >> 32), 0x1.0p-19f, ((float)(uint32_t)dmc + 0.5f) * 0x1.0p-51f);
         const float yf = logf(rf) - logf(rfc);
         const float xv = expf(icdf_lookup(C.T, true, minus ? 1 : 0, logf(st.chi), yf));
-        const float umin = (8.0f / 3.0f) / st.chi;
+        const float umin = (8.0f / 3.0f) * rcp_(st.chi);
         const float ut = umin + xv;
         // mu (1 - mu) = q = 2/(3 chi u~'), so 1 - 4q = x/u~' exactly and mu = (1 - sqrt(x/u~'))/2
         // = u~'_min / (2 u~' (1 + sqrt(x/u~'))), free of cancellation near the centre
-        const float mu = 0.5f * (umin / ut) / (1.0f + sqrtf(xv / ut));
+        const float iut = rcp_(ut);
+        const float mu = div_(0.5f * (umin * iut), 1.0f + sqrt_(xv * iut));
         const float lam = low ? mu : 1.0f - mu;
         const float one_m = low ? 1.0f - mu : mu;
         float bb[3];
@@ -488,13 +493,13 @@ static __device__ void photon_events(const Ctx& C, const Shared32& sh, const int
             F3 je, jp;
             nbw_j(lam, one_m, bb, st.xi, st.eps, st.beta, st.khat, w0v, je, jp);
             if (fl & QED_F_SPIN_COLLAPSE) {
-                const float jen = sqrtf(dot(je, je)), jpn = sqrtf(dot(jp, jp));
-                const F3 Se = jen > 0.0f ? (1.0f / jen) * je : F3{0, 0, 0};
-                const F3 Sp = jpn > 0.0f ? (1.0f / jpn) * jp : F3{0, 0, 0};
+                const float jen = sqrt_(dot(je, je)), jpn = sqrt_(dot(jp, jp));
+                const F3 Se = jen > 0.0f ? rcp_(jen) * je : F3{0, 0, 0};
+                const F3 Sp = jpn > 0.0f ? rcp_(jpn) * jp : F3{0, 0, 0};
                 // four correlated states, order (--, -+, +-, ++), first sign = positron
                 float cum = 0.0f;
                 int chosen = 3;
-                const float i4w = 1.0f / (4.0f * w0v);
+                const float i4w = rcp_(4.0f * w0v);
                 for (int s4 = 0; s4 < 3; ++s4) {
                     const float sa = (s4 & 2) ? 1.0f : -1.0f, sbb = (s4 & 1) ? 1.0f : -1.0f;
                     cum += nbw_G(lam, one_m, bb, st.xi, sa * Sp, sbb * Se, st.eps, st.beta, st.khat) * i4w;
@@ -507,8 +512,8 @@ static __device__ void photon_events(const Ctx& C, const Shared32& sh, const int
                 sp = sa * Sp;
                 se = sbb * Se;
             } else {
-                se = (1.0f / w0v) * je;
-                sp = (1.0f / w0v) * jp;
+                se = rcp_(w0v) * je;
+                sp = rcp_(w0v) * jp;
             }
         }
         const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
@@ -575,7 +580,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
         const float W0 = 0.5f * (st.Wp + st.Wm), Pi = 0.5f * (st.Wp - st.Wm);
         const float D = 1.0f - (W0 + Pi * st.xi[2]) * dt;
         if (D > 0.0f) {
-            const float iD = 1.0f / D, a1 = (1.0f - W0 * dt) * iD;
+            const float iD = rcp_(D), a1 = (1.0f - W0 * dt) * iD;
             float xn[3] = {st.xi[0] * a1, st.xi[1] * a1, st.xi[2] * a1 - Pi * dt * iD};
             if (xn[0] * xn[0] + xn[1] * xn[1] + xn[2] * xn[2] > 1.0f) {
                 const F3 r = renorm64(F3{xn[0], xn[1], xn[2]});
