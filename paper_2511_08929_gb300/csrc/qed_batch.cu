@@ -272,6 +272,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                 S.seed = I.seed;
                 S.store_min = P.store_min;
                 S.chi_floor = P.chi_floor;
+                S.store_min_f = (float)P.store_min;
+                S.chi_floor_f = (float)P.chi_floor;
                 C.S = S;
             }
             __syncwarp();

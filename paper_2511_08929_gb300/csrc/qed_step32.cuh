@@ -91,6 +91,22 @@ __device__ __forceinline__ double birth_tau32(uint64_t id, uint64_t seed) {
     return exp_draw(w.x, w.y);
 }
 
+// A positive normal float widened to double exactly by rearranging its bits on the integer units (the
+// FP64 pipe of this GPU is narrow): sign 0, exponent rebased from 127 to 1023, mantissa moved up 29
+// bits.  Zero, denormals, negatives, infinities and NaNs take the plain conversion.
+__device__ __forceinline__ double widen_pos(float v) {
+    const uint32_t u = __float_as_uint(v);
+    if (u < 0x00800000u || u >= 0x7F800000u) return (double)v;
+    const uint32_t hi = (((u >> 23) + (1023u - 127u)) << 20) | ((u & 0x7FFFFFu) >> 3);
+    const uint32_t lo = u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// A spin or Stokes vector is renormalised when |s|^2 exceeds 1 by more than the FP32 rounding of the
+// update that produced it; below that the excess is rounding noise (the exact update of Sec. 5 raises
+// |s|^2 by (P dt)^2 (1 - (s.beta)^2) / D^2, a real second-order excess, which still triggers it).
+constexpr float kRenormSlack = 0x1.0p-20f;
+
 // Rescale a vector that left the unit ball.  Its excess d = |s|^2 - 1 is computed in FP64 (the
 // products of floats are exact in double, so d is exact to 1e-16); the factor (1 + d)^{-1/2} =
 // 1 - d/2 + 3 d^2/8 (relative error 5 d^3/16 < 1e-11 for d < 2^-10) is then applied in FP32, whose
@@ -234,7 +250,7 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     if (!(fl & QED_F_EMIT)) return;
     st.chi = chi_of(C.F.eta0, st.gam, st.p, st.E, st.B);
     const float pn2 = dot(st.p, st.p);
-    if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < (float)C.S.chi_floor) return;
+    if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.khat = rsqrtf(pn2) * st.p;
     const F3 v = rg * st.p;
     if (!make_basis(st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
@@ -325,7 +341,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Shared32& 
         }
         if (fl & QED_F_TAU) tauf = exp_draw(w0.x, w0.y);
         c[C_EVENTS]++;
-        if (sqrt_(dot(k, k)) >= (float)C.S.store_min) {
+        if (sqrt_(dot(k, k)) >= C.S.store_min_f) {
             const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
             want = true;
             gx = st.x;
@@ -372,7 +388,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
     double tauf = tau;
     if (st.qed) {
         if (fl & QED_F_TAU) {
-            tauf = tau - (double)(st.Ws * dt);
+            tauf = tau - widen_pos(st.Ws * dt);
             if (tau_spent(tauf)) return true;
         } else {
             const uint4 w0 = draw(L.id[j], C.S.seed, C.S.step, kSlotTauBranch);
@@ -387,7 +403,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
         if (D > 0.0f) {
             const float iD = rcp_(D), a1 = (1.0f - W0 * dt) * iD, a2 = Pi * dt * iD;
             sf = F3{st.s.x * a1 - st.beta.x * a2, st.s.y * a1 - st.beta.y * a2, st.s.z * a1 - st.beta.z * a2};
-            if (dot(sf, sf) > 1.0f) {
+            if (dot(sf, sf) > 1.0f + kRenormSlack) {
                 sf = renorm64(sf);
                 c[C_RENORM]++;
             }
@@ -422,7 +438,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.qed = false;
     if (!(C.S.flags & QED_F_EMIT) || !(en2 > 0.0f)) return;
     st.chi = chi_of(C.F.eta0, st.en, st.k, st.E, st.B);
-    if (!(st.chi > 0.0f) || st.chi < (float)C.S.chi_floor) return;
+    if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     if (!make_basis(st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
@@ -458,7 +474,7 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Shared32& 
         P = st.P;
         w = st.w;
         tauf = tau_join(cc.z, cc.w);
-        if (fl & QED_F_TAU) tauf -= (double)(st.Wx * C.S.dt_f);
+        if (fl & QED_F_TAU) tauf -= widen_pos(st.Wx * C.S.dt_f);
         const uint64_t id = G.id[j];
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
         bool minus;
@@ -567,7 +583,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
     double tauf = tau;
     if (st.qed && st.Wx > 0.0f) {
         if (fl & QED_F_TAU) {
-            tauf = tau - (double)(st.Wx * dt);
+            tauf = tau - widen_pos(st.Wx * dt);
             if (tau_spent(tauf)) return true;
         } else {
             const uint4 w0 = draw(G.id[j], C.S.seed, C.S.step, kSlotTauBranch);
@@ -582,7 +598,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
         if (D > 0.0f) {
             const float iD = rcp_(D), a1 = (1.0f - W0 * dt) * iD;
             float xn[3] = {st.xi[0] * a1, st.xi[1] * a1, st.xi[2] * a1 - Pi * dt * iD};
-            if (xn[0] * xn[0] + xn[1] * xn[1] + xn[2] * xn[2] > 1.0f) {
+            if (xn[0] * xn[0] + xn[1] * xn[1] + xn[2] * xn[2] > 1.0f + kRenormSlack) {
                 const F3 r = renorm64(F3{xn[0], xn[1], xn[2]});
                 xn[0] = r.x;
                 xn[1] = r.y;

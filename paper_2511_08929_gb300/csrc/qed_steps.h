@@ -12,6 +12,7 @@ struct StepP {
     uint32_t flags;
     uint64_t step, seed;
     double store_min, chi_floor;
+    float store_min_f, chi_floor_f;  // the same thresholds rounded to float (FP32 path)
 };
 
 inline StepP step_params(const qed_step_desc& s, const qed_field& f) {
@@ -26,6 +27,8 @@ inline StepP step_params(const qed_step_desc& s, const qed_field& f) {
     p.seed = s.seed;
     p.store_min = s.photon_store_min;
     p.chi_floor = s.chi_floor;
+    p.store_min_f = (float)s.photon_store_min;
+    p.chi_floor_f = (float)s.chi_floor;
     return p;
 }
 
