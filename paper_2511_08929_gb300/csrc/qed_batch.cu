@@ -123,49 +123,47 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev*
 // the persistent step kernel
 // ------------------------------------------------------------------------------------------------
 
-// this warp's walk over the tile list: its i-th tile is tile_of(i), increasing in i, so the segment of
-// the next tile is found by moving a cursor forward (usually not at all)
-template <int STAGES>
-struct BatchStream {
-    Tile* tile;
-    uint64_t* bar;
-    const int64_t* tile0;  // shared memory: first tile of each segment, tile0[n_seg] = total
-    const SegDev* seg;
-    int n_seg;
-    int64_t total, wg, W;
-    int chunk;
-    int cs;  // the copy cursor (lane 0): segment of the last issued tile
-
-    __device__ __forceinline__ int64_t tile_of(int64_t i) const {
-        const int64_t k = i / chunk;
-        return (wg + k * W) * chunk + (i - k * chunk);
-    }
-    // lane 0: start the copies of this warp's i-th tile into stage i % STAGES
-    __device__ __forceinline__ void issue(int64_t i) {
-        const int64_t t = tile_of(i);
-        if (t >= total) return;
-        while (tile0[cs + 1] <= t) ++cs;
-        const SegDev g = seg[cs];
-        const int64_t b = (t - tile0[cs]) * 32;
-        const int st = (int)(i % STAGES);
-        const uint32_t bytes = (uint32_t)(min((int64_t)32, g.n - b) * 16);
-        mbar_expect_tx(&bar[st], 3 * bytes);
-        bulk_g2s(tile[st].q0, g.q0 + b, bytes, &bar[st]);
-        bulk_g2s(tile[st].q1, g.q1 + b, bytes, &bar[st]);
-        bulk_g2s(tile[st].q2, g.q2 + b, bytes, &bar[st]);
+// A warp's walk over the tile list: chunks of `chunk` consecutive tiles, chunk k of warp w starting at
+// tile (k W + w) chunk.  Incremental 32-bit counters (the batch holds fewer than 2^31 tiles): t is the
+// current tile (== total once the walk is over), r its place in the chunk.
+struct TileWalk {
+    int t, r;
+    __device__ __forceinline__ void next(int chunk, int jump, int total) {
+        if (++r == chunk) {
+            r = 0;
+            const long long n = (long long)t + jump;
+            t = n < total ? (int)n : total;
+        } else {
+            t = t + 1 < total ? t + 1 : total;
+        }
     }
 };
+
+// lane 0: start the copies of tile t into stage st, moving the copy cursor cs (segment of the last
+// issued tile; tiles only increase) forward
+template <int STAGES>
+__device__ __forceinline__ void batch_issue(Tile* tile, uint64_t* bar, const int* tile0, const SegDev* __restrict__ seg,
+                                            int t, int st, int& cs) {
+    while (tile0[cs + 1] <= t) ++cs;
+    const SegDev g = seg[cs];
+    const int b = (t - tile0[cs]) * 32;
+    const uint32_t bytes = (uint32_t)(min((int64_t)32, g.n - (int64_t)b) * 16);
+    mbar_expect_tx(&bar[st], 3 * bytes);
+    bulk_g2s(tile[st].q0, g.q0 + b, bytes, &bar[st]);
+    bulk_g2s(tile[st].q1, g.q1 + b, bytes, &bar[st]);
+    bulk_g2s(tile[st].q2, g.q2 + b, bytes, &bar[st]);
+}
 
 // per-warp state of the current segment, in shared memory (written by lane 0 at a segment change)
 struct WarpSeg {
     Ctx C;      // tables, field, step parameters and charge of the segment's instance and species
     PartDev L;  // the segment's buffer (planes, ids, count) for the streaming pass
-    int64_t t0, t1, n;  // its tile range and particle count
+    int t0, t1, n;  // its tile range and particle count
 };
 
 __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
     size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4);
-    off += align128((size_t)(n_seg + 1) * 8);
+    off += align128((size_t)(n_seg + 1) * 4);
     off += align128((size_t)warps * sizeof(WarpSeg));
     off += (size_t)warps * stages * sizeof(Tile);
     off += (size_t)warps * stages * 8;
@@ -184,8 +182,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     sh.bes = (float*)smem;
     sh.rates = sh.bes + 3 * kBesN;
     size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * T.n_chi * 4);
-    int64_t* s_tile0 = (int64_t*)(smem + off);
-    off += align128((size_t)(n_seg + 1) * 8);
+    int* s_tile0 = (int*)(smem + off);
+    off += align128((size_t)(n_seg + 1) * 4);
     WarpSeg* s_ws = (WarpSeg*)(smem + off);
     off += align128((size_t)WARPS * sizeof(WarpSeg));
     sh.tiles = (Tile*)(smem + off);
@@ -195,45 +193,44 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     sh.queue = (int64_t*)(smem + off);
 
     load_tables32(sh, bes_g, T);
-    for (int i = threadIdx.x; i <= n_seg; i += blockDim.x) s_tile0[i] = tile0_g[i];
+    for (int i = threadIdx.x; i <= n_seg; i += blockDim.x) s_tile0[i] = (int)tile0_g[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    BatchStream<STAGES> ts;
-    ts.tile = sh.tiles + warp * STAGES;
-    ts.bar = sh.bars + warp * STAGES;
-    ts.tile0 = s_tile0;
-    ts.seg = seg;
-    ts.n_seg = n_seg;
-    ts.wg = (int64_t)blockIdx.x * WARPS + warp;
-    ts.W = (int64_t)gridDim.x * WARPS;
-    ts.chunk = chunk;
-    ts.cs = 0;
+    Tile* tile = sh.tiles + warp * STAGES;
+    uint64_t* bar = sh.bars + warp * STAGES;
     int64_t* wq = sh.queue + warp * kWQ;
     WarpSeg& WS = s_ws[warp];
     Ctx& C = WS.C;
     if (lane == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&ts.bar[s], 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
+        WS.t1 = 0;
     }
     __syncthreads();  // tables, tile list and barriers ready
-    ts.total = s_tile0[n_seg];
+    const int total = s_tile0[n_seg];
+    const int W = gridDim.x * WARPS;
+    const int jump = (W - 1) * chunk + 1;
+    const long long first = ((long long)blockIdx.x * WARPS + warp) * chunk;
+    TileWalk walk{first < total ? (int)first : total, 0};
     const uint64_t step = clk->step;
     // time of this step: a product then a sum, each rounded (no contraction)
     const double t_now = __dadd_rn(clk->t0, __dmul_rn((double)(step - clk->step0), clk->dt));
     unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    TileWalk pre = walk;  // lane 0: the copy walk, STAGES tiles ahead
+    int cs = 0;
     if (lane == 0)
-        for (int s = 0; s < STAGES; ++s) ts.issue(s);
+        for (int s = 0; s < STAGES && pre.t < total; ++s) {
+            batch_issue<STAGES>(tile, bar, s_tile0, seg, pre.t, s, cs);
+            pre.next(chunk, jump, total);
+        }
     int qn = 0;    // queued event indices of the current segment (warp-uniform)
     int cur = -1;  // current segment
     int sp = 0, ii = 0;
-    if (lane == 0) WS.t1 = 0;
-    __syncwarp();
-    int64_t i = 0;
+    int st = 0;        // stage of the current tile
+    uint32_t ph = 0;   // its mbarrier phase parity
     bool timed_out = false;
-    for (;; ++i) {
-        const int64_t t = ts.tile_of(i);
-        if (t >= ts.total) break;
-        const int st = (int)(i % STAGES);
-        if (!mbar_wait(&ts.bar[st], (uint32_t)((i / STAGES) & 1))) {
+    for (; walk.t < total; walk.next(chunk, jump, total)) {
+        const int t = walk.t;
+        if (!mbar_wait(&bar[st], ph)) {
             timed_out = true;
             break;
         }
@@ -253,7 +250,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                 const InstDev& I = inst[ii];
                 WS.t0 = s_tile0[cur];
                 WS.t1 = s_tile0[cur + 1];
-                WS.n = seg[cur].n;
+                WS.n = (int)seg[cur].n;
                 WS.L = I.sp[sp];
                 C.T = T;
                 C.T.nlc_rate = sh.rates;
@@ -278,18 +275,25 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             }
             __syncwarp();
         }
-        const int64_t j = (t - WS.t0) * 32 + lane;
+        const int j = (t - WS.t0) * 32 + lane;
         const bool valid = j < WS.n;
         float4 a = make_float4(0, 0, 0, 0), b = a, cc = a;
         if (valid) {
-            a = ts.tile[st].q0[lane];
-            b = ts.tile[st].q1[lane];
-            cc = ts.tile[st].q2[lane];
+            a = tile[st].q0[lane];
+            b = tile[st].q1[lane];
+            cc = tile[st].q2[lane];
         }
         __syncwarp();
         if (lane == 0) {
             fence_proxy_async();  // this stage's reads happen before the next copy overwrites it
-            ts.issue(i + STAGES);
+            if (pre.t < total) {
+                batch_issue<STAGES>(tile, bar, s_tile0, seg, pre.t, st, cs);
+                pre.next(chunk, jump, total);
+            }
+        }
+        if (++st == STAGES) {
+            st = 0;
+            ph ^= 1u;
         }
         bool event = false;
         if (valid)
@@ -308,9 +312,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     }
     if (timed_out) {
         if (lane == 0) {
-            record_error(ctr, QED_ERR_TIMEOUT, ts.tile_of(i) * 32);
-            for (int64_t u = i; u < i + STAGES && ts.tile_of(u) < ts.total; ++u)  // let the copies in flight land
-                mbar_wait(&ts.bar[u % STAGES], (uint32_t)((u / STAGES) & 1));
+            record_error(ctr, QED_ERR_TIMEOUT, (long long)walk.t * 32);
+            TileWalk w2 = walk;  // let the copies in flight (this tile and up to STAGES - 1 after it) land
+            int s2 = st;
+            uint32_t p2 = ph;
+            for (int k = 0; k < STAGES && w2.t < total; ++k) {
+                mbar_wait(&bar[s2], p2);
+                w2.next(chunk, jump, total);
+                if (++s2 == STAGES) {
+                    s2 = 0;
+                    p2 ^= 1u;
+                }
+            }
         }
         __syncwarp();
     }
@@ -492,7 +505,8 @@ static bool valid_instance(const qed_instance& in) {
     const qed_particles* sp[3] = {&in.electrons, &in.positrons, &in.photons};
     const int32_t charge[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
     for (int k = 0; k < 3; ++k) {
-        if (check_particles(sp[k], k == 2) != QED_OK || sp[k]->layout != QED_FP32 || sp[k]->charge != charge[k])
+        if (check_particles(sp[k], k == 2) != QED_OK || sp[k]->layout != QED_FP32 || sp[k]->charge != charge[k] ||
+            sp[k]->capacity > (int64_t)INT32_MAX)  // particle indices within a buffer are 32-bit
             return false;
     }
     return valid_field(&in.field) && in.electrons.count != in.positrons.count && in.electrons.count != in.photons.count &&
@@ -504,7 +518,7 @@ static inline size_t r16(size_t v) { return (v + 15) & ~size_t(15); }
 extern "C" qed_status qed_batch_set_tuning(qed_batch_t b, const qed_batch_tuning* tn) {
     if (!valid_batch(b)) return QED_ERR_STATE;
     if (!tn || tn->variant < 0 || tn->variant >= QED_BATCH_VARIANTS || tn->blocks_per_sm < 0 || tn->chunk < 1 ||
-        tn->chunk > (1 << 20) || tn->graph_steps < 0 || tn->graph_steps > 4096)
+        tn->chunk > 4096 || tn->graph_steps < 0 || tn->graph_steps > 4096)
         return QED_ERR_ARG;
     const int occ = variant_occupancy(b, tn->variant);
     if (occ < 1) return QED_ERR_ARG;  // this variant does not fit this batch (shared memory)
@@ -568,6 +582,10 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
         b->capacity_total += instances[i].electrons.capacity + instances[i].positrons.capacity + instances[i].photons.capacity;
     }
     const int n_seg = kSpecies * n_inst;
+    if (b->capacity_total / 32 + n_seg >= (int64_t)INT32_MAX) {  // tile indices are 32-bit
+        qed_batch_destroy(b);
+        return QED_ERR_ARG;
+    }
     ok = ok && cudaMalloc(&b->d_inst, sizeof(InstDev) * n_inst) == cudaSuccess &&
          cudaMalloc(&b->d_seg, sizeof(SegDev) * n_seg) == cudaSuccess &&
          cudaMalloc(&b->d_tile0, sizeof(int64_t) * (n_seg + 1)) == cudaSuccess &&

@@ -152,24 +152,30 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
     const R dp = e1 + ph_lo;
     const R phi = ps + dp;
     const R a = f.a0 * envelope(phi, f);
-    R s, c;
-    phase_sincos(ps, &s, &c, dp);
-    const R ex = a * c, ey = f.kind == QED_FIELD_LP ? R(0) : a * s;
-    E = v3(ex, ey, R(0));
-    B = v3(-ey, ex, R(0));  // forward wave: B = z x E
+    E = v3(R(0), R(0), R(0));
+    B = E;
+    if (a != R(0)) {  // outside the envelope the carrier is not needed
+        R s, c;
+        phase_sincos(ps, &s, &c, dp);
+        const R ex = a * c, ey = f.kind == QED_FIELD_LP ? R(0) : a * s;
+        E = v3(ex, ey, R(0));
+        B = v3(-ey, ex, R(0));  // forward wave: B = z x E
+    }
     if (f.kind == QED_FIELD_CP_COUNTER) {
         R e2;
         const R ps2 = two_sum(ph_hi, x.z, e2);
         const R dp2 = e2 + ph_lo;
         const R phi2 = ps2 + dp2;
         const R a2 = f.a0 * envelope(phi2, f);
-        R s2, c2;
-        phase_sincos(ps2, &s2, &c2, dp2);
-        const R ex2 = a2 * c2, ey2 = a2 * s2;
-        E.x += ex2;
-        E.y += ey2;
-        B.x += ey2;  // backward wave: B = -z x E
-        B.y += -ex2;
+        if (a2 != R(0)) {
+            R s2, c2;
+            phase_sincos(ps2, &s2, &c2, dp2);
+            const R ex2 = a2 * c2, ey2 = a2 * s2;
+            E.x += ex2;
+            E.y += ey2;
+            B.x += ey2;  // backward wave: B = -z x E
+            B.y += -ex2;
+        }
     }
 }
 

@@ -17,7 +17,7 @@ constexpr int kT32 = 256;  // threads per block
 constexpr int kWarps32 = kT32 / 32;
 constexpr int kStages = 3;  // tiles in flight per warp
 constexpr int kWQ = 64;     // queued event indices per warp (drained 32 at a time)
-constexpr long long kWaitLimit = 1ll << 24;  // bounded mbarrier polling (~0.1 s) before reporting a timeout
+constexpr int kWaitLimit = 1 << 24;  // bounded mbarrier polling (~0.1 s) before reporting a timeout
 
 struct Tile {  // one tile of 32 particles in shared memory
     float4 q0[32], q1[32], q2[32];
@@ -53,7 +53,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 }
 // bounded wait for the phase of `parity` to complete (false: gave up)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
+    for (int i = 0; i < kWaitLimit; ++i)
         if (mbar_test(bar, parity)) return true;
     return false;
 }
