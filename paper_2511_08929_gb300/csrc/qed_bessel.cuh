@@ -174,8 +174,8 @@ __device__ __forceinline__ void nlc_rates(const TabP<R>& T, R chi, R lnchi, R& I
     }
     int i; R f;
     chi_coord(T, lnchi, i, f);
-    Iu = exp_((R(1) - f) * T.nlc_rate[i] + f * T.nlc_rate[i + 1]);
-    Id = exp_((R(1) - f) * T.nlc_rate[T.n_chi + i] + f * T.nlc_rate[T.n_chi + i + 1]);
+    Iu = exp_(fma_(f, T.nlc_rate[i + 1] - T.nlc_rate[i], T.nlc_rate[i]));
+    Id = exp_(fma_(f, T.nlc_rate[T.n_chi + i + 1] - T.nlc_rate[T.n_chi + i], T.nlc_rate[T.n_chi + i]));
 }
 
 // NBW rate integrals J_+, J_- at chi (zero below chi_min)
@@ -186,8 +186,8 @@ __device__ __forceinline__ void nbw_rates(const TabP<R>& T, R chi, R lnchi, R& J
     chi_coord(T, lnchi, i, f);
     const R chic = chi > T.chi_max ? T.chi_max : chi;
     const R sub = div_(R(8.0 / 3.0), chic);
-    Jp = exp_((R(1) - f) * T.nbw_rate[i] + f * T.nbw_rate[i + 1] - sub);
-    Jm = exp_((R(1) - f) * T.nbw_rate[T.n_chi + i] + f * T.nbw_rate[T.n_chi + i + 1] - sub);
+    Jp = exp_(fma_(f, T.nbw_rate[i + 1] - T.nbw_rate[i], T.nbw_rate[i]) - sub);
+    Jm = exp_(fma_(f, T.nbw_rate[T.n_chi + i + 1] - T.nbw_rate[T.n_chi + i], T.nbw_rate[T.n_chi + i]) - sub);
 }
 
 // one ICDF row at logit y: the cubic through the 4 nearest nodes inside the grid (written in Newton form

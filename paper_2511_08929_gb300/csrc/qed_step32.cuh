@@ -243,8 +243,7 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     const float rg = rcp_(st.gam);
     st.x = xold;
     if (fl & QED_F_MOVE) {
-        const float ig = dt * rg;
-        st.x = F3{xold.x + st.p.x * ig, xold.y + st.p.y * ig, xold.z + st.p.z * ig};
+        st.x = axpy(dt * rg, st.p, xold);
     }
     st.qed = false;
     if (!(fl & QED_F_EMIT)) return;
@@ -402,7 +401,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
         const float D = 1.0f - (W0 + Pi * st.sb) * dt;
         if (D > 0.0f) {
             const float iD = rcp_(D), a1 = (1.0f - W0 * dt) * iD, a2 = Pi * dt * iD;
-            sf = F3{st.s.x * a1 - st.beta.x * a2, st.s.y * a1 - st.beta.y * a2, st.s.z * a1 - st.beta.z * a2};
+            sf = axpy(-a2, st.beta, a1 * st.s);
             if (dot(sf, sf) > 1.0f + kRenormSlack) {
                 sf = renorm64(sf);
                 c[C_RENORM]++;
@@ -434,7 +433,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.en = sqrt_(en2);
     st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
     st.x = xold;
-    if (C.S.flags & QED_F_MOVE) st.x = xold + C.S.dt_f * st.khat;
+    if (C.S.flags & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;
     if (!(C.S.flags & QED_F_EMIT) || !(en2 > 0.0f)) return;
     st.chi = chi_of(C.F.eta0, st.en, st.k, st.E, st.B);
