@@ -103,6 +103,30 @@ def summarize_clocks(lines):
     return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("qed_batch.cu", "qed_step32.cuh", "qed_device.cuh", "qed_bessel.cuh", "qed_steps.h", "qed_internal.h")
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the sources the batched persistent kernel is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_08929_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per particle-step of the batched kernel from the committed ncu summary, if it was taken
+    on the kernel as it is now (same source hash); else None."""
+    p = os.path.join(ROOT, "profiles", "batch_step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d if d.get("source_sha256") == kernel_source_hash() else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -428,9 +452,15 @@ def native_batch(args):
     # 88 B per lepton-step, 76 B per photon-step, 8 B (id) per event, 52 B per stored daughter
     peak, peak_kind = measured_peaks()
     alg = 88.0 * (d_sp[0] + d_sp[1]) + 76.0 * d_sp[2] + 8.0 * ctr.events + 52.0 * ctr.stored
+    tr = measured_traffic()
+    traffic = None
+    if tr is not None:  # ncu DRAM bytes per particle-step of a smaller capture, scaled to this launch
+        traffic = tr["dram_bytes_per_particle_step"] * psteps / K
     roof = {"kernel": "batch_step_kernel", "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
-            "frac": None, "traffic": None, "peak_source": peak_kind,
+            "frac": None, "traffic": traffic, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": alg / K}
+    if tr is not None:
+        roof["traffic_source"] = tr["source"]
     if t_kern:
         tk = sum(t_kern)
         achieved = alg / (tk / 1e3) / 1e9
@@ -598,7 +628,7 @@ def _oracle_field(O, f):
     return O.field(f.kind, a0=f.a0, n_cycles=f.n_cycles, phase=f.phase, E0=tuple(f.E0), B0=tuple(f.B0), eta0=f.eta0)
 
 
-def batch_cpu_baseline(bt, wl, insts, fields, seeds, step0, seconds=15.0, frac=0.02, max_steps=40):
+def batch_cpu_baseline(bt, wl, insts, fields, seeds, step0, seconds=15.0, frac=0.1, max_steps=40):
     """The oracle on a bounded sample of the batch's current state: from every instance the first
     `frac` of its electrons, positrons and photons (at least one of each where present), stepped with
     the instance's own laser and seed for at most max_steps steps and about `seconds` of CPU work."""

@@ -276,7 +276,7 @@ qed_status qed_compact_noalloc(qed_particles *photons, void *stream);
  * qed_push_step, qed_pair_step and qed_compact give per instance with begin snapshots (the same
  * arithmetic and random draws; appended daughters may sit in another order), whatever the tuning. */
 #define QED_BATCH_MAX_INSTANCES 1024
-#define QED_BATCH_VARIANTS 4
+#define QED_BATCH_VARIANTS 5
 
 typedef struct qed_batch_s *qed_batch_t;
 
@@ -296,9 +296,9 @@ typedef struct {
 } qed_batch_desc;
 
 /* Launch shape of the batch step (no effect on results).
- *   variant       kernel build: 0 = 256 threads, 3-stage copies, registers for 3 blocks/SM;
- *                 1 = 256 threads, 3 stages, 2 blocks/SM; 2 = 128 threads, 4 stages, 5 blocks/SM;
- *                 3 = 512 threads, 2 stages, 1 block/SM
+ *   variant       kernel build (threads per block, tiles of 32 particles in flight per warp, registers
+ *                 sized for so many blocks per SM): 0 = 256, 3, 3; 1 = 256, 3, 2; 2 = 256, 2, 4;
+ *                 3 = 512, 2, 1; 4 = 512, 2, 2
  *   blocks_per_sm resident blocks per SM of the persistent grid (0: the occupancy maximum)
  *   chunk         consecutive tiles of 32 particles a warp takes before moving on by the grid's width
  *   graph_steps   time steps captured per CUDA graph (0: launch the kernels directly every step) */

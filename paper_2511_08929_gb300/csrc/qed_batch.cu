@@ -161,8 +161,10 @@ struct WarpSeg {
     int t0, t1, n;  // its tile range and particle count
 };
 
+// shared memory of the batched kernel: the 1-D rate tables (the Bessel table, read only at events, stays
+// in global memory behind L1), the tile list, the per-warp segment state, the tiles, barriers and queues
 __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
-    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * n_chi * 4);
+    size_t off = align128((size_t)4 * n_chi * 4);
     off += align128((size_t)(n_seg + 1) * 4);
     off += align128((size_t)warps * sizeof(WarpSeg));
     off += (size_t)warps * stages * sizeof(Tile);
@@ -173,15 +175,15 @@ __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_
 
 template <int WARPS, int STAGES, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
-    batch_step_kernel(TabP<float> T, const float* __restrict__ bes_g, const InstDev* __restrict__ inst,
+    batch_step_kernel(TabP<float> T, float* bes_g, const InstDev* __restrict__ inst,
                       const SegDev* __restrict__ seg, const int64_t* __restrict__ tile0_g, int n_inst,
                       const ClockDev* __restrict__ clk, BatchP P, int chunk, qed_counters* ctr) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int n_seg = kSpecies * n_inst;
     Shared32 sh;
-    sh.bes = (float*)smem;
-    sh.rates = sh.bes + 3 * kBesN;
-    size_t off = align128((size_t)3 * kBesN * 4 + (size_t)4 * T.n_chi * 4);
+    sh.bes = bes_g;
+    sh.rates = (float*)smem;
+    size_t off = align128((size_t)4 * T.n_chi * 4);
     int* s_tile0 = (int*)(smem + off);
     off += align128((size_t)(n_seg + 1) * 4);
     WarpSeg* s_ws = (WarpSeg*)(smem + off);
@@ -192,7 +194,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     off += (size_t)WARPS * STAGES * 8;
     sh.queue = (int64_t*)(smem + off);
 
-    load_tables32(sh, bes_g, T);
+    for (int i = threadIdx.x; i < 2 * T.n_chi; i += blockDim.x) {
+        sh.rates[i] = T.nlc_rate[i];
+        sh.rates[2 * T.n_chi + i] = T.nbw_rate[i];
+    }
     for (int i = threadIdx.x; i <= n_seg; i += blockDim.x) s_tile0[i] = (int)tile0_g[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Tile* tile = sh.tiles + warp * STAGES;
@@ -448,8 +453,9 @@ static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
 static const BatchVariant kVariants[QED_BATCH_VARIANTS] = {
     {(const void*)batch_step_kernel<8, 3, 3>, 8, 3, launch_variant<8, 3, 3>},
     {(const void*)batch_step_kernel<8, 3, 2>, 8, 3, launch_variant<8, 3, 2>},
-    {(const void*)batch_step_kernel<4, 4, 5>, 4, 4, launch_variant<4, 4, 5>},
+    {(const void*)batch_step_kernel<8, 2, 4>, 8, 2, launch_variant<8, 2, 4>},
     {(const void*)batch_step_kernel<16, 2, 1>, 16, 2, launch_variant<16, 2, 1>},
+    {(const void*)batch_step_kernel<16, 2, 2>, 16, 2, launch_variant<16, 2, 2>},
 };
 
 static size_t variant_smem(const qed_batch_s* b, int v) {

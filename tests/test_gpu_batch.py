@@ -172,7 +172,8 @@ def test_batch_matches_single_buffer_path(gpu_tables):
 @pytest.mark.gpu
 @pytest.mark.parametrize("tuning", [dict(variant=1, blocks_per_sm=1, chunk=1, graph_steps=0),
                                     dict(variant=2, blocks_per_sm=0, chunk=16, graph_steps=7),
-                                    dict(variant=3, blocks_per_sm=0, chunk=3, graph_steps=1)])
+                                    dict(variant=3, blocks_per_sm=0, chunk=3, graph_steps=1),
+                                    dict(variant=4, blocks_per_sm=0, chunk=2, graph_steps=3)])
 def test_batch_launch_shape_changes_nothing(gpu_tables, tuning):
     specs = _specs()
     steps = 16
@@ -278,7 +279,7 @@ def test_autotuner_picks_and_caches(gpu_tables, tmp_path):
     t1 = bt.tune(1, path)
     s1 = bt.stats().step
     assert s1 > s0  # the tuner's timed steps are real steps
-    assert 0 <= t1.variant < 4 and t1.blocks_per_sm >= 1 and t1.chunk in (1, 4, 16) and t1.graph_steps == 8
+    assert 0 <= t1.variant < 5 and t1.blocks_per_sm >= 1 and t1.chunk in (1, 4, 16) and t1.graph_steps == 8
     lines = open(path).read().strip().splitlines()
     assert len(lines) == 1 and '"variant": %d' % t1.variant in lines[0]
     t2 = bt.tune(1, path)  # cached: no timing, no steps
