@@ -144,6 +144,9 @@ def lib():
             L.orc_init_tau.argtypes = [_P(_Particles), C.c_uint64]
             L.orc_psi.restype = _D
             L.orc_psi.argtypes = [_D, C.c_int]
+            L.orc_mlp_target.argtypes = [_D, _D, _D, _P(_D)]
+            L.orc_mlp_cdf.restype = _D
+            L.orc_mlp_cdf.argtypes = [_D, _D, _D]
             L.orc_num_threads.restype = C.c_int
             L.orc_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -244,6 +247,19 @@ def set_quadrature(n_points: int, width: float):
 
 def psi(chi: float, which: int) -> float:
     return lib().orc_psi(float(chi), int(which))
+
+
+def mlp_target(chi: float, r: float, s: float):
+    """(ln u', xi1, xi2, xi3): the exact r-quantile of the NLC spectrum with spin projection s and the
+    photon Stokes vector there (final spin summed) -- the learned sampler's target."""
+    out = (_D * 4)()
+    lib().orc_mlp_target(float(chi), float(r), float(s), out)
+    return np.array(out[:])
+
+
+def mlp_cdf(chi: float, s: float, ln_up: float) -> float:
+    """Exact mixture CDF of the NLC spectrum with spin projection s at u' = exp(ln_up)."""
+    return lib().orc_mlp_cdf(float(chi), float(s), float(ln_up))
 
 
 def nlc_lambda(chi, up):

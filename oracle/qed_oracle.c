@@ -1216,3 +1216,83 @@ void orc_set_num_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Target of the learned sampler.  Sec. 4.1 samples the photon energy from    */
+/* the spin-resolved spectrum w(lambda; s_beta) and notes that a direct table */
+/* in (chi, r, s_beta) costs memory; a small network stands in for that 3-D   */
+/* inverse CDF.  Its target, written out from the definition:                 */
+/*   the r-quantile of w(lambda; s) in u' (t = u'^{1/3}):                      */
+/*     C_s(t) = int_0^t [w(s) d lambda/dt'] dt' / int_0^T [...] dt',           */
+/*     w(s) = -IntK13 + kappa K23 + lambda s K13  (linear in s, so the blend   */
+/*     of the two branch integrands with weights (1 +- s)/2);                  */
+/*   the photon Stokes vector at that lambda, final lepton spin summed         */
+/*   (s_f = 0), initial spin s_i = s beta_hat, basis eps = x, beta = y, k = z: */
+/*     xi_i = F_i / F_0 (App. A.1).                                            */
+/* out = {ln u', xi1, xi2, xi3}.  The exact mixture CDF at u' is              */
+/* orc_mlp_cdf.                                                                */
+/* ------------------------------------------------------------------------- */
+static double mix_integrand_t(double chi, double s, double t)
+{
+    return 0.5 * (1.0 + s) * nlc_integrand_t(chi, 1, t) + 0.5 * (1.0 - s) * nlc_integrand_t(chi, -1, t);
+}
+
+static double mix_segment(double chi, double s, double a, double b)
+{
+    gl_init();
+    double m = 0.5 * (a + b), r = 0.5 * (b - a), acc = 0.0;
+    for (int i = 0; i < gl_n; ++i) acc += gl_w[i] * mix_integrand_t(chi, s, m + r * gl_x[i]);
+    return acc * r;
+}
+
+/* exact C_s at u' (the quantity the learned sampler's check compares with r) */
+double orc_mlp_cdf(double chi, double s, double ln_up)
+{
+    double T = t_end(0), t = exp(ln_up / 3.0), total = 0.0, part = 0.0;
+    int np = (int)ceil(T / ORC_PANEL_W);
+    for (int p = 0; p < np; ++p) {
+        double a = p * ORC_PANEL_W, b = fmin(T, (p + 1) * ORC_PANEL_W);
+        double seg = mix_segment(chi, s, a, b);
+        total += seg;
+        if (b <= t) part += seg;
+        else if (a < t) part += mix_segment(chi, s, a, t);
+    }
+    return part / total;
+}
+
+void orc_mlp_target(double chi, double r, double s, double out[4])
+{
+    double T = t_end(0);
+    int np = (int)ceil(T / ORC_PANEL_W);
+    double *cum = (double *)malloc(sizeof(double) * (np + 1));
+    cum[0] = 0.0;
+    for (int p = 0; p < np; ++p) {
+        double a = p * ORC_PANEL_W, b = fmin(T, (p + 1) * ORC_PANEL_W);
+        cum[p + 1] = cum[p] + mix_segment(chi, s, a, b);
+    }
+    /* solve C_s(t) = r: the panel that brackets r, then Newton (derivative = integrand) kept in the bracket */
+    double target = r * cum[np];
+    int p = 0;
+    while (p < np - 1 && cum[p + 1] < target) ++p;
+    double a = p * ORC_PANEL_W, b = fmin(T, (p + 1) * ORC_PANEL_W), base = cum[p];
+    double lo = a, hi = b, t = a + (b - a) * (target - base) / (cum[p + 1] - base);
+    for (int it = 0; it < 200; ++it) {
+        double f = base + mix_segment(chi, s, a, t) - target;
+        if (f > 0) hi = t; else lo = t;
+        double tn = t - f / mix_integrand_t(chi, s, t);
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        if (fabs(tn - t) <= 1e-15 * fmax(t, 1e-300) || hi - lo <= 1e-15 * hi) { t = tn; break; }
+        t = tn;
+    }
+    free(cum);
+    double up = t * t * t, bes[3], F[4];
+    double lam = orc_nlc_lambda(chi, up);
+    orc_bessel(up, bes);
+    const double si[3] = {0.0, s, 0.0}, sf[3] = {0.0, 0.0, 0.0};
+    const double eps[3] = {1.0, 0.0, 0.0}, beta[3] = {0.0, 1.0, 0.0}, k[3] = {0.0, 0.0, 1.0};
+    orc_nlc_stokes(lam, bes, si, sf, eps, beta, k, F);
+    out[0] = 3.0 * log(t);
+    out[1] = F[1] / F[0];
+    out[2] = F[2] / F[0];
+    out[3] = F[3] / F[0];
+}
