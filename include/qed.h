@@ -343,6 +343,55 @@ qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate, const char
 qed_status qed_batch_stats_read(qed_batch_t b, qed_batch_stats *out, void *stream);
 void qed_batch_destroy(qed_batch_t b);
 
+/* ---- Learned sampler (no counterpart code in the paper; Sec. 4.1 rejects a direct table in
+ * (chi, r, s_beta) for its memory, and this network stands in for it) ----
+ * Network 3 -> 64 -> 64 -> 64 -> 4 with SiLU.  Inputs ((ln chi - m)/h over chi in [1e-3, 1e2],
+ * clamp(logit r, +-20)/10, s_beta).  Outputs: 100 x the corrections to the rate-weighted blend of the two
+ * spin-branch quantiles ln u'(chi, r) of the tables (and to xi3 there), and 100 xi1, 100 xi2.  Layer 1
+ * runs in FP32; layers 2-4 take BF16-rounded weights and activations on tensor cores with FP32
+ * accumulation.  Parameters: one FP32 array of QED_MLP_PARAMS = W1[64][3] b1[64] W2[64][64] b2[64]
+ * W3[64][64] b3[64] W4[4][64] b4[4] (weights row = output unit). */
+#define QED_MLP_PARAMS 8836
+#define QED_MLP_ALWAYS_TABLE 1 /* qed_mlp_sample flag: skip the network (the table path, for comparison) */
+
+typedef struct qed_mlp_s *qed_mlp_t;
+
+/* A network with the given initial parameters (host array of QED_MLP_PARAMS floats) and device scratch
+ * for training batches of up to max_batch samples.  Errors: QED_ERR_ARG, QED_ERR_NOMEM, QED_ERR_CUDA. */
+qed_status qed_mlp_create(int64_t max_batch, const float *init_params, qed_mlp_t *out);
+void qed_mlp_destroy(qed_mlp_t m);
+/* Copy the parameters to / from host memory (setting resets the optimiser state).  Synchronous. */
+qed_status qed_mlp_get_params(qed_mlp_t m, float *host_out);
+qed_status qed_mlp_set_params(qed_mlp_t m, const float *host_in);
+/* Training samples from the FP64 tables: sample first_index + i draws chi (log-uniform over [1e-3, 1e2]),
+ * r and s_beta (uniform) from Philox(id = first_index + i, seed, step 2^64 - 2, slots 0 and 1); x_dev gets
+ * its n x 3 features, y_dev its n x 4 targets (the exact mixture quantile, found by bisection between
+ * the branch quantiles on the mixture CDF of the interpolated branch rows, and xi3 there, minus the
+ * blend baseline, times 100), raw_dev (may be NULL) n x 3 doubles (chi, r, s_beta). */
+qed_status qed_mlp_targets(qed_tables_t t, int64_t n, uint64_t seed, int64_t first_index, float *x_dev, float *y_dev,
+                           double *raw_dev, void *stream);
+/* Forward and backward pass of one batch (n <= max_batch): grad_dev gets dL/dparameters for
+ * L = mean over the batch of the squared error summed over the four outputs; loss_dev (may be NULL) L. */
+qed_status qed_mlp_grad(qed_mlp_t m, const float *x_dev, const float *y_dev, int64_t n, float *grad_dev,
+                        float *loss_dev, void *stream);
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay on weights only). */
+qed_status qed_mlp_adamw(qed_mlp_t m, const float *grad_dev, float lr, float weight_decay, void *stream);
+/* steps x (fresh batch of targets at first_index + k batch, forward, backward, AdamW), learning rate
+ * decaying from lr to lr_final on a cosine; loss_per_step_dev (may be NULL) gets each step's loss. */
+qed_status qed_mlp_train(qed_mlp_t m, qed_tables_t t, int64_t steps, int64_t batch, uint64_t seed, int64_t first_index,
+                         float lr, float lr_final, float weight_decay, float *loss_per_step_dev, void *stream);
+/* Raw network outputs (n x 4) for feature rows x_dev (n x 3), on tensor cores. */
+qed_status qed_mlp_forward(qed_mlp_t m, const float *x_dev, int64_t n, float *out_dev, void *stream);
+/* The sampler: for device arrays chi, r, s_beta (n doubles each), out4 (n x 4 floats) = (ln u', xi1,
+ * xi2, xi3) from the network, checked: the exact mixture CDF of the tables at ln u' must be within tol of
+ * r and the Stokes vector within tol of its closed form there, else (or with QED_MLP_ALWAYS_TABLE) the
+ * table path (the mixture quantile by bisection, the closed-form Stokes vector).  fell_back (n bytes,
+ * may be NULL) marks the samples that took the table path; *n_fallback (device, may be NULL) is
+ * incremented by their number. */
+qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double *chi, const double *r, const double *s_beta,
+                          int64_t n, double tol, int32_t flags, float *out4, uint8_t *fell_back,
+                          unsigned long long *n_fallback, void *stream);
+
 /* *begin = *count for each of the n buffers (device-side copy; graph-capturable).  Call it at the start
  * of a time step that runs several step calls, so each call processes only the particles alive when the
  * step began (Sec. 3.3: an event's daughters join the simulation from the next step).  Buffers whose

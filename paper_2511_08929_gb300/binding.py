@@ -141,6 +141,16 @@ def lib():
                 "qed_batch_tune": (i32, [vp, i32, C.c_char_p, P(QedBatchTuning), vp]),
                 "qed_batch_stats_read": (i32, [vp, P(QedBatchStats), vp]),
                 "qed_batch_destroy": (None, [vp]),
+                "qed_mlp_create": (i32, [i64, vp, P(vp)]),
+                "qed_mlp_destroy": (None, [vp]),
+                "qed_mlp_get_params": (i32, [vp, vp]),
+                "qed_mlp_set_params": (i32, [vp, vp]),
+                "qed_mlp_targets": (i32, [vp, i64, u64, i64, vp, vp, vp, vp]),
+                "qed_mlp_grad": (i32, [vp, vp, vp, i64, vp, vp, vp]),
+                "qed_mlp_adamw": (i32, [vp, vp, C.c_float, C.c_float, vp]),
+                "qed_mlp_train": (i32, [vp, vp, i64, i64, u64, i64, C.c_float, C.c_float, C.c_float, vp, vp]),
+                "qed_mlp_forward": (i32, [vp, vp, i64, vp, vp]),
+                "qed_mlp_sample": (i32, [vp, vp, vp, vp, vp, i64, C.c_double, i32, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -285,6 +295,68 @@ def qed_batch_stats_read(batch: int, stream: int = 0) -> QedBatchStats:
 def qed_batch_destroy(batch: int):
     if batch:
         lib().qed_batch_destroy(batch)
+
+
+QED_MLP_PARAMS = int(re.search(r"#define QED_MLP_PARAMS (\d+)", open(HEADER).read()).group(1))
+QED_MLP_ALWAYS_TABLE = 1
+
+
+def qed_mlp_create(max_batch: int, init_params) -> int:
+    """init_params: float32 numpy array of QED_MLP_PARAMS values."""
+    a = np.ascontiguousarray(init_params, dtype=np.float32)
+    if a.size != QED_MLP_PARAMS:
+        raise ValueError(f"expected {QED_MLP_PARAMS} parameters, got {a.size}")
+    h = C.c_void_p()
+    _check(lib().qed_mlp_create(max_batch, a.ctypes.data, C.byref(h)), "qed_mlp_create")
+    return h.value
+
+
+def qed_mlp_destroy(m: int):
+    if m:
+        lib().qed_mlp_destroy(m)
+
+
+def qed_mlp_get_params(m: int) -> np.ndarray:
+    out = np.empty(QED_MLP_PARAMS, dtype=np.float32)
+    _check(lib().qed_mlp_get_params(m, out.ctypes.data), "qed_mlp_get_params")
+    return out
+
+
+def qed_mlp_set_params(m: int, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != QED_MLP_PARAMS:
+        raise ValueError(f"expected {QED_MLP_PARAMS} parameters, got {a.size}")
+    _check(lib().qed_mlp_set_params(m, a.ctypes.data), "qed_mlp_set_params")
+
+
+def qed_mlp_targets(tables: int, n: int, seed: int, first_index: int, x_dev: int, y_dev: int, raw_dev: int = 0,
+                    stream: int = 0):
+    _check(lib().qed_mlp_targets(tables, n, seed, first_index, x_dev, y_dev, raw_dev or None, stream or None),
+           "qed_mlp_targets")
+
+
+def qed_mlp_grad(m: int, x_dev: int, y_dev: int, n: int, grad_dev: int, loss_dev: int = 0, stream: int = 0):
+    _check(lib().qed_mlp_grad(m, x_dev, y_dev, n, grad_dev, loss_dev or None, stream or None), "qed_mlp_grad")
+
+
+def qed_mlp_adamw(m: int, grad_dev: int, lr: float, weight_decay: float, stream: int = 0):
+    _check(lib().qed_mlp_adamw(m, grad_dev, lr, weight_decay, stream or None), "qed_mlp_adamw")
+
+
+def qed_mlp_train(m: int, tables: int, steps: int, batch: int, seed: int, first_index: int, lr: float,
+                  lr_final: float, weight_decay: float, loss_dev: int = 0, stream: int = 0):
+    _check(lib().qed_mlp_train(m, tables, steps, batch, seed, first_index, lr, lr_final, weight_decay,
+                               loss_dev or None, stream or None), "qed_mlp_train")
+
+
+def qed_mlp_forward(m: int, x_dev: int, n: int, out_dev: int, stream: int = 0):
+    _check(lib().qed_mlp_forward(m, x_dev, n, out_dev, stream or None), "qed_mlp_forward")
+
+
+def qed_mlp_sample(m: int, tables: int, chi_dev: int, r_dev: int, s_dev: int, n: int, tol: float, flags: int,
+                   out_dev: int, fell_dev: int = 0, n_fallback_dev: int = 0, stream: int = 0):
+    _check(lib().qed_mlp_sample(m, tables, chi_dev, r_dev, s_dev, n, tol, flags, out_dev, fell_dev or None,
+                                n_fallback_dev or None, stream or None), "qed_mlp_sample")
 
 
 def declared_entry_points():

@@ -1,0 +1,705 @@
+// qed_mlp.cu -- the learned sampler: a 3-64-64-64-4 SiLU network standing in for the three-dimensional
+// inverse CDF in (chi, r, s_beta) that Sec. 4.1 rejects for its memory.
+//
+// Target (the map the network learns, computed from the FP64 tables): the exact r-quantile ln u' of the
+// NLC spectrum for a continuous spin projection s (w is linear in s: the mixture CDF is the rate-weighted
+// blend of the two branch CDFs, each the inverse of its interpolated ICDF row) and the photon Stokes
+// vector there (App. A.1, s_i = s beta_hat, final spin summed: xi1 = xi2 = 0, xi3 = F3/F0).  The network
+// predicts the correction to the rate-weighted blend of the two branch quantiles (and of xi3 there),
+// scaled by 100.
+//
+// Kernels: target generation (FP64), a BF16 tensor-core GEMM with FP32 accumulation (mma.sync m16n8k16;
+// split-K for the weight gradients), FP32 elementwise / first-layer / reduction / AdamW kernels for
+// training, and a fused inference kernel whose layer outputs stay in registers as the next layer's
+// tensor-core operands, followed by the CDF check and the table fallback.
+#include <cstring>
+
+#include <cuda_bf16.h>
+
+#include "qed_device.cuh"
+#include "qed_internal.h"
+
+namespace qed {
+
+// ---- parameter layout (FP32, one array): W1[64][3] b1[64] W2[64][64] b2 W3[64][64] b3 W4[4][64] b4[4]
+constexpr int kH = 64;
+constexpr int kOffW1 = 0, kOffB1 = 192, kOffW2 = 256, kOffB2 = 4352, kOffW3 = 4416, kOffB3 = 8512, kOffW4 = 8576,
+              kOffB4 = 8832, kParams = 8836;
+static_assert(kParams == QED_MLP_PARAMS, "parameter count");
+
+constexpr double kLnChiLo = -6.907755278982137, kLnChiHi = 4.605170185988092;  // ln 1e-3, ln 1e2
+constexpr double kYClamp = 20.0;
+constexpr double kOutScale = 100.0;
+constexpr uint64_t kMlpStep = 0xFFFFFFFFFFFFFFFEull;  // reserved Philox step of the training inputs
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+    const float s = 1.0f / (1.0f + expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// ---- the map from (chi, r, s) to the target, FP64 tables -------------------------------------------
+struct MixPoint {
+    double lnchi, y, s, a;  // a = (1 + s) I_up / ((1 + s) I_up + (1 - s) I_down)
+};
+
+__device__ inline MixPoint mix_point(const TabP<double>& T, double chi, double r, double s) {
+    MixPoint m;
+    m.lnchi = log(chi);
+    m.y = log(r) - log1p(-r);
+    m.s = s;
+    double Iu, Id;
+    nlc_rates(T, chi, m.lnchi, Iu, Id);
+    m.a = (1.0 + s) * Iu / ((1.0 + s) * Iu + (1.0 - s) * Id);
+    return m;
+}
+
+// CDF of one spin branch at ln u' = L: the logit y at which the interpolated ICDF equals L (bisection on
+// the monotone interpolant; the linear asymptote below the grid is inverted directly), mapped to r
+template <int ITERS>
+__device__ inline double branch_cdf(const TabP<double>& T, int b, double lnchi, double L) {
+    const double top = icdf_lookup(T, false, b, lnchi, T.y_lo + (T.n_r - 1) / T.inv_dy);
+    if (L >= top) return 1.0;
+    const double bot = icdf_lookup(T, false, b, lnchi, T.y_lo);
+    double y;
+    if (L <= bot) {
+        y = T.y_lo + (L - bot) / 3.0;  // slope 3 of ln u' in y below the grid (u' ~ r^3)
+    } else {
+        double lo = T.y_lo, hi = T.y_lo + (T.n_r - 1) / T.inv_dy;
+        for (int it = 0; it < ITERS; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (icdf_lookup(T, false, b, lnchi, mid) < L) lo = mid;
+            else hi = mid;
+        }
+        y = 0.5 * (lo + hi);
+    }
+    return 1.0 / (1.0 + exp(-y));
+}
+
+// ITERS bisection steps on y in [-20, 20]: 30 leave the CDF within 1e-8, 48 within 1e-13
+template <int ITERS>
+__device__ inline double mix_cdf(const TabP<double>& T, const MixPoint& m, double L) {
+    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L) + (1.0 - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L);
+}
+
+// the blend of the two branch quantiles (the baseline the network corrects)
+__device__ inline double mix_baseline(const TabP<double>& T, const MixPoint& m) {
+    return m.a * icdf_lookup(T, false, 0, m.lnchi, m.y) + (1.0 - m.a) * icdf_lookup(T, false, 1, m.lnchi, m.y);
+}
+
+// the exact mixture quantile: the mixture CDF lies between the branch CDFs, so its quantile lies between
+// the branch quantiles; bisection there
+template <int OUTER, int INNER>
+__device__ inline double mix_quantile(const TabP<double>& T, const MixPoint& m, double r) {
+    const double qu = icdf_lookup(T, false, 0, m.lnchi, m.y), qd = icdf_lookup(T, false, 1, m.lnchi, m.y);
+    double lo = fmin(qu, qd) - 1e-9, hi = fmax(qu, qd) + 1e-9;
+    for (int it = 0; it < OUTER; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mix_cdf<INNER>(T, m, mid) < r) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// xi3 = F3 / F0 at u' for s_i = s beta_hat, s_f = 0 (App. A.1)
+__device__ inline double xi3_at(const double* __restrict__ bes_tab, double chi, double L, double s) {
+    // a network output outside any physical range (or not finite) never reaches the Bessel evaluation
+    if (!(L > -200.0 && L < 50.0)) return nan("");
+    const double up = exp(L);
+    const double lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up), one_m = 1.0 - lam;
+    double b[3];
+    bessel64(bes_tab, up, b);
+    const double u = lam / one_m, kappa = 1.0 / one_m + one_m;
+    return (b[1] + u * s * b[0]) / (-b[2] + kappa * b[1] + lam * s * b[0]);
+}
+
+__device__ inline void mlp_features(double chi, double r, double s, float x[3]) {
+    const double y = fmin(kYClamp, fmax(-kYClamp, log(r) - log1p(-r)));
+    x[0] = (float)((log(chi) - 0.5 * (kLnChiLo + kLnChiHi)) / (0.5 * (kLnChiHi - kLnChiLo)));
+    x[1] = (float)(y / 10.0);
+    x[2] = (float)s;
+}
+
+__global__ void mlp_targets_kernel(TabP<double> T, const double* __restrict__ bes_tab, int64_t n, uint64_t seed,
+                                   int64_t first, float* __restrict__ X, float* __restrict__ Y, double* __restrict__ raw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t id = (uint64_t)(first + i);
+        const uint4 w0 = draw(id, seed, kMlpStep, 0), w1 = draw(id, seed, kMlpStep, 1);
+        const double lnchi = kLnChiLo + uniform52(w0.x, w0.y) * (kLnChiHi - kLnChiLo);
+        const double chi = exp(lnchi), r = uniform52(w0.z, w0.w), s = 2.0 * uniform52(w1.x, w1.y) - 1.0;
+        const MixPoint m = mix_point(T, chi, r, s);
+        const double Lb = mix_baseline(T, m), L = mix_quantile<56, 48>(T, m, r);
+        float x[3];
+        mlp_features(chi, r, s, x);
+        X[3 * i] = x[0];
+        X[3 * i + 1] = x[1];
+        X[3 * i + 2] = x[2];
+        Y[4 * i] = (float)(kOutScale * (L - Lb));
+        Y[4 * i + 1] = 0.0f;
+        Y[4 * i + 2] = 0.0f;
+        Y[4 * i + 3] = (float)(kOutScale * (xi3_at(bes_tab, chi, L, s) - xi3_at(bes_tab, chi, Lb, s)));
+        if (raw) {
+            raw[3 * i] = chi;
+            raw[3 * i + 1] = r;
+            raw[3 * i + 2] = s;
+        }
+    }
+}
+
+// ---- BF16 tensor-core GEMM (FP32 in global memory, rounded to BF16 when staged; FP32 accumulation) -----
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower 16 bits), .y = hi
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kGM = 64, kGN = 64, kGK = 32, kGP = kGK + 8;  // tile and padded row pitch (bf16 elements)
+
+// C(m, n) (+)= sum_k A(m, k) B(k, n); A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn];
+// C row-major with leading dimension ldc.  grid = (ceil(N/64), ceil(M/64), ksplit); with ksplit > 1
+// the partial sums are added atomically (C zeroed by the caller).
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, int64_t sam,
+                                                         int64_t sak, const float* __restrict__ B, int64_t sbk,
+                                                         int64_t sbn, float* __restrict__ C, int64_t ldc, int ksplit) {
+    __shared__ __align__(16) __nv_bfloat16 As[kGM][kGP];
+    __shared__ __align__(16) __nv_bfloat16 Bs[kGN][kGP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
+    const int kchunk = ((K + ksplit - 1) / ksplit + kGK - 1) / kGK * kGK;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+    for (int k0 = kb; k0 < ke; k0 += kGK) {
+        for (int e = threadIdx.x; e < kGM * kGK; e += 128) {
+            const int mm = e / kGK, kk = e % kGK, m = m0 + mm, k = k0 + kk;
+            As[mm][kk] = __float2bfloat16_rn(m < M && k < ke ? A[m * sam + k * sak] : 0.0f);
+        }
+        for (int e = threadIdx.x; e < kGN * kGK; e += 128) {
+            const int nn = e / kGK, kk = e % kGK, n = n0 + nn, k = k0 + kk;
+            Bs[nn][kk] = __float2bfloat16_rn(n < N && k < ke ? B[k * sbk + n * sbn] : 0.0f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kGK; ks += 16) {
+            uint32_t a[4];
+            const int r0 = warp * 16 + g;
+            a[0] = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * t]);
+            a[1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * t]);
+            a[2] = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 8 + 2 * t]);
+            a[3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 8 + 2 * t]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[8 * j + g][ks + 2 * t]);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[8 * j + g][ks + 8 + 2 * t]);
+                mma_bf16(acc[j], a, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int m = m0 + warp * 16 + g + (h >> 1) * 8, n = n0 + 8 * j + 2 * t + (h & 1);
+            if (m < M && n < N) {
+                if (ksplit > 1) atomicAdd(&C[m * ldc + n], acc[j][h]);
+                else C[m * ldc + n] = acc[j][h];
+            }
+        }
+    }
+}
+
+// ---- training kernels (FP32) ------------------------------------------------------------------------
+// layer 1: Z1 = X W1^T + b1, H1 = silu(Z1)
+__global__ void mlp_layer1_kernel(const float* __restrict__ P, const float* __restrict__ X, int64_t n, float* Z,
+                                  float* H) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kH; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / kH;
+        const int j = (int)(e % kH);
+        const float* w = P + kOffW1 + 3 * j;
+        const float z = fmaf(w[0], X[3 * b], fmaf(w[1], X[3 * b + 1], fmaf(w[2], X[3 * b + 2], P[kOffB1 + j])));
+        Z[e] = z;
+        H[e] = silu_f(z);
+    }
+}
+
+// Z += bias (in place), H = silu(Z)
+__global__ void mlp_bias_silu_kernel(const float* __restrict__ bias, int64_t n, float* Z, float* H) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kH; e += (int64_t)gridDim.x * blockDim.x) {
+        const float z = Z[e] + bias[e % kH];
+        Z[e] = z;
+        H[e] = silu_f(z);
+    }
+}
+
+// O += b4; dO = 2 (O - T) / n; loss += sum (O - T)^2 / n
+__global__ void mlp_out_loss_kernel(const float* __restrict__ P, const float* __restrict__ Tg, int64_t n, float* O,
+                                    float* dO, float* loss) {
+    float acc = 0.0f;
+    const float inv = 1.0f / (float)n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * 4; e += (int64_t)gridDim.x * blockDim.x) {
+        const float o = O[e] + P[kOffB4 + (e & 3)];
+        O[e] = o;
+        const float d = o - Tg[e];
+        dO[e] = 2.0f * d * inv;
+        acc = fmaf(d * inv, d, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc);
+}
+
+// dZ = dH * silu'(Z) (in place on dH)
+__global__ void mlp_silu_back_kernel(const float* __restrict__ Z, int64_t n, float* dH) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kH; e += (int64_t)gridDim.x * blockDim.x)
+        dH[e] *= dsilu_f(Z[e]);
+}
+
+// column sums of D[n][w] into out[w] (one block per column; deterministic order)
+__global__ void mlp_colsum_kernel(const float* __restrict__ D, int64_t n, int w, float* out) {
+    __shared__ float red[32];
+    const int col = blockIdx.x;
+    float acc = 0.0f;
+    for (int64_t b = threadIdx.x; b < n; b += blockDim.x) acc += D[b * w + col];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) out[col] = acc;
+    }
+}
+
+// dW1[j][i] = sum_b dZ1[b][j] X[b][i] (one block per entry, FP32)
+__global__ void mlp_dw1_kernel(const float* __restrict__ dZ, const float* __restrict__ X, int64_t n, float* g) {
+    __shared__ float red[32];
+    const int j = blockIdx.x / 3, i = blockIdx.x % 3;
+    float acc = 0.0f;
+    for (int64_t b = threadIdx.x; b < n; b += blockDim.x) acc = fmaf(dZ[b * kH + j], X[3 * b + i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) g[kOffW1 + 3 * j + i] = acc;
+    }
+}
+
+__device__ __forceinline__ bool is_weight(int k) {
+    return k < kOffB1 || (k >= kOffW2 && k < kOffB2) || (k >= kOffW3 && k < kOffB3) || (k >= kOffW4 && k < kOffB4);
+}
+
+// AdamW (decoupled weight decay on weights only); t = step count after this update
+__global__ void mlp_adamw_kernel(float* P, float* Mm, float* Vv, const float* __restrict__ G, float lr, float wd,
+                                 float b1t, float b2t) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kParams) return;
+    const float g = G[k];
+    const float m = 0.9f * Mm[k] + 0.1f * g;
+    const float v = 0.999f * Vv[k] + 0.001f * g * g;
+    Mm[k] = m;
+    Vv[k] = v;
+    const float mh = m / (1.0f - b1t), vh = v / (1.0f - b2t);
+    float upd = mh / (sqrtf(vh) + 1e-8f);
+    if (is_weight(k)) upd += wd * P[k];
+    P[k] -= lr * upd;
+}
+
+// ---- fused inference: layers 2-4 on tensor cores with the fragments chained in registers -------------
+constexpr int kIW = 4;       // warps per block
+constexpr int kWP = kH + 8;  // padded row pitch of the BF16 weights in shared memory
+
+struct InferShared {
+    float w1[kOffW2];          // W1, b1 (FP32)
+    float b2[kH], b3[kH], b4[8];
+    __nv_bfloat16 w2[kH][kWP], w3[kH][kWP], w4[8][kWP];  // W4 padded to 8 rows
+    float out[kIW][32][4];
+    int64_t queue[kIW][64];  // sampler: indices of samples waiting for the table path
+};
+
+// one 16-sample row tile: inputs x (rows g and g + 8 of this lane), outputs o (16 x 4, into out rows)
+__device__ __forceinline__ void infer_tile(const InferShared& S, const float xg[3], const float xh[3], int g, int t,
+                                           float (*out)[4]) {
+    // layer 1 (FP32) straight into the A operand of layer 2: k-step s holds columns 16s + 2t, +1, +8, +9
+    uint32_t a[4][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int col = 16 * s + 2 * t + (q & 1) + (q >> 1) * 8;
+            const float* w = S.w1 + 3 * col;
+            const float b = S.w1[kOffB1 + col];
+            v[2 * q] = silu_f(fmaf(w[0], xg[0], fmaf(w[1], xg[1], fmaf(w[2], xg[2], b))));
+            v[2 * q + 1] = silu_f(fmaf(w[0], xh[0], fmaf(w[1], xh[1], fmaf(w[2], xh[2], b))));
+        }
+        a[s][0] = pack_bf16(v[0], v[2]);  // row g, columns c, c + 1
+        a[s][1] = pack_bf16(v[1], v[3]);  // row g + 8
+        a[s][2] = pack_bf16(v[4], v[6]);  // row g, columns c + 8, c + 9
+        a[s][3] = pack_bf16(v[5], v[7]);  // row g + 8
+    }
+    float c[8][4];
+    // layers 2 and 3
+#pragma unroll
+    for (int layer = 0; layer < 2; ++layer) {
+        const __nv_bfloat16(*W)[kWP] = layer == 0 ? S.w2 : S.w3;
+        const float* bias = layer == 0 ? S.b2 : S.b3;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&W[8 * j + g][16 * s + 2 * t]);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&W[8 * j + g][16 * s + 8 + 2 * t]);
+                mma_bf16(c[j], a[s], b0, b1);
+            }
+        }
+        // bias + SiLU, repacked as the next layer's A operand (n-tiles 2s, 2s + 1 form k-step s)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int c0 = 16 * s + 2 * t, c1 = c0 + 8;
+            a[s][0] = pack_bf16(silu_f(c[2 * s][0] + bias[c0]), silu_f(c[2 * s][1] + bias[c0 + 1]));
+            a[s][1] = pack_bf16(silu_f(c[2 * s][2] + bias[c0]), silu_f(c[2 * s][3] + bias[c0 + 1]));
+            a[s][2] = pack_bf16(silu_f(c[2 * s + 1][0] + bias[c1]), silu_f(c[2 * s + 1][1] + bias[c1 + 1]));
+            a[s][3] = pack_bf16(silu_f(c[2 * s + 1][2] + bias[c1]), silu_f(c[2 * s + 1][3] + bias[c1 + 1]));
+        }
+    }
+    // layer 4 (4 outputs in an 8-column tile)
+    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w4[g][16 * s + 2 * t]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w4[g][16 * s + 8 + 2 * t]);
+        mma_bf16(o, a[s], b0, b1);
+    }
+    if (t < 2) {
+        out[g][2 * t] = o[0] + S.b4[2 * t];
+        out[g][2 * t + 1] = o[1] + S.b4[2 * t + 1];
+        out[g + 8][2 * t] = o[2] + S.b4[2 * t];
+        out[g + 8][2 * t + 1] = o[3] + S.b4[2 * t + 1];
+    }
+}
+
+__device__ void load_infer_shared(InferShared& S, const float* __restrict__ P) {
+    for (int i = threadIdx.x; i < kOffW2; i += blockDim.x) S.w1[i] = P[i];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        S.b2[i] = P[kOffB2 + i];
+        S.b3[i] = P[kOffB3 + i];
+    }
+    for (int i = threadIdx.x; i < 8; i += blockDim.x) S.b4[i] = i < 4 ? P[kOffB4 + i] : 0.0f;
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+        S.w2[i / kH][i % kH] = __float2bfloat16_rn(P[kOffW2 + i]);
+        S.w3[i / kH][i % kH] = __float2bfloat16_rn(P[kOffW3 + i]);
+    }
+    for (int i = threadIdx.x; i < 8 * kH; i += blockDim.x)
+        S.w4[i / kH][i % kH] = __float2bfloat16_rn(i < 4 * kH ? P[kOffW4 + i] : 0.0f);
+}
+
+// raw network outputs for feature rows X[n][3]
+__global__ void __launch_bounds__(kIW * 32) mlp_forward_kernel(const float* __restrict__ P, const float* __restrict__ X,
+                                                              int64_t n, float* __restrict__ O) {
+    __shared__ InferShared S;
+    load_infer_shared(S, P);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int64_t base = ((int64_t)blockIdx.x * kIW + warp) * 16; base < n; base += (int64_t)gridDim.x * kIW * 16) {
+        float xg[3] = {0, 0, 0}, xh[3] = {0, 0, 0};
+        if (base + g < n)
+            for (int q = 0; q < 3; ++q) xg[q] = X[3 * (base + g) + q];
+        if (base + g + 8 < n)
+            for (int q = 0; q < 3; ++q) xh[q] = X[3 * (base + g + 8) + q];
+        infer_tile(S, xg, xh, g, t, S.out[warp]);
+        __syncwarp();
+        for (int e = lane; e < 64; e += 32) {
+            const int64_t row = base + e / 4;
+            if (row < n) O[4 * row + (e & 3)] = S.out[warp][e / 4][e & 3];
+        }
+        __syncwarp();
+    }
+}
+
+// the table path for the queued samples q[0, cnt): lane e takes q[e] (all lanes call it)
+__device__ void table_path(const TabP<double>& T, const double* __restrict__ bes_tab, const double* __restrict__ chi_in,
+                           const double* __restrict__ r_in, const double* __restrict__ s_in, const int64_t* q, int cnt,
+                           float* __restrict__ out4) {
+    const int e = threadIdx.x & 31;
+    if (e < cnt) {
+        const int64_t i = q[e];
+        const double chi = chi_in[i], r = r_in[i], s = s_in[i];
+        const MixPoint m = mix_point(T, chi, r, s);
+        const double L = mix_quantile<44, 32>(T, m, r);
+        out4[4 * i] = (float)L;
+        out4[4 * i + 1] = 0.0f;
+        out4[4 * i + 2] = 0.0f;
+        out4[4 * i + 3] = (float)xi3_at(bes_tab, chi, L, s);
+    }
+}
+
+// the sampler: network, CDF check; samples that fail it (or all, flags bit 0) wait in a per-warp queue
+// and take the table path 32 at a time, so that a warp never idles on one slow lane
+__global__ void __launch_bounds__(kIW * 32) mlp_sample_kernel(const float* __restrict__ P, TabP<double> T,
+                                                             const double* __restrict__ bes_tab,
+                                                             const double* __restrict__ chi_in, const double* __restrict__ r_in,
+                                                             const double* __restrict__ s_in, int64_t n, double tol,
+                                                             int flags, float* __restrict__ out4, uint8_t* __restrict__ fell,
+                                                             unsigned long long* n_fallback) {
+    __shared__ InferShared S;
+    load_infer_shared(S, P);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    int64_t* q = S.queue[warp];
+    int qn = 0;
+    unsigned long long nf = 0;
+    for (int64_t base = ((int64_t)blockIdx.x * kIW + warp) * 32; base < n; base += (int64_t)gridDim.x * kIW * 32) {
+        // two row tiles of 16 samples; the network outputs of sample base + e land in out[e]
+        for (int half = 0; half < 2; ++half) {
+            const int64_t b0 = base + 16 * half;
+            float xg[3] = {0, 0, 0}, xh[3] = {0, 0, 0};
+            if (b0 + g < n) mlp_features(chi_in[b0 + g], r_in[b0 + g], s_in[b0 + g], xg);
+            if (b0 + g + 8 < n) mlp_features(chi_in[b0 + g + 8], r_in[b0 + g + 8], s_in[b0 + g + 8], xh);
+            infer_tile(S, xg, xh, g, t, S.out[warp] + 16 * half);
+        }
+        __syncwarp();
+        const int64_t i = base + lane;
+        bool fb = false;
+        if (i < n) {
+            fb = (flags & 1) != 0;
+            if (!fb) {
+                const double chi = chi_in[i], r = r_in[i], s = s_in[i];
+                const MixPoint m = mix_point(T, chi, r, s);
+                const double Lb = mix_baseline(T, m);
+                const float* o = S.out[warp][lane];
+                const double L = Lb + (double)o[0] / kOutScale;
+                const double xi1 = (double)o[1] / kOutScale, xi2 = (double)o[2] / kOutScale;
+                const double xi3 = xi3_at(bes_tab, chi, Lb, s) + (double)o[3] / kOutScale;
+                const double err_q = fabs(mix_cdf<30>(T, m, L) - r);  // the CDF check
+                const double xi3x = xi3_at(bes_tab, chi, L, s);
+                fb = !(err_q <= tol) || !(fabs(xi3 - xi3x) <= tol) || !(fabs(xi1) <= tol) || !(fabs(xi2) <= tol);
+                if (!fb) {
+                    out4[4 * i] = (float)L;
+                    out4[4 * i + 1] = (float)xi1;
+                    out4[4 * i + 2] = (float)xi2;
+                    out4[4 * i + 3] = (float)xi3;
+                }
+            }
+            if (fell) fell[i] = fb ? 1 : 0;
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, fb);
+        if (fb) q[qn + __popc(mk & ((1u << lane) - 1u))] = i;
+        qn += __popc(mk);
+        nf += lane == 0 ? (unsigned long long)__popc(mk) : 0ull;
+        __syncwarp();
+        if (qn >= 32) {
+            table_path(T, bes_tab, chi_in, r_in, s_in, q + (qn - 32), 32, out4);
+            qn -= 32;
+        }
+        __syncwarp();
+    }
+    if (qn > 0) table_path(T, bes_tab, chi_in, r_in, s_in, q, qn, out4);
+    if (lane == 0 && nf && n_fallback) atomicAdd(n_fallback, nf);
+}
+
+}  // namespace qed
+
+// ---- host side -------------------------------------------------------------------------------------
+using namespace qed;
+
+constexpr uint32_t kMlpMagic = 0x514D4C50u;  // "QMLP"
+
+struct qed_mlp_s {
+    uint32_t magic;
+    int64_t max_batch;
+    float *P, *M, *V, *G;  // parameters, Adam moments, gradients
+    float *X, *T, *Z1, *H1, *Z2, *H2, *Z3, *H3, *O, *dO, *dA, *dB, *loss;
+    int64_t steps;         // AdamW steps taken
+};
+
+static bool valid_mlp(const qed_mlp_s* m) { return m && m->magic == kMlpMagic; }
+
+static int grid_for(int64_t work, int threads) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, 152 * 16));
+}
+
+static void gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk,
+                 int64_t sbn, float* C, int64_t ldc, int ksplit, cudaStream_t st) {
+    const dim3 grid((N + kGN - 1) / kGN, (M + kGM - 1) / kGM, ksplit);
+    gemm_bf16_kernel<<<grid, 128, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, ksplit);
+}
+
+extern "C" void qed_mlp_destroy(qed_mlp_t m) {
+    if (!valid_mlp(m)) return;
+    for (float* p : {m->P, m->M, m->V, m->G, m->X, m->T, m->Z1, m->H1, m->Z2, m->H2, m->Z3, m->H3, m->O, m->dO, m->dA,
+                     m->dB, m->loss})
+        cudaFree(p);
+    m->magic = 0;
+    delete m;
+}
+
+extern "C" qed_status qed_mlp_create(int64_t max_batch, const float* init_params, qed_mlp_t* out) {
+    if (!out || max_batch < 1 || max_batch > (1ll << 26) || !init_params) return QED_ERR_ARG;
+    *out = nullptr;
+    qed_mlp_s* m = new qed_mlp_s();
+    m->magic = kMlpMagic;
+    m->max_batch = max_batch;
+    const size_t np = sizeof(float) * kParams, nb = (size_t)max_batch;
+    bool ok = cudaMalloc(&m->P, np) == cudaSuccess && cudaMalloc(&m->M, np) == cudaSuccess &&
+              cudaMalloc(&m->V, np) == cudaSuccess && cudaMalloc(&m->G, np) == cudaSuccess &&
+              cudaMalloc(&m->X, 3 * nb * 4) == cudaSuccess && cudaMalloc(&m->T, 4 * nb * 4) == cudaSuccess;
+    for (float** p : {&m->Z1, &m->H1, &m->Z2, &m->H2, &m->Z3, &m->H3, &m->dA, &m->dB})
+        ok = ok && cudaMalloc(p, kH * nb * 4) == cudaSuccess;
+    ok = ok && cudaMalloc(&m->O, 4 * nb * 4) == cudaSuccess && cudaMalloc(&m->dO, 4 * nb * 4) == cudaSuccess &&
+         cudaMalloc(&m->loss, 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        qed_mlp_destroy(m);
+        return QED_ERR_NOMEM;
+    }
+    if (cudaMemcpy(m->P, init_params, np, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->M, 0, np) != cudaSuccess || cudaMemset(m->V, 0, np) != cudaSuccess) {
+        qed_mlp_destroy(m);
+        return QED_ERR_CUDA;
+    }
+    *out = m;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_get_params(qed_mlp_t m, float* host_out) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (!host_out) return QED_ERR_ARG;
+    return cudaMemcpy(host_out, m->P, sizeof(float) * kParams, cudaMemcpyDeviceToHost) == cudaSuccess ? QED_OK
+                                                                                                    : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_mlp_set_params(qed_mlp_t m, const float* host_in) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (!host_in) return QED_ERR_ARG;
+    if (cudaMemcpy(m->P, host_in, sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->M, 0, sizeof(float) * kParams) != cudaSuccess ||
+        cudaMemset(m->V, 0, sizeof(float) * kParams) != cudaSuccess)
+        return QED_ERR_CUDA;
+    m->steps = 0;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_mlp_targets(qed_tables_t t, int64_t n, uint64_t seed, int64_t first_index, float* x_dev,
+                                      float* y_dev, double* raw_dev, void* stream) {
+    if (!valid_tables(t)) return QED_ERR_STATE;
+    if (n < 0 || first_index < 0 || (n > 0 && (!x_dev || !y_dev))) return QED_ERR_ARG;
+    if (n == 0) return QED_OK;
+    mlp_targets_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(tab_params<double>(t), t->bes64, n, seed,
+                                                                         first_index, x_dev, y_dev, raw_dev);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+// forward and backward of one batch (features x, targets y); gradients into grad (kParams floats)
+static void mlp_grad_launch(qed_mlp_s* m, const float* x, const float* y, int64_t n, float* grad, float* loss,
+                            cudaStream_t st) {
+    const float* P = m->P;
+    const int eg = grid_for(n * kH, 256);
+    const int ks = (int)std::min<int64_t>(64, std::max<int64_t>(1, n / 512));
+    mlp_layer1_kernel<<<eg, 256, 0, st>>>(P, x, n, m->Z1, m->H1);
+    gemm((int)n, kH, kH, m->H1, kH, 1, P + kOffW2, 1, kH, m->Z2, kH, 1, st);
+    mlp_bias_silu_kernel<<<eg, 256, 0, st>>>(P + kOffB2, n, m->Z2, m->H2);
+    gemm((int)n, kH, kH, m->H2, kH, 1, P + kOffW3, 1, kH, m->Z3, kH, 1, st);
+    mlp_bias_silu_kernel<<<eg, 256, 0, st>>>(P + kOffB3, n, m->Z3, m->H3);
+    gemm((int)n, 4, kH, m->H3, kH, 1, P + kOffW4, 1, kH, m->O, 4, 1, st);
+    if (loss) cudaMemsetAsync(loss, 0, sizeof(float), st);
+    mlp_out_loss_kernel<<<grid_for(n * 4, 256), 256, 0, st>>>(P, y, n, m->O, m->dO, loss);
+    cudaMemsetAsync(grad, 0, sizeof(float) * kParams, st);
+    // layer 4
+    gemm(4, kH, (int)n, m->dO, 1, 4, m->H3, kH, 1, grad + kOffW4, kH, ks, st);
+    mlp_colsum_kernel<<<4, 256, 0, st>>>(m->dO, n, 4, grad + kOffB4);
+    gemm((int)n, kH, 4, m->dO, 4, 1, P + kOffW4, kH, 1, m->dA, kH, 1, st);
+    mlp_silu_back_kernel<<<eg, 256, 0, st>>>(m->Z3, n, m->dA);
+    // layer 3
+    gemm(kH, kH, (int)n, m->dA, 1, kH, m->H2, kH, 1, grad + kOffW3, kH, ks, st);
+    mlp_colsum_kernel<<<kH, 256, 0, st>>>(m->dA, n, kH, grad + kOffB3);
+    gemm((int)n, kH, kH, m->dA, kH, 1, P + kOffW3, kH, 1, m->dB, kH, 1, st);
+    mlp_silu_back_kernel<<<eg, 256, 0, st>>>(m->Z2, n, m->dB);
+    // layer 2
+    gemm(kH, kH, (int)n, m->dB, 1, kH, m->H1, kH, 1, grad + kOffW2, kH, ks, st);
+    mlp_colsum_kernel<<<kH, 256, 0, st>>>(m->dB, n, kH, grad + kOffB2);
+    gemm((int)n, kH, kH, m->dB, kH, 1, P + kOffW2, kH, 1, m->dA, kH, 1, st);
+    mlp_silu_back_kernel<<<eg, 256, 0, st>>>(m->Z1, n, m->dA);
+    // layer 1 (FP32)
+    mlp_dw1_kernel<<<3 * kH, 256, 0, st>>>(m->dA, x, n, grad);
+    mlp_colsum_kernel<<<kH, 256, 0, st>>>(m->dA, n, kH, grad + kOffB1);
+}
+
+extern "C" qed_status qed_mlp_grad(qed_mlp_t m, const float* x_dev, const float* y_dev, int64_t n, float* grad_dev,
+                                   float* loss_dev, void* stream) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (n < 1 || n > m->max_batch || !x_dev || !y_dev || !grad_dev) return QED_ERR_ARG;
+    mlp_grad_launch(m, x_dev, y_dev, n, grad_dev, loss_dev, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_mlp_adamw(qed_mlp_t m, const float* grad_dev, float lr, float weight_decay, void* stream) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (!grad_dev || !(lr >= 0.0f) || !(weight_decay >= 0.0f)) return QED_ERR_ARG;
+    m->steps += 1;
+    const float b1t = (float)std::pow(0.9, (double)m->steps), b2t = (float)std::pow(0.999, (double)m->steps);
+    mlp_adamw_kernel<<<(kParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->P, m->M, m->V, grad_dev, lr,
+                                                                               weight_decay, b1t, b2t);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_mlp_train(qed_mlp_t m, qed_tables_t t, int64_t steps, int64_t batch, uint64_t seed,
+                                    int64_t first_index, float lr, float lr_final, float weight_decay,
+                                    float* loss_per_step_dev, void* stream) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (!valid_tables(t)) return QED_ERR_STATE;
+    if (steps < 0 || batch < 1 || batch > m->max_batch || first_index < 0 || !(lr >= 0.0f) || !(lr_final >= 0.0f))
+        return QED_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t k = 0; k < steps; ++k) {
+        // cosine decay from lr to lr_final
+        const double c = steps > 1 ? 0.5 * (1.0 + std::cos(3.141592653589793 * (double)k / (double)(steps - 1))) : 1.0;
+        const float lrk = (float)(lr_final + (lr - lr_final) * c);
+        qed_status s = qed_mlp_targets(t, batch, seed, first_index + k * batch, m->X, m->T, nullptr, stream);
+        if (s != QED_OK) return s;
+        mlp_grad_launch(m, m->X, m->T, batch, m->G, loss_per_step_dev ? loss_per_step_dev + k : nullptr, st);
+        s = qed_mlp_adamw(m, m->G, lrk, weight_decay, stream);
+        if (s != QED_OK) return s;
+    }
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_mlp_forward(qed_mlp_t m, const float* x_dev, int64_t n, float* out_dev, void* stream) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (n < 0 || (n > 0 && (!x_dev || !out_dev))) return QED_ERR_ARG;
+    if (n == 0) return QED_OK;
+    mlp_forward_kernel<<<grid_for((n + 15) / 16, kIW), kIW * 32, 0, (cudaStream_t)stream>>>(m->P, x_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* chi, const double* r, const double* s,
+                                     int64_t n, double tol, int32_t flags, float* out4, uint8_t* fell_back,
+                                     unsigned long long* n_fallback, void* stream) {
+    if (!valid_mlp(m)) return QED_ERR_STATE;
+    if (!valid_tables(t)) return QED_ERR_STATE;
+    if (n < 0 || (n > 0 && (!chi || !r || !s || !out4)) || !(tol >= 0.0) || (flags & ~QED_MLP_ALWAYS_TABLE)) return QED_ERR_ARG;
+    if (n == 0) return QED_OK;
+    // persistent grid (one resident wave): each warp streams many 32-sample batches, so its fallback queue
+    // drains full
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 1, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_sample_kernel, kIW * 32, 0);
+        resident = sms * std::max(1, per_sm);
+    }
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kIW - 1) / (32 * kIW), resident));
+    mlp_sample_kernel<<<blocks, kIW * 32, 0, (cudaStream_t)stream>>>(
+        m->P, tab_params<double>(t), t->bes64, chi, r, s, n, tol, flags, out4, fell_back, n_fallback);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
