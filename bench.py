@@ -51,6 +51,9 @@ def parse():
                     help="untimed steps before warm-up (into the interaction; default 450 batched, 620 headon)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU-baseline legs")
     ap.add_argument("--no-tune", action="store_true", help="batched: keep the default launch shape")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the learned-sampler leg")
+    ap.add_argument("--mlp-train", type=float, default=5e7, help="learned sampler: training samples")
+    ap.add_argument("--mlp-eval", type=float, default=1e8, help="learned sampler: evaluated events")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="batched: multiply every instance's electron count (small cases for profiling)")
     a = ap.parse_args()
@@ -470,6 +473,10 @@ def native_batch(args):
     extras = {}
     if not args.no_extras and rank == 0:
         extras = batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, torch, stream)
+    if not args.no_extras and not args.no_mlp and rank == 0:
+        bt.close()
+        torch.cuda.empty_cache()
+        extras["mlp"] = mlp_leg(args, tables, torch)
     n_el = sum(x["n"] for x in insts)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -496,6 +503,66 @@ def native_batch(args):
     if rank != 0:
         return None
     return out
+
+
+def mlp_leg(args, tables, torch):
+    """The learned sampler: 3-64-64-64-4 SiLU, BF16 weights and activations with FP32 accumulation on
+    tensor cores, trained on table samples at chi in [1e-3, 1e2], evaluated on events with the table
+    fallback wherever the network's CDF error (or Stokes error) exceeds 1e-4; the table path beside it."""
+    from paper_2511_08929_gb300 import mlp as GM
+    batch = 4096
+    steps = int(math.ceil(args.mlp_train / batch))
+    smp = GM.Sampler(GM.init_params(1), max_batch=batch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = smp.train(tables, steps, batch, seed=21, lr=3e-3, lr_final=3e-5)
+    e1.record()
+    torch.cuda.synchronize()
+    train_s = e0.elapsed_time(e1) / 1e3
+    lo, hi = math.log(1e-3), math.log(1e2)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+
+    def inputs(n):
+        chi = torch.exp(lo + (hi - lo) * torch.rand(n, dtype=torch.float64, device="cuda", generator=gen))
+        r = torch.rand(n, dtype=torch.float64, device="cuda", generator=gen) * (1 - 2.0 ** -40) + 2.0 ** -41
+        s = 2 * torch.rand(n, dtype=torch.float64, device="cuda", generator=gen) - 1
+        return chi, r, s
+
+    total, chunk = int(args.mlp_eval), 1 << 24
+    done, t_net, n_fb = 0, 0.0, 0
+    edges = [0.0, 1e-7, 1e-6, 1e-5, 1e-4, 1e-3, float("inf")]
+    hist = np.zeros(len(edges) - 1)
+    first = None
+    while done < total:
+        n = min(chunk, total - done)
+        chi, r, s = inputs(n)
+        if first is None:
+            first = (chi, r, s)
+        e0.record()
+        _, _, nf, err = smp.sample(tables, chi, r, s, tol=1e-4, with_error=True)
+        e1.record()
+        torch.cuda.synchronize()
+        t_net += e0.elapsed_time(e1) / 1e3
+        n_fb += int(nf.item())
+        hist += np.histogram(err.cpu().numpy(), bins=edges)[0]
+        done += n
+    chi, r, s = first
+    e0.record()
+    smp.sample(tables, chi, r, s, table_only=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_tab = e0.elapsed_time(e1) / 1e3
+    net_rate, tab_rate = total / t_net, chi.shape[0] / t_tab
+    smp.close()
+    labels = ["<1e-7", "1e-7..1e-6", "1e-6..1e-5", "1e-5..1e-4", "1e-4..1e-3", ">1e-3"]
+    return {"train_samples": steps * batch, "train_steps": steps, "train_s": round(train_s, 2),
+            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-100:].mean()),
+            "eval_events": total, "samples_per_s": net_rate, "fallback_fraction": n_fb / total,
+            "network_cdf_error_hist": {k: float(v / total) for k, v in zip(labels, hist)},
+            "table_path_samples_per_s": tab_rate, "table_path_events": int(chi.shape[0]),
+            "gain_over_table_path": net_rate / tab_rate, "tolerance": 1e-4,
+            "parameters": 8836, "weights_bytes_bf16": 2 * (192 + 4096 + 4096 + 256)}
 
 
 def _to_fp64(b32, b64, torch):

@@ -386,10 +386,11 @@ qed_status qed_mlp_forward(qed_mlp_t m, const float *x_dev, int64_t n, float *ou
  * xi2, xi3) from the network, checked: the exact mixture CDF of the tables at ln u' must be within tol of
  * r and the Stokes vector within tol of its closed form there, else (or with QED_MLP_ALWAYS_TABLE) the
  * table path (the mixture quantile by bisection, the closed-form Stokes vector).  fell_back (n bytes,
- * may be NULL) marks the samples that took the table path; *n_fallback (device, may be NULL) is
- * incremented by their number. */
+ * may be NULL) marks the samples that took the table path; err_out (n floats, may be NULL) gets the
+ * network's CDF error |C(ln u') - r| (-1 where the network was skipped); *n_fallback (device, may be
+ * NULL) is incremented by the number of fallbacks. */
 qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double *chi, const double *r, const double *s_beta,
-                          int64_t n, double tol, int32_t flags, float *out4, uint8_t *fell_back,
+                          int64_t n, double tol, int32_t flags, float *out4, uint8_t *fell_back, float *err_out,
                           unsigned long long *n_fallback, void *stream);
 
 /* *begin = *count for each of the n buffers (device-side copy; graph-capturable).  Call it at the start

@@ -150,7 +150,7 @@ def lib():
                 "qed_mlp_adamw": (i32, [vp, vp, C.c_float, C.c_float, vp]),
                 "qed_mlp_train": (i32, [vp, vp, i64, i64, u64, i64, C.c_float, C.c_float, C.c_float, vp, vp]),
                 "qed_mlp_forward": (i32, [vp, vp, i64, vp, vp]),
-                "qed_mlp_sample": (i32, [vp, vp, vp, vp, vp, i64, C.c_double, i32, vp, vp, vp, vp]),
+                "qed_mlp_sample": (i32, [vp, vp, vp, vp, vp, i64, C.c_double, i32, vp, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -354,9 +354,9 @@ def qed_mlp_forward(m: int, x_dev: int, n: int, out_dev: int, stream: int = 0):
 
 
 def qed_mlp_sample(m: int, tables: int, chi_dev: int, r_dev: int, s_dev: int, n: int, tol: float, flags: int,
-                   out_dev: int, fell_dev: int = 0, n_fallback_dev: int = 0, stream: int = 0):
+                   out_dev: int, fell_dev: int = 0, n_fallback_dev: int = 0, stream: int = 0, err_dev: int = 0):
     _check(lib().qed_mlp_sample(m, tables, chi_dev, r_dev, s_dev, n, tol, flags, out_dev, fell_dev or None,
-                                n_fallback_dev or None, stream or None), "qed_mlp_sample")
+                                err_dev or None, n_fallback_dev or None, stream or None), "qed_mlp_sample")
 
 
 def declared_entry_points():

@@ -128,7 +128,7 @@ __global__ void mlp_targets_kernel(TabP<double> T, const double* __restrict__ be
         const double lnchi = kLnChiLo + uniform52(w0.x, w0.y) * (kLnChiHi - kLnChiLo);
         const double chi = exp(lnchi), r = uniform52(w0.z, w0.w), s = 2.0 * uniform52(w1.x, w1.y) - 1.0;
         const MixPoint m = mix_point(T, chi, r, s);
-        const double Lb = mix_baseline(T, m), L = mix_quantile<56, 48>(T, m, r);
+        const double Lb = mix_baseline(T, m), L = mix_quantile<44, 32>(T, m, r);
         float x[3];
         mlp_features(chi, r, s, x);
         X[3 * i] = x[0];
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kIW * 32) mlp_sample_kernel(const float* __res
                                                              const double* __restrict__ chi_in, const double* __restrict__ r_in,
                                                              const double* __restrict__ s_in, int64_t n, double tol,
                                                              int flags, float* __restrict__ out4, uint8_t* __restrict__ fell,
-                                                             unsigned long long* n_fallback) {
+                                                             float* __restrict__ err_out, unsigned long long* n_fallback) {
     __shared__ InferShared S;
     load_infer_shared(S, P);
     __syncthreads();
@@ -482,6 +482,7 @@ __global__ void __launch_bounds__(kIW * 32) mlp_sample_kernel(const float* __res
                 const double xi3 = xi3_at(bes_tab, chi, Lb, s) + (double)o[3] / kOutScale;
                 const double err_q = fabs(mix_cdf<30>(T, m, L) - r);  // the CDF check
                 const double xi3x = xi3_at(bes_tab, chi, L, s);
+                if (err_out) err_out[i] = (float)err_q;
                 fb = !(err_q <= tol) || !(fabs(xi3 - xi3x) <= tol) || !(fabs(xi1) <= tol) || !(fabs(xi2) <= tol);
                 if (!fb) {
                     out4[4 * i] = (float)L;
@@ -490,6 +491,7 @@ __global__ void __launch_bounds__(kIW * 32) mlp_sample_kernel(const float* __res
                     out4[4 * i + 3] = (float)xi3;
                 }
             }
+            else if (err_out) err_out[i] = -1.0f;
             if (fell) fell[i] = fb ? 1 : 0;
         }
         const unsigned mk = __ballot_sync(0xffffffffu, fb);
@@ -683,7 +685,7 @@ extern "C" qed_status qed_mlp_forward(qed_mlp_t m, const float* x_dev, int64_t n
 
 extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* chi, const double* r, const double* s,
                                      int64_t n, double tol, int32_t flags, float* out4, uint8_t* fell_back,
-                                     unsigned long long* n_fallback, void* stream) {
+                                     float* err_out, unsigned long long* n_fallback, void* stream) {
     if (!valid_mlp(m)) return QED_ERR_STATE;
     if (!valid_tables(t)) return QED_ERR_STATE;
     if (n < 0 || (n > 0 && (!chi || !r || !s || !out4)) || !(tol >= 0.0) || (flags & ~QED_MLP_ALWAYS_TABLE)) return QED_ERR_ARG;
@@ -700,6 +702,6 @@ extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* 
     }
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kIW - 1) / (32 * kIW), resident));
     mlp_sample_kernel<<<blocks, kIW * 32, 0, (cudaStream_t)stream>>>(
-        m->P, tab_params<double>(t), t->bes64, chi, r, s, n, tol, flags, out4, fell_back, n_fallback);
+        m->P, tab_params<double>(t), t->bes64, chi, r, s, n, tol, flags, out4, fell_back, err_out, n_fallback);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
