@@ -278,12 +278,7 @@ def native(args):
     tmax = ms
     psteps_all = psteps
     if dist is not None:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        p = torch.tensor([psteps], device=device, dtype=torch.float64)
-        dist.all_reduce(p)
-        psteps_all = float(p.item())
+        tmax, psteps_all = reduce_over_ranks(ms, psteps, dist, device)
     value = psteps_all / (tmax / 1e3)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / its event-timed duration
@@ -342,21 +337,37 @@ def z_order(beam: dict) -> dict:
     return {k: v[o] for k, v in beam.items()}
 
 
+def reduce_over_ranks(ms: float, psteps: float, dist, device):
+    """Whole-job timing of independent replicas: the slowest rank's time and every rank's particle-steps."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([psteps], dtype=torch.float64, device=device)
+    dist.all_reduce(p)
+    return float(t.item()), float(p.item())
+
+
+def replica_plan(wl, rank: int):
+    """Rank `rank`'s replica of a batched workload: the same instances, Philox seeds offset by 1000 rank
+    and particle ids by rank 2^48, so that no two ranks share a key (the replicas are independent)."""
+    insts = wl.instances()
+    seeds = [x["seed"] + 1000 * rank for x in insts]
+    return insts, seeds, np.uint64(rank << 48)
+
+
 def batch_setup(Q, B, I, tables, rank, device, scale=1.0):
     import dataclasses
     wl = I.BATCHED_96
     if scale != 1.0:
         wl = dataclasses.replace(wl, name=f"{wl.name}_x{scale:g}", n_min=wl.n_min * scale, n_max=wl.n_max * scale)
-    insts = wl.instances()
+    insts, seeds, id_offset = replica_plan(wl, rank)
     fields = [Q.laser_field(wl.laser(x)) for x in insts]
-    seeds = [x["seed"] + 1000 * rank for x in insts]
     caps = [tuple(max(4096, int(wl.capacity_factor * x["n"])) for _ in range(3)) for x in insts]
     bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
                  device=device)
     for k, (x, (e, p, g)) in enumerate(zip(insts, bt.buffers())):
         b = z_order(wl.beam(k, x))
-        if rank:
-            b["id"] = b["id"] + np.uint64(rank << 48)
+        b["id"] = b["id"] + id_offset
         e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"])
         e.init_tau(seeds[k])
     return wl, insts, fields, seeds, caps, bt
@@ -443,12 +454,7 @@ def native_batch(args):
     d_sp = [float(s1.species_steps[i] - s0.species_steps[i]) for i in range(3)]
     tmax, psteps_all = ms, psteps
     if dist is not None:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        p = torch.tensor([psteps], device=device, dtype=torch.float64)
-        dist.all_reduce(p)
-        psteps_all = float(p.item())
+        tmax, psteps_all = reduce_over_ranks(ms, psteps, dist, device)
     value = psteps_all / (tmax / 1e3)
 
     # roofline of the persistent kernel: algorithmic bytes per launch / its event-timed duration
