@@ -300,7 +300,8 @@ typedef struct {
  *                 sized for so many blocks per SM): 0 = 256, 3, 3; 1 = 256, 3, 2; 2 = 256, 2, 4;
  *                 3 = 512, 2, 1; 4 = 512, 2, 2
  *   blocks_per_sm resident blocks per SM of the persistent grid (0: the occupancy maximum)
- *   chunk         consecutive tiles of 32 particles a warp takes before moving on by the grid's width
+ *   chunk         the most consecutive tiles of 32 particles a warp takes from the step's work counter at
+ *                 once (takes shrink towards 2 as the step's work runs out)
  *   graph_steps   time steps captured per CUDA graph (0: launch the kernels directly every step) */
 typedef struct {
     int32_t variant, blocks_per_sm, chunk, graph_steps;

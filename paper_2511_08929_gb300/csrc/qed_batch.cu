@@ -5,10 +5,11 @@
 // One time step of the batch is six launches on one stream:
 //   plan      alive counts at step start (counts clamped to capacity), the tile list over all segments
 //             (segment = one species of one instance, species-major), particle-step accounting;
-//   step      the persistent kernel: every warp walks its share of the tile list (chunks of `chunk`
-//             consecutive tiles, chunk k of warp w at k * warps + w) with the same bulk-copy pipeline,
-//             per-particle arithmetic and per-warp event queue as the single-buffer FP32 kernels; the
-//             event queue is drained when a warp crosses into another segment;
+//   step      the persistent kernel: every warp takes runs of consecutive tiles from a work counter
+//             (guided: long runs first, short ones at the end, at most `chunk` tiles) and streams them
+//             with the same bulk-copy pipeline, per-particle arithmetic and per-warp event queue as the
+//             single-buffer FP32 kernels; the event queue is drained when a warp crosses into another
+//             segment;
 //   compact   head / classify / tail / move of every instance's photons (converted photons leave,
 //             Sec. 3.3), the last one also advancing the device step counter.
 // Daughters appended during a step sit beyond the counts taken by `plan`, so they are first stepped in
@@ -46,6 +47,7 @@ struct ClockDev {
     unsigned long long psteps;
     unsigned long long species_steps[kSpecies];
     long long alive[kSpecies];
+    int next_tile;  // the persistent kernel's work counter (tiles handed out), reset by the plan kernel
 };
 
 struct BatchP {
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev*
         ex += loc[k];
     }
     if (threadIdx.x == 0) {
+        clk->next_tile = 0;
         clk->psteps += tot[0] + tot[1] + tot[2];
         for (int k = 0; k < kSpecies; ++k) {
             clk->species_steps[k] += tot[k];
@@ -123,21 +126,21 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev*
 // the persistent step kernel
 // ------------------------------------------------------------------------------------------------
 
-// A warp's walk over the tile list: chunks of `chunk` consecutive tiles, chunk k of warp w starting at
-// tile (k W + w) chunk.  Incremental 32-bit counters (the batch holds fewer than 2^31 tiles): t is the
-// current tile (== total once the walk is over), r its place in the chunk.
-struct TileWalk {
-    int t, r;
-    __device__ __forceinline__ void next(int chunk, int jump, int total) {
-        if (++r == chunk) {
-            r = 0;
-            const long long n = (long long)t + jump;
-            t = n < total ? (int)n : total;
-        } else {
-            t = t + 1 < total ? t + 1 : total;
-        }
-    }
-};
+// Guided self-scheduling of the tile list: a warp takes [start, start + size) from the work counter
+// with one atomic add, size = (tiles not yet handed out by its last take) / (2 x warps), clamped to
+// [min(kMinChunk, chunk), chunk].  Early takes are long runs of consecutive tiles (few segment changes), the last
+// ones short, so the warps finish together whatever the cost of their tiles.  Takes return increasing
+// starts, so every warp walks the tile list forward.  The copy walk (lane 0) takes the chunks one ahead
+// and passes their bounds to the compute walk through a per-warp ring in shared memory.
+constexpr int kMinChunk = 2;
+constexpr int kChunkRing = 8;  // > STAGES + 1: the chunks between the compute and the copy walks
+
+__device__ __forceinline__ int guided_size(int total, int from, int warps2, int chunk) {
+    const int left = total - from;
+    const int g = left > 0 ? left / warps2 : 0;
+    const int lo = chunk < kMinChunk ? chunk : kMinChunk;
+    return g < lo ? lo : (g > chunk ? chunk : g);
+}
 
 // lane 0: start the copies of tile t into stage st, moving the copy cursor cs (segment of the last
 // issued tile; tiles only increase) forward
@@ -162,7 +165,8 @@ struct WarpSeg {
 };
 
 // shared memory of the batched kernel: the 1-D rate tables (the Bessel table, read only at events, stays
-// in global memory behind L1), the tile list, the per-warp segment state, the tiles, barriers and queues
+// in global memory behind L1), the tile list, the per-warp segment state, the tiles, barriers, queues
+// and chunk rings
 __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
     size_t off = align128((size_t)4 * n_chi * 4);
     off += align128((size_t)(n_seg + 1) * 4);
@@ -170,6 +174,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_
     off += (size_t)warps * stages * sizeof(Tile);
     off += (size_t)warps * stages * 8;
     off += (size_t)warps * kWQ * 8;
+    off += (size_t)warps * kChunkRing * 8;
     return off;
 }
 
@@ -177,7 +182,7 @@ template <int WARPS, int STAGES, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     batch_step_kernel(TabP<float> T, float* bes_g, const InstDev* __restrict__ inst,
                       const SegDev* __restrict__ seg, const int64_t* __restrict__ tile0_g, int n_inst,
-                      const ClockDev* __restrict__ clk, BatchP P, int chunk, qed_counters* ctr) {
+                      const ClockDev* __restrict__ clk, BatchP P, int chunk, int* work, qed_counters* ctr) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int n_seg = kSpecies * n_inst;
     Shared32 sh;
@@ -193,6 +198,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     sh.bars = (uint64_t*)(smem + off);
     off += (size_t)WARPS * STAGES * 8;
     sh.queue = (int64_t*)(smem + off);
+    off += (size_t)WARPS * kWQ * 8;
+    int2* s_chunks = (int2*)(smem + off);
 
     for (int i = threadIdx.x; i < 2 * T.n_chi; i += blockDim.x) {
         sh.rates[i] = T.nlc_rate[i];
@@ -212,29 +219,49 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     }
     __syncthreads();  // tables, tile list and barriers ready
     const int total = s_tile0[n_seg];
-    const int W = gridDim.x * WARPS;
-    const int jump = (W - 1) * chunk + 1;
-    const long long first = ((long long)blockIdx.x * WARPS + warp) * chunk;
-    TileWalk walk{first < total ? (int)first : total, 0};
-    const uint64_t step = clk->step;
-    // time of this step: a product then a sum, each rounded (no contraction)
-    const double t_now = __dadd_rn(clk->t0, __dmul_rn((double)(step - clk->step0), clk->dt));
+    const int W2 = 2 * gridDim.x * WARPS;
     unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
-    TileWalk pre = walk;  // lane 0: the copy walk, STAGES tiles ahead
+    int2* ring = s_chunks + warp * kChunkRing;
+    // lane 0: the copy walk (tile pt of a chunk ending at pe), the chunks it has put in the ring (pk),
+    // the prefetched take (ns, nsz) and the tiles issued (ni)
+    int pt = total, pe = total, pk = 0, ns = total, nsz = 0, ni = 0;
     int cs = 0;
-    if (lane == 0)
-        for (int s = 0; s < STAGES && pre.t < total; ++s) {
-            batch_issue<STAGES>(tile, bar, s_tile0, seg, pre.t, s, cs);
-            pre.next(chunk, jump, total);
+    if (lane == 0) {
+        int sz = guided_size(total, 0, W2, chunk);
+        const int s0 = atomicAdd(work, sz);
+        pt = min(s0, total);
+        pe = min(s0 + sz, total);
+        ring[pk++ & (kChunkRing - 1)] = make_int2(pt, pe);
+        if (pt < pe) {
+            nsz = guided_size(total, s0, W2, chunk);
+            ns = atomicAdd(work, nsz);
         }
+        for (int s = 0; s < STAGES && pt < pe; ++s) {
+            batch_issue<STAGES>(tile, bar, s_tile0, seg, pt, s, cs);
+            ++ni;
+            if (++pt == pe) {  // the chunk is issued: take the prefetched one
+                pt = min(ns, total);
+                pe = min(ns + nsz, total);
+                ring[pk++ & (kChunkRing - 1)] = make_int2(pt, pe);
+                if (pt < pe) {
+                    const int from = ns;
+                    nsz = guided_size(total, from, W2, chunk);
+                    ns = atomicAdd(work, nsz);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    int2 ch = ring[0];
+    int t = ch.x, te = ch.y, rk = 1;  // the compute walk: tile t of a chunk ending at te; ring entries read
+    int nd = 0;                       // tiles consumed
     int qn = 0;    // queued event indices of the current segment (warp-uniform)
     int cur = -1;  // current segment
     int sp = 0, ii = 0;
     int st = 0;        // stage of the current tile
     uint32_t ph = 0;   // its mbarrier phase parity
     bool timed_out = false;
-    for (; walk.t < total; walk.next(chunk, jump, total)) {
-        const int t = walk.t;
+    while (t < te) {
         if (!mbar_wait(&bar[st], ph)) {
             timed_out = true;
             break;
@@ -253,6 +280,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             __syncwarp();
             if (lane == 0) {
                 const InstDev& I = inst[ii];
+                const uint64_t step = clk->step;
+                // time of this step: a product then a sum, each rounded (no contraction)
+                const double t_now = __dadd_rn(clk->t0, __dmul_rn((double)(step - clk->step0), clk->dt));
                 WS.t0 = s_tile0[cur];
                 WS.t1 = s_tile0[cur + 1];
                 WS.n = (int)seg[cur].n;
@@ -291,9 +321,19 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         __syncwarp();
         if (lane == 0) {
             fence_proxy_async();  // this stage's reads happen before the next copy overwrites it
-            if (pre.t < total) {
-                batch_issue<STAGES>(tile, bar, s_tile0, seg, pre.t, st, cs);
-                pre.next(chunk, jump, total);
+            if (pt < pe) {
+                batch_issue<STAGES>(tile, bar, s_tile0, seg, pt, st, cs);
+                ++ni;
+                if (++pt == pe) {  // the chunk is issued: take the prefetched one
+                    pt = min(ns, total);
+                    pe = min(ns + nsz, total);
+                    ring[pk++ & (kChunkRing - 1)] = make_int2(pt, pe);
+                    if (pt < pe) {
+                        const int from = ns;
+                        nsz = guided_size(total, from, W2, chunk);
+                        ns = atomicAdd(work, nsz);
+                    }
+                }
             }
         }
         if (++st == STAGES) {
@@ -314,21 +354,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             qn -= 32;
             __syncwarp();
         }
+        ++nd;
+        if (++t == te) {  // the chunk is done: the next one (its entry was written when its copies began)
+            ch = ring[rk++ & (kChunkRing - 1)];
+            t = ch.x;
+            te = ch.y;
+        }
     }
     if (timed_out) {
         if (lane == 0) {
-            record_error(ctr, QED_ERR_TIMEOUT, (long long)walk.t * 32);
-            TileWalk w2 = walk;  // let the copies in flight (this tile and up to STAGES - 1 after it) land
-            int s2 = st;
-            uint32_t p2 = ph;
-            for (int k = 0; k < STAGES && w2.t < total; ++k) {
-                mbar_wait(&bar[s2], p2);
-                w2.next(chunk, jump, total);
-                if (++s2 == STAGES) {
-                    s2 = 0;
-                    p2 ^= 1u;
-                }
-            }
+            record_error(ctr, QED_ERR_TIMEOUT, (long long)t * 32);
+            for (int m = nd; m < ni; ++m)  // let the copies in flight land
+                mbar_wait(&bar[m % STAGES], (uint32_t)((m / STAGES) & 1));
         }
         __syncwarp();
     }
@@ -447,7 +484,8 @@ static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
     P.store_min = b->desc.photon_store_min;
     P.chi_floor = b->desc.chi_floor;
     batch_step_kernel<WARPS, STAGES, MINB><<<grid, WARPS * 32, smem, st>>>(
-        tab_params<float>(t), t->bes32, b->d_inst, b->d_seg, b->d_tile0, b->n_inst, b->d_clk, P, b->tuning.chunk, b->ctr);
+        tab_params<float>(t), t->bes32, b->d_inst, b->d_seg, b->d_tile0, b->n_inst, b->d_clk, P, b->tuning.chunk,
+        &b->d_clk->next_tile, b->ctr);
 }
 
 static const BatchVariant kVariants[QED_BATCH_VARIANTS] = {
@@ -635,7 +673,7 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
         qed_batch_destroy(b);
         return QED_ERR_CUDA;
     }
-    const qed_batch_tuning def{0, 0, 4, 8};
+    const qed_batch_tuning def{0, 0, 64, 8};
     if (qed_batch_set_tuning(b, &def) != QED_OK) {
         qed_batch_destroy(b);
         return QED_ERR_CUDA;
@@ -769,12 +807,13 @@ extern "C" qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate,
             return QED_OK;
         }
     }
-    // candidates: every variant that fits, at its occupancy maximum and one block fewer, three chunk sizes
+    // candidates: every variant that fits, at its occupancy maximum and one block fewer, three largest
+    // chunk sizes
     std::vector<qed_batch_tuning> cand;
     for (int v = 0; v < QED_BATCH_VARIANTS; ++v) {
         const int occ = variant_occupancy(b, v);
         for (int bps = occ; bps >= 1 && bps >= occ - 1; --bps)
-            for (int ch : {1, 4, 16}) cand.push_back(qed_batch_tuning{v, bps, ch, 0});
+            for (int ch : {16, 64, 256}) cand.push_back(qed_batch_tuning{v, bps, ch, 0});
     }
     if (cand.empty()) return QED_ERR_CUDA;
     std::vector<double> score(cand.size(), 1e300);
