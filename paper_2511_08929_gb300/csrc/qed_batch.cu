@@ -142,19 +142,31 @@ __device__ __forceinline__ int guided_size(int total, int from, int warps2, int 
     return g < lo ? lo : (g > chunk ? chunk : g);
 }
 
-// lane 0: start the copies of tile t into stage st, moving the copy cursor cs (segment of the last
-// issued tile; tiles only increase) forward
-template <int STAGES>
-__device__ __forceinline__ void batch_issue(Tile* tile, uint64_t* bar, const int* tile0, const SegDev* __restrict__ seg,
-                                            int t, int st, int& cs) {
+// per-thread asynchronous 16-byte copies global -> shared (cp.async, L2 only), committed and awaited in
+// groups: every lane copies its own particle of a tile and later reads only what it copied itself
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// all lanes: start the copies of tile t into stage st (one commit group), moving the copy cursor cs
+// (segment of the last issued tile; tiles only increase) forward
+__device__ __forceinline__ void batch_issue(Tile* tile, const int* tile0, const SegDev* __restrict__ seg, int t, int st,
+                                            int& cs) {
     while (tile0[cs + 1] <= t) ++cs;
     const SegDev g = seg[cs];
-    const int b = (t - tile0[cs]) * 32;
-    const uint32_t bytes = (uint32_t)(min((int64_t)32, g.n - (int64_t)b) * 16);
-    mbar_expect_tx(&bar[st], 3 * bytes);
-    bulk_g2s(tile[st].q0, g.q0 + b, bytes, &bar[st]);
-    bulk_g2s(tile[st].q1, g.q1 + b, bytes, &bar[st]);
-    bulk_g2s(tile[st].q2, g.q2 + b, bytes, &bar[st]);
+    const int j = (t - tile0[cs]) * 32 + (threadIdx.x & 31);
+    if (j < g.n) {
+        const int l = threadIdx.x & 31;
+        cp_async16(&tile[st].q0[l], g.q0 + j);
+        cp_async16(&tile[st].q1[l], g.q1 + j);
+        cp_async16(&tile[st].q2[l], g.q2 + j);
+    }
+    cp_async_commit();
 }
 
 // per-warp state of the current segment, in shared memory (written by lane 0 at a segment change)
@@ -165,14 +177,13 @@ struct WarpSeg {
 };
 
 // shared memory of the batched kernel: the 1-D rate tables (the Bessel table, read only at events, stays
-// in global memory behind L1), the tile list, the per-warp segment state, the tiles, barriers, queues
-// and chunk rings
+// in global memory behind L1), the tile list, the per-warp segment state, the tiles, queues and chunk
+// rings
 __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
     size_t off = align128((size_t)4 * n_chi * 4);
     off += align128((size_t)(n_seg + 1) * 4);
     off += align128((size_t)warps * sizeof(WarpSeg));
     off += (size_t)warps * stages * sizeof(Tile);
-    off += (size_t)warps * stages * 8;
     off += (size_t)warps * kWQ * 8;
     off += (size_t)warps * kChunkRing * 8;
     return off;
@@ -195,8 +206,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     off += align128((size_t)WARPS * sizeof(WarpSeg));
     sh.tiles = (Tile*)(smem + off);
     off += (size_t)WARPS * STAGES * sizeof(Tile);
-    sh.bars = (uint64_t*)(smem + off);
-    off += (size_t)WARPS * STAGES * 8;
+    sh.bars = nullptr;
     sh.queue = (int64_t*)(smem + off);
     off += (size_t)WARPS * kWQ * 8;
     int2* s_chunks = (int2*)(smem + off);
@@ -208,64 +218,58 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     for (int i = threadIdx.x; i <= n_seg; i += blockDim.x) s_tile0[i] = (int)tile0_g[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Tile* tile = sh.tiles + warp * STAGES;
-    uint64_t* bar = sh.bars + warp * STAGES;
     int64_t* wq = sh.queue + warp * kWQ;
     WarpSeg& WS = s_ws[warp];
     Ctx& C = WS.C;
-    if (lane == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
-        WS.t1 = 0;
-    }
-    __syncthreads();  // tables, tile list and barriers ready
+    if (lane == 0) WS.t1 = 0;
+    __syncthreads();  // tables and tile list ready
     const int total = s_tile0[n_seg];
     const int W2 = 2 * gridDim.x * WARPS;
     unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
     int2* ring = s_chunks + warp * kChunkRing;
-    // lane 0: the copy walk (tile pt of a chunk ending at pe), the chunks it has put in the ring (pk),
-    // the prefetched take (ns, nsz) and the tiles issued (ni)
-    int pt = total, pe = total, pk = 0, ns = total, nsz = 0, ni = 0;
+    // the copy walk (warp-uniform): tile pt of a chunk ending at pe, the chunks put in the ring (pk), the
+    // prefetched take (ns, nsz; lane 0 adds, the warp shares the result)
+    int pt, pe, pk = 0, ns = total, nsz = 0;
     int cs = 0;
-    if (lane == 0) {
-        int sz = guided_size(total, 0, W2, chunk);
-        const int s0 = atomicAdd(work, sz);
+    {
+        const int sz = guided_size(total, 0, W2, chunk);
+        const int s0 = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(work, sz) : 0, 0);
         pt = min(s0, total);
         pe = min(s0 + sz, total);
-        ring[pk++ & (kChunkRing - 1)] = make_int2(pt, pe);
+        if (lane == 0) ring[pk & (kChunkRing - 1)] = make_int2(pt, pe);
+        ++pk;
         if (pt < pe) {
             nsz = guided_size(total, s0, W2, chunk);
-            ns = atomicAdd(work, nsz);
+            ns = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(work, nsz) : 0, 0);
         }
-        for (int s = 0; s < STAGES && pt < pe; ++s) {
-            batch_issue<STAGES>(tile, bar, s_tile0, seg, pt, s, cs);
-            ++ni;
-            if (++pt == pe) {  // the chunk is issued: take the prefetched one
-                pt = min(ns, total);
-                pe = min(ns + nsz, total);
-                ring[pk++ & (kChunkRing - 1)] = make_int2(pt, pe);
-                if (pt < pe) {
-                    const int from = ns;
-                    nsz = guided_size(total, from, W2, chunk);
-                    ns = atomicAdd(work, nsz);
+        for (int s = 0; s < STAGES; ++s) {
+            if (pt < pe) {
+                batch_issue(tile, s_tile0, seg, pt, s, cs);
+                if (++pt == pe) {  // the chunk is issued: take the prefetched one
+                    pt = min(ns, total);
+                    pe = min(ns + nsz, total);
+                    if (lane == 0) ring[pk & (kChunkRing - 1)] = make_int2(pt, pe);
+                    ++pk;
+                    if (pt < pe) {
+                        const int from = ns;
+                        nsz = guided_size(total, from, W2, chunk);
+                        ns = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(work, nsz) : 0, 0);
+                    }
                 }
+            } else {
+                cp_async_commit();  // an empty group keeps one group per stage
             }
         }
     }
     __syncwarp();
     int2 ch = ring[0];
     int t = ch.x, te = ch.y, rk = 1;  // the compute walk: tile t of a chunk ending at te; ring entries read
-    int nd = 0;                       // tiles consumed
     int qn = 0;    // queued event indices of the current segment (warp-uniform)
     int cur = -1;  // current segment
     int sp = 0, ii = 0;
-    int st = 0;        // stage of the current tile
-    uint32_t ph = 0;   // its mbarrier phase parity
-    bool timed_out = false;
+    int st = 0;  // stage of the current tile
     while (t < te) {
-        if (!mbar_wait(&bar[st], ph)) {
-            timed_out = true;
-            break;
-        }
+        cp_async_wait<STAGES - 1>();  // this lane's copies of the current tile have landed
         if (t >= WS.t1) {  // the tile lies in a later segment
             if (qn > 0) {    // the queue holds indices of the previous segment: drain it first
                 const InstDev& I = inst[ii];
@@ -318,28 +322,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             b = tile[st].q1[lane];
             cc = tile[st].q2[lane];
         }
-        __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async();  // this stage's reads happen before the next copy overwrites it
-            if (pt < pe) {
-                batch_issue<STAGES>(tile, bar, s_tile0, seg, pt, st, cs);
-                ++ni;
-                if (++pt == pe) {  // the chunk is issued: take the prefetched one
-                    pt = min(ns, total);
-                    pe = min(ns + nsz, total);
-                    ring[pk++ & (kChunkRing - 1)] = make_int2(pt, pe);
-                    if (pt < pe) {
-                        const int from = ns;
-                        nsz = guided_size(total, from, W2, chunk);
-                        ns = atomicAdd(work, nsz);
-                    }
+        if (pt < pe) {  // the copies of the tile STAGES ahead, into the stage just read
+            batch_issue(tile, s_tile0, seg, pt, st, cs);
+            if (++pt == pe) {  // the chunk is issued: take the prefetched one
+                pt = min(ns, total);
+                pe = min(ns + nsz, total);
+                if (lane == 0) ring[pk & (kChunkRing - 1)] = make_int2(pt, pe);
+                ++pk;
+                if (pt < pe) {
+                    const int from = ns;
+                    nsz = guided_size(total, from, W2, chunk);
+                    ns = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(work, nsz) : 0, 0);
                 }
             }
+        } else {
+            cp_async_commit();
         }
-        if (++st == STAGES) {
-            st = 0;
-            ph ^= 1u;
-        }
+        if (++st == STAGES) st = 0;
         bool event = false;
         if (valid)
             event = sp == 2 ? photon_stream_one(C, WS.L, j, a, b, cc, ctr, c) : lepton_stream_one(C, WS.L, j, a, b, cc, ctr, c);
@@ -354,21 +353,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             qn -= 32;
             __syncwarp();
         }
-        ++nd;
         if (++t == te) {  // the chunk is done: the next one (its entry was written when its copies began)
             ch = ring[rk++ & (kChunkRing - 1)];
             t = ch.x;
             te = ch.y;
         }
     }
-    if (timed_out) {
-        if (lane == 0) {
-            record_error(ctr, QED_ERR_TIMEOUT, (long long)t * 32);
-            for (int m = nd; m < ni; ++m)  // let the copies in flight land
-                mbar_wait(&bar[m % STAGES], (uint32_t)((m / STAGES) & 1));
-        }
-        __syncwarp();
-    }
+    cp_async_wait<0>();  // no copy outlives the kernel (the trailing groups are empty)
     if (qn > 0) {
         const InstDev& I = inst[ii];
         if (sp == 2) photon_events(C, sh, wq, qn, I.sp[2], I.sp[0], I.sp[1], ctr, c);
