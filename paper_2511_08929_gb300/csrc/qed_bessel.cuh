@@ -156,11 +156,12 @@ struct TabP {
 template <class R>
 __device__ __forceinline__ void chi_coord(const TabP<R>& T, R lnchi, int& i, R& f) {
     const R s = (lnchi - T.lnchi_min) * T.inv_dlnchi;
-    if (!(s > R(0))) { i = 0; f = R(0); return; }
-    if (s >= R(T.n_chi - 1)) { i = T.n_chi - 2; f = R(1); return; }
-    i = (int)s;
-    if (i > T.n_chi - 2) i = T.n_chi - 2;
-    f = s - R(i);
+    const bool below = !(s > R(0)), above = s >= R(T.n_chi - 1);
+    int k = (int)(below || above ? R(0) : s);  // selects, not branches: lanes differ in chi
+    if (k > T.n_chi - 2) k = T.n_chi - 2;
+    const R fk = s - R(k);
+    i = below ? 0 : (above ? T.n_chi - 2 : k);
+    f = below ? R(0) : (above ? R(1) : fk);
 }
 
 // NLC rate integrals I_up, I_down at chi (classical chi-proportional below chi_min, clamped above chi_max)

@@ -138,12 +138,12 @@ __device__ __forceinline__ R two_sum(R a, R b, R& e) {
     return s;
 }
 
+// (written as a select, not a branch: lanes of a warp straddle the pulse edges)
 template <class R>
 __device__ __forceinline__ R envelope(R phi, const FieldP<R>& f) {
-    if (phi < R(0) || phi > f.phimax) return R(0);
     R s, c;
     phase_sincos(phi * f.inv2n, &s, &c);
-    return s * s;
+    return (phi < R(0) || phi > f.phimax) ? R(0) : s * s;
 }
 
 // phase_t = t + phase (split by the caller for the FP32 path as hi + lo)
@@ -336,21 +336,18 @@ __device__ __forceinline__ R nbw_G(R lam, R one_m, const R bes[3], const R xi[3]
 // with half-angle identities: (l cos dth)^2 = l (l + xi3)/2, (l sin dth)^2 = l (l - xi3)/2 and
 // (l cos dth)(l sin dth) = l xi1 / 2.  The larger component comes from its square root (no cancellation),
 // the smaller one from the product; cos dth >= 0.
+// Both cases are evaluated with the same operations and chosen by selects (no divergent branch).
 template <class R>
 __device__ __forceinline__ V3<R> stokes_to_P(const R xi[3], const V3<R>& eps, const V3<R>& beta, const V3<R>& k) {
     const R l = sqrt_(xi[0] * xi[0] + xi[2] * xi[2]);
-    R c = R(0), s = R(0);
-    if (l > R(0)) {
-        const R half = R(0.5) * l * xi[0];
-        if (xi[2] >= R(0)) {
-            c = sqrt_(R(0.5) * l * (l + xi[2]));
-            s = div_(half, c);
-        } else {
-            s = sqrt_(R(0.5) * l * (l - xi[2]));
-            if (xi[0] < R(0)) s = -s;
-            c = div_(half, s);
-        }
-    }
+    const bool up = xi[2] >= R(0);  // cos dth is the larger component
+    const R half = R(0.5) * l * xi[0];
+    R big = sqrt_(R(0.5) * l * (up ? l + xi[2] : l - xi[2]));
+    if (!up && xi[0] < R(0)) big = -big;
+    const R small = div_(half, big);
+    const bool some = l > R(0);
+    const R c = some ? (up ? big : small) : R(0);
+    const R s = some ? (up ? small : big) : R(0);
     return axpy(s, beta, axpy(c, eps, xi[1] * k));
 }
 
@@ -360,14 +357,10 @@ __device__ __forceinline__ void P_to_stokes(const V3<R>& P, const V3<R>& eps, co
     const R P1 = dot(P, eps), P2 = dot(P, beta);
     const R l2 = P1 * P1 + P2 * P2;
     xi[1] = dot(P, k);
-    if (l2 > R(0)) {
-        const R il = rsqrt_(l2);
-        xi[0] = R(2) * P1 * P2 * il;
-        xi[2] = (P1 * P1 - P2 * P2) * il;
-    } else {
-        xi[0] = R(0);
-        xi[2] = R(0);
-    }
+    const bool some = l2 > R(0);
+    const R il = rsqrt_(some ? l2 : R(1));
+    xi[0] = some ? R(2) * P1 * P2 * il : R(0);
+    xi[2] = some ? (P1 * P1 - P2 * P2) * il : R(0);
 }
 
 // ---------------------------------------------------------------------------------------------
