@@ -313,170 +313,252 @@ __global__ void mlp_adamw_kernel(float* P, float* Mm, float* Vv, const float* __
     P[k] -= lr * upd;
 }
 
-// ---- fused inference: layers 2-4 on tensor cores with the fragments chained in registers -------------
-constexpr int kIW = 4;       // warps per block
-constexpr int kWP = kH + 8;  // padded row pitch of the BF16 weights in shared memory
+// ---- fused inference on the 5th-generation tensor cores ---------------------------------------------
+// A block of 128 threads takes 128 samples at a time, one per thread and one per TMEM lane.  Layer 1
+// (K = 3) runs in FP32 on the CUDA cores; each thread writes its 64 SiLU outputs as BF16 into the A
+// tile in shared memory; one thread issues the 128 x 64 x 64 layer as four tcgen05.mma (K = 16 each)
+// with the FP32 accumulator in TMEM and commits them to an mbarrier; every thread then reads its row
+// of the accumulator (tcgen05.ld), adds the bias, applies SiLU and writes the next layer's A row.  The
+// output layer is padded to 16 rows (the smallest MMA width at M = 128).  Operands are K-major without
+// swizzle: core matrices of 8 rows x 16 bytes, 128 bytes apart along K, 8-row groups 1024 bytes apart.
+constexpr int kIW = 4;         // warps per block
+constexpr int kTR = kIW * 32;  // samples per tile (the MMA's M)
+constexpr int kTN4 = 16;       // output layer rows after padding
+constexpr uint32_t kTmemCols = 64;
+constexpr int kTcWaitLimit = 1 << 24;  // bounded mbarrier polling (~0.1 s) before giving up
 
-struct InferShared {
-    float w1[kOffW2];          // W1, b1 (FP32)
-    float b2[kH], b3[kH], b4[8];
-    __nv_bfloat16 w2[kH][kWP], w3[kH][kWP], w4[8][kWP];  // W4 padded to 8 rows
-    float out[kIW][32][4];
-    int64_t queue[kIW][64];  // sampler: indices of samples waiting for the table path
+struct TcShared {
+    alignas(1024) unsigned char a[kTR * kH * 2];  // activations (A operand), 16 KB
+    alignas(1024) unsigned char w2[kH * kH * 2];  // W2, W3 as B operands (N = 64 rows of K = 64)
+    alignas(1024) unsigned char w3[kH * kH * 2];
+    alignas(1024) unsigned char w4[kTN4 * kH * 2];  // W4 padded to 16 rows
+    float w1[kOffW2];                               // W1, b1 (FP32)
+    float b2[kH], b3[kH], b4[4];
+    int64_t queue[2 * kTR];  // sampler: indices of samples waiting for the table path
+    int queued;
+    uint64_t bar;            // MMA completion
+    uint32_t tmem;           // TMEM base address of the accumulator
 };
 
-// one 16-sample row tile: inputs x (rows g and g + 8 of this lane), outputs o (16 x 4, into out rows)
-__device__ __forceinline__ void infer_tile(const InferShared& S, const float xg[3], const float xh[3], int g, int t,
-                                           float (*out)[4]) {
-    // layer 1 (FP32) straight into the A operand of layer 2: k-step s holds columns 16s + 2t, +1, +8, +9
-    uint32_t a[4][4];
+// byte offset of element (row r, column k) in a K-major tile with K = 64
+__device__ __forceinline__ uint32_t kmaj(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row group) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTR >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// the 16 accumulator columns c0.. of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        float v[8];
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// D = A W^T for the A tile and the B operand w (n rows): thread 0 issues, every thread waits.  Returns
+// false (in every thread) if the wait gave up.
+__device__ bool tc_layer(TcShared& S, const unsigned char* w, int n, uint32_t& phase) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the A rows written above, to the MMA
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        const uint32_t id = tc_idesc(n);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int col = 16 * s + 2 * t + (q & 1) + (q >> 1) * 8;
-            const float* w = S.w1 + 3 * col;
-            const float b = S.w1[kOffB1 + col];
-            v[2 * q] = silu_f(fmaf(w[0], xg[0], fmaf(w[1], xg[1], fmaf(w[2], xg[2], b))));
-            v[2 * q + 1] = silu_f(fmaf(w[0], xh[0], fmaf(w[1], xh[1], fmaf(w[2], xh[2], b))));
+        for (int ks = 0; ks < kH / 16; ++ks) {
+            const uint64_t da = tc_desc(sm_u32(S.a) + 256 * ks), db = tc_desc(sm_u32(w) + 256 * ks);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(S.tmem),
+                "l"(da), "l"(db), "r"(id), "r"((uint32_t)ks)
+                : "memory");
         }
-        a[s][0] = pack_bf16(v[0], v[2]);  // row g, columns c, c + 1
-        a[s][1] = pack_bf16(v[1], v[3]);  // row g + 8
-        a[s][2] = pack_bf16(v[4], v[6]);  // row g, columns c + 8, c + 9
-        a[s][3] = pack_bf16(v[5], v[7]);  // row g + 8
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sm_u32(&S.bar))
+                     : "memory");
     }
-    float c[8][4];
-    // layers 2 and 3
-#pragma unroll
-    for (int layer = 0; layer < 2; ++layer) {
-        const __nv_bfloat16(*W)[kWP] = layer == 0 ? S.w2 : S.w3;
-        const float* bias = layer == 0 ? S.b2 : S.b3;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&W[8 * j + g][16 * s + 2 * t]);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&W[8 * j + g][16 * s + 8 + 2 * t]);
-                mma_bf16(c[j], a[s], b0, b1);
-            }
-        }
-        // bias + SiLU, repacked as the next layer's A operand (n-tiles 2s, 2s + 1 form k-step s)
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int c0 = 16 * s + 2 * t, c1 = c0 + 8;
-            a[s][0] = pack_bf16(silu_f(c[2 * s][0] + bias[c0]), silu_f(c[2 * s][1] + bias[c0 + 1]));
-            a[s][1] = pack_bf16(silu_f(c[2 * s][2] + bias[c0]), silu_f(c[2 * s][3] + bias[c0 + 1]));
-            a[s][2] = pack_bf16(silu_f(c[2 * s + 1][0] + bias[c1]), silu_f(c[2 * s + 1][1] + bias[c1 + 1]));
-            a[s][3] = pack_bf16(silu_f(c[2 * s + 1][2] + bias[c1]), silu_f(c[2 * s + 1][3] + bias[c1 + 1]));
-        }
+    bool done = false;
+    for (int i = 0; i < kTcWaitLimit && !done; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(sm_u32(&S.bar)), "r"(phase)
+            : "memory");
+        done = ok != 0;
     }
-    // layer 4 (4 outputs in an 8-column tile)
-    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    phase ^= 1u;
+    tc_fence_after();
+    return __syncthreads_and(done) != 0;
+}
+
+// this thread's 64 activations, bias + SiLU, into its A row as BF16
+__device__ __forceinline__ void tc_store_row(TcShared& S, const float v[kH]) {
+    const int r = threadIdx.x;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w4[g][16 * s + 2 * t]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w4[g][16 * s + 8 + 2 * t]);
-        mma_bf16(o, a[s], b0, b1);
-    }
-    if (t < 2) {
-        out[g][2 * t] = o[0] + S.b4[2 * t];
-        out[g][2 * t + 1] = o[1] + S.b4[2 * t + 1];
-        out[g + 8][2 * t] = o[2] + S.b4[2 * t];
-        out[g + 8][2 * t + 1] = o[3] + S.b4[2 * t + 1];
+    for (int c = 0; c < kH / 8; ++c) {
+        uint4 q;
+        q.x = pack_bf16(v[8 * c], v[8 * c + 1]);
+        q.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4*>(S.a + kmaj(r, 8 * c)) = q;
     }
 }
 
-__device__ void load_infer_shared(InferShared& S, const float* __restrict__ P) {
-    for (int i = threadIdx.x; i < kOffW2; i += blockDim.x) S.w1[i] = P[i];
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+// layers 1-4 for this thread's features x; o = raw outputs.  False if the tensor cores did not answer.
+__device__ bool tc_infer(TcShared& S, const float x[3], uint32_t& phase, float o[4]) {
+    float v[kH];
+#pragma unroll
+    for (int k = 0; k < kH; ++k) {
+        const float* w = S.w1 + 3 * k;
+        v[k] = silu_f(fmaf(w[0], x[0], fmaf(w[1], x[1], fmaf(w[2], x[2], S.w1[kOffB1 + k]))));
+    }
+    tc_store_row(S, v);
+    const uint32_t lane_addr = S.tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
+#pragma unroll 1
+    for (int layer = 0; layer < 2; ++layer) {
+        if (!tc_layer(S, layer == 0 ? S.w2 : S.w3, kH, phase)) return false;
+        const float* bias = layer == 0 ? S.b2 : S.b3;
+#pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 16) tc_ld16(lane_addr + (uint32_t)c0, v + c0);
+#pragma unroll
+        for (int k = 0; k < kH; ++k) v[k] = silu_f(v[k] + bias[k]);
+        tc_store_row(S, v);
+    }
+    if (!tc_layer(S, S.w4, kTN4, phase)) return false;
+    float u[16];
+    tc_ld16(lane_addr, u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = u[j] + S.b4[j];
+    return true;
+}
+
+// weights into shared memory, the mbarrier, and the TMEM accumulator (warp 0)
+__device__ void tc_setup(TcShared& S, const float* __restrict__ P) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kOffW2; i += blockDim.x) S.w1[i] = P[i];
+    for (int i = tid; i < kH; i += blockDim.x) {
         S.b2[i] = P[kOffB2 + i];
         S.b3[i] = P[kOffB3 + i];
     }
-    for (int i = threadIdx.x; i < 8; i += blockDim.x) S.b4[i] = i < 4 ? P[kOffB4 + i] : 0.0f;
-    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-        S.w2[i / kH][i % kH] = __float2bfloat16_rn(P[kOffW2 + i]);
-        S.w3[i / kH][i % kH] = __float2bfloat16_rn(P[kOffW3 + i]);
+    if (tid < 4) S.b4[tid] = P[kOffB4 + tid];
+    for (int i = tid; i < kH * kH; i += blockDim.x) {
+        const int r = i / kH, k = i % kH;
+        *reinterpret_cast<__nv_bfloat16*>(S.w2 + kmaj(r, k)) = __float2bfloat16_rn(P[kOffW2 + i]);
+        *reinterpret_cast<__nv_bfloat16*>(S.w3 + kmaj(r, k)) = __float2bfloat16_rn(P[kOffW3 + i]);
     }
-    for (int i = threadIdx.x; i < 8 * kH; i += blockDim.x)
-        S.w4[i / kH][i % kH] = __float2bfloat16_rn(i < 4 * kH ? P[kOffW4 + i] : 0.0f);
-}
-
-// raw network outputs for feature rows X[n][3]
-__global__ void __launch_bounds__(kIW * 32) mlp_forward_kernel(const float* __restrict__ P, const float* __restrict__ X,
-                                                              int64_t n, float* __restrict__ O) {
-    __shared__ InferShared S;
-    load_infer_shared(S, P);
+    for (int i = tid; i < kTN4 * kH; i += blockDim.x) {
+        const int r = i / kH, k = i % kH;
+        *reinterpret_cast<__nv_bfloat16*>(S.w4 + kmaj(r, k)) = __float2bfloat16_rn(r < 4 ? P[kOffW4 + i] : 0.0f);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&S.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int64_t base = ((int64_t)blockIdx.x * kIW + warp) * 16; base < n; base += (int64_t)gridDim.x * kIW * 16) {
-        float xg[3] = {0, 0, 0}, xh[3] = {0, 0, 0};
-        if (base + g < n)
-            for (int q = 0; q < 3; ++q) xg[q] = X[3 * (base + g) + q];
-        if (base + g + 8 < n)
-            for (int q = 0; q < 3; ++q) xh[q] = X[3 * (base + g + 8) + q];
-        infer_tile(S, xg, xh, g, t, S.out[warp]);
-        __syncwarp();
-        for (int e = lane; e < 64; e += 32) {
-            const int64_t row = base + e / 4;
-            if (row < n) O[4 * row + (e & 3)] = S.out[warp][e / 4][e & 3];
-        }
-        __syncwarp();
-    }
+    tc_fence_after();
 }
 
-// the table path for the queued samples q[0, cnt): lane e takes q[e] (all lanes call it)
+__device__ void tc_teardown(TcShared& S) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(kTmemCols) : "memory");
+}
+
+// raw network outputs for feature rows X[n][3] (NaN where the tensor cores did not answer)
+__global__ void __launch_bounds__(kTR) mlp_forward_kernel(const float* __restrict__ P, const float* __restrict__ X,
+                                                          int64_t n, float* __restrict__ O) {
+    __shared__ TcShared S;
+    tc_setup(S, P);
+    uint32_t phase = 0;
+    bool broken = false;  // a wait gave up: the remaining tiles skip the network (the same in every thread)
+    for (int64_t base = (int64_t)blockIdx.x * kTR; base < n; base += (int64_t)gridDim.x * kTR) {
+        const int64_t i = base + threadIdx.x;
+        float x[3] = {0.0f, 0.0f, 0.0f}, o[4];
+        if (i < n)
+            for (int q = 0; q < 3; ++q) x[q] = X[3 * i + q];
+        broken = broken || !tc_infer(S, x, phase, o);
+        if (broken)
+            for (int j = 0; j < 4; ++j) o[j] = __int_as_float(0x7FC00000);
+        if (i < n)
+            for (int j = 0; j < 4; ++j) O[4 * i + j] = o[j];
+    }
+    tc_teardown(S);
+}
+
+// the table path for sample i (the exact mixture quantile by bisection, and xi3 there)
 __device__ void table_path(const TabP<double>& T, const double* __restrict__ bes_tab, const double* __restrict__ chi_in,
-                           const double* __restrict__ r_in, const double* __restrict__ s_in, const int64_t* q, int cnt,
+                           const double* __restrict__ r_in, const double* __restrict__ s_in, int64_t i,
                            float* __restrict__ out4) {
-    const int e = threadIdx.x & 31;
-    if (e < cnt) {
-        const int64_t i = q[e];
-        const double chi = chi_in[i], r = r_in[i], s = s_in[i];
-        const MixPoint m = mix_point(T, chi, r, s);
-        const double L = mix_quantile<44, 32>(T, m, r);
-        out4[4 * i] = (float)L;
-        out4[4 * i + 1] = 0.0f;
-        out4[4 * i + 2] = 0.0f;
-        out4[4 * i + 3] = (float)xi3_at(bes_tab, chi, L, s);
-    }
+    const double chi = chi_in[i], r = r_in[i], s = s_in[i];
+    const MixPoint m = mix_point(T, chi, r, s);
+    const double L = mix_quantile<44, 32>(T, m, r);
+    out4[4 * i] = (float)L;
+    out4[4 * i + 1] = 0.0f;
+    out4[4 * i + 2] = 0.0f;
+    out4[4 * i + 3] = (float)xi3_at(bes_tab, chi, L, s);
 }
 
-// the sampler: network, CDF check; samples that fail it (or all, flags bit 0) wait in a per-warp queue
-// and take the table path 32 at a time, so that a warp never idles on one slow lane
-__global__ void __launch_bounds__(kIW * 32) mlp_sample_kernel(const float* __restrict__ P, TabP<double> T,
-                                                             const double* __restrict__ bes_tab,
-                                                             const double* __restrict__ chi_in, const double* __restrict__ r_in,
-                                                             const double* __restrict__ s_in, int64_t n, double tol,
-                                                             int flags, float* __restrict__ out4, uint8_t* __restrict__ fell,
-                                                             float* __restrict__ err_out, unsigned long long* n_fallback) {
-    __shared__ InferShared S;
-    load_infer_shared(S, P);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    int64_t* q = S.queue[warp];
-    int qn = 0;
-    unsigned long long nf = 0;
-    for (int64_t base = ((int64_t)blockIdx.x * kIW + warp) * 32; base < n; base += (int64_t)gridDim.x * kIW * 32) {
-        // two row tiles of 16 samples; the network outputs of sample base + e land in out[e]
-        for (int half = 0; half < 2; ++half) {
-            const int64_t b0 = base + 16 * half;
-            float xg[3] = {0, 0, 0}, xh[3] = {0, 0, 0};
-            if (b0 + g < n) mlp_features(chi_in[b0 + g], r_in[b0 + g], s_in[b0 + g], xg);
-            if (b0 + g + 8 < n) mlp_features(chi_in[b0 + g + 8], r_in[b0 + g + 8], s_in[b0 + g + 8], xh);
-            infer_tile(S, xg, xh, g, t, S.out[warp] + 16 * half);
+// the sampler: network, CDF check; samples that fail it (or all, flags bit 0) wait in a block-wide queue
+// and take the table path 128 at a time, one per thread, so that the block never waits on a few slow
+// threads (the tiles of the network keep the block in step)
+__global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict__ P, TabP<double> T,
+                                                         const double* __restrict__ bes_tab,
+                                                         const double* __restrict__ chi_in, const double* __restrict__ r_in,
+                                                         const double* __restrict__ s_in, int64_t n, double tol,
+                                                         int flags, float* __restrict__ out4, uint8_t* __restrict__ fell,
+                                                         float* __restrict__ err_out, unsigned long long* n_fallback) {
+    __shared__ TcShared S;
+    if (threadIdx.x == 0) S.queued = 0;
+    tc_setup(S, P);
+    unsigned long long nf = 0;  // thread 0: fallbacks of this block
+    uint32_t phase = 0;
+    bool broken = false;  // a wait gave up: the remaining tiles take the table path (the same in every thread)
+    const bool table_only = (flags & 1) != 0;
+    for (int64_t base = (int64_t)blockIdx.x * kTR; base < n; base += (int64_t)gridDim.x * kTR) {
+        const int64_t i = base + threadIdx.x;
+        float x[3] = {0.0f, 0.0f, 0.0f}, o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (i < n) mlp_features(chi_in[i], r_in[i], s_in[i], x);
+        bool net = false;  // the network ran for this tile
+        if (!table_only && !broken) {
+            net = tc_infer(S, x, phase, o);
+            broken = !net;
         }
-        __syncwarp();
-        const int64_t i = base + lane;
-        bool fb = false;
         if (i < n) {
-            fb = (flags & 1) != 0;
+            bool fb = !net;
             if (!fb) {
                 const double chi = chi_in[i], r = r_in[i], s = s_in[i];
                 const MixPoint m = mix_point(T, chi, r, s);
                 const double Lb = mix_baseline(T, m);
-                const float* o = S.out[warp][lane];
                 const double L = Lb + (double)o[0] / kOutScale;
                 const double xi1 = (double)o[1] / kOutScale, xi2 = (double)o[2] / kOutScale;
                 const double xi3 = xi3_at(bes_tab, chi, Lb, s) + (double)o[3] / kOutScale;
@@ -490,23 +572,29 @@ __global__ void __launch_bounds__(kIW * 32) mlp_sample_kernel(const float* __res
                     out4[4 * i + 2] = (float)xi2;
                     out4[4 * i + 3] = (float)xi3;
                 }
+            } else if (err_out) {
+                err_out[i] = -1.0f;
             }
-            else if (err_out) err_out[i] = -1.0f;
             if (fell) fell[i] = fb ? 1 : 0;
+            if (fb) S.queue[atomicAdd(&S.queued, 1)] = i;  // at most 2 kTR - 1 entries
         }
-        const unsigned mk = __ballot_sync(0xffffffffu, fb);
-        if (fb) q[qn + __popc(mk & ((1u << lane) - 1u))] = i;
-        qn += __popc(mk);
-        nf += lane == 0 ? (unsigned long long)__popc(mk) : 0ull;
-        __syncwarp();
-        if (qn >= 32) {
-            table_path(T, bes_tab, chi_in, r_in, s_in, q + (qn - 32), 32, out4);
-            qn -= 32;
+        __syncthreads();
+        const int qn = S.queued;  // the same in every thread
+        if (qn >= kTR) {
+            table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[qn - kTR + threadIdx.x], out4);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.queued = qn - kTR;
+                nf += kTR;
+            }
+            __syncthreads();
         }
-        __syncwarp();
     }
-    if (qn > 0) table_path(T, bes_tab, chi_in, r_in, s_in, q, qn, out4);
-    if (lane == 0 && nf && n_fallback) atomicAdd(n_fallback, nf);
+    __syncthreads();
+    const int qn = S.queued;
+    if ((int)threadIdx.x < qn) table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[threadIdx.x], out4);
+    if (threadIdx.x == 0 && n_fallback && nf + (unsigned long long)qn) atomicAdd(n_fallback, nf + (unsigned long long)qn);
+    tc_teardown(S);
 }
 
 }  // namespace qed
@@ -675,11 +763,23 @@ extern "C" qed_status qed_mlp_train(qed_mlp_t m, qed_tables_t t, int64_t steps, 
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
+// persistent grid for the tensor-core kernels: one resident wave of 128-thread blocks, at most 4 per SM
+// (each holds 64 TMEM columns of the SM's 512, and its 38 KB of shared memory)
+static int tc_blocks(int64_t n, const void* kern) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTR, 0);
+    const int64_t resident = (int64_t)sms * std::max(1, std::min(per_sm, 4));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kTR - 1) / kTR, resident));
+}
+
 extern "C" qed_status qed_mlp_forward(qed_mlp_t m, const float* x_dev, int64_t n, float* out_dev, void* stream) {
     if (!valid_mlp(m)) return QED_ERR_STATE;
     if (n < 0 || (n > 0 && (!x_dev || !out_dev))) return QED_ERR_ARG;
     if (n == 0) return QED_OK;
-    mlp_forward_kernel<<<grid_for((n + 15) / 16, kIW), kIW * 32, 0, (cudaStream_t)stream>>>(m->P, x_dev, n, out_dev);
+    mlp_forward_kernel<<<tc_blocks(n, (const void*)mlp_forward_kernel), kTR, 0, (cudaStream_t)stream>>>(m->P, x_dev, n,
+                                                                                                   out_dev);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
@@ -690,18 +790,10 @@ extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* 
     if (!valid_tables(t)) return QED_ERR_STATE;
     if (n < 0 || (n > 0 && (!chi || !r || !s || !out4)) || !(tol >= 0.0) || (flags & ~QED_MLP_ALWAYS_TABLE)) return QED_ERR_ARG;
     if (n == 0) return QED_OK;
-    // persistent grid (one resident wave): each warp streams many 32-sample batches, so its fallback queue
+    // persistent grid (one resident wave): each warp streams many 32-sample rows, so its fallback queue
     // drains full
-    static int resident = 0;
-    if (resident == 0) {
-        int dev = 0, sms = 1, per_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_sample_kernel, kIW * 32, 0);
-        resident = sms * std::max(1, per_sm);
-    }
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kIW - 1) / (32 * kIW), resident));
-    mlp_sample_kernel<<<blocks, kIW * 32, 0, (cudaStream_t)stream>>>(
+    const int blocks = tc_blocks(n, (const void*)mlp_sample_kernel);
+    mlp_sample_kernel<<<blocks, kTR, 0, (cudaStream_t)stream>>>(
         m->P, tab_params<double>(t), t->bes64, chi, r, s, n, tol, flags, out4, fell_back, err_out, n_fallback);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
