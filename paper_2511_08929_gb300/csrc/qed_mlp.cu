@@ -8,10 +8,11 @@
 // predicts the correction to the rate-weighted blend of the two branch quantiles (and of xi3 there),
 // scaled by 100.
 //
-// Kernels: target generation (FP64), a BF16 tensor-core GEMM with FP32 accumulation (mma.sync m16n8k16;
-// split-K for the weight gradients), FP32 elementwise / first-layer / reduction / AdamW kernels for
-// training, and a fused inference kernel whose layer outputs stay in registers as the next layer's
-// tensor-core operands, followed by the CDF check and the table fallback.
+// Kernels: target generation (FP64), a BF16 GEMM on the tensor cores (tcgen05.mma, FP32 accumulator in
+// TMEM; split-K for the weight gradients), FP32 elementwise / first-layer / reduction / AdamW kernels for
+// training, and a fused inference kernel (layers 2-4 as tcgen05.mma on 128-sample tiles, bias and SiLU
+// between them applied on the way from TMEM back to shared memory), followed by the CDF check and the
+// table fallback.
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -146,74 +147,10 @@ __global__ void mlp_targets_kernel(TabP<double> T, const double* __restrict__ be
     }
 }
 
-// ---- BF16 tensor-core GEMM (FP32 in global memory, rounded to BF16 when staged; FP32 accumulation) -----
+// ---- BF16 helpers -------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower 16 bits), .y = hi
     return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-constexpr int kGM = 64, kGN = 64, kGK = 32, kGP = kGK + 8;  // tile and padded row pitch (bf16 elements)
-
-// C(m, n) (+)= sum_k A(m, k) B(k, n); A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn];
-// C row-major with leading dimension ldc.  grid = (ceil(N/64), ceil(M/64), ksplit); with ksplit > 1
-// the partial sums are added atomically (C zeroed by the caller).
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, int64_t sam,
-                                                         int64_t sak, const float* __restrict__ B, int64_t sbk,
-                                                         int64_t sbn, float* __restrict__ C, int64_t ldc, int ksplit) {
-    __shared__ __align__(16) __nv_bfloat16 As[kGM][kGP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[kGN][kGP];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
-    const int kchunk = ((K + ksplit - 1) / ksplit + kGK - 1) / kGK * kGK;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-    for (int k0 = kb; k0 < ke; k0 += kGK) {
-        for (int e = threadIdx.x; e < kGM * kGK; e += 128) {
-            const int mm = e / kGK, kk = e % kGK, m = m0 + mm, k = k0 + kk;
-            As[mm][kk] = __float2bfloat16_rn(m < M && k < ke ? A[m * sam + k * sak] : 0.0f);
-        }
-        for (int e = threadIdx.x; e < kGN * kGK; e += 128) {
-            const int nn = e / kGK, kk = e % kGK, n = n0 + nn, k = k0 + kk;
-            Bs[nn][kk] = __float2bfloat16_rn(n < N && k < ke ? B[k * sbk + n * sbn] : 0.0f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < kGK; ks += 16) {
-            uint32_t a[4];
-            const int r0 = warp * 16 + g;
-            a[0] = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * t]);
-            a[1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * t]);
-            a[2] = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 8 + 2 * t]);
-            a[3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 8 + 2 * t]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[8 * j + g][ks + 2 * t]);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[8 * j + g][ks + 8 + 2 * t]);
-                mma_bf16(acc[j], a, b0, b1);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int m = m0 + warp * 16 + g + (h >> 1) * 8, n = n0 + 8 * j + 2 * t + (h & 1);
-            if (m < M && n < N) {
-                if (ksplit > 1) atomicAdd(&C[m * ldc + n], acc[j][h]);
-                else C[m * ldc + n] = acc[j][h];
-            }
-        }
-    }
 }
 
 // ---- training kernels (FP32) ------------------------------------------------------------------------
@@ -486,12 +423,116 @@ __device__ void tc_setup(TcShared& S, const float* __restrict__ P) {
     tc_fence_after();
 }
 
-__device__ void tc_teardown(TcShared& S) {
+__device__ void tc_teardown(uint32_t tmem) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// ---- BF16 GEMM on the tensor cores for training (FP32 in global memory, rounded to BF16 when staged;
+// FP32 accumulation in TMEM) ----------------------------------------------------------------------------
+// C(m, n) (+)= sum_k A(m, k) B(k, n); A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]; C row-major
+// with leading dimension ldc.  A block of 128 threads computes a 128 x 64 tile of C, staging 64-wide K
+// slices of A and B (any strides) as K-major BF16 operands and accumulating with tcgen05.mma.
+// grid = (ceil(N/64), ceil(M/128), ksplit); with ksplit > 1 the partial sums are added atomically (C
+// zeroed by the caller).  If the tensor cores do not answer within the wait limit the tile is NaN.
+struct GemmShared {
+    alignas(1024) unsigned char a[kTR * kH * 2];  // A slice: 128 rows x 64 K
+    alignas(1024) unsigned char b[kH * kH * 2];   // B slice: 64 columns of C x 64 K
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(kTR) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, int64_t sam,
+                                                         int64_t sak, const float* __restrict__ B, int64_t sbk,
+                                                         int64_t sbn, float* __restrict__ C, int64_t ldc, int ksplit) {
+    __shared__ GemmShared S;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&S.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const int m0 = blockIdx.y * kTR, n0 = blockIdx.x * kH;
+    const int kchunk = ((K + ksplit - 1) / ksplit + kH - 1) / kH * kH;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const uint32_t id = tc_idesc(kH);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = kb; k0 < ke && ok; k0 += kH) {
+        for (int e = tid; e < kTR * kH; e += kTR) {
+            const int mm = e / kH, kk = e % kH, m = m0 + mm, k = k0 + kk;
+            *reinterpret_cast<__nv_bfloat16*>(S.a + kmaj(mm, kk)) =
+                __float2bfloat16_rn(m < M && k < ke ? A[m * sam + k * sak] : 0.0f);
+        }
+        for (int e = tid; e < kH * kH; e += kTR) {
+            const int nn = e / kH, kk = e % kH, n = n0 + nn, k = k0 + kk;
+            *reinterpret_cast<__nv_bfloat16*>(S.b + kmaj(nn, kk)) =
+                __float2bfloat16_rn(n < N && k < ke ? B[k * sbk + n * sbn] : 0.0f);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < kH / 16; ++ks) {
+                const uint64_t da = tc_desc(sm_u32(S.a) + 256 * ks), db = tc_desc(sm_u32(S.b) + 256 * ks);
+                const uint32_t acc = (k0 > kb || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(S.tmem),
+                    "l"(da), "l"(db), "r"(id), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             sm_u32(&S.bar))
+                         : "memory");
+        }
+        bool done = false;
+        for (int i = 0; i < kTcWaitLimit && !done; ++i) {
+            uint32_t r;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(r)
+                : "r"(sm_u32(&S.bar)), "r"(phase)
+                : "memory");
+            done = r != 0;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        ok = __syncthreads_and(done) != 0;  // also: the slices may be restaged
+    }
+    if (kb < ke) {
+        const int m = m0 + tid;
+        const uint32_t lane_addr = S.tmem + ((uint32_t)(tid & ~31) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tc_ld16(lane_addr + (uint32_t)c0, v);
+            if (m < M)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < N) {
+                        const float x = ok ? v[j] : __int_as_float(0x7FC00000);
+                        if (ksplit > 1) atomicAdd(&C[m * ldc + n], x);
+                        else C[m * ldc + n] = x;
+                    }
+                }
+        }
+    }
+    tc_teardown(S.tmem);
 }
 
 // raw network outputs for feature rows X[n][3] (NaN where the tensor cores did not answer)
@@ -512,7 +553,7 @@ __global__ void __launch_bounds__(kTR) mlp_forward_kernel(const float* __restric
         if (i < n)
             for (int j = 0; j < 4; ++j) O[4 * i + j] = o[j];
     }
-    tc_teardown(S);
+    tc_teardown(S.tmem);
 }
 
 // the table path for sample i (the exact mixture quantile by bisection, and xi3 there)
@@ -594,7 +635,7 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
     const int qn = S.queued;
     if ((int)threadIdx.x < qn) table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[threadIdx.x], out4);
     if (threadIdx.x == 0 && n_fallback && nf + (unsigned long long)qn) atomicAdd(n_fallback, nf + (unsigned long long)qn);
-    tc_teardown(S);
+    tc_teardown(S.tmem);
 }
 
 }  // namespace qed
@@ -620,8 +661,8 @@ static int grid_for(int64_t work, int threads) {
 
 static void gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk,
                  int64_t sbn, float* C, int64_t ldc, int ksplit, cudaStream_t st) {
-    const dim3 grid((N + kGN - 1) / kGN, (M + kGM - 1) / kGM, ksplit);
-    gemm_bf16_kernel<<<grid, 128, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, ksplit);
+    const dim3 grid((N + kH - 1) / kH, (M + kTR - 1) / kTR, ksplit);
+    gemm_bf16_kernel<<<grid, kTR, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, ksplit);
 }
 
 extern "C" void qed_mlp_destroy(qed_mlp_t m) {
