@@ -2,14 +2,18 @@
 // time step, the step index and time on the device (so a CUDA graph of whole steps replays unchanged),
 // and an autotuner for the launch shape.
 //
-// One time step of the batch is six launches on one stream:
+// One time step of the batch is seven launches on one stream:
 //   plan      alive counts at step start (counts clamped to capacity), the tile list over all segments
-//             (segment = one species of one instance, species-major), particle-step accounting;
+//             (segment = one species of one instance, species-major), each segment's step context,
+//             particle-step accounting;
 //   step      the persistent kernel: every warp takes runs of consecutive tiles from a work counter
 //             (guided: long runs first, short ones at the end, at most `chunk` tiles) and streams them
-//             with the same bulk-copy pipeline, per-particle arithmetic and per-warp event queue as the
-//             single-buffer FP32 kernels; the event queue is drained when a warp crosses into another
-//             segment;
+//             with the same copy pipeline and per-particle arithmetic as the single-buffer FP32 kernels;
+//             a particle whose optical depth runs out is left untouched and listed (segment, index) in
+//             the step's event list, 32 entries per atomic add;
+//   events    the event branch for every listed particle, 32 per warp with a context per lane (out of
+//             the persistent kernel, whose registers then hold only the streaming pass: no calls, no
+//             spills);
 //   compact   head / classify / tail / move of every instance's photons (converted photons leave,
 //             Sec. 3.3), the last one also advancing the device step counter.
 // Daughters appended during a step sit beyond the counts taken by `plan`, so they are first stepped in
@@ -48,6 +52,7 @@ struct ClockDev {
     unsigned long long species_steps[kSpecies];
     long long alive[kSpecies];
     int next_tile;  // the persistent kernel's work counter (tiles handed out), reset by the plan kernel
+    unsigned long long n_events;  // entries in the step's event list, reset by the plan kernel
 };
 
 struct BatchP {
@@ -56,13 +61,21 @@ struct BatchP {
     double store_min, chi_floor;
 };
 
+// The step context of one segment (one species of one instance), written by the plan kernel every
+// step for the event kernel: its lanes take events of several segments at once.
+struct SegCtx {
+    Ctx C;       // tables (global memory), field, step parameters and charge
+    int ii, sp;  // instance and species
+};
+
 // ------------------------------------------------------------------------------------------------
 // plan: one block of kPlanThreads threads, each owning up to 3 consecutive segments
 // ------------------------------------------------------------------------------------------------
 constexpr int kPlanThreads = 1024;
 
-__global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev* __restrict__ inst, int n_inst, SegDev* seg,
-                                                                 int64_t* tile0, ClockDev* clk) {
+__global__ void __launch_bounds__(kPlanThreads)
+    batch_plan_kernel(const InstDev* __restrict__ inst, int n_inst, SegDev* seg, int64_t* tile0, ClockDev* clk,
+                      SegCtx* ctx, TabP<float> T, const float* bes, BatchP P) {
     __shared__ long long wsum[32];
     __shared__ unsigned long long tot[kSpecies];
     const int n_seg = kSpecies * n_inst;
@@ -75,11 +88,11 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev*
         const int s = s0 + k;
         if (s >= n_seg) break;
         const int sp = s / n_inst, i = s - sp * n_inst;
-        const PartDev& P = inst[i].sp[sp];
-        const int64_t c = *P.count;
-        const int64_t n = c < 0 ? 0 : (c > P.capacity ? P.capacity : c);
-        if (c != n) *P.count = n;  // reservations that did not fit
-        seg[s] = SegDev{P.q0, P.q1, P.q2, n};
+        const PartDev& Pd = inst[i].sp[sp];
+        const int64_t c = *Pd.count;
+        const int64_t n = c < 0 ? 0 : (c > Pd.capacity ? Pd.capacity : c);
+        if (c != n) *Pd.count = n;  // reservations that did not fit
+        seg[s] = SegDev{Pd.q0, Pd.q1, Pd.q2, n};
         loc[k] = (n + 31) / 32;
         mine += loc[k];
         atomicAdd(&tot[sp], (unsigned long long)n);
@@ -106,14 +119,40 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const InstDev*
     }
     __syncthreads();
     long long ex = wsum[wid] + incl - mine;
+    const uint64_t step = clk->step;
+    // time of this step: a product then a sum, each rounded (no contraction)
+    const double t_now = __dadd_rn(clk->t0, __dmul_rn((double)(step - clk->step0), clk->dt));
     for (int k = 0; k < per; ++k) {
         const int s = s0 + k;
         if (s >= n_seg) break;
         tile0[s] = ex;
         ex += loc[k];
+        const int sp = s / n_inst, i = s - sp * n_inst;
+        const InstDev& I = inst[i];
+        SegCtx& X = ctx[s];
+        X.ii = i;
+        X.sp = sp;
+        X.C.T = T;
+        X.C.bes = bes;
+        X.C.F = I.F;
+        X.C.q = sp == 0 ? -1.0f : (sp == 1 ? 1.0f : 0.0f);
+        StepP& S = X.C.S;
+        S.dt = clk->dt;
+        S.ph_hi = __dadd_rn(t_now, I.phase);
+        S.ph_hi_f = (float)S.ph_hi;
+        S.ph_lo_f = (float)(S.ph_hi - (double)S.ph_hi_f);
+        S.dt_f = P.dt_f;
+        S.flags = P.flags;
+        S.step = step;
+        S.seed = I.seed;
+        S.store_min = P.store_min;
+        S.chi_floor = P.chi_floor;
+        S.store_min_f = (float)P.store_min;
+        S.chi_floor_f = (float)P.chi_floor;
     }
     if (threadIdx.x == 0) {
         clk->next_tile = 0;
+        clk->n_events = 0;
         clk->psteps += tot[0] + tot[1] + tot[2];
         for (int k = 0; k < kSpecies; ++k) {
             clk->species_steps[k] += tot[k];
@@ -193,7 +232,8 @@ template <int WARPS, int STAGES, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     batch_step_kernel(TabP<float> T, float* bes_g, const InstDev* __restrict__ inst,
                       const SegDev* __restrict__ seg, const int64_t* __restrict__ tile0_g, int n_inst,
-                      const ClockDev* __restrict__ clk, BatchP P, int chunk, int* work, qed_counters* ctr) {
+                      const ClockDev* __restrict__ clk, BatchP P, int chunk, int* work, long long* ev,
+                      unsigned long long* n_ev, qed_counters* ctr) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int n_seg = kSpecies * n_inst;
     Shared32 sh;
@@ -271,12 +311,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     while (t < te) {
         cp_async_wait<STAGES - 1>();  // this lane's copies of the current tile have landed
         if (t >= WS.t1) {  // the tile lies in a later segment
-            if (qn > 0) {    // the queue holds indices of the previous segment: drain it first
-                const InstDev& I = inst[ii];
-                if (sp == 2) photon_events(C, sh, wq, qn, I.sp[2], I.sp[0], I.sp[1], ctr, c);
-                else lepton_events(C, sh, wq, qn, I.sp[sp], I.sp[2], ctr, c);
-                qn = 0;
-            }
             do ++cur;
             while (s_tile0[cur + 1] <= t);
             sp = cur / n_inst;
@@ -343,13 +377,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         if (valid)
             event = sp == 2 ? photon_stream_one(C, WS.L, j, a, b, cc, ctr, c) : lepton_stream_one(C, WS.L, j, a, b, cc, ctr, c);
         const unsigned m = __ballot_sync(0xffffffffu, event);
-        if (event) wq[qn + __popc(m & ((1u << lane) - 1u))] = j;
+        if (event) wq[qn + __popc(m & ((1u << lane) - 1u))] = ((long long)cur << 32) | (long long)j;
         qn += __popc(m);
         __syncwarp();
-        if (qn >= 32) {
-            const InstDev& I = inst[ii];
-            if (sp == 2) photon_events(C, sh, wq + (qn - 32), 32, I.sp[2], I.sp[0], I.sp[1], ctr, c);
-            else lepton_events(C, sh, wq + (qn - 32), 32, I.sp[sp], I.sp[2], ctr, c);
+        if (qn >= 32) {  // 32 entries to the step's event list with one atomic add
+            const unsigned long long base = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(n_ev, 32ull) : 0ull, 0);
+            ev[base + lane] = wq[qn - 32 + lane];
             qn -= 32;
             __syncwarp();
         }
@@ -361,9 +394,40 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     }
     cp_async_wait<0>();  // no copy outlives the kernel (the trailing groups are empty)
     if (qn > 0) {
-        const InstDev& I = inst[ii];
-        if (sp == 2) photon_events(C, sh, wq, qn, I.sp[2], I.sp[0], I.sp[1], ctr, c);
-        else lepton_events(C, sh, wq, qn, I.sp[sp], I.sp[2], ctr, c);
+        const unsigned long long base =
+            __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(n_ev, (unsigned long long)qn) : 0ull, 0);
+        if (lane < qn) ev[base + lane] = wq[lane];
+    }
+    flush_warp(c, ctr);
+}
+
+// ------------------------------------------------------------------------------------------------
+// the event pass of the step: every event the persistent kernel listed (a particle whose optical depth
+// ran out, left untouched by it), 32 per warp, each lane with the context of its own segment
+// ------------------------------------------------------------------------------------------------
+constexpr int kEventThreads = 256;
+
+__global__ void __launch_bounds__(kEventThreads) batch_event_kernel(const InstDev* __restrict__ inst,
+                                                                   const SegCtx* __restrict__ ctx,
+                                                                   const long long* __restrict__ ev,
+                                                                   const ClockDev* __restrict__ clk, qed_counters* ctr) {
+    const unsigned long long n = clk->n_events;
+    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (kEventThreads / 32);
+    for (unsigned long long k = ((unsigned long long)blockIdx.x * (kEventThreads / 32) + (threadIdx.x >> 5)) * 32; k < n;
+         k += warps * 32) {
+        const long long e = k + lane < n ? ev[k + lane] : -1;
+        const int seg0 = __shfl_sync(0xffffffffu, (int)(e >> 32), 0);  // lane 0 always holds an entry
+        const int s = e >= 0 ? (int)(e >> 32) : seg0;
+        const int64_t j = e >= 0 ? (int64_t)(uint32_t)e : -1;
+        const SegCtx& X = ctx[s];
+        const InstDev& I = inst[X.ii];
+        const bool ph = X.sp == 2;
+        // both passes are warp-collective; a lane takes part in the one of its species with its particle
+        if (__ballot_sync(0xffffffffu, j >= 0 && !ph))
+            lepton_events(X.C, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], ctr, c);
+        if (__ballot_sync(0xffffffffu, j >= 0 && ph)) photon_events(X.C, ph ? j : -1, I.sp[2], I.sp[0], I.sp[1], ctr, c);
     }
     flush_warp(c, ctr);
 }
@@ -451,6 +515,9 @@ struct qed_batch_s {
     qed_counters* ctr;
     InstDev* d_inst;
     SegDev* d_seg;
+    SegCtx* d_ctx;     // per-segment step contexts (plan kernel -> event kernel)
+    long long* d_ev;   // the step's event list: segment << 32 | particle index, one slot per particle
+    int ev_grid;       // event kernel grid
     int64_t* d_tile0;
     ClockDev* d_clk;
     int64_t* d_hdr;
@@ -476,7 +543,7 @@ static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
     P.chi_floor = b->desc.chi_floor;
     batch_step_kernel<WARPS, STAGES, MINB><<<grid, WARPS * 32, smem, st>>>(
         tab_params<float>(t), t->bes32, b->d_inst, b->d_seg, b->d_tile0, b->n_inst, b->d_clk, P, b->tuning.chunk,
-        &b->d_clk->next_tile, b->ctr);
+        &b->d_clk->next_tile, b->d_ev, &b->d_clk->n_events, b->ctr);
 }
 
 static const BatchVariant kVariants[QED_BATCH_VARIANTS] = {
@@ -509,9 +576,16 @@ static bool valid_batch(const qed_batch_s* b) { return b != nullptr && b->magic 
 static void launch_batch_step(const qed_batch_s* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
                               bool capturing = false) {
     const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b->d_inst, b->n_inst, b->d_seg, b->d_tile0, b->d_clk);
+    BatchP P;
+    P.flags = b->desc.flags;
+    P.dt_f = (float)b->desc.dt;
+    P.store_min = b->desc.photon_store_min;
+    P.chi_floor = b->desc.chi_floor;
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b->d_inst, b->n_inst, b->d_seg, b->d_tile0, b->d_clk, b->d_ctx,
+                                                  tab_params<float>(b->tables), b->tables->bes32, P);
     if (e0) cudaEventRecordWithFlags(e0, st, rec);
     kVariants[b->tuning.variant].launch(b, b->grid, st);
+    batch_event_kernel<<<b->ev_grid, kEventThreads, 0, st>>>(b->d_inst, b->d_ctx, b->d_ev, b->d_clk, b->ctr);
     if (e1) cudaEventRecordWithFlags(e1, st, rec);
     batch_compact_head<<<(b->n_inst + 255) / 256, 256, 0, st>>>(b->d_inst, b->n_inst);
     const dim3 g(kCompactBlocks, b->n_inst);
@@ -578,6 +652,8 @@ extern "C" void qed_batch_destroy(qed_batch_t b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     cudaFree(b->d_inst);
     cudaFree(b->d_seg);
+    cudaFree(b->d_ctx);
+    cudaFree(b->d_ev);
     cudaFree(b->d_tile0);
     cudaFree(b->d_clk);
     cudaFree(b->d_hdr);
@@ -623,6 +699,8 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
     }
     ok = ok && cudaMalloc(&b->d_inst, sizeof(InstDev) * n_inst) == cudaSuccess &&
          cudaMalloc(&b->d_seg, sizeof(SegDev) * n_seg) == cudaSuccess &&
+         cudaMalloc(&b->d_ctx, sizeof(SegCtx) * n_seg) == cudaSuccess &&
+         cudaMalloc(&b->d_ev, sizeof(long long) * (size_t)std::max<int64_t>(1, b->capacity_total)) == cudaSuccess &&
          cudaMalloc(&b->d_tile0, sizeof(int64_t) * (n_seg + 1)) == cudaSuccess &&
          cudaMalloc(&b->d_clk, sizeof(ClockDev)) == cudaSuccess &&
          cudaMalloc(&b->d_hdr, sizeof(int64_t) * 4 * n_inst) == cudaSuccess &&
@@ -664,6 +742,9 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
         qed_batch_destroy(b);
         return QED_ERR_CUDA;
     }
+    int ev_per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, batch_event_kernel, kEventThreads, 0);
+    b->ev_grid = b->sms * std::max(1, ev_per_sm);
     const qed_batch_tuning def{0, 0, 64, 8};
     if (qed_batch_set_tuning(b, &def) != QED_OK) {
         qed_batch_destroy(b);

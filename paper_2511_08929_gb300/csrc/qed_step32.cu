@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            if (PHOTON) photon_events(C, sh, wq + (qn - 32), 32, P, D1, D2, ctr, c);
-            else lepton_events(C, sh, wq + (qn - 32), 32, P, D1, ctr, c);
+            const int64_t je = wq[qn - 32 + lane];
+            if (PHOTON) photon_events(C, je, P, D1, D2, ctr, c);
+            else lepton_events(C, je, P, D1, ctr, c);
             qn -= 32;
             __syncwarp();
         }
@@ -107,8 +108,9 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
         __syncwarp();
     }
     if (qn > 0) {
-        if (PHOTON) photon_events(C, sh, wq, qn, P, D1, D2, ctr, c);
-        else lepton_events(C, sh, wq, qn, P, D1, ctr, c);
+        const int64_t je = lane < qn ? wq[lane] : -1;
+        if (PHOTON) photon_events(C, je, P, D1, D2, ctr, c);
+        else lepton_events(C, je, P, D1, ctr, c);
     }
     flush_warp(c, ctr);
 }

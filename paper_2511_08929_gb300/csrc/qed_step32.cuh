@@ -203,6 +203,22 @@ struct TileStream {
     }
 };
 
+// Slot reservation on per-lane device counters (all 32 lanes call it): the lanes that name the same
+// counter form one group, whose first wanting lane takes the group's slots with one atomic add; a lane
+// that does not want a slot (or names no counter) gets -1.  Lanes of one event pass may belong to
+// different buffers (the batched event kernel takes events of several instances at once).
+__device__ __forceinline__ long long reserve_grouped(int64_t* counter, bool want) {
+    want = want && counter != nullptr;
+    const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)counter);
+    const unsigned m = __ballot_sync(0xffffffffu, want) & grp;
+    if (m == 0) return -1;  // uniform over the group
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    long long base = 0;
+    if (lane == leader) base = (long long)atomicAdd((unsigned long long*)counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(grp, base, leader);
+    return want ? base + (long long)__popc(m & ((1u << lane) - 1u)) : -1;
+}
+
 // ------------------------------------------------------------------------------------------------
 // lepton step
 // ------------------------------------------------------------------------------------------------
@@ -273,18 +289,16 @@ __device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x
     L.q2[j] = make_float4(s.z, w, lo, hi);
 }
 
-// the event pass of one warp: lane l takes the particle index q[l] if l < cnt (all 32 lanes call it)
-static __device__ __noinline__ void lepton_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& L, const PartDev& G,
-                              qed_counters* ctr, unsigned long long* c) {
+// the event pass of one warp (all 32 lanes call it): a lane with j >= 0 takes particle j of buffer L,
+// whose step context is C (lanes may differ in both)
+static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const PartDev& L, const PartDev& G,
+                                                 qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = C.S.flags;
-    const int e = threadIdx.x & 31;
     bool want = false;
     F3 gx{0, 0, 0}, gk{0, 0, 0}, gP{0, 0, 0};
     float gw = 0.0f;
     uint64_t gid = 0;
-    int64_t j = -1;
-    if (e < cnt) {
-        j = q[e];
+    if (j >= 0) {
         const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
         LState st;
         lepton_classical(C, a, b, cc, st, nullptr);  // the streaming pass's arithmetic, repeated
@@ -307,7 +321,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Shared32& 
         const F3 k = lam * st.p;
         if (fl & QED_F_RECOIL) pf = one_m * st.p;
         float bb[3];
-        bessel32(sh.bes, up, bb);
+        bessel32(C.bes, up, bb);
         const bool resolved = (fl & QED_F_RESOLVED) != 0;
         const F3 si = resolved ? st.s : F3{0, 0, 0};
         F3 sfu{0, 0, 0};
@@ -353,9 +367,9 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Shared32& 
         }
         store32(L, j, st.x, pf, sf, st.w, tauf);
     }
-    if (G.count != nullptr) {
-        const long long slot = reserve_slots(G.count, want, 1);
-        if (want) {
+    {
+        const long long slot = reserve_grouped(G.count, want);
+        if (want && G.count != nullptr) {
             if (slot < G.capacity) {
                 store32(G, slot, gx, gk, gP, gw, birth_tau32(gid, C.S.seed));
                 G.id[slot] = gid;
@@ -364,9 +378,9 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Shared32& 
                 c[C_DROPPED]++;
                 record_error(ctr, QED_ERR_CAPACITY, j);
             }
+        } else if (want) {
+            c[C_DROPPED]++;
         }
-    } else if (want) {
-        c[C_DROPPED]++;
     }
 }
 
@@ -452,19 +466,16 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.Wx = st.Wp * (1.0f + st.xi[2]) * 0.5f + st.Wmp;
 }
 
-static __device__ __noinline__ void photon_events(const Ctx& C, const Shared32& sh, const int64_t* q, int cnt, const PartDev& G, const PartDev& El,
-                              const PartDev& Po, qed_counters* ctr, unsigned long long* c) {
+static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const PartDev& G, const PartDev& El,
+                                                 const PartDev& Po, qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = C.S.flags;
     const bool have = El.count != nullptr && Po.count != nullptr;
-    const int e = threadIdx.x & 31;
     bool want = false;
     F3 x{0, 0, 0}, k{0, 0, 0}, P{0, 0, 0}, pe{0, 0, 0}, pp{0, 0, 0}, se{0, 0, 0}, sp{0, 0, 0};
     float w = 0.0f;
     double tauf = 0.0;
     uint64_t ide = 0, idp = 0;
-    int64_t j = -1;
-    if (e < cnt) {
-        j = q[e];
+    if (j >= 0) {
         const float4 a = __ldcg(G.q0 + j), b = __ldcg(G.q1 + j), cc = __ldcg(G.q2 + j);
         PState st;
         photon_classical(C, a, b, cc, st, nullptr);
@@ -500,7 +511,7 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Shared32& 
         const float lam = low ? mu : 1.0f - mu;
         const float one_m = low ? 1.0f - mu : mu;
         float bb[3];
-        bessel32(sh.bes, ut, bb);
+        bessel32(C.bes, ut, bb);
         pp = lam * st.k;
         pe = one_m * st.k;
         if (fl & QED_F_SPIN_EVENT) {
@@ -537,10 +548,10 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Shared32& 
         want = true;
     }
     bool ok = false;
-    if (have) {
-        const long long s_e = reserve_slots(El.count, want, 1);
-        const bool e_ok = want && s_e < El.capacity;
-        const long long s_p = reserve_slots(Po.count, e_ok, 1);
+    {
+        const long long s_e = reserve_grouped(have ? El.count : nullptr, want);
+        const bool e_ok = want && have && s_e < El.capacity;
+        const long long s_p = reserve_grouped(have ? Po.count : nullptr, e_ok);
         ok = e_ok && s_p < Po.capacity;
         if (ok) {
             store32(El, s_e, x, pe, se, w, birth_tau32(ide, C.S.seed));
@@ -551,7 +562,7 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Shared32& 
             store32(El, s_e, x, F3{0, 0, 0}, F3{0, 0, 0}, 0.0f, INFINITY);
             El.id[s_e] = ide;
         }
-        const long long s_d = reserve_slots(G.n_dead, ok, 1);
+        const long long s_d = reserve_grouped(have ? G.n_dead : nullptr, ok);
         if (ok && s_d < G.capacity) G.dead[s_d] = j;
     }
     if (want) {
