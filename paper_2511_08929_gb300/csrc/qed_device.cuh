@@ -390,7 +390,11 @@ __device__ __forceinline__ void flush_counters(unsigned long long (&c)[N], unsig
     }
 }
 
+// The first error wins.  Once the status is set (the common case when a buffer overflows on every
+// event of a step) a plain load sees it and no atomic is issued, so a flood of errors does not
+// serialise on the one word.
 __device__ __forceinline__ void record_error(qed_counters* ctr, int32_t status, int64_t idx) {
+    if (*reinterpret_cast<volatile int32_t*>(&ctr->status) != 0) return;
     if (atomicCAS(&ctr->status, 0, status) == 0) ctr->first_bad = idx;
 }
 
