@@ -407,7 +407,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 // ------------------------------------------------------------------------------------------------
 constexpr int kEventThreads = 256;
 
-__global__ void __launch_bounds__(kEventThreads) batch_event_kernel(const InstDev* __restrict__ inst,
+// (two blocks per SM: the register cap keeps 16 warps per SM to hide the global-memory latency of the
+// event branch)
+__global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const InstDev* __restrict__ inst,
                                                                    const SegCtx* __restrict__ ctx,
                                                                    const long long* __restrict__ ev,
                                                                    const ClockDev* __restrict__ clk, qed_counters* ctr) {
@@ -885,7 +887,7 @@ extern "C" qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate,
     for (int v = 0; v < QED_BATCH_VARIANTS; ++v) {
         const int occ = variant_occupancy(b, v);
         for (int bps = occ; bps >= 1 && bps >= occ - 1; --bps)
-            for (int ch : {16, 64, 256}) cand.push_back(qed_batch_tuning{v, bps, ch, 0});
+            for (int ch : {32, 64, 128}) cand.push_back(qed_batch_tuning{v, bps, ch, 0});
     }
     if (cand.empty()) return QED_ERR_CUDA;
     std::vector<double> score(cand.size(), 1e300);

@@ -293,16 +293,20 @@ __device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x
 // whose step context is C (lanes may differ in both)
 static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const PartDev& L, const PartDev& G,
                                                  qed_counters* ctr, unsigned long long* c) {
+    // Two phases around the photon's slot reservation: the lepton's outcome (energy fraction, recoil,
+    // spin) for every event, then the photon's polarization only for photons that have a slot (with
+    // full buffers most are dropped, and their Stokes vectors would be computed for nothing).
     const uint32_t fl = C.S.flags;
     bool want = false;
-    F3 gx{0, 0, 0}, gk{0, 0, 0}, gP{0, 0, 0};
-    float gw = 0.0f;
-    uint64_t gid = 0;
+    LState st;
+    uint64_t id = 0;
+    float lam = 0.0f, one_m = 0.0f, wv = 0.0f;
+    float bb[3] = {0.0f, 0.0f, 0.0f};
+    F3 k{0, 0, 0}, si{0, 0, 0}, sfu{0, 0, 0}, g{0, 0, 0};
     if (j >= 0) {
         const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
-        LState st;
         lepton_classical(C, a, b, cc, st, nullptr);  // the streaming pass's arithmetic, repeated
-        const uint64_t id = L.id[j];
+        id = L.id[j];
         F3 pf = st.p, sf = st.s;
         double tauf = tau_join(cc.z, cc.w);
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
@@ -310,24 +314,18 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const
         if (fl & QED_F_TAU) down = u52f(w0.z, w0.w) * st.Ws < st.Wdn;
         else down = u52f(w0.x, w0.y) < st.Wdn * C.S.dt_f;
         const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
-        const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
-        const float r3 = u52f(w1.z, w1.w), r4 = u52f(w2.x, w2.y);
+        const float r3 = u52f(w1.z, w1.w);
         const float y = logit52(w1.x, w1.y);
         // the sampled value to full FP32 accuracy: accurate logarithm of chi and exponential
         const float up = expf(icdf_lookup(C.T, false, down ? 1 : 0, logf(st.chi), y));
         const float den = 2.0f + 3.0f * st.chi * up;
         const float iden = rcp_(den);
-        const float lam = 3.0f * st.chi * up * iden, one_m = 2.0f * iden;
-        const F3 k = lam * st.p;
+        lam = 3.0f * st.chi * up * iden;
+        one_m = 2.0f * iden;
+        k = lam * st.p;
         if (fl & QED_F_RECOIL) pf = one_m * st.p;
-        float bb[3];
         bessel32(C.bes, up, bb);
-        const bool resolved = (fl & QED_F_RESOLVED) != 0;
-        const F3 si = resolved ? st.s : F3{0, 0, 0};
-        F3 sfu{0, 0, 0};
-        float xi[3] = {0.0f, 0.0f, 0.0f};
-        float wv = 0.0f;
-        F3 g{0, 0, 0};
+        si = (fl & QED_F_RESOLVED) ? st.s : F3{0, 0, 0};
         if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, bb, si, st.beta, st.khat, wv, g);
         if (fl & QED_F_SPIN_EVENT) {
             const float gn = sqrt_(dot(g, g));
@@ -339,7 +337,23 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const
             }
             sfu = sf;
         }
+        if (fl & QED_F_TAU) tauf = exp_draw(w0.x, w0.y);
+        c[C_EVENTS]++;
+        want = sqrt_(dot(k, k)) >= C.S.store_min_f;
+        if (!want) c[C_BELOW]++;
+        store32(L, j, st.x, pf, sf, st.w, tauf);
+    }
+    const long long slot = reserve_grouped(G.count, want);
+    const bool keep = want && G.count != nullptr && slot < G.capacity;
+    if (want && !keep) {
+        c[C_DROPPED]++;
+        if (G.count != nullptr) record_error(ctr, QED_ERR_CAPACITY, j);
+    }
+    if (keep) {
+        float xi[3] = {0.0f, 0.0f, 0.0f};
         if (fl & QED_F_POL_EVENT) {
+            const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
+            const float r4 = u52f(w2.x, w2.y);
             float Fv[4];
             nlc_stokes(lam, one_m, bb, si, sfu, wv, g, st.eps, st.beta, st.khat, Fv);
             const float Fn = sqrt_(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
@@ -352,35 +366,11 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const
                 for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
             }
         }
-        if (fl & QED_F_TAU) tauf = exp_draw(w0.x, w0.y);
-        c[C_EVENTS]++;
-        if (sqrt_(dot(k, k)) >= C.S.store_min_f) {
-            const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
-            want = true;
-            gx = st.x;
-            gk = k;
-            gP = stokes_to_P(xi, st.eps, st.beta, st.khat);
-            gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
-            gw = st.w;
-        } else {
-            c[C_BELOW]++;
-        }
-        store32(L, j, st.x, pf, sf, st.w, tauf);
-    }
-    {
-        const long long slot = reserve_grouped(G.count, want);
-        if (want && G.count != nullptr) {
-            if (slot < G.capacity) {
-                store32(G, slot, gx, gk, gP, gw, birth_tau32(gid, C.S.seed));
-                G.id[slot] = gid;
-                c[C_STORED]++;
-            } else {
-                c[C_DROPPED]++;
-                record_error(ctr, QED_ERR_CAPACITY, j);
-            }
-        } else if (want) {
-            c[C_DROPPED]++;
-        }
+        const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
+        const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
+        store32(G, slot, st.x, k, stokes_to_P(xi, st.eps, st.beta, st.khat), st.w, birth_tau32(gid, C.S.seed));
+        G.id[slot] = gid;
+        c[C_STORED]++;
     }
 }
 

@@ -279,7 +279,7 @@ def test_autotuner_picks_and_caches(gpu_tables, tmp_path):
     t1 = bt.tune(1, path)
     s1 = bt.stats().step
     assert s1 > s0  # the tuner's timed steps are real steps
-    assert 0 <= t1.variant < 5 and t1.blocks_per_sm >= 1 and t1.chunk in (16, 64, 256) and t1.graph_steps == 8
+    assert 0 <= t1.variant < 5 and t1.blocks_per_sm >= 1 and t1.chunk in (32, 64, 128) and t1.graph_steps == 8
     lines = open(path).read().strip().splitlines()
     assert len(lines) == 1 and '"variant": %d' % t1.variant in lines[0]
     t2 = bt.tune(1, path)  # cached: no timing, no steps
