@@ -228,7 +228,8 @@ __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_
     return off;
 }
 
-template <int WARPS, int STAGES, int MINB>
+// FIX: the step flags fixed at compile time (0: read from the context)
+template <int WARPS, int STAGES, int MINB, uint32_t FIX>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     batch_step_kernel(TabP<float> T, float* bes_g, const InstDev* __restrict__ inst,
                       const SegDev* __restrict__ seg, const int64_t* __restrict__ tile0_g, int n_inst,
@@ -375,7 +376,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         if (++st == STAGES) st = 0;
         bool event = false;
         if (valid)
-            event = sp == 2 ? photon_stream_one(C, WS.L, j, a, b, cc, ctr, c) : lepton_stream_one(C, WS.L, j, a, b, cc, ctr, c);
+            event = sp == 2 ? photon_stream_one<FIX>(C, WS.L, j, a, b, cc, ctr, c)
+                            : lepton_stream_one<FIX>(C, WS.L, j, a, b, cc, ctr, c);
         const unsigned m = __ballot_sync(0xffffffffu, event);
         if (event) wq[qn + __popc(m & ((1u << lane) - 1u))] = ((long long)cur << 32) | (long long)j;
         qn += __popc(m);
@@ -534,7 +536,7 @@ struct qed_batch_s {
     long long direct_steps;        // directly launched steps (event pair index of the next one)
 };
 
-template <int WARPS, int STAGES, int MINB>
+template <int WARPS, int STAGES, int MINB, uint32_t FIX>
 static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
     const qed_tables_s* t = b->tables;
     const size_t smem = batch_smem_bytes(WARPS, STAGES, t->desc.n_chi, kSpecies * b->n_inst);
@@ -543,31 +545,36 @@ static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
     P.dt_f = (float)b->desc.dt;
     P.store_min = b->desc.photon_store_min;
     P.chi_floor = b->desc.chi_floor;
-    batch_step_kernel<WARPS, STAGES, MINB><<<grid, WARPS * 32, smem, st>>>(
+    batch_step_kernel<WARPS, STAGES, MINB, FIX><<<grid, WARPS * 32, smem, st>>>(
         tab_params<float>(t), t->bes32, b->d_inst, b->d_seg, b->d_tile0, b->n_inst, b->d_clk, P, b->tuning.chunk,
         &b->d_clk->next_tile, b->d_ev, &b->d_clk->n_events, b->ctr);
 }
 
-static const BatchVariant kVariants[QED_BATCH_VARIANTS] = {
-    {(const void*)batch_step_kernel<8, 3, 3>, 8, 3, launch_variant<8, 3, 3>},
-    {(const void*)batch_step_kernel<8, 3, 2>, 8, 3, launch_variant<8, 3, 2>},
-    {(const void*)batch_step_kernel<8, 2, 4>, 8, 2, launch_variant<8, 2, 4>},
-    {(const void*)batch_step_kernel<16, 2, 1>, 16, 2, launch_variant<16, 2, 1>},
-    {(const void*)batch_step_kernel<16, 2, 2>, 16, 2, launch_variant<16, 2, 2>},
-};
+#define QED_VARIANTS(FIX)                                                                \
+    {{(const void*)batch_step_kernel<8, 3, 3, FIX>, 8, 3, launch_variant<8, 3, 3, FIX>},      \
+     {(const void*)batch_step_kernel<8, 3, 2, FIX>, 8, 3, launch_variant<8, 3, 2, FIX>},      \
+     {(const void*)batch_step_kernel<8, 2, 4, FIX>, 8, 2, launch_variant<8, 2, 4, FIX>},      \
+     {(const void*)batch_step_kernel<16, 2, 1, FIX>, 16, 2, launch_variant<16, 2, 1, FIX>},   \
+     {(const void*)batch_step_kernel<16, 2, 2, FIX>, 16, 2, launch_variant<16, 2, 2, FIX>}}
+
+// [0]: flags read at run time; [1]: built for QED_F_FULL (every flag test of the streaming pass folded)
+static const BatchVariant kVariants[2][QED_BATCH_VARIANTS] = {QED_VARIANTS(0u), QED_VARIANTS(QED_F_FULL)};
+
+static const BatchVariant& variant_of(const qed_batch_s* b, int v) {
+    return kVariants[b->desc.flags == QED_F_FULL ? 1 : 0][v];
+}
 
 static size_t variant_smem(const qed_batch_s* b, int v) {
-    return batch_smem_bytes(kVariants[v].warps, kVariants[v].stages, b->tables->desc.n_chi, kSpecies * b->n_inst);
+    return batch_smem_bytes(variant_of(b, v).warps, variant_of(b, v).stages, b->tables->desc.n_chi, kSpecies * b->n_inst);
 }
 
 // resident blocks per SM of variant v for this batch (0 if it does not fit)
 static int variant_occupancy(const qed_batch_s* b, int v) {
     int per_sm = 0;
     const size_t smem = variant_smem(b, v);
-    if (cudaFuncSetAttribute(kVariants[v].kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kVariants[v].kern, kVariants[v].warps * 32, smem) != cudaSuccess)
-        return 0;
+    const BatchVariant& k = variant_of(b, v);
+    if (cudaFuncSetAttribute(k.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.kern, k.warps * 32, smem) != cudaSuccess) return 0;
     return per_sm;
 }
 
@@ -586,7 +593,7 @@ static void launch_batch_step(const qed_batch_s* b, cudaStream_t st, cudaEvent_t
     batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b->d_inst, b->n_inst, b->d_seg, b->d_tile0, b->d_clk, b->d_ctx,
                                                   tab_params<float>(b->tables), b->tables->bes32, P);
     if (e0) cudaEventRecordWithFlags(e0, st, rec);
-    kVariants[b->tuning.variant].launch(b, b->grid, st);
+    variant_of(b, b->tuning.variant).launch(b, b->grid, st);
     batch_event_kernel<<<b->ev_grid, kEventThreads, 0, st>>>(b->d_inst, b->d_ctx, b->d_ev, b->d_clk, b->ctr);
     if (e1) cudaEventRecordWithFlags(e1, st, rec);
     batch_compact_head<<<(b->n_inst + 255) / 256, 256, 0, st>>>(b->d_inst, b->n_inst);

@@ -230,6 +230,12 @@ struct Ctx {
     float q;
 };
 
+// the step flags: FIX when the caller fixes them at compile time (nonzero), else the context's
+template <uint32_t FIX>
+__device__ __forceinline__ uint32_t flags_of(const Ctx& C) {
+    return FIX ? FIX : C.S.flags;
+}
+
 // state after the classical part of the step, shared by the streaming pass and the event pass
 struct LState {
     F3 x, p, s, E, B;
@@ -240,9 +246,10 @@ struct LState {
 };
 
 // fields at x_old, Boris push, T-BMT precession, move, chi, basis and rates
+template <uint32_t FIX = 0>
 __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, LState& st,
                                                  unsigned long long* c) {
-    const uint32_t fl = C.S.flags;
+    const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
     const F3 xold{a.x, a.y, a.z};
     st.p = F3{a.w, b.x, b.y};
@@ -376,9 +383,10 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const
 
 // the streaming pass of one particle (no event): non-emission update and store; returns true if the
 // particle's optical depth ran out (it is then left untouched for the event pass)
+template <uint32_t FIX = 0>
 __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L, int64_t j, const float4& a, const float4& b,
                                                   const float4& cc, qed_counters* ctr, unsigned long long* c) {
-    const uint32_t fl = C.S.flags;
+    const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
     if (!(finite4(a) && finite4(b) && isfinite(cc.x) && isfinite(cc.y))) {
         c[C_NONFINITE]++;
@@ -386,7 +394,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
         return false;
     }
     LState st;
-    lepton_classical(C, a, b, cc, st, c);
+    lepton_classical<FIX>(C, a, b, cc, st, c);
     const double tau = tau_join(cc.z, cc.w);
     double tauf = tau;
     if (st.qed) {
@@ -426,6 +434,7 @@ struct PState {
     float chi, lnchi, xi[3], Wp, Wm, Wmp, Wx;
 };
 
+template <uint32_t FIX = 0>
 __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, PState& st,
                                                  unsigned long long* c) {
     const F3 xold{a.x, a.y, a.z};
@@ -437,15 +446,15 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.en = sqrt_(en2);
     st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
     st.x = xold;
-    if (C.S.flags & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
+    if (flags_of<FIX>(C) & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;
-    if (!(C.S.flags & QED_F_EMIT) || !(en2 > 0.0f)) return;
+    if (!(flags_of<FIX>(C) & QED_F_EMIT) || !(en2 > 0.0f)) return;
     st.chi = chi_of(C.F.eta0, st.en, st.k, st.E, st.B);
     if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     if (!make_basis(st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
-    if (!(C.S.flags & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
+    if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
     nbw_rates(C.T, st.chi, st.lnchi, st.Wp, st.Wm);
@@ -568,9 +577,10 @@ static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const
     }
 }
 
+template <uint32_t FIX = 0>
 __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G, int64_t j, const float4& a, const float4& b,
                                                   const float4& cc, qed_counters* ctr, unsigned long long* c) {
-    const uint32_t fl = C.S.flags;
+    const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
     if (!(finite4(a) && finite4(b) && isfinite(cc.x) && isfinite(cc.y))) {
         c[C_NONFINITE]++;
@@ -578,7 +588,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
         return false;
     }
     PState st;
-    photon_classical(C, a, b, cc, st, c);
+    photon_classical<FIX>(C, a, b, cc, st, c);
     const double tau = tau_join(cc.z, cc.w);
     double tauf = tau;
     if (st.qed && st.Wx > 0.0f) {
