@@ -236,6 +236,37 @@ __device__ __forceinline__ uint32_t flags_of(const Ctx& C) {
     return FIX ? FIX : C.S.flags;
 }
 
+// chi and the basis vector f = E + v x B for the FP32 path.  In a single plane wave travelling along +z
+// (the linear and circular lasers: E transverse, B = z x E) the invariant reduces exactly to
+// chi = eta0 |e - p_z| |E| (free of the cancellation of the general form) and f to
+// (1 - v_z) E + (v . E) z; other fields take the general forms.
+__device__ __forceinline__ bool single_wave(const Ctx& C) {
+    return C.F.kind == QED_FIELD_LP || C.F.kind == QED_FIELD_CP;
+}
+
+__device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B) {
+    if (single_wave(C)) return C.F.eta0 * fabsf(e - p.z) * sqrt_(fma_(E.x, E.x, E.y * E.y));
+    return chi_of(C.F.eta0, e, p, E, B);
+}
+
+__device__ __forceinline__ bool basis32(const Ctx& C, const F3& E, const F3& B, const F3& v, const F3& khat, float sign,
+                                       F3& eps, F3& beta) {
+    F3 f;
+    if (single_wave(C)) {
+        const float g = 1.0f - v.z;
+        f = F3{g * E.x, g * E.y, fma_(v.x, E.x, v.y * E.y)};
+    } else {
+        f = E + cross(v, B);
+    }
+    const float fk = dot(f, khat);
+    const F3 fp = axpy(-fk, khat, f);
+    const float n2 = dot(fp, fp);
+    if (!(n2 > 0.0f)) return false;
+    eps = (sign * rsqrtf(n2)) * fp;
+    beta = cross(khat, eps);
+    return true;
+}
+
 // state after the classical part of the step, shared by the streaming pass and the event pass
 struct LState {
     F3 x, p, s, E, B;
@@ -270,12 +301,12 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     }
     st.qed = false;
     if (!(fl & QED_F_EMIT)) return;
-    st.chi = chi_of(C.F.eta0, st.gam, st.p, st.E, st.B);
+    st.chi = chi32(C, st.gam, st.p, st.E, st.B);
     const float pn2 = dot(st.p, st.p);
     if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.khat = rsqrtf(pn2) * st.p;
     const F3 v = rg * st.p;
-    if (!make_basis(st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
+    if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
     st.qed = true;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
@@ -449,9 +480,9 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     if (flags_of<FIX>(C) & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;
     if (!(flags_of<FIX>(C) & QED_F_EMIT) || !(en2 > 0.0f)) return;
-    st.chi = chi_of(C.F.eta0, st.en, st.k, st.E, st.B);
+    st.chi = chi32(C, st.en, st.k, st.E, st.B);
     if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
-    if (!make_basis(st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
+    if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
     if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
