@@ -130,7 +130,21 @@ __device__ __forceinline__ F3 renorm64(const F3& s) {
 // with the sign bit set compare <= 0 as signed 64-bit integers)
 __device__ __forceinline__ bool tau_spent(double t) { return __double_as_longlong(t) <= 0ll; }
 
-__device__ __forceinline__ bool finite4(const float4& v) { return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w); }
+// true if the ten state words a particle's step reads (x, p or k, s or P, w) are all finite: 0 * v is
+// zero for finite v and NaN for infinities and NaNs, so the fused sum below is zero exactly when all are
+__device__ __forceinline__ bool finite_state(const float4& a, const float4& b, const float4& cc) {
+    float z = 0.0f * a.x;
+    z = fmaf(0.0f, a.y, z);
+    z = fmaf(0.0f, a.z, z);
+    z = fmaf(0.0f, a.w, z);
+    z = fmaf(0.0f, b.x, z);
+    z = fmaf(0.0f, b.y, z);
+    z = fmaf(0.0f, b.z, z);
+    z = fmaf(0.0f, b.w, z);
+    z = fmaf(0.0f, cc.x, z);
+    z = fmaf(0.0f, cc.y, z);
+    return z == 0.0f;
+}
 
 // ------------------------------------------------------------------------------------------------
 // shared memory
@@ -419,7 +433,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
                                                   const float4& cc, qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
-    if (!(finite4(a) && finite4(b) && isfinite(cc.x) && isfinite(cc.y))) {
+    if (!finite_state(a, b, cc)) {
         c[C_NONFINITE]++;
         record_error(ctr, QED_ERR_NAN, j);
         return false;
@@ -613,7 +627,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
                                                   const float4& cc, qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
-    if (!(finite4(a) && finite4(b) && isfinite(cc.x) && isfinite(cc.y))) {
+    if (!finite_state(a, b, cc)) {
         c[C_NONFINITE]++;
         record_error(ctr, QED_ERR_NAN, j);
         return false;
