@@ -51,6 +51,8 @@ def parse():
                     help="untimed steps before warm-up (into the interaction; default 450 batched, 620 headon)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU-baseline legs")
     ap.add_argument("--no-tune", action="store_true", help="batched: keep the default launch shape")
+    ap.add_argument("--tuning", default=None,
+                    help="batched: fixed launch shape 'variant,blocks_per_sm,chunk' instead of the autotuner")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-sampler leg")
     ap.add_argument("--mlp-train", type=float, default=5e7, help="learned sampler: training samples")
     ap.add_argument("--mlp-eval", type=float, default=1e8, help="learned sampler: evaluated events")
@@ -404,12 +406,16 @@ def native_batch(args):
     bt.step(half, stream)
     tuning = bt.tuning()
     tune_s = 0.0
-    if not args.no_tune:
+    if args.tuning:
+        v, bps, ch = (int(x) for x in args.tuning.split(","))
+        bt.set_tuning(v, bps, ch, tuning.graph_steps)
+        tuning = bt.tuning()
+    elif not args.no_tune:
         cache = os.environ.get("QED_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qedgb",
                                                               "autotune.jsonl"))
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         t0 = time.time()
-        tuning = bt.tune(1, cache, stream)
+        tuning = bt.tune(3, cache, stream)  # 3 steps per candidate and pass: less noise than one
         tune_s = time.time() - t0
     st = bt.stats(stream)
     if st.step < args.advance:

@@ -281,6 +281,41 @@ __device__ __forceinline__ bool basis32(const Ctx& C, const F3& E, const F3& B, 
     return true;
 }
 
+// The Boris push and the T-BMT vector for fields with E_z = B_z = 0 (the plane waves along z: every
+// field kind but the constant one): the general forms with the products by the zero components left
+// out.  A product by zero only adds a signed zero, so the results are the general forms' bit for bit
+// (for finite inputs).
+__device__ __forceinline__ F3 cross_t(const F3& a, const F3& b) {  // b.z = 0
+    return F3{-(a.z * b.y), a.z * b.x, fma_(a.x, b.y, -(a.y * b.x))};
+}
+
+__device__ __forceinline__ F3 boris_t(const F3& p, const F3& E, const F3& B, float q, float dt) {
+    const float h = 0.5f * q * dt;
+    const F3 pm{fma_(h, E.x, p.x), fma_(h, E.y, p.y), p.z};
+    const float ig = rsqrt_(1.0f + dot(pm, pm));
+    const float hi = h * ig;
+    const F3 t{hi * B.x, hi * B.y, 0.0f};
+    const float sfac = div_(2.0f, 1.0f + fma_(t.x, t.x, t.y * t.y));
+    const F3 pp = pm + cross_t(pm, t);
+    const F3 pl = pm + cross_t(pp, F3{sfac * t.x, sfac * t.y, 0.0f});
+    return F3{fma_(h, E.x, pl.x), fma_(h, E.y, pl.y), pl.z};
+}
+
+__device__ __forceinline__ F3 tbmt_omega_t(const F3& pb, const F3& E, const F3& B, float q, bool paper_form) {
+    const float ae = (float)(kAlpha / (2.0 * kPi));
+    const float gb = sqrt_(1.0f + dot(pb, pb));
+    const float ig = rcp_(gb);
+    const F3 bb = ig * pb;
+    const float bB = fma_(bb.x, B.x, bb.y * B.y);
+    const F3 bxE = cross_t(bb, E);
+    const float c1 = ae + ig, c2 = div_(ae * gb, gb + 1.0f);
+    if (paper_form) return (-q) * axpy(-(c2 * bB), bb, c1 * F3{B.x - bxE.x, B.y - bxE.y, 0.0f - bxE.z});
+    const float c3 = ae + rcp_(gb + 1.0f);
+    const float m = -(c2 * bB);
+    const F3 w{fma_(m, bb.x, c1 * B.x), fma_(m, bb.y, c1 * B.y), m * bb.z};
+    return (-q) * axpy(-c3, bxE, w);
+}
+
 // state after the classical part of the step, shared by the streaming pass and the event pass
 struct LState {
     F3 x, p, s, E, B;
@@ -302,10 +337,12 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     st.w = cc.y;
     field_eval(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const F3 pold = st.p;
-    if (fl & QED_F_PUSH) st.p = boris(st.p, st.E, st.B, C.q, dt);
+    const bool transverse = C.F.kind != QED_FIELD_CONST;
+    if (fl & QED_F_PUSH) st.p = transverse ? boris_t(st.p, st.E, st.B, C.q, dt) : boris(st.p, st.E, st.B, C.q, dt);
     if (fl & QED_F_TBMT) {
         const F3 pb = 0.5f * (pold + st.p);
-        st.s = rotate(st.s, tbmt_omega(pb, st.E, st.B, C.q, (fl & QED_F_TBMT_PAPER) != 0), dt);
+        const bool paper = (fl & QED_F_TBMT_PAPER) != 0;
+        st.s = rotate(st.s, transverse ? tbmt_omega_t(pb, st.E, st.B, C.q, paper) : tbmt_omega(pb, st.E, st.B, C.q, paper), dt);
     }
     st.gam = sqrt_(1.0f + dot(st.p, st.p));
     const float rg = rcp_(st.gam);
