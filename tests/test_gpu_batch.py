@@ -82,9 +82,9 @@ def _load(bufs, k, sp):
         e.init_tau(sp["seed"])
 
 
-def _make_batch(tables, specs, tuning=None):
+def _make_batch(tables, specs, tuning=None, flags=None):
     bt = Q.Batch(tables, [s["field"] for s in specs], [s["seed"] for s in specs], [_caps(s) for s in specs],
-                 DT, t0=T0, step0=STEP0)
+                 DT, t0=T0, step0=STEP0, flags=flags)
     for k, sp in enumerate(specs):
         _load(bt.buffers()[k], k, sp)
     if tuning is not None:
@@ -92,7 +92,7 @@ def _make_batch(tables, specs, tuning=None):
     return bt
 
 
-def _single_path(tables, specs, steps):
+def _single_path(tables, specs, steps, flags=None):
     """The same instances through the single-buffer entry points, one instance after another."""
     out, ctr = [], Q.Counters()
     for k, sp in enumerate(specs):
@@ -103,7 +103,7 @@ def _single_path(tables, specs, steps):
         _load((e, p, g), k, sp)
         ws = Q.CompactWorkspace(cg)
         for s in range(steps):
-            st = Q.step_desc(DT, T0 + float(s) * DT, STEP0 + s, sp["seed"])
+            st = Q.step_desc(DT, T0 + float(s) * DT, STEP0 + s, sp["seed"], flags)
             B.qed_snapshot_counts([e.s, p.s, g.s])
             B.qed_pair_step(tables.handle, sp["field"], st, g.s, e.s, p.s, ctr.ptr)
             B.qed_push_step(tables.handle, sp["field"], st, e.s, g.s, ctr.ptr)
@@ -170,6 +170,26 @@ def test_batch_matches_single_buffer_path(gpu_tables):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("flags", [B.QED_F_FULL | B.QED_F_TBMT_PAPER,
+                                   B.QED_F_FULL & ~(B.QED_F_POL_COLLAPSE | B.QED_F_SPIN_COLLAPSE)])
+def test_batch_matches_single_buffer_path_other_flags(gpu_tables, flags):
+    """A flag set other than the full one runs the batched kernels that read the flags at run time."""
+    specs = _specs()
+    steps = 12
+    bt = _make_batch(gpu_tables, specs, dict(variant=0, blocks_per_sm=0, chunk=4, graph_steps=4), flags=flags)
+    bt.step(steps)
+    torch.cuda.synchronize()
+    ref, rctr = _single_path(gpu_tables, specs, steps, flags=flags)
+    c = bt.ctr.read()
+    assert c.status == 0 and rctr.status == 0, (c.status, rctr.status)
+    assert c.events > 100
+    _assert_same(bt.buffers(), ref, f"batch vs single-buffer, flags {flags:#x}")
+    for k in ("events", "stored", "dropped_capacity", "renormalised", "below_store"):
+        assert getattr(c, k) == getattr(rctr, k), (k, getattr(c, k), getattr(rctr, k))
+    bt.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("tuning", [dict(variant=1, blocks_per_sm=1, chunk=1, graph_steps=0),
                                     dict(variant=2, blocks_per_sm=0, chunk=16, graph_steps=7),
                                     dict(variant=3, blocks_per_sm=0, chunk=3, graph_steps=1),
@@ -227,7 +247,7 @@ def test_batch_against_oracle():
     for sp, (oe, op, og) in zip(specs, ora):
         of = as_oracle_field(sp["field"])
         for s in range(steps):
-            st = Q.step_desc(DT, T0 + float(s) * DT, STEP0 + s, sp["seed"])
+            st = Q.step_desc(DT, T0 + float(s) * DT, STEP0 + s, sp["seed"], flags)
             oracle_full_step(ot, of, as_oracle_step(st), [(oe, -1), (op, 1)], og, oe, op)
     torch.cuda.synchronize()
     tol = 1e-5 * steps
