@@ -247,7 +247,7 @@ def test_batch_against_oracle():
     for sp, (oe, op, og) in zip(specs, ora):
         of = as_oracle_field(sp["field"])
         for s in range(steps):
-            st = Q.step_desc(DT, T0 + float(s) * DT, STEP0 + s, sp["seed"], flags)
+            st = Q.step_desc(DT, T0 + float(s) * DT, STEP0 + s, sp["seed"])
             oracle_full_step(ot, of, as_oracle_step(st), [(oe, -1), (op, 1)], og, oe, op)
     torch.cuda.synchronize()
     tol = 1e-5 * steps
