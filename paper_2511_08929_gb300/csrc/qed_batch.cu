@@ -265,6 +265,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     if (lane == 0) WS.t1 = 0;
     __syncthreads();  // tables and tile list ready
     const int total = s_tile0[n_seg];
+    // the tables as the streaming pass reads them: the kernel's parameters, with the rate rows in shared
+    // memory (the segment contexts in shared memory keep a copy for the event branch)
+    TabP<float> Tl = T;
+    Tl.nlc_rate = sh.rates;
+    Tl.nbw_rate = sh.rates + 2 * T.n_chi;
     const int W2 = 2 * gridDim.x * WARPS;
     unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
     int2* ring = s_chunks + warp * kChunkRing;
@@ -376,8 +381,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         if (++st == STAGES) st = 0;
         bool event = false;
         if (valid)
-            event = sp == 2 ? photon_stream_one<FIX>(C, WS.L, j, a, b, cc, ctr, c)
-                            : lepton_stream_one<FIX>(C, WS.L, j, a, b, cc, ctr, c);
+            event = sp == 2 ? photon_stream_one<FIX>(C, WS.L, j, a, b, cc, ctr, c, &Tl)
+                            : lepton_stream_one<FIX>(C, WS.L, j, a, b, cc, ctr, c, &Tl);
         const unsigned m = __ballot_sync(0xffffffffu, event);
         if (event) wq[qn + __popc(m & ((1u << lane) - 1u))] = ((long long)cur << 32) | (long long)j;
         qn += __popc(m);

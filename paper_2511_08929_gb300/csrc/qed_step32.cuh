@@ -328,7 +328,9 @@ struct LState {
 // fields at x_old, Boris push, T-BMT precession, move, chi, basis and rates
 template <uint32_t FIX = 0>
 __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, LState& st,
-                                                 unsigned long long* c) {
+                                                 unsigned long long* c,
+                                                 const TabP<float>* Tp = nullptr) {
+    const TabP<float>& T = Tp ? *Tp : C.T;  // the caller may hand the tables over from its parameters
     const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
     const F3 xold{a.x, a.y, a.z};
@@ -360,8 +362,8 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
     st.qed = true;
     st.lnchi = __logf(st.chi);
-    if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
-    nlc_rates(C.T, st.chi, st.lnchi, st.Wu, st.Wd);
+    if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
+    nlc_rates(T, st.chi, st.lnchi, st.Wu, st.Wd);
     const float pref = (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0) * rg;
     st.Wu *= pref;
     st.Wd *= pref;
@@ -467,7 +469,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const
 // particle's optical depth ran out (it is then left untouched for the event pass)
 template <uint32_t FIX = 0>
 __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L, int64_t j, const float4& a, const float4& b,
-                                                  const float4& cc, qed_counters* ctr, unsigned long long* c) {
+                                                  const float4& cc, qed_counters* ctr, unsigned long long* c, const TabP<float>* Tp = nullptr) {
     const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
     if (!finite_state(a, b, cc)) {
@@ -476,7 +478,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
         return false;
     }
     LState st;
-    lepton_classical<FIX>(C, a, b, cc, st, c);
+    lepton_classical<FIX>(C, a, b, cc, st, c, Tp);
     const double tau = tau_join(cc.z, cc.w);
     double tauf = tau;
     if (st.qed) {
@@ -518,7 +520,9 @@ struct PState {
 
 template <uint32_t FIX = 0>
 __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, PState& st,
-                                                 unsigned long long* c) {
+                                                 unsigned long long* c,
+                                                 const TabP<float>* Tp = nullptr) {
+    const TabP<float>& T = Tp ? *Tp : C.T;  // the caller may hand the tables over from its parameters
     const F3 xold{a.x, a.y, a.z};
     st.k = F3{a.w, b.x, b.y};
     st.P = F3{b.z, b.w, cc.x};
@@ -538,8 +542,8 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
     if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
     st.lnchi = __logf(st.chi);
-    if (c && st.chi > C.T.chi_max) c[C_CLAMPED]++;
-    nbw_rates(C.T, st.chi, st.lnchi, st.Wp, st.Wm);
+    if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
+    nbw_rates(T, st.chi, st.lnchi, st.Wp, st.Wm);
     const float pref = (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0 * st.en);
     st.Wp *= pref;
     st.Wm *= pref;
@@ -661,7 +665,7 @@ static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const
 
 template <uint32_t FIX = 0>
 __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G, int64_t j, const float4& a, const float4& b,
-                                                  const float4& cc, qed_counters* ctr, unsigned long long* c) {
+                                                  const float4& cc, qed_counters* ctr, unsigned long long* c, const TabP<float>* Tp = nullptr) {
     const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
     if (!finite_state(a, b, cc)) {
@@ -670,7 +674,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
         return false;
     }
     PState st;
-    photon_classical<FIX>(C, a, b, cc, st, c);
+    photon_classical<FIX>(C, a, b, cc, st, c, Tp);
     const double tau = tau_join(cc.z, cc.w);
     double tauf = tau;
     if (st.qed && st.Wx > 0.0f) {
