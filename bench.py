@@ -661,7 +661,8 @@ def batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, tor
         for hx, x in zip(host, bt.buffers()):
             for (hq, hi), b in zip(hx, x):
                 nn = n_now[k]
-                b.q[:, :nn].copy_(hq[:, :nn], non_blocking=True)
+                for pl in range(3):  # one contiguous copy per float4 plane
+                    b.q[pl, :nn].copy_(hq[pl, :nn], non_blocking=True)
                 b.ids[:nn].copy_(hi[:nn], non_blocking=True)
                 bi += 3 * nn * 16 + 8 * nn
                 k += 1
@@ -674,7 +675,8 @@ def batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, tor
         for hx, x in zip(host, bt.buffers()):
             for (hq, hi), b in zip(hx, x):
                 nn = n_now[k]
-                hq[:, :nn].copy_(b.q[:, :nn], non_blocking=True)
+                for pl in range(3):
+                    hq[pl, :nn].copy_(b.q[pl, :nn], non_blocking=True)
                 hi[:nn].copy_(b.ids[:nn], non_blocking=True)
                 bo += 3 * nn * 16 + 8 * nn
                 k += 1
@@ -842,7 +844,8 @@ def extra_legs(args, sim, Q, B, I, wl, tables, device, torch):
     for _ in range(Ke):
         n_now = [sim.el.count(), sim.po.count(), sim.ph.count()]
         for (key, buf), nn in zip((("el", sim.el), ("po", sim.po), ("ph", sim.ph)), n_now):
-            buf.q[:, :nn].copy_(host[key][0][:, :nn], non_blocking=True)
+            for pl in range(3):  # one contiguous copy per float4 plane
+                buf.q[pl, :nn].copy_(host[key][0][pl, :nn], non_blocking=True)
             buf.ids[:nn].copy_(host[key][1][:nn], non_blocking=True)
             bi += 3 * nn * 16 + 8 * nn
         ps_e += sum(n_now)
@@ -850,7 +853,8 @@ def extra_legs(args, sim, Q, B, I, wl, tables, device, torch):
         h_counts.copy_(torch.stack([sim.el.counts[0], sim.po.counts[0], sim.ph.counts[0]]), non_blocking=True)
         torch.cuda.synchronize()
         for (key, buf), nn in zip((("el", sim.el), ("po", sim.po), ("ph", sim.ph)), h_counts.tolist()):
-            host[key][0][:, :nn].copy_(buf.q[:, :nn], non_blocking=True)
+            for pl in range(3):
+                host[key][0][pl, :nn].copy_(buf.q[pl, :nn], non_blocking=True)
             host[key][1][:nn].copy_(buf.ids[:nn], non_blocking=True)
             bo += 3 * nn * 16 + 8 * nn
         torch.cuda.synchronize()
