@@ -112,12 +112,16 @@ KERNEL_SOURCES = ("qed_batch.cu", "qed_step32.cuh", "qed_device.cuh", "qed_besse
 
 
 def kernel_source_hash() -> str:
-    """sha256 over the sources the batched persistent kernel is built from."""
+    """sha256 over the code of the sources the batched kernels are built from: `//` comments and blank
+    lines are left out, so a change of wording keeps a capture of the same kernels valid."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2511_08929_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2511_08929_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

@@ -8,7 +8,8 @@
 //             particle-step accounting;
 //   step      the persistent kernel: every warp takes runs of consecutive tiles from a work counter
 //             (guided: long runs first, short ones at the end, at most `chunk` tiles) and streams them
-//             with the same copy pipeline and per-particle arithmetic as the single-buffer FP32 kernels;
+//             through shared memory with per-lane asynchronous copies, running the per-particle
+//             arithmetic of the single-buffer FP32 kernels;
 //             a particle whose optical depth runs out is left untouched and listed (segment, index) in
 //             the step's event list, 32 entries per atomic add;
 //   events    the event branch for every listed particle, 32 per warp with a context per lane (out of
