@@ -216,9 +216,9 @@ struct WarpSeg {
     int t0, t1, n;  // its tile range and particle count
 };
 
-// shared memory of the batched kernel: the 1-D rate tables (the Bessel table, read only at events, stays
-// in global memory behind L1), the tile list, the per-warp segment state, the tiles, queues and chunk
-// rings
+// shared memory of the batched kernel: the 1-D rate tables (the Bessel table, read only by the event
+// kernel, stays in global memory behind L1), the tile list, the per-warp segment state, the tiles, the
+// event queues and the chunk rings
 __host__ __device__ inline size_t batch_smem_bytes(int warps, int stages, int n_chi, int n_seg) {
     size_t off = align128((size_t)4 * n_chi * 4);
     off += align128((size_t)(n_seg + 1) * 4);
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     __syncwarp();
     int2 ch = ring[0];
     int t = ch.x, te = ch.y, rk = 1;  // the compute walk: tile t of a chunk ending at te; ring entries read
-    int qn = 0;    // queued event indices of the current segment (warp-uniform)
+    int qn = 0;    // queued event entries, segment << 32 | index (warp-uniform), flushed 32 at a time
     int cur = -1;  // current segment
     int sp = 0, ii = 0;
     int st = 0;  // stage of the current tile
