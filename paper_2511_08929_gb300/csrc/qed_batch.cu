@@ -894,8 +894,8 @@ extern "C" qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate,
             return QED_OK;
         }
     }
-    // candidates: every variant that fits, at its occupancy maximum and one block fewer, three largest
-    // chunk sizes
+    // candidates: every variant that fits, at its occupancy maximum and one block fewer, with the longest
+    // runs of the guided schedule capped at 32, 64 or 128 tiles
     std::vector<qed_batch_tuning> cand;
     for (int v = 0; v < QED_BATCH_VARIANTS; ++v) {
         const int occ = variant_occupancy(b, v);
