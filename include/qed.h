@@ -268,10 +268,11 @@ qed_status qed_compact_noalloc(qed_particles *photons, void *stream);
 /* ---- Batched collisions: many independent instances stepped together ----
  * A batch is a set of independent collision instances (each its own laser, seed and three FP32 species
  * buffers) advanced in lockstep.  One time step of the whole batch is: a planning kernel (alive counts
- * at step start, the tile list over all instances and species), one persistent kernel that streams every
- * tile of 32 particles of every instance (the lepton step of Sec. 4.1 for electrons and positrons, the
- * photon step of Sec. 4.2 for photons, each as qed_push_step / qed_pair_step do), and the photon
- * compaction of every instance.  The step index and time live in device memory and advance on the
+ * at step start, the tile list over all instances and species, each one's step context), one
+ * persistent kernel that streams every tile of 32 particles of every instance (the lepton step of
+ * Sec. 4.1 for electrons and positrons, the photon step of Sec. 4.2 for photons, each as qed_push_step /
+ * qed_pair_step do) and lists the particles whose optical depth ran out, an event kernel that runs the
+ * emission / pair branch for the listed particles, and the photon compaction of every instance.  The step index and time live in device memory and advance on the
  * device, so a captured CUDA graph of one or more steps is replayed unchanged.  Results are the ones
  * qed_push_step, qed_pair_step and qed_compact give per instance with begin snapshots (the same
  * arithmetic and random draws; appended daughters may sit in another order), whatever the tuning. */
@@ -316,8 +317,8 @@ typedef struct {
 
 /* Create a batch of n_inst (1 .. QED_BATCH_MAX_INSTANCES) instances.  The instance array is copied; the
  * particle buffers stay the caller's and must outlive the batch.  The batch owns its device planning
- * state and the compaction workspace (17 B per photon of capacity), and writes its counters to
- * counters_dev.  Errors: QED_ERR_ARG, QED_ERR_STATE (tables), QED_ERR_NOMEM, QED_ERR_CUDA. */
+ * state, the compaction workspace (17 B per photon of capacity) and the step's event list (8 B per
+ * particle of capacity), and writes its counters to counters_dev.  Errors: QED_ERR_ARG, QED_ERR_STATE (tables), QED_ERR_NOMEM, QED_ERR_CUDA. */
 qed_status qed_batch_create(qed_tables_t t, const qed_instance *instances, int32_t n_inst, const qed_batch_desc *desc,
                             qed_counters *counters_dev, qed_batch_t *out);
 /* Set / read the launch shape; setting it discards any captured graph. */
@@ -329,13 +330,13 @@ qed_status qed_batch_get_tuning(qed_batch_t b, qed_batch_tuning *out);
  * instantiation can be kept out of a timed region. */
 qed_status qed_batch_step(qed_batch_t b, int32_t n_steps, void *stream);
 /* Kernel timing: events[2k], events[2k+1] (cudaEvent_t, created by the caller with timing enabled) are
- * recorded around the persistent kernel of the k-th step (k modulo n_pairs) of every CUDA graph captured
- * from now on (step k of the graph) and of directly launched steps (counted from this call).  n_pairs = 0
- * switches it off.  Discards any captured graph. */
+ * recorded before the persistent kernel and after the event kernel of the k-th step (k modulo n_pairs)
+ * of every CUDA graph captured from now on (step k of the graph) and of directly launched steps (counted
+ * from this call).  n_pairs = 0 switches it off.  Discards any captured graph. */
 qed_status qed_batch_set_kernel_events(qed_batch_t b, void *const *events, int32_t n_pairs);
-/* Autotuner: times the persistent kernel of every launch shape it considers on the batch's own next
- * steps (they are real steps: results do not depend on the shape), picks the one with the least time
- * per particle-step and sets it.  steps_per_candidate >= 1.  cache_path (may be NULL): a text file of
+/* Autotuner: times the persistent and event kernels of every launch shape it considers on the batch's
+ * own next steps (they are real steps: results do not depend on the shape), picks the one with the least
+ * time per particle-step and sets it.  steps_per_candidate >= 1.  cache_path (may be NULL): a text file of
  * one JSON object per line, keyed by device, SM count and workload size; a matching line is used
  * without timing, a new result is appended.  Synchronizes `stream`. */
 qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate, const char *cache_path, qed_batch_tuning *out,
