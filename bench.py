@@ -405,9 +405,11 @@ def native_batch(args):
     wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device, args.scale)
     stream = torch.cuda.current_stream().cuda_stream
 
-    # untimed advance into the interaction; the autotuner times its candidates on real steps mid-way
-    half = args.advance // 2
-    bt.step(half, stream)
+    # untimed advance into the interaction; the autotuner times its candidates on real steps near its end
+    # (about 180 steps: up to 30 shapes, two passes, three steps each), where the particle populations
+    # are closest to those of the timed steps
+    pre = max(0, args.advance - 180)
+    bt.step(pre, stream)
     tuning = bt.tuning()
     tune_s = 0.0
     if args.tuning:
