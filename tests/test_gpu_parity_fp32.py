@@ -186,6 +186,41 @@ def test_photon_pairs_and_compaction(gpu_tables, ora_tables):
     assert f1 + f2 + f3 <= max(3, 1e-5 * 4000 * steps * 3), (f1, f2, f3)
 
 
+def test_constant_field_general_forms(gpu_tables, ora_tables):
+    """A constant field with every component nonzero: the FP32 path takes the general forms of chi, the
+    basis vector, the Boris push and the T-BMT vector here (the plane-wave forms do not apply)."""
+    f = Q.field(B.QED_FIELD_CONST, E0=(20.0, -15.0, 10.0), B0=(12.0, 25.0, -18.0), eta0=ETA0)
+    b = I.random_states(3000, seed=41, gamma_range=(300.0, 6000.0), field_region=(-5.0, 5.0))
+    steps = 3
+    for q in (-1, 1):
+        gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, steps, q=q, t0=0.0)
+        assert oc.events > 20 and c.status == 0
+        fl1, _ = compare_with_flips(gL.read(), oL.view(), 1e-5 * steps, "leptons")
+        fl2, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True, frac_ok=1e-2,
+                                    hard=3e-5 * steps)
+        assert fl1 + fl2 <= 2, (fl1, fl2)
+    pb = _photon_inputs(3000, seed=43, energy=20000.0)
+    gG, oG = _pair(pb, B.QED_PHOTON, seed=5, photons=True)
+    gE, gP = Q.ParticleBuffer(6000, FP32, B.QED_ELECTRON), Q.ParticleBuffer(6000, FP32, B.QED_POSITRON)
+    oE, oP = O.Particles(6000), O.Particles(6000)
+    ctr, octr = Q.Counters(), O.Counters()
+    ws = Q.CompactWorkspace(gG.capacity)
+    of = as_oracle_field(f)
+    for s_ in range(steps):
+        st = Q.step_desc(0.2, 0.2 * s_, s_, 5)
+        B.qed_pair_step(gpu_tables.handle, f, st, gG.s, gE.s, gP.s, ctr.ptr)
+        B.qed_compact(gG.s, ws.ptr, ws.bytes)  # converted photons leave, as in the oracle's step
+        O.photon_step(ora_tables, of, as_oracle_step(st), oG, oE, oP, octr)
+    torch.cuda.synchronize()
+    assert ctr.read().status == 0
+    # P is headless: its transverse part is fixed only up to sign (the representative with P.eps >= 0),
+    # and a photon whose P is nearly perpendicular to eps may land on either side in FP32 and FP64
+    f1, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
+    f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5, "electrons", frac_ok=1e-2, hard=1e-3)
+    f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5, "positrons", frac_ok=1e-2, hard=1e-3)
+    assert f1 + f2 + f3 <= 3, (f1, f2, f3)
+
+
 def test_coupled_species(gpu_tables, ora_tables):
     f = Q.field(B.QED_FIELD_CP_COUNTER, a0=300.0, n_cycles=3.0, phase=3 * math.pi - 4.0,
                 eta0=I.eta0_for_wavelength(1.0))
