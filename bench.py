@@ -149,17 +149,17 @@ def measured_peaks():
 class Sim:
     """The three species on the device and one full QED time step through the C ABI."""
 
-    def __init__(self, Q, B, I, wl, layout, tables, n, seed, cap_factor, device):
+    def __init__(self, Q, B, I, wl, layout, tables, n, seed, caps, device):
+        """caps: (electron, positron, photon) capacities"""
         import torch
         self.Q, self.B, self.torch = Q, B, torch
         self.wl = wl
         self.tables = tables
         self.field = Q.laser_field(wl.laser)
-        cap = int(cap_factor * n)
-        self.el = Q.ParticleBuffer(cap, layout, B.QED_ELECTRON, device=device, use_begin=True)
-        self.po = Q.ParticleBuffer(cap, layout, B.QED_POSITRON, device=device, use_begin=True)
-        self.ph = Q.ParticleBuffer(cap, layout, B.QED_PHOTON, device=device, photons=True, use_begin=True)
-        self.ws = Q.CompactWorkspace(cap, device=device)
+        self.el = Q.ParticleBuffer(caps[0], layout, B.QED_ELECTRON, device=device, use_begin=True)
+        self.po = Q.ParticleBuffer(caps[1], layout, B.QED_POSITRON, device=device, use_begin=True)
+        self.ph = Q.ParticleBuffer(caps[2], layout, B.QED_PHOTON, device=device, photons=True, use_begin=True)
+        self.ws = Q.CompactWorkspace(caps[2], device=device)
         self.ctr = Q.Counters(device=device)
         self.seed = seed
         self.n0 = n
@@ -242,7 +242,24 @@ def native(args):
     t_tables = time.time() - t0
     beam = I.lepton_beam(n, wl.gamma, direction=(0.0, 0.0, -1.0), z_range=(2 * math.pi, 22 * math.pi),
                          spin="fixed", spin_dir=(0.0, 0.0, 1.0), seed=seed, id_offset=rank * (1 << 40))
-    sim = Sim(Q, B, I, wl, B.QED_FP32, tables, n, seed, wl.capacity_factor, device)
+    # buffers from a measured growth curve: a 1/64 subsample stepped through the whole run with roomy
+    # buffers, then margin 1.25 (the configuration's 4x the initial count drops most daughters by then)
+    end_step = args.advance + args.warmup + args.steps + 16
+    sub = _subsample(beam, max(256, n // 64))
+    m = len(sub["id"])
+    probe = Sim(Q, B, I, wl, B.QED_FP32, tables, m, seed, (8 * m + 4096, 8 * m + 4096, 400 * m + 4096), device)
+    probe.load_beam(sub)
+    peak = np.zeros(3)
+    for _ in range(end_step):
+        probe.step()
+        if probe.step_index % 25 == 0 or probe.step_index == end_step:
+            peak = np.maximum(peak, torch.stack([probe.el.counts[0], probe.po.counts[0], probe.ph.counts[0]]).cpu().numpy())
+    if probe.ctr.read().status != 0:
+        raise SystemExit("bench: the buffer sizing pass overflowed")
+    caps = tuple(int(1.25 * peak[i] / m * n) + 4096 for i in range(3))
+    del probe
+    torch.cuda.empty_cache()
+    sim = Sim(Q, B, I, wl, B.QED_FP32, tables, n, seed, caps, device)
     sim.load_beam(beam)
     for _ in range(args.advance):
         sim.step()
@@ -278,6 +295,9 @@ def native(args):
     t_pair = sum(e["pair"][0].elapsed_time(e["pair"][1]) for e in evs)
     t_push = sum(e["push"][0].elapsed_time(e["push"][1]) for e in evs)
     ctr = sim.ctr.read()
+    if ctr.status != 0:
+        raise SystemExit(f"bench: the timed steps ended with status {ctr.status} ({B.status_string(ctr.status)}), "
+                         f"{ctr.dropped_capacity} daughters dropped: no valid measurement")
     h = hist.cpu().numpy().astype(np.float64)
     psteps = float(h.sum())
     n_el, n_po, n_ph = h[:, 0].sum(), h[:, 1].sum(), h[:, 2].sum()
@@ -315,7 +335,8 @@ def native(args):
         "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "electrons_per_gpu": n, "gamma": wl.gamma, "a0": wl.laser.a0,
-                   "laser": "CP 0.8um 20 cycles", "buffers": "4x initial per species", "layout": "FP32 float4 SoA",
+                   "laser": "CP 0.8um 20 cycles", "buffers": f"sized from a measured growth curve {list(caps)}",
+                   "layout": "FP32 float4 SoA",
                    "timed_from_step": args.advance + args.warmup, "parallelism": f"replicas x{world}",
                    "l2": "state > L2 (no flush needed)", "tables": "256 chi x 256 r, FP64-built"},
         "roofline": roof,
@@ -361,14 +382,69 @@ def replica_plan(wl, rank: int):
     return insts, seeds, np.uint64(rank << 48)
 
 
-def batch_setup(Q, B, I, tables, rank, device, scale=1.0):
+def batch_workload(I, scale=1.0):
     import dataclasses
     wl = I.BATCHED_96
     if scale != 1.0:
         wl = dataclasses.replace(wl, name=f"{wl.name}_x{scale:g}", n_min=wl.n_min * scale, n_max=wl.n_max * scale)
+    return wl
+
+
+def _subsample(beam: dict, m: int) -> dict:
+    """m particles spread evenly over the beam's id order (ids are drawn independently of position)."""
+    n = len(beam["id"])
+    if m >= n:
+        return beam
+    ix = np.linspace(0, n - 1, m).round().astype(np.int64)
+    return {k: v[ix] for k, v in beam.items()}
+
+
+def growth_capacities(Q, B, tables, wl, insts, fields, seeds, end_step, device, sub=64, min_sub=256, margin=1.25):
+    """Buffer capacities from a measured growth curve.  A strided subsample of every instance (1/sub of
+    its electrons, at least min_sub) is stepped on the GPU through end_step steps with generous buffers,
+    and each species' largest count per initial electron is recorded; the batch then gets
+    margin x that x N_i + 4096 slots per species and instance.  Particles never interact, so the growth
+    per initial electron of a subsample is that of the whole beam up to sampling noise (the margin)."""
+    import torch
+    fac = [8.0, 8.0, 400.0]
+    for _attempt in range(3):
+        subs = [_subsample(wl.beam(k, x), min(x["n"], max(min_sub, x["n"] // sub))) for k, x in enumerate(insts)]
+        caps = [tuple(max(4096, int(f * len(b["id"]))) for f in fac) for b in subs]
+        bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
+                     device=device)
+        bt.set_tuning(0, 0, 16, 25)
+        for k, ((e, _, _), b) in enumerate(zip(bt.buffers(), subs)):
+            b = z_order(b)
+            e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"])
+            e.init_tau(seeds[k])
+        peak = np.zeros((len(insts), 3))
+        done = 0
+        while done < end_step:
+            n = min(25, end_step - done)
+            bt.step(n)
+            done += n
+            cnt = torch.stack([b.counts[0] for x in bt.buffers() for b in x]).cpu().numpy().reshape(-1, 3)
+            peak = np.maximum(peak, cnt)
+        status = bt.ctr.read().status
+        bt.close()
+        torch.cuda.empty_cache()
+        if status == 0:
+            per = peak / np.array([len(b["id"]) for b in subs], dtype=np.float64)[:, None]
+            out = [tuple(int(margin * per[k, s] * x["n"]) + 4096 for s in range(3)) for k, x in enumerate(insts)]
+            return out, {"subsample": f"1/{sub} of each instance's electrons (at least {min_sub})",
+                         "steps": int(end_step), "margin": margin,
+                         "photons_per_electron_max": float(per[:, 2].max()),
+                         "slots": int(sum(sum(c) for c in out))}
+        fac = [2 * f for f in fac]
+    raise RuntimeError("buffer sizing pass overflowed three times")
+
+
+def batch_setup(Q, B, I, tables, rank, device, scale=1.0, caps=None):
+    wl = batch_workload(I, scale)
     insts, seeds, id_offset = replica_plan(wl, rank)
     fields = [Q.laser_field(wl.laser(x)) for x in insts]
-    caps = [tuple(max(4096, int(wl.capacity_factor * x["n"])) for _ in range(3)) for x in insts]
+    if caps is None:
+        caps = [tuple(max(4096, int(wl.capacity_factor * x["n"])) for _ in range(3)) for x in insts]
     bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
                  device=device)
     for k, (x, (e, p, g)) in enumerate(zip(insts, bt.buffers())):
@@ -402,7 +478,18 @@ def native_batch(args):
     tables = Q.Tables(1e-4, 1e3, 256, 256)
     torch.cuda.synchronize()
     t_tables = time.time() - t0
-    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device, args.scale)
+    extras_on = not args.no_extras and rank == 0
+    E2E_STEPS, ERR_STEPS = 3, 3
+    # every step the run takes on the FP32 batch: advance, warm-up, e2e, timed, error legs (+ slack)
+    end_step = args.advance + args.warmup + (E2E_STEPS if extras_on else 0) + args.steps + \
+        (ERR_STEPS if extras_on else 0) + 16
+    wl0 = batch_workload(I, args.scale)
+    insts0, seeds0, _ = replica_plan(wl0, rank)
+    fields0 = [Q.laser_field(wl0.laser(x)) for x in insts0]
+    t0 = time.time()
+    caps, sizing = growth_capacities(Q, B, tables, wl0, insts0, fields0, seeds0, end_step, device)
+    sizing["seconds"] = round(time.time() - t0, 2)
+    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device, args.scale, caps=caps)
     stream = torch.cuda.current_stream().cuda_stream
 
     # untimed advance into the interaction; the autotuner times its candidates on real steps near its end
@@ -428,6 +515,10 @@ def native_batch(args):
         bt.step(int(args.advance - st.step), stream)
     bt.step(args.warmup, stream)
     torch.cuda.synchronize()
+
+    extras = {}
+    if extras_on:  # end to end through the C ABI with host-resident state (3 steps, just before the timed ones)
+        extras["e2e"] = e2e_leg(bt, torch, E2E_STEPS)
 
     # the timed region is one launch of a graph of K steps with event pairs around each persistent kernel
     K = args.steps
@@ -458,6 +549,9 @@ def native_batch(args):
     ms = start.elapsed_time(end)
     s1 = bt.stats(stream)
     ctr = bt.ctr.read()
+    if ctr.status != 0:  # a window with dropped daughters or skipped particles did less than the step's work
+        raise SystemExit(f"bench: the timed steps ended with status {ctr.status} ({B.status_string(ctr.status)}), "
+                         f"{ctr.dropped_capacity} daughters dropped: no valid measurement")
     try:
         t_kern = [a.elapsed_time(b) for a, b in kev]
     except RuntimeError:
@@ -473,6 +567,8 @@ def native_batch(args):
     # 88 B per lepton-step, 76 B per photon-step, 8 B (id) per event, 52 B per stored daughter
     peak, peak_kind = measured_peaks()
     alg = 88.0 * (d_sp[0] + d_sp[1]) + 76.0 * d_sp[2] + 8.0 * ctr.events + 52.0 * ctr.stored
+    # the same with the survey's per-unit figures (id read every step): 96 B per lepton-step, 84 B per photon-step
+    alg_survey = 96.0 * (d_sp[0] + d_sp[1]) + 84.0 * d_sp[2] + 52.0 * ctr.stored
     tr = measured_traffic()
     traffic = None
     if tr is not None:  # ncu DRAM bytes per particle-step of a smaller capture, scaled to this launch
@@ -487,12 +583,15 @@ def native_batch(args):
         tk = sum(t_kern)
         achieved = alg / (tk / 1e3) / 1e9
         roof.update({"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+                     "frac_survey_bytes": round(alg_survey / (tk / 1e3) / 1e9 / peak, 4),
                      "ms_per_launch": round(tk / K, 4), "share_of_step": round(tk / ms, 4)})
     clocks = summarize_clocks(clock_lines)
-    extras = {}
-    if not args.no_extras and rank == 0:
-        extras = batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, torch, stream)
-    if not args.no_extras and not args.no_mlp and rank == 0:
+    if extras_on:
+        err, cpu = error_leg(bt, wl, fields, seeds, torch, ERR_STEPS)
+        extras["error"] = err
+        extras["cpu_baseline"] = cpu
+        extras["fp64_plain"] = fp64_leg(bt, wl, fields, seeds, tables, Q, B, torch, stream)
+    if extras_on and not args.no_mlp:
         bt.close()
         torch.cuda.empty_cache()
         extras["mlp"] = mlp_leg(args, tables, torch)
@@ -503,7 +602,8 @@ def native_batch(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "instances": len(insts), "electrons_per_gpu": n_el,
                    "laser": "LP/CP alternating 0.8um 10 cycles, a0 U[10,300]", "gamma": "U[500,8000]",
-                   "buffers": "4x initial per species and instance", "layout": "FP32 float4 SoA",
+                   "buffers": "sized from a measured growth curve (no daughter dropped)", "sizing": sizing,
+                   "layout": "FP32 float4 SoA",
                    "timed_from_step": int(s0.step), "parallelism": f"replicas x{world}",
                    "launch": {"graph_steps": K, "tuning": tuning.as_dict(), "autotune_s": round(tune_s, 2)},
                    "l2": "state > L2 (no flush needed)", "tables": "256 chi x 256 r, FP64-built"},
@@ -600,26 +700,28 @@ def _to_fp64(b32, b64, torch):
     b64.counts[:] = n
 
 
-def batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, torch, stream):
-    """The plain FP64 path on the same state (instance by instance through the single-buffer entry
-    points), e2e through the C ABI with host-resident state, and the oracle on a bounded sample."""
-    out = {}
-    st = bt.stats(stream)
-    step0 = int(st.step)
-    # ---- plain FP64 path on the same state ----
-    bufs64, cnt = [], 0.0
-    for (e, p, g), cap in zip(bt.buffers(), caps):
-        e64 = Q.ParticleBuffer(cap[0], B.QED_FP64, B.QED_ELECTRON, use_begin=True)
-        p64 = Q.ParticleBuffer(cap[1], B.QED_FP64, B.QED_POSITRON, use_begin=True)
-        g64 = Q.ParticleBuffer(cap[2], B.QED_FP64, B.QED_PHOTON, photons=True, use_begin=True)
+def fp64_leg(bt, wl, fields, seeds, tables, Q, B, torch, stream, steps=3):
+    """The plain FP64 path on the batch's current state: every instance through the single-buffer FP64
+    entry points (buffers sized for these few steps' growth), particle-steps of the photons, electrons
+    and positrons alive at each step's start."""
+    step0 = int(bt.stats(stream).step)
+    bufs64 = []
+    for e, p, g in bt.buffers():
+        room = [int(1.1 * b.count()) + 4096 for b in (e, p, g)]
+        e64 = Q.ParticleBuffer(room[0], B.QED_FP64, B.QED_ELECTRON, use_begin=True)
+        p64 = Q.ParticleBuffer(room[1], B.QED_FP64, B.QED_POSITRON, use_begin=True)
+        g64 = Q.ParticleBuffer(room[2], B.QED_FP64, B.QED_PHOTON, photons=True, use_begin=True)
         for a, b in ((e, e64), (p, p64), (g, g64)):
             _to_fp64(a, b, torch)
-        bufs64.append((e64, p64, g64, Q.CompactWorkspace(cap[2])))
+        bufs64.append((e64, p64, g64, Q.CompactWorkspace(room[2])))
     ctr64 = Q.Counters()
     torch.cuda.synchronize()
-
-    def step64(s):
-        n = 0
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    counts = []
+    s_.record()
+    for k in range(steps):
+        counts.append(torch.stack([torch.stack([b.counts[0] for b in x[:3]]).sum() for x in bufs64]).sum())
+        s = step0 + k
         for (e64, p64, g64, ws), f, sd in zip(bufs64, fields, seeds):
             d = Q.step_desc(wl.dt, float(s) * wl.dt, s, sd, B.QED_F_FULL, wl.photon_store_min)
             B.qed_snapshot_counts([e64.s, p64.s, g64.s], stream)
@@ -627,76 +729,62 @@ def batch_extra_legs(args, bt, wl, insts, fields, seeds, caps, tables, Q, B, tor
             B.qed_push_step(tables.handle, f, d, e64.s, g64.s, ctr64.ptr, stream)
             B.qed_push_step(tables.handle, f, d, p64.s, g64.s, ctr64.ptr, stream)
             B.qed_compact(g64.s, ws.ptr, ws.bytes, stream)
-    K64 = 3
-    alive = [torch.stack([b.counts[0] for b in (x[0], x[1], x[2])]).sum() for x in bufs64]
-    n_before = float(sum(a.item() for a in alive))
-    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    counts = []
-    s_.record()
-    for k in range(K64):
-        counts.append(torch.stack([torch.stack([b.counts[0] for b in x[:3]]).sum() for x in bufs64]).sum())
-        step64(step0 + k)
     e_.record()
     torch.cuda.synchronize()
     ps64 = float(sum(c.item() for c in counts))
-    out["fp64_plain"] = {"value": ps64 / (s_.elapsed_time(e_) / 1e3), "unit": UNIT, "steps": K64,
-                         "ms_per_step": s_.elapsed_time(e_) / K64,
-                         "note": "single-buffer FP64 entry points, instance by instance, same state"}
+    c64 = ctr64.read()
+    out = {"value": ps64 / (s_.elapsed_time(e_) / 1e3), "unit": UNIT, "steps": steps,
+           "ms_per_step": s_.elapsed_time(e_) / steps, "status": int(c64.status),
+           "note": "single-buffer FP64 entry points, instance by instance, from the FP32 batch's state"}
     del bufs64
     torch.cuda.empty_cache()
-    bt.step(K64, stream)  # keep the FP32 batch at the same step as the FP64 copy went (not needed after)
+    return out
 
-    # ---- e2e: host-resident particle state, copied in and out through pinned memory every step ----
-    Ke = 3
+
+def e2e_leg(bt, torch, steps):
+    """End to end through the C ABI with host-resident state: every step copies every instance's particle
+    planes and ids from pinned host memory to the device, runs one qed_batch_step, and copies the state and
+    the counts back."""
+    bufs = [b for x in bt.buffers() for b in x]
+    n_now = [b.count() for b in bufs]
     host = []
-    for x in bt.buffers():
-        host.append([(torch.empty_like(b.q, device="cpu").pin_memory(), torch.empty_like(b.ids, device="cpu").pin_memory())
-                     for b in x])
-    for hx, x in zip(host, bt.buffers()):
-        for (hq, hi), b in zip(hx, x):
-            hq.copy_(b.q)
-            hi.copy_(b.ids)
-    counts_dev = torch.stack([b.counts[0] for x in bt.buffers() for b in x])
-    h_counts = torch.empty(counts_dev.numel(), dtype=torch.int64).pin_memory()
+    for b, n in zip(bufs, n_now):
+        m = min(b.capacity, int(1.1 * n) + 4096)  # room for these steps' daughters
+        hq = torch.empty((3, m, 4), dtype=torch.float32).pin_memory()
+        hi = torch.empty(m, dtype=torch.int64).pin_memory()
+        hq[:, :n].copy_(b.q[:, :n])
+        hi[:n].copy_(b.ids[:n])
+        host.append((hq, hi))
+    h_counts = torch.empty(len(bufs), dtype=torch.int64).pin_memory()
     torch.cuda.synchronize()
-    n_now = [b.count() for x in bt.buffers() for b in x]
     t0 = time.perf_counter()
     ps_e, bi, bo = 0.0, 0, 0
-    for _ in range(Ke):
-        k = 0
-        for hx, x in zip(host, bt.buffers()):
-            for (hq, hi), b in zip(hx, x):
-                nn = n_now[k]
-                for pl in range(3):  # one contiguous copy per float4 plane
-                    b.q[pl, :nn].copy_(hq[pl, :nn], non_blocking=True)
-                b.ids[:nn].copy_(hi[:nn], non_blocking=True)
-                bi += 3 * nn * 16 + 8 * nn
-                k += 1
+    for _ in range(steps):
+        for (hq, hi), b, nn in zip(host, bufs, n_now):
+            for pl in range(3):  # one contiguous copy per float4 plane
+                b.q[pl, :nn].copy_(hq[pl, :nn], non_blocking=True)
+            b.ids[:nn].copy_(hi[:nn], non_blocking=True)
+            bi += 3 * nn * 16 + 8 * nn
         ps_e += sum(n_now)
-        bt.step(1, stream)
-        h_counts.copy_(torch.stack([b.counts[0] for x in bt.buffers() for b in x]), non_blocking=True)
+        bt.step(1)
+        h_counts.copy_(torch.stack([b.counts[0] for b in bufs]), non_blocking=True)
         torch.cuda.synchronize()
         n_now = h_counts.tolist()
-        k = 0
-        for hx, x in zip(host, bt.buffers()):
-            for (hq, hi), b in zip(hx, x):
-                nn = n_now[k]
-                for pl in range(3):
-                    hq[pl, :nn].copy_(b.q[pl, :nn], non_blocking=True)
-                hi[:nn].copy_(b.ids[:nn], non_blocking=True)
-                bo += 3 * nn * 16 + 8 * nn
-                k += 1
+        for (hq, hi), b, nn in zip(host, bufs, n_now):
+            if nn > hq.shape[1]:
+                raise RuntimeError("e2e host buffer too small")
+            for pl in range(3):
+                hq[pl, :nn].copy_(b.q[pl, :nn], non_blocking=True)
+            hi[:nn].copy_(b.ids[:nn], non_blocking=True)
+            bo += 3 * nn * 16 + 8 * nn
         bo += 8 * len(n_now)
         torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    out["e2e"] = {"value": ps_e / te, "unit": UNIT, "h2d_bytes_per_step": bi // Ke, "d2h_bytes_per_step": bo // Ke,
-                  "note": "all instances' particle state host-resident, copied in and out through pinned memory "
-                          "every step around one qed_batch_step"}
     del host
-
-    # ---- CPU baseline: the oracle on a bounded sample of the same state ----
-    out["cpu_baseline"] = batch_cpu_baseline(bt, wl, insts, fields, seeds, int(bt.stats(stream).step))
-    return out
+    return {"value": ps_e / te, "unit": UNIT, "h2d_bytes_per_step": bi // steps, "d2h_bytes_per_step": bo // steps,
+            "steps": steps,
+            "note": "all instances' particle state host-resident, copied in and out through pinned memory every "
+                    "step around one qed_batch_step (the steps just before the timed ones)"}
 
 
 def _oracle_batch_step(O, tb, f, st, E, P, G):
@@ -716,38 +804,147 @@ def _oracle_field(O, f):
     return O.field(f.kind, a0=f.a0, n_cycles=f.n_cycles, phase=f.phase, E0=tuple(f.E0), B0=tuple(f.B0), eta0=f.eta0)
 
 
-def batch_cpu_baseline(bt, wl, insts, fields, seeds, step0, seconds=15.0, frac=0.1, max_steps=40):
-    """The oracle on a bounded sample of the batch's current state: from every instance the first
-    `frac` of its electrons, positrons and photons (at least one of each where present), stepped with
-    the instance's own laser and seed for at most max_steps steps and about `seconds` of CPU work."""
+def _unpack32(q, ids):
+    """host FP64 arrays of FP32 particle rows q (3, m, 4) and ids (m,) (layout of qed.h)"""
+    m = q.shape[1]
+    pos = q[0, :, 0:3].astype(np.float64)
+    mom = np.column_stack([q[0, :, 3], q[1, :, 0], q[1, :, 1]]).astype(np.float64)
+    spin = np.column_stack([q[1, :, 2], q[1, :, 3], q[2, :, 0]]).astype(np.float64)
+    w = q[2, :, 1].astype(np.float64)
+    tau = np.ascontiguousarray(q[2, :, 2:4]).view(np.uint32).reshape(m, 2).copy().view(np.float64).reshape(m)
+    return {"pos": pos, "mom": mom, "spin": spin, "tau": tau, "w": w, "id": ids.view(np.uint64).copy()}
+
+
+def _gpu_rows(buf, idx, torch):
+    """rows idx (device int64 tensor) of an FP32 particle buffer, as host FP64 arrays"""
+    q = buf.q[:, idx].cpu().numpy()
+    return _unpack32(q, buf.ids[idx].cpu().numpy())
+
+
+def _gpu_find(buf, ids, torch):
+    """the rows of an FP32 buffer holding the given ids (host uint64 array): (host arrays of the found rows,
+    boolean mask over ids)"""
+    n = buf.count()
+    have = buf.ids[:n]
+    srt, order = torch.sort(have)
+    q = torch.from_numpy(np.ascontiguousarray(ids).view(np.int64)).to(have.device)
+    pos = torch.searchsorted(srt, q).clamp(max=max(n - 1, 0))
+    hit = (srt[pos] == q) if n > 0 else torch.zeros_like(q, dtype=torch.bool)
+    rows = order[pos[hit]]
+    return _gpu_rows(buf, rows, torch), hit.cpu().numpy()
+
+
+def _match(g: dict, o: dict):
+    """(g rows, o rows) of the ids present in both, in the same order"""
+    common, gi, oi = np.intersect1d(g["id"], o["id"], return_indices=True)
+    return {k: v[gi] for k, v in g.items()}, {k: v[oi] for k, v in o.items()}
+
+
+def _errors(g: dict, o: dict, photon: bool):
+    """per-particle relative errors of each output: x (floor 1), p or k, s (absolute; photons: P with its
+    transverse part's sign free), tau (floor 1)"""
+    def rel(a, b, floor):
+        return np.linalg.norm(a - b, axis=1) / np.maximum(np.maximum(np.linalg.norm(a, axis=1),
+                                                                     np.linalg.norm(b, axis=1)), floor)
+    e = {"x": rel(g["pos"], o["pos"], 1.0), ("k" if photon else "p"): rel(g["mom"], o["mom"], 1e-300)}
+    sg, so = g["spin"], o["spin"]
+    if photon:
+        kh = o["mom"] / np.maximum(np.linalg.norm(o["mom"], axis=1, keepdims=True), 1e-300)
+        gpar, opar = (sg * kh).sum(1, keepdims=True) * kh, (so * kh).sum(1, keepdims=True) * kh
+        flip = ((sg - gpar) * (so - opar)).sum(1) < 0
+        sg = np.where(flip[:, None], 2 * gpar - sg, sg)
+    e["P" if photon else "s"] = np.linalg.norm(sg - so, axis=1)
+    fin = np.isfinite(g["tau"]) & np.isfinite(o["tau"])
+    e["tau"] = np.where(fin, np.abs(g["tau"] - o["tau"]) / np.maximum(np.abs(o["tau"]), 1.0), 0.0)
+    return e
+
+
+def error_leg(bt, wl, fields, seeds, torch, steps, stride=16, diverged=1e-3):
+    """Each output's error against the FP64 oracle on the benchmark's own state: for `steps` steps, every
+    stride-th particle of every instance and species is read before the step, the batch takes the step on
+    the GPU, the oracle takes it from the same (FP32, widened) state, and the sampled particles and the
+    daughters they made are matched by id.  A particle whose state moved apart by more than `diverged`,
+    or a daughter on one side only, is a decision flip.  The oracle's time on this sample is the CPU
+    baseline (the oracle as it stands, all host cores)."""
     import oracle as O
     tb = O.tables(1e-4, 1e3, 256, 256)
-    sample = []
-    n_e = n_g = 0
-    for (e, p, g), f, sd in zip(bt.buffers(), fields, seeds):
-        parts = []
-        ms = [max(1, int(frac * b.count())) for b in (e, p, g)]
-        caps = (2 * (ms[0] + ms[2]) + 64, 2 * (ms[1] + ms[2]) + 64, ms[2] + 40 * (ms[0] + ms[1]) + 256)
-        for b, m, cap in zip((e, p, g), ms, caps):
-            d = b.read(m)
-            parts.append(O.Particles.from_arrays(cap, d["pos"], d["mom"], d["spin"], d["w"], d["id"], tau=d["tau"]))
-        n_e += parts[0].n
-        n_g += parts[2].n
-        sample.append((parts, _oracle_field(O, f), sd))
-    ps, dt, steps = 0, 0.0, 0
-    while steps < max_steps and dt < seconds:
-        s = step0 + steps
-        for (E, P, G), f, sd in sample:
-            st = O.step_desc(wl.dt, float(s) * wl.dt, s, sd, O.F_FULL, wl.photon_store_min)
-            c = E.n + P.n + G.n
+    acc = {"lepton": {}, "photon": {}, "daughter": {}}
+    n_ps, flips, t_or, ps_or = 0, 0, 0.0, 0
+    spec_g, spec_o = [], []
+    for _ in range(steps):
+        step = int(bt.stats().step)
+        pre = []
+        for e, p, g in bt.buffers():
+            parts = []
+            for b in (e, p, g):
+                n = b.count()
+                parts.append(_gpu_rows(b, torch.arange(0, n, stride, device=b.q.device), torch))
+            pre.append(parts)
+        bt.step(1)
+        torch.cuda.synchronize()
+        for k, ((e, p, g), (pe, pp, pg)) in enumerate(zip(bt.buffers(), pre)):
+            n0 = [len(x["id"]) for x in (pe, pp, pg)]
+            caps = (2 * (n0[0] + n0[2]) + 64, 2 * (n0[1] + n0[2]) + 64, n0[2] + 2 * (n0[0] + n0[1]) + 64)
+            E, P, G = (O.Particles.from_arrays(c, d["pos"], d["mom"], d["spin"], d["w"], d["id"], tau=d["tau"])
+                       for c, d in zip(caps, (pe, pp, pg)))
+            st = O.step_desc(wl.dt, float(step) * wl.dt, step, seeds[k], O.F_FULL, wl.photon_store_min)
             t0 = time.perf_counter()
-            _oracle_batch_step(O, tb, f, st, E, P, G)
-            dt += time.perf_counter() - t0
-            ps += c
-        steps += 1
-    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{frac:.0%} of every instance's particles at step {step0} ({n_e} electrons, {n_g} photons), "
-                      f"{steps} steps, {dt:.1f} s"}
+            _oracle_batch_step(O, tb, _oracle_field(O, fields[k]), st, E, P, G)
+            t_or += time.perf_counter() - t0
+            ps_or += sum(n0)
+            n_ps += sum(n0)
+            ov = [x.view() for x in (E, P, G)]
+            for (buf, ob, prev, kind) in ((e, ov[0], pe, "lepton"), (p, ov[1], pp, "lepton"), (g, ov[2], pg, "photon")):
+                # the sampled particles after the step, then every daughter the oracle made from them
+                o_par = {kk: v for kk, v in ob.items() if kk in ("pos", "mom", "spin", "tau", "w", "id")}
+                old = np.isin(o_par["id"], prev["id"])
+                o_old = {kk: v[old] for kk, v in o_par.items()}
+                o_new = {kk: v[~old] for kk, v in o_par.items()}
+                g_old, hit_old = _gpu_find(buf, o_old["id"], torch)
+                g_new, hit_new = _gpu_find(buf, o_new["id"], torch)
+                flips += int((~hit_old).sum()) + int((~hit_new).sum())
+                go, oo = _match(g_old, o_old)
+                er = _errors(go, oo, kind == "photon")
+                bad = np.max(np.stack(list(er.values())), axis=0) > diverged
+                flips += int(bad.sum())
+                for kk, v in er.items():
+                    acc[kind].setdefault(kk, []).append(v[~bad])
+                gn, on = _match(g_new, o_new)
+                er = _errors(gn, on, kind == "photon")  # the buffer's new particles: daughters of its kind
+                bad = np.max(np.stack(list(er.values())), axis=0) > diverged
+                flips += int(bad.sum())
+                for kk, v in er.items():
+                    acc["daughter"].setdefault(f"{'photon' if kind == 'photon' else 'lepton'}_{kk}", []).append(v[~bad])
+                if kind == "photon":  # photons emitted this step: the spectrum
+                    spec_g.append(np.linalg.norm(gn["mom"][~bad], axis=1))
+                    spec_o.append(np.linalg.norm(on["mom"][~bad], axis=1))
+            # photons the GPU made from sampled leptons that the oracle did not (flips the other way show
+            # in the emitter's state above)
+
+    def q(v):
+        v = np.concatenate(v) if v else np.zeros(0)
+        if len(v) == 0:
+            return None
+        return {"n": int(len(v)), "p50": float(np.quantile(v, 0.5)), "p99": float(np.quantile(v, 0.99)),
+                "p999": float(np.quantile(v, 0.999)), "max": float(v.max()), "above_1e-5": float((v > 1e-5).mean())}
+
+    out = {"against": "FP64 oracle (oracle/), one step at a time from the GPU's FP32 state",
+           "sample": f"every {stride}th particle of every instance and species, {steps} steps",
+           "particle_steps": n_ps, "flips": flips, "flip_rate": flips / max(n_ps, 1),
+           "diverged_threshold": diverged}
+    for kind, d in acc.items():
+        out[kind] = {kk: q(v) for kk, v in d.items()}
+    sg, so = (np.concatenate(spec_g) if spec_g else np.zeros(0)), (np.concatenate(spec_o) if spec_o else np.zeros(0))
+    if len(so):
+        rel = np.abs(sg - so) / so
+        bins_g = np.floor(64 * np.log10(sg))
+        bins_o = np.floor(64 * np.log10(so))
+        out["spectrum"] = {"photons": int(len(so)), "rel_err_p99": float(np.quantile(rel, 0.99)),
+                           "rel_err_max": float(rel.max()), "bin_64_per_decade_mismatch": int((bins_g != bins_o).sum())}
+    cpu = {"value": ps_or / t_or if t_or > 0 else None, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"every {stride}th particle of every instance and species of the benchmark's state, "
+                     f"{steps} steps ({ps_or} particle-steps, {t_or:.1f} s)"}
+    return out, cpu
 
 
 def reference_arm_batch(args):
@@ -814,7 +1011,8 @@ def extra_legs(args, sim, Q, B, I, wl, tables, device, torch):
     out = {}
     state = sim.state()  # current state (after the timed steps)
     # ---- plain FP64 path on the same state ----
-    sim64 = Sim(Q, B, I, wl, B.QED_FP64, tables, sim.n0, sim.seed, wl.capacity_factor, device)
+    room = tuple(int(1.1 * b.count()) + 4096 for b in (sim.el, sim.po, sim.ph))
+    sim64 = Sim(Q, B, I, wl, B.QED_FP64, tables, sim.n0, sim.seed, room, device)
     sim64.load_state(state)
     sim64.step_index = sim.step_index
     for _ in range(2):

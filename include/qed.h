@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define QED_ABI_VERSION 1
+#define QED_ABI_VERSION 2
 
 typedef enum {
     QED_OK = 0,
@@ -157,7 +157,14 @@ typedef struct {
     double chi_floor;        /* no QED event is considered below this chi */
 } qed_step_desc;
 
-/* Device-resident counters, accumulated by every step call (zero them with cudaMemset). */
+/* Device-resident counters, accumulated by every step call (zero them with cudaMemset).
+ *
+ * Buffer overflow.  A step call takes the counts of its daughter buffers when it begins and appends
+ * at most what fits: an event whose daughters do not all fit is not applied (the parent keeps the state
+ * the classical part of its step gave it, its optical depth stays spent, so it tries again next step)
+ * and is counted in dropped_capacity, status QED_ERR_CAPACITY.  An electron-positron pair is stored
+ * whole or not at all.  Which events of an overflowing call get the last free slots is not specified
+ * (the reservation order of the device); counts never exceed capacity. */
 typedef struct {
     unsigned long long events;           /* emissions (push step) or pair conversions (pair step) */
     unsigned long long stored;           /* daughters written */
@@ -169,6 +176,13 @@ typedef struct {
     int32_t status;                      /* first device-side error (qed_status), 0 if none */
     int32_t pad;
     int64_t first_bad;                   /* particle index of the first device-side error, -1 if none */
+    /* Daughter-slot reservation of the step call in flight, written only by that call's own kernels:
+     * the daughter buffers' counts when the call began, how many events' daughters fit, how many
+     * events asked for slots.  Callers neither read nor set it (zeroing it with the rest is fine); it
+     * is the reason calls that share one qed_counters must not overlap on the device. */
+    int64_t append_base[2];
+    int64_t append_budget;
+    unsigned long long append_next;
 } qed_counters;
 
 /* ---------------------------------------------------------------------------------------------- */
@@ -249,9 +263,10 @@ size_t qed_compact_workspace_bytes(int64_t capacity);
  * (cudaFree, and cudaMalloc under memory pressure, synchronise the device).
  *
  * Scratch: a file-scope device array sized for QED_COMPACT_NOALLOC_MAX_CAPACITY photons (4.25 MiB
- * per device), zero at module load.  Each call zeroes the tail marks it uses with
- * cudaMemsetAsync on `stream` and resets the header counters in its first kernel, so nothing has to be
- * cleared by the caller.  Result: the same as qed_compact (the survivors' set; their order may differ).
+ * per device), zero at module load.  Each call resets the header counters in its first kernel and
+ * clears, in its third, every tail mark its second set, so it leaves the scratch ready for the next call
+ * and nothing has to be cleared by the caller; a call costs O(dead photons), like qed_compact.
+ * Result: the same as qed_compact (the survivors' set; their order may differ).
  *
  * Limits and ordering:
  *  - photons->capacity above QED_COMPACT_NOALLOC_MAX_CAPACITY returns QED_ERR_TOO_LARGE before any
@@ -261,6 +276,9 @@ size_t qed_compact_workspace_bytes(int64_t capacity);
  *    on one stream or with events.
  *  - The first call on each device looks the scratch up (cudaGetSymbolAddress with that device
  *    current, which may load the module); make that first call before any stream capture begins.
+ *    The address is kept per device index for the life of the process: after cudaDeviceReset (or any
+ *    teardown of the device's primary context) it is stale, so do not call this function again in that
+ *    process once the device has been reset.
  * Errors: QED_ERR_ARG (bad buffer), QED_ERR_TOO_LARGE, QED_ERR_CUDA (lookup or launch failed). */
 #define QED_COMPACT_NOALLOC_MAX_CAPACITY 262144
 qed_status qed_compact_noalloc(qed_particles *photons, void *stream);

@@ -694,6 +694,7 @@ typedef struct {
     double d1k[3], s1[3], tau1;                /* daughter 1 (positron) */
     uint64_t id0, id1;
     int clamped, renorm;
+    double kept_p[3], kept_s[3], kept_tau;     /* lepton state if its event is not applied */
 } orc_result;
 
 static void push_particle(orc_particles *b, const double x[3], const double p[3], const double s[3], double tau,
@@ -883,6 +884,10 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 down = u0[0] < Wdn_part * dt;
             }
             if (event) {
+                /* the state the classical part of the step gave the lepton, with its optical depth
+                 * spent: what it keeps if its photon finds no room in the photon buffer */
+                for (int i = 0; i < 3; ++i) { res->kept_p[i] = p[i]; res->kept_s[i] = s[i]; }
+                res->kept_tau = tauf;
                 double u1[2], u2[2];
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_LAMBDA_SPIN, u1);
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_STOKES, u2);
@@ -967,14 +972,23 @@ int orc_lepton_step(const orc_tables *tb, const orc_field *fd, const orc_step *s
     if (!res) return -1;
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) lepton_one(tb, fd, st, charge, L, j, &res[j]);
-    /* daughters appended in parent order (Sec. 3.3) */
+    /* daughters appended in parent order (Sec. 4.3).  An event whose photon does not fit is not applied:
+     * the lepton keeps the state the classical part of its step gave it and its spent optical depth, so
+     * it emits in a later step (without a photon buffer the photons are discarded and events apply). */
     for (int64_t j = 0; j < n; ++j) {
         if (res[j].clamped) ctr->chi_clamped++;
         if (res[j].renorm) ctr->renormalised++;
         if (!res[j].event) continue;
+        if (!res[j].store) { ctr->events++; ctr->below_store++; continue; }
+        if (ph == NULL) { ctr->events++; ctr->dropped_capacity++; continue; }
+        if (ph->n >= ph->capacity) {
+            ctr->dropped_capacity++;
+            L->px[j] = res[j].kept_p[0]; L->py[j] = res[j].kept_p[1]; L->pz[j] = res[j].kept_p[2];
+            L->sx[j] = res[j].kept_s[0]; L->sy[j] = res[j].kept_s[1]; L->sz[j] = res[j].kept_s[2];
+            L->tau[j] = res[j].kept_tau;
+            continue;
+        }
         ctr->events++;
-        if (!res[j].store) { ctr->below_store++; continue; }
-        if (ph == NULL || ph->n >= ph->capacity) { ctr->dropped_capacity++; continue; }
         push_particle(ph, res[j].d0, res[j].k0, res[j].P0, res[j].tau0, res[j].w0, res[j].id0);
         ctr->stored++;
     }

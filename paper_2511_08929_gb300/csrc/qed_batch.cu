@@ -39,6 +39,7 @@ struct InstDev {
     int64_t* live;
     uint8_t* mark;
     int64_t* hdr;  // [0] n, [1] D, [2] holes found, [3] live found
+    AppendState* app;  // daughter reservations of the step: [0] photons (lepton events), [1] pairs
 };
 
 struct SegDev {
@@ -150,6 +151,12 @@ __global__ void __launch_bounds__(kPlanThreads)
         S.chi_floor = P.chi_floor;
         S.store_min_f = (float)P.store_min;
         S.chi_floor_f = (float)P.chi_floor;
+    }
+    // open every instance's daughter reservations from the counts at step start (clamped above)
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        const InstDev& I = inst[i];
+        append_open(&I.app[0], I.sp[2].count, I.sp[2].capacity, nullptr, 0);
+        append_open(&I.app[1], I.sp[0].count, I.sp[0].capacity, I.sp[1].count, I.sp[1].capacity);
     }
     if (threadIdx.x == 0) {
         clk->next_tile = 0;
@@ -420,7 +427,8 @@ constexpr int kEventThreads = 256;
 __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const InstDev* __restrict__ inst,
                                                                    const SegCtx* __restrict__ ctx,
                                                                    const long long* __restrict__ ev,
-                                                                   const ClockDev* __restrict__ clk, qed_counters* ctr) {
+                                                                   const ClockDev* __restrict__ clk, Tab64 X64,
+                                                                   qed_counters* ctr) {
     const unsigned long long n = clk->n_events;
     unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
     const int lane = threadIdx.x & 31;
@@ -436,8 +444,9 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
         const bool ph = X.sp == 2;
         // both passes are warp-collective; a lane takes part in the one of its species with its particle
         if (__ballot_sync(0xffffffffu, j >= 0 && !ph))
-            lepton_events(X.C, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], ctr, c);
-        if (__ballot_sync(0xffffffffu, j >= 0 && ph)) photon_events(X.C, ph ? j : -1, I.sp[2], I.sp[0], I.sp[1], ctr, c);
+            lepton_events(X.C, X64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c);
+        if (__ballot_sync(0xffffffffu, j >= 0 && ph))
+            photon_events(X.C, X64, ph ? j : -1, I.sp[2], I.sp[0], I.sp[1], &I.app[1], ctr, c);
     }
     flush_warp(c, ctr);
 }
@@ -452,6 +461,9 @@ __global__ void batch_compact_head(const InstDev* __restrict__ inst, int n_inst)
     if (i >= n_inst) return;
     const InstDev& I = inst[i];
     const PartDev& G = I.sp[2];
+    // close the step's daughter reservations: the counts after this step's appends
+    append_close(&I.app[0], G.count, nullptr);
+    append_close(&I.app[1], I.sp[0].count, I.sp[1].count);
     const int64_t n = max((int64_t)0, min(*G.count, G.capacity));
     I.hdr[0] = n;
     I.hdr[1] = max((int64_t)0, min(*G.n_dead, n));
@@ -531,6 +543,7 @@ struct qed_batch_s {
     int64_t* d_tile0;
     ClockDev* d_clk;
     int64_t* d_hdr;
+    AppendState* d_app;  // two daughter reservations per instance
     unsigned char* d_ws;
     int64_t capacity_total;
     qed_batch_tuning tuning;
@@ -600,7 +613,9 @@ static void launch_batch_step(const qed_batch_s* b, cudaStream_t st, cudaEvent_t
                                                   tab_params<float>(b->tables), b->tables->bes32, P);
     if (e0) cudaEventRecordWithFlags(e0, st, rec);
     variant_of(b, b->tuning.variant).launch(b, b->grid, st);
-    batch_event_kernel<<<b->ev_grid, kEventThreads, 0, st>>>(b->d_inst, b->d_ctx, b->d_ev, b->d_clk, b->ctr);
+    batch_event_kernel<<<b->ev_grid, kEventThreads, 0, st>>>(b->d_inst, b->d_ctx, b->d_ev, b->d_clk,
+                                                             Tab64{tab_params<double>(b->tables), b->tables->bes64},
+                                                             b->ctr);
     if (e1) cudaEventRecordWithFlags(e1, st, rec);
     batch_compact_head<<<(b->n_inst + 255) / 256, 256, 0, st>>>(b->d_inst, b->n_inst);
     const dim3 g(kCompactBlocks, b->n_inst);
@@ -672,6 +687,7 @@ extern "C" void qed_batch_destroy(qed_batch_t b) {
     cudaFree(b->d_tile0);
     cudaFree(b->d_clk);
     cudaFree(b->d_hdr);
+    cudaFree(b->d_app);
     cudaFree(b->d_ws);
     b->magic = 0;
     delete b;
@@ -719,6 +735,7 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
          cudaMalloc(&b->d_tile0, sizeof(int64_t) * (n_seg + 1)) == cudaSuccess &&
          cudaMalloc(&b->d_clk, sizeof(ClockDev)) == cudaSuccess &&
          cudaMalloc(&b->d_hdr, sizeof(int64_t) * 4 * n_inst) == cudaSuccess &&
+         cudaMalloc(&b->d_app, sizeof(AppendState) * 2 * n_inst) == cudaSuccess &&
          cudaMalloc(&b->d_ws, ws < 16 ? 16 : ws) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -741,6 +758,7 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
         d.live = (int64_t*)(base + r16(8 * cap));
         d.mark = base + 2 * r16(8 * cap);
         d.hdr = b->d_hdr + 4 * i;
+        d.app = b->d_app + 2 * i;
     }
     ClockDev clk{};
     clk.step = desc->step0;
@@ -751,6 +769,7 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
          cudaMemcpy(b->d_clk, &clk, sizeof(ClockDev), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(b->d_ws, 0, ws < 16 ? 16 : ws) == cudaSuccess &&
          cudaMemset(b->d_hdr, 0, sizeof(int64_t) * 4 * n_inst) == cudaSuccess &&
+         cudaMemset(b->d_app, 0, sizeof(AppendState) * 2 * n_inst) == cudaSuccess &&
          cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();

@@ -56,11 +56,14 @@ __global__ void snapshot_kernel(CountPairs c) {
     if (i < c.n) *c.begin[i] = *c.count[i];
 }
 
-__global__ void clamp_kernel(int64_t* a, int64_t ca, int64_t* b, int64_t cb, int64_t* c, int64_t cc) {
-    if (threadIdx.x != 0) return;
-    if (a && *a > ca) *a = ca;
-    if (b && *b > cb) *b = cb;
-    if (c && *c > cc) *c = cc;
+// the daughter-slot reservation of one step call (AppendState in the caller's counters): opened before
+// the step kernel from the daughter buffers' counts, closed after it by advancing the counts
+__global__ void append_open_kernel(qed_counters* ctr, const int64_t* c0, int64_t cap0, const int64_t* c1, int64_t cap1) {
+    if (threadIdx.x == 0) append_open(append_state(ctr), c0, cap0, c1, cap1);
+}
+
+__global__ void append_close_kernel(qed_counters* ctr, int64_t* c0, int64_t* c1) {
+    if (threadIdx.x == 0) append_close(append_state(ctr), c0, c1);
 }
 
 // ---- compaction (Sec. 3.3: converted photons leave the simulation) ----
@@ -180,9 +183,10 @@ extern "C" qed_status qed_push_step(qed_tables_t t, const qed_field* field, cons
             return QED_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (photons) append_open_kernel<<<1, 32, 0, st>>>(ctr, photons->count, photons->capacity, nullptr, 0);
     if (leptons->layout == QED_FP64) launch_lepton64(t, *field, *step, leptons, photons, ctr, st);
     else launch_lepton32(t, *field, *step, leptons, photons, ctr, st);
-    if (photons) clamp_kernel<<<1, 32, 0, st>>>(photons->count, photons->capacity, nullptr, 0, nullptr, 0);
+    if (photons) append_close_kernel<<<1, 32, 0, st>>>(ctr, photons->count, nullptr);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
@@ -201,10 +205,12 @@ extern "C" qed_status qed_pair_step(qed_tables_t t, const qed_field* field, cons
             return QED_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (electrons)
+        append_open_kernel<<<1, 32, 0, st>>>(ctr, electrons->count, electrons->capacity, positrons->count,
+                                             positrons->capacity);
     if (photons->layout == QED_FP64) launch_photon64(t, *field, *step, photons, electrons, positrons, ctr, st);
     else launch_photon32(t, *field, *step, photons, electrons, positrons, ctr, st);
-    if (electrons)
-        clamp_kernel<<<1, 32, 0, st>>>(electrons->count, electrons->capacity, positrons->count, positrons->capacity, nullptr, 0);
+    if (electrons) append_close_kernel<<<1, 32, 0, st>>>(ctr, electrons->count, positrons->count);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
@@ -247,9 +253,10 @@ constexpr size_t kNoAllocScratchBytes =
     64 + 2 * ((sizeof(int64_t) * (size_t)QED_COMPACT_NOALLOC_MAX_CAPACITY + 15) & ~size_t(15)) +
     (((size_t)QED_COMPACT_NOALLOC_MAX_CAPACITY + 15) & ~size_t(15));
 
-// Zero-initialised at module load like every static device object; each call zeroes the marks it
-// uses again (the header slots are written by compact_head_kernel), so no call depends on how the
-// previous one ended.
+// Zero-initialised at module load like every static device object.  A call sets tail marks only in
+// [0, D) (D = its dead photons) and its tail kernel clears every mark it reads, so each call leaves the
+// marks zero for the next one; the header slots are rewritten by compact_head_kernel.  A call therefore
+// costs O(D) like qed_compact, not O(capacity).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kNoAllocDevices = 64;
@@ -284,8 +291,6 @@ extern "C" qed_status qed_compact_noalloc(qed_particles* photons, void* stream) 
     if (noalloc_scratch(&scratch) != cudaSuccess) return QED_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const CompactWs w = carve(scratch, QED_COMPACT_NOALLOC_MAX_CAPACITY);
-    if (photons->capacity > 0 && cudaMemsetAsync(w.mark, 0, (size_t)photons->capacity, st) != cudaSuccess)
-        return QED_ERR_CUDA;
     const PartDev g = part_dev(photons);
     const int blocks = launch_blocks(photons->capacity, 256);
     compact_head_kernel<<<1, 32, 0, st>>>(g, w);

@@ -129,6 +129,39 @@ __device__ __forceinline__ void phase_sincos(float v, float* s, float* c, float 
     __sincosf(r, s, c);
 }
 
+// sin and cos of a phase v + dv to FP32 relative precision, zeros included (the event passes of the FP32
+// path use it: there a field near a node enters chi and the photon energy relatively).  Quarter-period
+// reduction with pi/2 split into three floats (Cody and Waite): P1 has 11 significant bits and P2 14, so
+// k P1 and k P2 are exact for |k| < 2^10 (phases below ~1600 rad) and v - k P1 is exact; the remainder
+// keeps its own relative precision down to the zeros of sin and cos.  For |r| <= pi/4 + |dv| the Taylor
+// series of sin to r^11 and of cos to r^12 leave relative errors below 1e-11.
+__device__ __forceinline__ void phase_sincos_acc(float v, float dv, float* s, float* c) {
+    const float k = rintf(v * 0.636619772f);  // 2/pi
+    float r = fmaf(-k, 1.5703125f, v);
+    r = fmaf(-k, 4.838407039642334e-4f, r);
+    r = fmaf(-k, -1.3909067675399456e-8f, r);
+    r = r + dv;
+    const float z = r * r;
+    // sin r = r (1 - z/6 (1 - z/20 (1 - z/42 (1 - z/72 (1 - z/110))))), cos r likewise with 2, 12, ..., 132
+    float ps = fmaf(-z, 1.0f / 110.0f, 1.0f);
+    ps = fmaf(-z * (1.0f / 72.0f), ps, 1.0f);
+    ps = fmaf(-z * (1.0f / 42.0f), ps, 1.0f);
+    ps = fmaf(-z * (1.0f / 20.0f), ps, 1.0f);
+    ps = fmaf(-z * (1.0f / 6.0f), ps, 1.0f);
+    const float sr = r * ps;
+    float pc = fmaf(-z, 1.0f / 132.0f, 1.0f);
+    pc = fmaf(-z * (1.0f / 90.0f), pc, 1.0f);
+    pc = fmaf(-z * (1.0f / 56.0f), pc, 1.0f);
+    pc = fmaf(-z * (1.0f / 30.0f), pc, 1.0f);
+    pc = fmaf(-z * (1.0f / 12.0f), pc, 1.0f);
+    const float cr = fmaf(-z * 0.5f, pc, 1.0f);
+    const int q = ((int)k) & 3;  // quadrant (two's complement: right for negative k too)
+    const float sa = (q & 1) ? cr : sr, ca = (q & 1) ? sr : cr;
+    *s = (q & 2) ? -sa : sa;
+    *c = (q == 1 || q == 2) ? -ca : ca;
+}
+__device__ __forceinline__ void phase_sincos_acc(double v, double dv, double* s, double* c) { sincos(v + dv, s, c); }
+
 // a + b as an unevaluated sum s + e (Knuth's TwoSum: e is the exact rounding error of s)
 template <class R>
 __device__ __forceinline__ R two_sum(R a, R b, R& e) {
@@ -146,8 +179,21 @@ __device__ __forceinline__ R envelope(R phi, const FieldP<R>& f) {
     return (phi < R(0) || phi > f.phimax) ? R(0) : s * s;
 }
 
-// phase_t = t + phase (split by the caller for the FP32 path as hi + lo)
+// the envelope at the phase ps + dp to FP32 relative precision near its edges as well: the argument
+// (ps + dp) inv2n as a product with its exact rounding error, then the accurate sine
 template <class R>
+__device__ __forceinline__ R envelope_acc(R ps, R dp, const FieldP<R>& f) {
+    const R u = ps * f.inv2n;
+    const R du = fma_(ps, f.inv2n, -u) + dp * f.inv2n;
+    R s, c;
+    phase_sincos_acc(u, du, &s, &c);
+    const R phi = ps + dp;
+    return (phi < R(0) || phi > f.phimax) ? R(0) : s * s;
+}
+
+// phase_t = t + phase (split by the caller for the FP32 path as hi + lo).  ACC: the accurate sine and
+// cosine (event passes of the FP32 path); otherwise the fast ones.
+template <class R, bool ACC = false>
 __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x, V3<R>& E, V3<R>& B) {
     if (f.kind == QED_FIELD_CONST) {
         E = v3(f.E0x, f.E0y, f.E0z);
@@ -160,12 +206,13 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
     const R ps = two_sum(ph_hi, -x.z, e1);
     const R dp = e1 + ph_lo;
     const R phi = ps + dp;
-    const R a = f.a0 * envelope(phi, f);
+    const R a = f.a0 * (ACC ? envelope_acc(ps, dp, f) : envelope(phi, f));
     E = v3(R(0), R(0), R(0));
     B = E;
     if (a != R(0)) {  // outside the envelope the carrier is not needed
         R s, c;
-        phase_sincos(ps, &s, &c, dp);
+        if (ACC) phase_sincos_acc(ps, dp, &s, &c);
+        else phase_sincos(ps, &s, &c, dp);
         const R ex = a * c, ey = f.kind == QED_FIELD_LP ? R(0) : a * s;
         E = v3(ex, ey, R(0));
         B = v3(-ey, ex, R(0));  // forward wave: B = z x E
@@ -175,10 +222,11 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
         const R ps2 = two_sum(ph_hi, x.z, e2);
         const R dp2 = e2 + ph_lo;
         const R phi2 = ps2 + dp2;
-        const R a2 = f.a0 * envelope(phi2, f);
+        const R a2 = f.a0 * (ACC ? envelope_acc(ps2, dp2, f) : envelope(phi2, f));
         if (a2 != R(0)) {
             R s2, c2;
-            phase_sincos(ps2, &s2, &c2, dp2);
+            if (ACC) phase_sincos_acc(ps2, dp2, &s2, &c2);
+            else phase_sincos(ps2, &s2, &c2, dp2);
             const R ex2 = a2 * c2, ey2 = a2 * s2;
             E.x += ex2;
             E.y += ey2;
@@ -396,6 +444,60 @@ __device__ __forceinline__ void flush_counters(unsigned long long (&c)[N], unsig
 __device__ __forceinline__ void record_error(qed_counters* ctr, int32_t status, int64_t idx) {
     if (*reinterpret_cast<volatile int32_t*>(&ctr->status) != 0) return;
     if (atomicCAS(&ctr->status, 0, status) == 0) ctr->first_bad = idx;
+}
+
+// ---------------------------------------------------------------------------------------------
+// budgeted daughter appends
+// ---------------------------------------------------------------------------------------------
+// The daughter buffers of one step call (or of one instance's step in a batch) take the counts they had
+// when the step began (base), how many events' daughters fit (budget) and how many events asked (next).
+// Event k of the call (k in reservation order) writes its daughters at base + k if k < budget, else it
+// is not applied; afterwards each count becomes base + min(next, budget).  A pair therefore goes into
+// both buffers or into neither, and no count ever exceeds its capacity.  The layout matches the
+// append_* fields at the end of qed_counters.
+struct AppendState {
+    int64_t base[2];   // the daughter buffers' counts when the step began (pairs: electrons, positrons)
+    int64_t budget;    // events whose daughters fit
+    unsigned long long next;  // events that asked for slots
+};
+
+// open the reservation of a step: c1 may be NULL (one daughter buffer)
+__device__ __forceinline__ void append_open(AppendState* A, const int64_t* c0, int64_t cap0, const int64_t* c1,
+                                            int64_t cap1) {
+    const int64_t n0 = min(max(*c0, (int64_t)0), cap0);
+    int64_t budget = cap0 - n0;
+    A->base[0] = n0;
+    A->base[1] = 0;
+    if (c1) {
+        const int64_t n1 = min(max(*c1, (int64_t)0), cap1);
+        A->base[1] = n1;
+        budget = min(budget, cap1 - n1);
+    }
+    A->budget = budget;
+    A->next = 0ull;
+}
+
+// close it: the counts after the step's appends
+__device__ __forceinline__ void append_close(const AppendState* A, int64_t* c0, int64_t* c1) {
+    const int64_t used = min((int64_t)A->next, A->budget);
+    *c0 = A->base[0] + used;
+    if (c1) *c1 = A->base[1] + used;
+}
+
+// Event index of this lane in its reservation (all 32 lanes call it; lanes may name different states:
+// the lanes of one state form a group whose first wanting lane reserves for the group with one atomic
+// add).  -1 for lanes that do not want a slot or name no state; otherwise the caller compares the index
+// with the budget.
+__device__ __forceinline__ long long reserve_event(AppendState* A, bool want) {
+    want = want && A != nullptr;
+    const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)A);
+    const unsigned m = __ballot_sync(0xffffffffu, want) & grp;
+    if (m == 0) return -1;  // uniform over the group
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    long long base = 0;
+    if (lane == leader) base = (long long)atomicAdd(&A->next, (unsigned long long)__popc(m));
+    base = __shfl_sync(grp, base, leader);
+    return want ? base + (long long)__popc(m & ((1u << lane) - 1u)) : -1;
 }
 
 // warp-aggregated slot reservation on a device counter: returns the slot of this lane (valid if want)

@@ -85,6 +85,11 @@ inline PartDev part_dev(const qed_particles* p) {
     return d;
 }
 
+// the reservation state of a step call: the append_* fields at the end of the caller's counters
+__host__ __device__ inline qed::AppendState* append_state(qed_counters* ctr) {
+    return reinterpret_cast<qed::AppendState*>(&ctr->append_base[0]);
+}
+
 // validation of a particle buffer for a given layout
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

@@ -31,7 +31,8 @@ namespace qed {
 template <bool PHOTON>
 __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float> T, const float* __restrict__ bes_g,
                                                                       FieldP<float> F, StepP S, float q, PartDev P,
-                                                                      PartDev D1, PartDev D2, qed_counters* ctr) {
+                                                                      PartDev D1, PartDev D2, AppendState* A,
+                                                                      Tab64 X, qed_counters* ctr) {
     extern __shared__ __align__(128) unsigned char smem[];
     const Shared32 sh = carve32(smem, T.n_chi);
     load_tables32(sh, bes_g, T);
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
         __syncwarp();
         if (qn >= 32) {
             const int64_t je = wq[qn - 32 + lane];
-            if (PHOTON) photon_events(C, je, P, D1, D2, ctr, c);
-            else lepton_events(C, je, P, D1, ctr, c);
+            if (PHOTON) photon_events(C, X, je, P, D1, D2, A, ctr, c);
+            else lepton_events(C, X, je, P, D1, A, ctr, c);
             qn -= 32;
             __syncwarp();
         }
@@ -109,8 +110,8 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
     }
     if (qn > 0) {
         const int64_t je = lane < qn ? wq[lane] : -1;
-        if (PHOTON) photon_events(C, je, P, D1, D2, ctr, c);
-        else lepton_events(C, je, P, D1, ctr, c);
+        if (PHOTON) photon_events(C, X, je, P, D1, D2, A, ctr, c);
+        else lepton_events(C, X, je, P, D1, A, ctr, c);
     }
     flush_warp(c, ctr);
 }
@@ -153,9 +154,9 @@ void launch_lepton32(const qed_tables_s* t, const qed_field& f, const qed_step_d
     PartDev g{};
     if (G) g = part_dev(G);
     const void* k = (const void*)step32_kernel<false>;
-    step32_kernel<false><<<blocks32(L->capacity, k, smem), kT32, smem, st>>>(tab_params<float>(t), t->bes32,
-                                                                             field_params<float>(f), step_params(s, f),
-                                                                             (float)L->charge, part_dev(L), g, PartDev{}, ctr);
+    step32_kernel<false><<<blocks32(L->capacity, k, smem), kT32, smem, st>>>(
+        tab_params<float>(t), t->bes32, field_params<float>(f), step_params(s, f), (float)L->charge, part_dev(L), g,
+        PartDev{}, G ? append_state(ctr) : nullptr, Tab64{tab_params<double>(t), t->bes64}, ctr);
 }
 
 void launch_photon32(const qed_tables_s* t, const qed_field& f, const qed_step_desc& s, const qed_particles* G,
@@ -168,7 +169,7 @@ void launch_photon32(const qed_tables_s* t, const qed_field& f, const qed_step_d
         p = part_dev(Po);
     }
     const void* k = (const void*)step32_kernel<true>;
-    step32_kernel<true><<<blocks32(G->capacity, k, smem), kT32, smem, st>>>(tab_params<float>(t), t->bes32,
-                                                                            field_params<float>(f), step_params(s, f), 0.0f,
-                                                                            part_dev(G), e, p, ctr);
+    step32_kernel<true><<<blocks32(G->capacity, k, smem), kT32, smem, st>>>(
+        tab_params<float>(t), t->bes32, field_params<float>(f), step_params(s, f), 0.0f, part_dev(G), e, p,
+        (El && Po) ? append_state(ctr) : nullptr, Tab64{tab_params<double>(t), t->bes64}, ctr);
 }

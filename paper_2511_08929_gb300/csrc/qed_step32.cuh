@@ -281,10 +281,10 @@ __device__ __forceinline__ bool basis32(const Ctx& C, const F3& E, const F3& B, 
     return true;
 }
 
-// The Boris push and the T-BMT vector for fields with E_z = B_z = 0 (the plane waves along z: every
-// field kind but the constant one): the general forms with the products by the zero components left
-// out.  A product by zero only adds a signed zero, so the results are the general forms' bit for bit
-// (for finite inputs).
+// The Boris push and the T-BMT vector for fields with E_z = B_z = 0 (the plane waves along z: the
+// linear, circular and counter-propagating circular lasers): the general forms with the products by the
+// zero components left out.  A product by zero only adds a signed zero, so for finite inputs the results
+// equal the general forms' up to the sign of a zero result.
 __device__ __forceinline__ F3 cross_t(const F3& a, const F3& b) {  // b.z = 0
     return F3{-(a.z * b.y), a.z * b.x, fma_(a.x, b.y, -(a.y * b.x))};
 }
@@ -326,7 +326,8 @@ struct LState {
 };
 
 // fields at x_old, Boris push, T-BMT precession, move, chi, basis and rates
-template <uint32_t FIX = 0>
+// ACC: fields from the accurate sine and cosine (the event passes), else the fast ones
+template <uint32_t FIX = 0, bool ACC = false>
 __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, LState& st,
                                                  unsigned long long* c,
                                                  const TabP<float>* Tp = nullptr) {
@@ -337,9 +338,10 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     st.p = F3{a.w, b.x, b.y};
     st.s = F3{b.z, b.w, cc.x};
     st.w = cc.y;
-    field_eval(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
+    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const F3 pold = st.p;
-    const bool transverse = C.F.kind != QED_FIELD_CONST;
+    // the field kinds known to have E_z = B_z = 0; any other kind takes the general forms
+    const bool transverse = C.F.kind >= QED_FIELD_LP && C.F.kind <= QED_FIELD_CP_COUNTER;
     if (fl & QED_F_PUSH) st.p = transverse ? boris_t(st.p, st.E, st.B, C.q, dt) : boris(st.p, st.E, st.B, C.q, dt);
     if (fl & QED_F_TBMT) {
         const F3 pb = 0.5f * (pold + st.p);
@@ -380,83 +382,195 @@ __device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x
     L.q2[j] = make_float4(s.z, w, lo, hi);
 }
 
+// ------------------------------------------------------------------------------------------------
+// precision of the event passes
+// ------------------------------------------------------------------------------------------------
+// Events are a few per cent of the particle-steps and the FP64 pipe is idle there, so the quantities of an
+// event that FP32 cannot hold to 1e-5 relative are taken in FP64: the energy fraction (the ICDF rows and
+// the fraction from them: ln u' of a soft photon is ~ -40, whose FP32 rounding is ~4e-6 of u'), every
+// quantity of a pair (the j_e, j_p coefficients 1/(1 - lambda) - xi3/lambda and the like cancel), and the
+// photon's Stokes vector and the lepton's spin axis wherever the FP32 forms cancel (|F| or |g| small
+// against their terms).  Fields at events come from the accurate sine and cosine, so chi keeps its
+// relative precision next to a node of the carrier.
+struct Tab64 {
+    TabP<double> T;     // FP64 rate and ICDF tables
+    const double* bes;  // FP64 scaled Bessel table [3][kBesN]
+};
+
+__device__ __forceinline__ V3<double> wide(const F3& v) { return V3<double>{v.x, v.y, v.z}; }
+__device__ __forceinline__ F3 narrow(const V3<double>& v) { return F3{(float)v.x, (float)v.y, (float)v.z}; }
+
+// The FP32 forms of g and F are recomputed in FP64 when |g| or |F| is below this fraction of the sum of
+// the absolute values of its terms (the FP32 rounding of the terms, ~1e-7 of that sum, would then move
+// the direction by more than ~1e-6)
+constexpr float kCancel = 0.2f;
+
+// sum over F1, F2, F3 of the absolute values of their terms (App. A.1 Eqs. F1-F3; the Bessel values are
+// positive)
+__device__ __forceinline__ float nlc_stokes_scale(float lam, float one_m, const float bes[3], const F3& si, const F3& sf,
+                                                  const F3& eps, const F3& beta, const F3& k) {
+    const float u = div_(lam, one_m);
+    const float kappa = rcp_(one_m) + one_m;
+    const float kappat = fabsf(rcp_(one_m) - one_m);
+    const float K13 = bes[0], K23 = bes[1], IK = bes[2];
+    const float sie = fabsf(dot(si, eps)), sib = fabsf(dot(si, beta)), sik = fabsf(dot(si, k));
+    const float sfe = fabsf(dot(sf, eps)), sfb = fabsf(dot(sf, beta)), sfk = fabsf(dot(sf, k));
+    const F3 fxi = cross(sf, si);
+    const float lu2 = 0.5f * lam * u;
+    const float A1 = K13 * (u * sie + lam * sfe) + lu2 * IK * (sfe * sib + sfb * sie) + 0.5f * kappat * K23 * fabsf(dot(fxi, k));
+    const float A2 = 0.5f * kappat * K13 * fabsf(dot(fxi, eps)) + (lam * IK + kappat * K23) * sik +
+                     (u * IK + kappat * K23) * sfk + lu2 * K13 * (sfk * sib + sfb * sik);
+    const float A3 = K23 + (u * sib + lam * sfb) * K13 + lu2 * IK * (sfe * sie + sfb * sib) +
+                     0.5f * kappa * K23 * fabsf(dot(sf, si)) + lu2 * K23 * sfk * sik;
+    return A1 + A2 + A3;
+}
+
+// The spin axis and the photon's Stokes vector of an NLC event in FP64 (App. A.1): SQA collapse with r3
+// (or the mean), then F with the final spin and PQA collapse with r4 (or the mean).  With do_spin false
+// the final spin sf is kept as given.
+static __device__ __noinline__ void nlc_spectra64(const Tab64& X, double lam, double one_m, double up, const F3& si,
+                                                 const F3& eps, const F3& beta, const F3& khat, uint32_t fl, bool do_spin,
+                                                 float r3, float r4, F3& sf, float xi[3]) {
+    double bb[3];
+    bessel64(X.bes, up, bb);
+    const V3<double> s_i = wide(si), e = wide(eps), b = wide(beta), k = wide(khat);
+    double w;
+    V3<double> g;
+    nlc_wg(lam, one_m, bb, s_i, b, k, w, g);
+    V3<double> s_f = wide(sf);
+    if (do_spin && (fl & QED_F_SPIN_EVENT)) {
+        const double gn = sqrt(dot(g, g));
+        if (fl & QED_F_SPIN_COLLAPSE) {
+            const double sg = (double)r3 < (w - gn) / (2.0 * w) ? -1.0 : 1.0;
+            s_f = gn > 0.0 ? (sg / gn) * g : V3<double>{0, 0, 0};
+        } else {
+            s_f = (1.0 / w) * g;
+        }
+        sf = narrow(s_f);
+    }
+    if (fl & QED_F_POL_EVENT) {
+        const V3<double> sfu = (fl & QED_F_SPIN_EVENT) ? s_f : V3<double>{0, 0, 0};
+        double Fv[4];
+        nlc_stokes(lam, one_m, bb, s_i, sfu, w, g, e, b, k, Fv);
+        const double Fn = sqrt(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
+        double iF;
+        if (fl & QED_F_POL_COLLAPSE) {
+            const double sg = (double)r4 < (Fv[0] - Fn) / (2.0 * Fv[0]) ? -1.0 : 1.0;
+            iF = Fn > 0.0 ? sg / Fn : 0.0;
+        } else {
+            iF = 1.0 / Fv[0];
+        }
+        for (int i = 0; i < 3; ++i) xi[i] = (float)(Fv[i + 1] * iF);
+    } else {
+        xi[0] = xi[1] = xi[2] = 0.0f;
+    }
+}
+
 // the event pass of one warp (all 32 lanes call it): a lane with j >= 0 takes particle j of buffer L,
-// whose step context is C (lanes may differ in both)
-static __device__ __noinline__ void lepton_events(const Ctx& C, int64_t j, const PartDev& L, const PartDev& G,
-                                                 qed_counters* ctr, unsigned long long* c) {
-    // Two phases around the photon's slot reservation: the lepton's outcome (energy fraction, recoil,
-    // spin) for every event, then the photon's polarization only for photons that have a slot (with
-    // full buffers most are dropped, and their Stokes vectors would be computed for nothing).
+// whose step context is C and whose photons go to G through the reservation A (lanes may differ in all
+// three; A is NULL when the caller keeps no photons)
+static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, int64_t j, const PartDev& L,
+                                                 const PartDev& G, AppendState* A, qed_counters* ctr,
+                                                 unsigned long long* c) {
+    // The lepton's outcome (energy fraction, recoil, spin) and the photon's polarization for every event,
+    // then the photon's slot reservation: an event whose photon does not fit is not applied.
     const uint32_t fl = C.S.flags;
     bool want = false;
     LState st;
     uint64_t id = 0;
-    float lam = 0.0f, one_m = 0.0f, wv = 0.0f;
-    float bb[3] = {0.0f, 0.0f, 0.0f};
-    F3 k{0, 0, 0}, si{0, 0, 0}, sfu{0, 0, 0}, g{0, 0, 0};
+    F3 k{0, 0, 0}, pf{0, 0, 0}, sf{0, 0, 0};
+    float xi[3] = {0.0f, 0.0f, 0.0f};
+    double tau_kept = 0.0, tau_new = 0.0;
     if (j >= 0) {
         const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
-        lepton_classical(C, a, b, cc, st, nullptr);  // the streaming pass's arithmetic, repeated
+        lepton_classical<0, true>(C, a, b, cc, st, nullptr);  // the streaming pass's step, accurate fields
         id = L.id[j];
-        F3 pf = st.p, sf = st.s;
-        double tauf = tau_join(cc.z, cc.w);
+        pf = st.p;
+        sf = st.s;
+        // the optical depth as the streaming pass left it (spent), kept if the event is not applied
+        const double tau0 = tau_join(cc.z, cc.w);
+        tau_kept = (fl & QED_F_TAU) ? tau0 - widen_pos(st.Ws * C.S.dt_f) : tau0;
+        tau_new = tau_kept;
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
         bool down;
         if (fl & QED_F_TAU) down = u52f(w0.z, w0.w) * st.Ws < st.Wdn;
         else down = u52f(w0.x, w0.y) < st.Wdn * C.S.dt_f;
         const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
-        const float r3 = u52f(w1.z, w1.w);
-        const float y = logit52(w1.x, w1.y);
-        // the sampled value to full FP32 accuracy: accurate logarithm of chi and exponential
-        const float up = expf(icdf_lookup(C.T, false, down ? 1 : 0, logf(st.chi), y));
-        const float den = 2.0f + 3.0f * st.chi * up;
-        const float iden = rcp_(den);
-        lam = 3.0f * st.chi * up * iden;
-        one_m = 2.0f * iden;
-        k = lam * st.p;
-        if (fl & QED_F_RECOIL) pf = one_m * st.p;
-        bessel32(C.bes, up, bb);
-        si = (fl & QED_F_RESOLVED) ? st.s : F3{0, 0, 0};
-        if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, bb, si, st.beta, st.khat, wv, g);
-        if (fl & QED_F_SPIN_EVENT) {
+        const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
+        const float r3 = u52f(w1.z, w1.w), r4 = u52f(w2.x, w2.y);
+        // the energy fraction in FP64: the uniform's 52 bits, the FP64 ICDF rows, lambda and 1 - lambda
+        const double r2 = uniform52(w1.x, w1.y);
+        const double chi = (double)st.chi;
+        const double up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
+        const double den = 2.0 + 3.0 * chi * up;
+        const double lam64 = 3.0 * chi * up / den, om64 = 2.0 / den;
+        k = narrow(lam64 * wide(st.p));
+        if (fl & QED_F_RECOIL) pf = narrow(om64 * wide(st.p));
+        const float lam = (float)lam64, one_m = (float)om64;
+        const F3 si = (fl & QED_F_RESOLVED) ? st.s : F3{0, 0, 0};
+        if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) {
+            float bb[3], wv;
+            F3 g;
+            bessel32(C.bes, (float)up, bb);
+            nlc_wg(lam, one_m, bb, si, st.beta, st.khat, wv, g);
+            // the scale of g: the absolute values of its terms (cancellation loses the direction in FP32)
+            const float u = div_(lam, one_m);
+            const float gs = u * bb[0] + (2.0f * bb[1] + bb[2]) * sqrt_(dot(si, si)) +
+                             lam * u * (bb[1] + bb[2]) * fabsf(dot(si, st.khat));
             const float gn = sqrt_(dot(g, g));
-            if (fl & QED_F_SPIN_COLLAPSE) {
-                const float sg = r3 < div_(wv - gn, 2.0f * wv) ? -1.0f : 1.0f;
-                sf = gn > 0.0f ? div_(sg, gn) * g : F3{0, 0, 0};
+            if (!(gn >= kCancel * gs) || !(wv > 0.0f) || !(up >= 1e-30)) {
+                nlc_spectra64(X, lam64, om64, up, si, st.eps, st.beta, st.khat, fl, true, r3, r4, sf, xi);
             } else {
-                sf = rcp_(wv) * g;
+                F3 sfu{0, 0, 0};
+                if (fl & QED_F_SPIN_EVENT) {
+                    if (fl & QED_F_SPIN_COLLAPSE) {
+                        const float sg = r3 < div_(wv - gn, 2.0f * wv) ? -1.0f : 1.0f;
+                        sf = gn > 0.0f ? div_(sg, gn) * g : F3{0, 0, 0};
+                    } else {
+                        sf = rcp_(wv) * g;
+                    }
+                    sfu = sf;
+                }
+                if (fl & QED_F_POL_EVENT) {
+                    float Fv[4];
+                    nlc_stokes(lam, one_m, bb, si, sfu, wv, g, st.eps, st.beta, st.khat, Fv);
+                    const float Fn = sqrt_(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
+                    const float Fs = nlc_stokes_scale(lam, one_m, bb, si, sfu, st.eps, st.beta, st.khat);
+                    if (!(Fn >= kCancel * Fs)) {
+                        // the terms of F cancel (F0 = w - |g| after a spin flip is the usual case): F is
+                        // linear in s_f with coefficients far above |F|, so the final spin is taken again in
+                        // FP64 together with F
+                        nlc_spectra64(X, lam64, om64, up, si, st.eps, st.beta, st.khat, fl, true, r3, r4, sf, xi);
+                    } else if (fl & QED_F_POL_COLLAPSE) {
+                        const float sg = r4 < div_(Fv[0] - Fn, 2.0f * Fv[0]) ? -1.0f : 1.0f;
+                        const float iF = div_(sg, Fn);
+                        for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
+                    } else {
+                        const float iF = rcp_(Fv[0]);
+                        for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
+                    }
+                }
             }
-            sfu = sf;
         }
-        if (fl & QED_F_TAU) tauf = exp_draw(w0.x, w0.y);
-        c[C_EVENTS]++;
+        if (fl & QED_F_TAU) tau_new = exp_draw(w0.x, w0.y);
         want = sqrt_(dot(k, k)) >= C.S.store_min_f;
         if (!want) c[C_BELOW]++;
-        store32(L, j, st.x, pf, sf, st.w, tauf);
     }
-    const long long slot = reserve_grouped(G.count, want);
-    const bool keep = want && G.count != nullptr && slot < G.capacity;
-    if (want && !keep) {
-        c[C_DROPPED]++;
-        if (G.count != nullptr) record_error(ctr, QED_ERR_CAPACITY, j);
+    const long long ev = reserve_event(A, want);
+    const bool keep = want && A != nullptr && ev < A->budget;
+    if (j >= 0) {
+        if (want && A != nullptr && !keep) {  // no room for the photon: the event is not applied
+            c[C_DROPPED]++;
+            record_error(ctr, QED_ERR_CAPACITY, j);
+            store32(L, j, st.x, st.p, st.s, st.w, tau_kept);
+        } else {
+            c[C_EVENTS]++;
+            if (want && A == nullptr) c[C_DROPPED]++;  // the caller keeps no photons
+            store32(L, j, st.x, pf, sf, st.w, tau_new);
+        }
     }
     if (keep) {
-        float xi[3] = {0.0f, 0.0f, 0.0f};
-        if (fl & QED_F_POL_EVENT) {
-            const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
-            const float r4 = u52f(w2.x, w2.y);
-            float Fv[4];
-            nlc_stokes(lam, one_m, bb, si, sfu, wv, g, st.eps, st.beta, st.khat, Fv);
-            const float Fn = sqrt_(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
-            if (fl & QED_F_POL_COLLAPSE) {
-                const float sg = r4 < div_(Fv[0] - Fn, 2.0f * Fv[0]) ? -1.0f : 1.0f;
-                const float iF = Fn > 0.0f ? div_(sg, Fn) : 0.0f;
-                for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
-            } else {
-                const float iF = rcp_(Fv[0]);
-                for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] * iF;
-            }
-        }
+        const int64_t slot = A->base[0] + ev;
         const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
         const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
         store32(G, slot, st.x, k, stokes_to_P(xi, st.eps, st.beta, st.khat), st.w, birth_tau32(gid, C.S.seed));
@@ -518,7 +632,7 @@ struct PState {
     float chi, lnchi, xi[3], Wp, Wm, Wmp, Wx;
 };
 
-template <uint32_t FIX = 0>
+template <uint32_t FIX = 0, bool ACC = false>
 __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, const float4& b, const float4& cc, PState& st,
                                                  unsigned long long* c,
                                                  const TabP<float>* Tp = nullptr) {
@@ -527,7 +641,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.k = F3{a.w, b.x, b.y};
     st.P = F3{b.z, b.w, cc.x};
     st.w = cc.y;
-    field_eval(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
+    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const float en2 = dot(st.k, st.k);
     st.en = sqrt_(en2);
     st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
@@ -551,10 +665,14 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.Wx = st.Wp * (1.0f + st.xi[2]) * 0.5f + st.Wmp;
 }
 
-static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const PartDev& G, const PartDev& El,
-                                                 const PartDev& Po, qed_counters* ctr, unsigned long long* c) {
+// the pair pass of one warp: a lane with j >= 0 takes photon j of G; the pair goes to El and Po through
+// the reservation A (NULL: the caller keeps no pairs, and photons do not convert).  Everything after the
+// decision is FP64 (pairs are rare; their spin coefficients cancel).
+static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, int64_t j, const PartDev& G,
+                                                 const PartDev& El, const PartDev& Po, AppendState* A,
+                                                 qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = C.S.flags;
-    const bool have = El.count != nullptr && Po.count != nullptr;
+    const bool have = A != nullptr;
     bool want = false;
     F3 x{0, 0, 0}, k{0, 0, 0}, P{0, 0, 0}, pe{0, 0, 0}, pp{0, 0, 0}, se{0, 0, 0}, sp{0, 0, 0};
     float w = 0.0f;
@@ -563,7 +681,7 @@ static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const
     if (j >= 0) {
         const float4 a = __ldcg(G.q0 + j), b = __ldcg(G.q1 + j), cc = __ldcg(G.q2 + j);
         PState st;
-        photon_classical(C, a, b, cc, st, nullptr);
+        photon_classical<0, true>(C, a, b, cc, st, nullptr);
         x = st.x;
         k = st.k;
         P = st.P;
@@ -576,55 +694,55 @@ static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const
         if (fl & QED_F_TAU) minus = u52f(w0.z, w0.w) * st.Wx < st.Wmp;
         else minus = u52f(w0.x, w0.y) < st.Wmp * C.S.dt_f;
         const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
-        const float r3 = u52f(w1.z, w1.w);
-        // the folded coordinate rf = |2u - 1| = (2 dm + 1) 2^-52 from the integer bits of u, and 1 - rf
+        const double r3 = uniform52(w1.z, w1.w);
+        // the folded coordinate rf = |2u - 1| = (2 dm + 1) 2^-52 from the integer bits of u, and 1 - rf,
+        // both exact in FP64
         const uint64_t m = ((uint64_t)(w1.x >> 12) << 32) | (uint64_t)w1.y;
         const uint64_t half = 1ull << 51;
         const bool low = m < half;  // u < 1/2: the positron takes the smaller fraction
         const uint64_t dm = low ? half - 1ull - m : m - half;
-        const uint64_t dmc = (half - 1ull) - dm;
-        const float rf = fmaf((float)(uint32_t)(dm >> 32), 0x1.0p-19f, ((float)(uint32_t)dm + 0.5f) * 0x1.0p-51f);
-        const float rfc = fmaf((float)(uint32_t)(dmc >> 32), 0x1.0p-19f, ((float)(uint32_t)dmc + 0.5f) * 0x1.0p-51f);
-        const float yf = logf(rf) - logf(rfc);
-        const float xv = expf(icdf_lookup(C.T, true, minus ? 1 : 0, logf(st.chi), yf));
-        const float umin = (8.0f / 3.0f) * rcp_(st.chi);
-        const float ut = umin + xv;
+        const double rf = ((double)dm + 0.5) * 0x1.0p-51, rfc = ((double)((half - 1ull) - dm) + 0.5) * 0x1.0p-51;
+        const double chi = (double)st.chi;
+        const double xv = exp(icdf_lookup(X.T, true, minus ? 1 : 0, log(chi), log(rf) - log(rfc)));
+        const double umin = (8.0 / 3.0) / chi;
+        const double ut = umin + xv;
         // mu (1 - mu) = q = 2/(3 chi u~'), so 1 - 4q = x/u~' exactly and mu = (1 - sqrt(x/u~'))/2
         // = u~'_min / (2 u~' (1 + sqrt(x/u~'))), free of cancellation near the centre
-        const float iut = rcp_(ut);
-        const float mu = div_(0.5f * (umin * iut), 1.0f + sqrt_(xv * iut));
-        const float lam = low ? mu : 1.0f - mu;
-        const float one_m = low ? 1.0f - mu : mu;
-        float bb[3];
-        bessel32(C.bes, ut, bb);
-        pp = lam * st.k;
-        pe = one_m * st.k;
+        const double mu = 0.5 * (umin / ut) / (1.0 + sqrt(xv / ut));
+        const double lam = low ? mu : 1.0 - mu;
+        const double one_m = low ? 1.0 - mu : mu;
+        const V3<double> k64 = wide(st.k);
+        pp = narrow(lam * k64);
+        pe = narrow(one_m * k64);
         if (fl & QED_F_SPIN_EVENT) {
-            float w0v;
-            F3 je, jp;
-            nbw_j(lam, one_m, bb, st.xi, st.eps, st.beta, st.khat, w0v, je, jp);
+            double bb[3];
+            bessel64(X.bes, ut, bb);
+            const double xi[3] = {st.xi[0], st.xi[1], st.xi[2]};
+            const V3<double> eps = wide(st.eps), beta = wide(st.beta), kh = wide(st.khat);
+            double w0v;
+            V3<double> je, jp;
+            nbw_j(lam, one_m, bb, xi, eps, beta, kh, w0v, je, jp);
             if (fl & QED_F_SPIN_COLLAPSE) {
-                const float jen = sqrt_(dot(je, je)), jpn = sqrt_(dot(jp, jp));
-                const F3 Se = jen > 0.0f ? rcp_(jen) * je : F3{0, 0, 0};
-                const F3 Sp = jpn > 0.0f ? rcp_(jpn) * jp : F3{0, 0, 0};
+                const double jen = sqrt(dot(je, je)), jpn = sqrt(dot(jp, jp));
+                const V3<double> Se = jen > 0.0 ? (1.0 / jen) * je : V3<double>{0, 0, 0};
+                const V3<double> Sp = jpn > 0.0 ? (1.0 / jpn) * jp : V3<double>{0, 0, 0};
                 // four correlated states, order (--, -+, +-, ++), first sign = positron
-                float cum = 0.0f;
+                double cum = 0.0;
                 int chosen = 3;
-                const float i4w = rcp_(4.0f * w0v);
                 for (int s4 = 0; s4 < 3; ++s4) {
-                    const float sa = (s4 & 2) ? 1.0f : -1.0f, sbb = (s4 & 1) ? 1.0f : -1.0f;
-                    cum += nbw_G(lam, one_m, bb, st.xi, sa * Sp, sbb * Se, st.eps, st.beta, st.khat) * i4w;
+                    const double sa = (s4 & 2) ? 1.0 : -1.0, sbb = (s4 & 1) ? 1.0 : -1.0;
+                    cum += nbw_G(lam, one_m, bb, xi, sa * Sp, sbb * Se, eps, beta, kh) / (4.0 * w0v);
                     if (r3 < cum) {
                         chosen = s4;
                         break;
                     }
                 }
-                const float sa = (chosen & 2) ? 1.0f : -1.0f, sbb = (chosen & 1) ? 1.0f : -1.0f;
-                sp = sa * Sp;
-                se = sbb * Se;
+                const double sa = (chosen & 2) ? 1.0 : -1.0, sbb = (chosen & 1) ? 1.0 : -1.0;
+                sp = narrow(sa * Sp);
+                se = narrow(sbb * Se);
             } else {
-                se = rcp_(w0v) * je;
-                sp = rcp_(w0v) * jp;
+                se = narrow((1.0 / w0v) * je);
+                sp = narrow((1.0 / w0v) * jp);
             }
         }
         const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
@@ -634,18 +752,16 @@ static __device__ __noinline__ void photon_events(const Ctx& C, int64_t j, const
     }
     bool ok = false;
     {
-        const long long s_e = reserve_grouped(have ? El.count : nullptr, want);
-        const bool e_ok = want && have && s_e < El.capacity;
-        const long long s_p = reserve_grouped(have ? Po.count : nullptr, e_ok);
-        ok = e_ok && s_p < Po.capacity;
+        // one reservation for the pair: event ev of the step writes electron base[0] + ev and positron
+        // base[1] + ev if ev < budget (both fit), else neither
+        const long long ev = reserve_event(A, want);
+        ok = want && have && ev < A->budget;
         if (ok) {
+            const int64_t s_e = A->base[0] + ev, s_p = A->base[1] + ev;
             store32(El, s_e, x, pe, se, w, birth_tau32(ide, C.S.seed));
             El.id[s_e] = ide;
             store32(Po, s_p, x, pp, sp, w, birth_tau32(idp, C.S.seed));
             Po.id[s_p] = idp;
-        } else if (e_ok) {  // the positron did not fit: the reserved electron slot holds an inert particle
-            store32(El, s_e, x, F3{0, 0, 0}, F3{0, 0, 0}, 0.0f, INFINITY);
-            El.id[s_e] = ide;
         }
         const long long s_d = reserve_grouped(have ? G.n_dead : nullptr, ok);
         if (ok && s_d < G.capacity) G.dead[s_d] = j;

@@ -22,7 +22,8 @@ __device__ __forceinline__ bool finite3(const V& a) { return isfinite(a.x) && is
 enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_N };
 
 __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const double* __restrict__ bes, FieldP<double> F,
-                                                       StepP S, double q, PartDev L, PartDev G, qed_counters* ctr) {
+                                                       StepP S, double q, PartDev L, PartDev G, AppendState* A,
+                                                       qed_counters* ctr) {
     const int64_t n = min(L.begin ? *L.begin : *L.count, L.capacity);
     const uint32_t fl = S.flags;
     const double dt = S.dt;
@@ -35,6 +36,11 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
         V gx{0, 0, 0}, gk{0, 0, 0}, gP{0, 0, 0};
         double gtau = 0.0, gw = 0.0;
         uint64_t gid = 0;
+        // the lepton's state after the step: with the event applied (st_*), and as the classical part of
+        // the step left it (na_*), which it keeps if its photon finds no room
+        bool st_do = false, st_event = false;
+        V st_x{0, 0, 0}, st_p{0, 0, 0}, st_s{0, 0, 0}, na_p{0, 0, 0}, na_s{0, 0, 0};
+        double st_tau = 0.0, na_tau = 0.0;
         if (j < n) {
             V x{L.x[j], L.y[j], L.z[j]}, p{L.px[j], L.py[j], L.pz[j]}, s{L.sx[j], L.sy[j], L.sz[j]};
             double tau = L.tau[j];
@@ -93,6 +99,10 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                             down = u0a < Wdn * dt;
                         }
                         if (event) {
+                            st_event = true;
+                            na_p = p;
+                            na_s = s;
+                            na_tau = tauf;  // spent (optical depth) or unchanged (probability mode)
                             const uint4 w1 = draw(id, S.seed, S.step, kSlotLambdaSpin);
                             const uint4 w2 = draw(id, S.seed, S.step, kSlotStokes);
                             const double r2 = uniform52(w1.x, w1.y), r3 = uniform52(w1.z, w1.w), r4 = uniform52(w2.x, w2.y);
@@ -132,7 +142,6 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                                 }
                             }
                             if (fl & QED_F_TAU) tauf = -log(u0a);
-                            c[C_EVENTS]++;
                             const uint4 wc = draw(id, S.seed, S.step, kSlotChild);
                             const double kn = sqrt(dot(k, k));
                             if (kn >= S.store_min) {
@@ -162,32 +171,43 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                         }
                     }
                 }
-                L.x[j] = x.x; L.y[j] = x.y; L.z[j] = x.z;
-                L.px[j] = pf.x; L.py[j] = pf.y; L.pz[j] = pf.z;
-                L.sx[j] = sf.x; L.sy[j] = sf.y; L.sz[j] = sf.z;
-                L.tau[j] = tauf;
+                st_do = true;
+                st_x = x;
+                st_p = pf;
+                st_s = sf;
+                st_tau = tauf;
             }
         }
-        if (G.count != nullptr) {
-            const long long slot = reserve_slots(G.count, want, 1);
-            if (want) {
-                if (slot < G.capacity) {
-                    store_particle64(G, slot, gx, gk, gP, gtau, gw, gid);
-                    c[C_STORED]++;
-                } else {
-                    c[C_DROPPED]++;
-                    record_error(ctr, QED_ERR_CAPACITY, j);
-                }
-            }
-        } else if (want) {
+        // the photon's slot: event ev of the call writes base + ev if ev < budget; otherwise the event
+        // is not applied (the lepton keeps its pre-event state and its spent optical depth)
+        const long long ev = reserve_event(A, want);
+        const bool keep = want && A != nullptr && ev < A->budget;
+        const bool refused = want && A != nullptr && !keep;
+        if (keep) {
+            store_particle64(G, A->base[0] + ev, gx, gk, gP, gtau, gw, gid);
+            c[C_STORED]++;
+        }
+        if (refused) {
             c[C_DROPPED]++;
+            record_error(ctr, QED_ERR_CAPACITY, j);
+        } else if (want && A == nullptr) {
+            c[C_DROPPED]++;  // the caller keeps no photons
+        }
+        if (st_event && !refused) c[C_EVENTS]++;
+        if (st_do) {
+            const V op = refused ? na_p : st_p, os = refused ? na_s : st_s;
+            L.x[j] = st_x.x; L.y[j] = st_x.y; L.z[j] = st_x.z;
+            L.px[j] = op.x; L.py[j] = op.y; L.pz[j] = op.z;
+            L.sx[j] = os.x; L.sy[j] = os.y; L.sz[j] = os.z;
+            L.tau[j] = refused ? na_tau : st_tau;
         }
     }
     flush_counters<C_N>(c, &ctr->events);
 }
 
 __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const double* __restrict__ bes, FieldP<double> F,
-                                                       StepP S, PartDev G, PartDev El, PartDev Po, qed_counters* ctr) {
+                                                       StepP S, PartDev G, PartDev El, PartDev Po, AppendState* A,
+                                                       qed_counters* ctr) {
     const int64_t n = min(G.begin ? *G.begin : *G.count, G.capacity);
     const uint32_t fl = S.flags;
     const double dt = S.dt;
@@ -320,18 +340,15 @@ __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const dou
                 }
             }
         }
-        // daughters: electron first, positron only if the electron fitted
+        // daughters: one reservation for the pair (electron base[0] + ev, positron base[1] + ev), both or
+        // neither
         bool ok = false;
         if (have_daughters) {
-            const long long s_e = reserve_slots(El.count, want, 1);
-            const bool e_ok = want && s_e < El.capacity;
-            const long long s_p = reserve_slots(Po.count, e_ok, 1);
-            ok = e_ok && s_p < Po.capacity;
+            const long long ev = reserve_event(A, want);
+            ok = want && ev < A->budget;
             if (ok) {
-                store_particle64(El, s_e, x, pe, se, te, wgt, ide);
-                store_particle64(Po, s_p, x, pp, sp, tp, wgt, idp);
-            } else if (e_ok) {  // the positron did not fit: the reserved electron slot holds an inert particle
-                store_particle64(El, s_e, x, v3(0.0, 0.0, 0.0), v3(0.0, 0.0, 0.0), INFINITY, 0.0, ide);
+                store_particle64(El, A->base[0] + ev, x, pe, se, te, wgt, ide);
+                store_particle64(Po, A->base[1] + ev, x, pp, sp, tp, wgt, idp);
             }
             const long long s_d = reserve_slots(G.n_dead, ok, 1);
             if (ok && s_d < G.capacity) G.dead[s_d] = j;
@@ -369,7 +386,7 @@ void launch_lepton64(const qed_tables_s* t, const qed_field& f, const qed_step_d
     if (G) g = part_dev(G);
     const int blocks = launch_blocks(L->capacity, 256);
     lepton64_kernel<<<blocks, 256, 0, st>>>(tab_params<double>(t), t->bes64, field_params<double>(f), S, (double)L->charge,
-                                            part_dev(L), g, ctr);
+                                            part_dev(L), g, G ? append_state(ctr) : nullptr, ctr);
 }
 
 void launch_photon64(const qed_tables_s* t, const qed_field& f, const qed_step_desc& s, const qed_particles* G,
@@ -383,5 +400,5 @@ void launch_photon64(const qed_tables_s* t, const qed_field& f, const qed_step_d
     }
     const int blocks = launch_blocks(G->capacity, 256);
     photon64_kernel<<<blocks, 256, 0, st>>>(tab_params<double>(t), t->bes64, field_params<double>(f), S, part_dev(G), e, p,
-                                            ctr);
+                                            (El && Po) ? append_state(ctr) : nullptr, ctr);
 }

@@ -1,18 +1,12 @@
-"""Parity of the FP32 path (FP32 push, lookups and sampling; FP64 optical depth and renormalisation)
-with the FP64 oracle on the same inputs (the oracle starts from the float-rounded state read back from
-the device).
+"""Parity of the FP32 path (FP32 push, lookups and sampling; FP64 optical depth and renormalisation;
+the event branch with accurate fields and FP64 where FP32 cancels) with the FP64 oracle on the same
+inputs (the oracle starts from the float-rounded state read back from the device).
 
-Bar per step: 1e-5 relative on momenta, spins, Stokes vectors, positions and optical depths.  Two kinds
-of outputs carry a documented tail above it:
-  * quantities proportional to chi where the field is near a node: chi is small there, and the absolute
-    error of the FP32 carrier (~1e-7 in the reduced phase) becomes a larger relative error; such photons
-    are very soft (the worst measured: lambda = 1.3e-7, error 1.04e-5).  At most 1 % may exceed 1e-5,
-    none 3e-5 (measured: median 5e-7, 0.3 % above 1e-5);
-  * directions that are differences of nearly equal terms (the axis j/|j| of a pair daughter's spin when
-    a coefficient such as 1/(1-lambda) - xi3/lambda almost cancels) amplify the ~1e-7 error of their FP32
-    inputs: at most 1 % above 1e-5, none above 1e-3.
-Decisions taken in FP32 next to their threshold may flip: fewer than 1e-5 per particle-step.  Over many
-steps the per-step error compounds at most linearly: an n-step trajectory is held to n x 1e-5.
+Bar per step: 1e-5 relative on momenta, spins, Stokes vectors, positions and optical depths, with no
+tail: every compared particle is inside it.  Decisions taken in FP32 next to their threshold (the
+optical-depth crossing, a collapse sign) may flip: fewer than 1e-5 per particle-step, shown on a run of
+4e5 particle-steps.  Over many steps the per-step error compounds at most linearly: an n-step
+trajectory is held to n x 1e-5.
 """
 import math
 
@@ -84,15 +78,33 @@ def test_lepton_single_step(gpu_tables, ora_tables, n):
     for q in (-1, 1):
         gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 1, q=q, t0=10.0)
         fl1, w1 = compare_with_flips(gL.read(), oL.view(), 1e-5, "leptons")
-        fl2, w2 = compare_with_flips(gG.read(), oG.view(), 1e-5, "photons", P_headless=True, frac_ok=1e-2, hard=3e-5)
-        assert fl1 + fl2 <= 2, (fl1, fl2)
-        assert c.status == 0 and abs(int(c.events) - oc.events) <= 1
+        fl2, w2 = compare_with_flips(gG.read(), oG.view(), 1e-5, "photons", P_headless=True)
+        assert fl1 + fl2 <= 1e-5 * n, (fl1, fl2)
+        assert c.status == 0 and int(c.events) == oc.events
+
+
+def test_flip_rate_per_particle_step(gpu_tables, ora_tables):
+    """1e5 leptons of both charges through two steps of a linear laser (4e5 particle-steps, about 8 %
+    of them events): every matched particle within the bar, and fewer than 1e-5 decision flips per
+    particle-step."""
+    n, steps = 100000, 2
+    b = I.random_states(n, seed=77, gamma_range=(300.0, 6000.0), field_region=(-40.0, 10.0))
+    f = Q.field(B.QED_FIELD_LP, a0=150.0, n_cycles=5.0, eta0=ETA0)
+    flips, events = 0, 0
+    for q in (-1, 1):
+        gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, steps, q=q, t0=10.0, dt=0.15)
+        f1, _ = compare_with_flips(gL.read(), oL.view(), 1e-5 * steps, "leptons")
+        f2, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
+        flips += f1 + f2
+        events += oc.events
+    psteps = 2 * n * steps
+    assert events > 0.02 * psteps
+    assert flips <= 1e-5 * psteps, (flips, psteps, flips / psteps)
 
 
 def test_emitted_spectrum_error(gpu_tables, ora_tables):
-    """Emitted photon energies matched by id: 99 % within 1e-5 of the oracle's, none beyond 3e-5; the
-    spectrum (counts on 64 log-spaced bins per decade) identical except for photons within 3e-5 of an
-    edge."""
+    """Emitted photon energies matched by id: every one within 1e-5 of the oracle's; the spectrum (counts
+    on 64 log-spaced bins per decade) identical except for photons within 1e-5 of an edge."""
     b = I.random_states(6000, seed=3, gamma_range=(300.0, 6000.0), field_region=(-35.0, 5.0))
     f = Q.field(B.QED_FIELD_CP, a0=100.0, n_cycles=4.0, eta0=ETA0)
     gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 3)
@@ -102,11 +114,11 @@ def test_emitted_spectrum_error(gpu_tables, ora_tables):
     eg = np.linalg.norm(g["mom"][gi], axis=1)
     eo = np.linalg.norm(o["mom"][oi], axis=1)
     err = np.abs(eg / eo - 1)
-    assert np.quantile(err, 0.99) <= 1e-5 and err.max() <= 3e-5, (np.quantile(err, 0.99), err.max())
+    assert err.max() <= 1e-5, (np.quantile(err, 0.99), err.max())
     edges = 10 ** (np.arange(-8, 4 + 1e-9, 1 / 64))
     hg, _ = np.histogram(eg, edges)
     ho, _ = np.histogram(eo, edges)
-    near = np.min(np.abs(np.log(eo[:, None] / edges[None, :])), axis=1) < 3e-5
+    near = np.min(np.abs(np.log(eo[:, None] / edges[None, :])), axis=1) < 1e-5
     assert np.abs(hg - ho).sum() <= 2 * near.sum()
 
 
@@ -143,10 +155,11 @@ def test_headon_lp_trajectory(gpu_tables, ora_tables):
 def test_lepton_modes(gpu_tables, ora_tables, flags):
     b = I.random_states(1500, seed=flags % 997, gamma_range=(100.0, 4000.0), field_region=(-30.0, 5.0))
     f = Q.field(B.QED_FIELD_LP, a0=100.0, n_cycles=4.0, eta0=ETA0)
-    gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, 4, flags=flags, dt=0.15)
-    fl1, _ = compare_with_flips(gL.read(), oL.view(), 2e-5, "leptons")
-    fl2, _ = compare_with_flips(gG.read(), oG.view(), 2e-5, "photons", P_headless=True, frac_ok=1e-2, hard=6e-5)
-    assert fl1 + fl2 <= 2
+    steps = 4
+    gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, steps, flags=flags, dt=0.15)
+    fl1, _ = compare_with_flips(gL.read(), oL.view(), 1e-5 * steps, "leptons")
+    fl2, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
+    assert fl1 + fl2 <= max(1, 1e-5 * 1500 * steps)
 
 
 def _photon_inputs(n, seed, energy=3000.0):
@@ -179,11 +192,12 @@ def test_photon_pairs_and_compaction(gpu_tables, ora_tables):
         O.photon_step(ora_tables, of, as_oracle_step(st), oG, oE, oP, octr)
     torch.cuda.synchronize()
     assert octr.events > 200 and ctr.read().status == 0
-    # photons are held to the n-step bar; daughters are made in one event and keep their birth state
+    # photons are held to the n-step bar, and so are their daughters: a pair made at step k inherits its
+    # photon's k-step state (pairs made from the same state in one step: test_gpu_overflow, at 1e-5)
     f1, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons")
-    f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5, "electrons", frac_ok=1e-2, hard=1e-3)
-    f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5, "positrons", frac_ok=1e-2, hard=1e-3)
-    assert f1 + f2 + f3 <= max(3, 1e-5 * 4000 * steps * 3), (f1, f2, f3)
+    f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5 * steps, "electrons")
+    f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5 * steps, "positrons")
+    assert f1 + f2 + f3 <= max(1, 1e-5 * 4000 * steps), (f1, f2, f3)
 
 
 def test_constant_field_general_forms(gpu_tables, ora_tables):
@@ -196,9 +210,8 @@ def test_constant_field_general_forms(gpu_tables, ora_tables):
         gL, gG, oL, oG, c, oc = _run_lepton(gpu_tables, ora_tables, b, f, steps, q=q, t0=0.0)
         assert oc.events > 20 and c.status == 0
         fl1, _ = compare_with_flips(gL.read(), oL.view(), 1e-5 * steps, "leptons")
-        fl2, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True, frac_ok=1e-2,
-                                    hard=3e-5 * steps)
-        assert fl1 + fl2 <= 2, (fl1, fl2)
+        fl2, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
+        assert fl1 + fl2 <= 1, (fl1, fl2)
     pb = _photon_inputs(3000, seed=43, energy=20000.0)
     gG, oG = _pair(pb, B.QED_PHOTON, seed=5, photons=True)
     gE, gP = Q.ParticleBuffer(6000, FP32, B.QED_ELECTRON), Q.ParticleBuffer(6000, FP32, B.QED_POSITRON)
@@ -216,9 +229,9 @@ def test_constant_field_general_forms(gpu_tables, ora_tables):
     # P is headless: its transverse part is fixed only up to sign (the representative with P.eps >= 0),
     # and a photon whose P is nearly perpendicular to eps may land on either side in FP32 and FP64
     f1, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
-    f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5, "electrons", frac_ok=1e-2, hard=1e-3)
-    f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5, "positrons", frac_ok=1e-2, hard=1e-3)
-    assert f1 + f2 + f3 <= 3, (f1, f2, f3)
+    f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5 * steps, "electrons")
+    f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5 * steps, "positrons")
+    assert f1 + f2 + f3 <= 1, (f1, f2, f3)
 
 
 def test_coupled_species(gpu_tables, ora_tables):
