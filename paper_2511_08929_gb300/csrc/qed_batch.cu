@@ -32,6 +32,7 @@ constexpr int kSpecies = 3;  // electrons, positrons, photons
 
 struct InstDev {
     FieldP<float> F;
+    FieldP<double> F64;  // the same laser in FP64 (events taken again in FP64)
     double phase;
     uint64_t seed;
     PartDev sp[kSpecies];
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
         const bool ph = X.sp == 2;
         // both passes are warp-collective; a lane takes part in the one of its species with its particle
         if (__ballot_sync(0xffffffffu, j >= 0 && !ph))
-            lepton_events(X.C, X64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c);
+            lepton_events(X.C, X64, I.F64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c);
         if (__ballot_sync(0xffffffffu, j >= 0 && ph))
             photon_events(X.C, X64, ph ? j : -1, I.sp[2], I.sp[0], I.sp[1], &I.app[1], ctr, c);
     }
@@ -747,6 +748,7 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
         const qed_instance& in = instances[i];
         InstDev& d = h[i];
         d.F = field_params<float>(in.field);
+        d.F64 = field_params<double>(in.field);
         d.phase = in.field.phase;
         d.seed = in.seed;
         d.sp[0] = part_dev(&in.electrons);

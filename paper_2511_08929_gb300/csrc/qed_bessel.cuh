@@ -147,8 +147,9 @@ struct TabP {
     const R* nbw_rate;  // [2][n_chi]
     const R* nlc_icdf;  // [2][n_chi][n_r]
     const R* nbw_icdf;  // [2][n_chi][n_r]
+    const R* nlc_icdf_lo;  // FP32 only: nlc_icdf's rounding remainders (entry = nlc_icdf + nlc_icdf_lo)
     R lnchi_min, inv_dlnchi, chi_min, chi_max;
-    R y_lo, inv_dy;
+    R y_lo, inv_dy, inv_dy_lo;  // inv_dy + inv_dy_lo: (n_r - 1)/(y_hi - y_lo) to twice the precision of R
     int n_chi, n_r;
 };
 
@@ -223,6 +224,120 @@ __device__ __forceinline__ R icdf_lookup(const TabP<R>& T, bool nbw, int s, R ln
     const R v0 = icdf_row(base + (size_t)i * T.n_r, T, slope, y);
     const R v1 = icdf_row(base + (size_t)(i + 1) * T.n_r, T, slope, y);
     return v0 + f * (v1 - v0);
+}
+
+// --------------------------------------------------------------------------------------------
+// the NLC energy fraction of an event to FP32 relative precision (the FP32 path's event pass)
+// --------------------------------------------------------------------------------------------
+// ln u' of a soft photon is ~ -40; in plain FP32 its rounding (4e-6) would be the relative error of
+// the photon's energy.  Here every large quantity is carried as an unevaluated sum of two floats
+// (hi exact or exactly rounded, lo the small rest) and only small corrections are rounded: the logit
+// y of the uniform from its 52 integer bits, the cell coordinate, the ICDF entries (hi + lo tables),
+// and u' = exp(hi) exp(correction).  Relative error of u' ~3e-7.
+
+// a + b = s + e exactly (TwoSum)
+__device__ __forceinline__ float two_sum_f(float a, float b, float& e) {
+    const float s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+    return s;
+}
+
+// ln of u = (m + 1/2) 2^-52 (m = (h20 << 32) | lo, 52 bits) as hi + lo: u = A + B + C exactly with
+// A = h20 2^-20, B = (lo & ~0xFF) 2^-52, C = ((lo & 0xFF) + 1/2) 2^-52; s + e = u (TwoSum), s = 2^E M
+// with M in [1, 2); ln u = E ln2_hi (exact: ln2_hi has 17 significant bits) + (E ln2_lo + ln M + e/s).
+// Also returns u rounded to float.
+__device__ __forceinline__ float ln_u52(uint32_t h20, uint32_t lo, float& ln_lo, float& u_f) {
+    const float A = (float)h20 * 0x1.0p-20f;
+    const float Bv = (float)(lo & 0xFFFFFF00u) * 0x1.0p-52f;
+    const float Cv = ((float)(lo & 0xFFu) + 0.5f) * 0x1.0p-52f;
+    float e1, e2;
+    float s = two_sum_f(A, Bv, e1);
+    s = two_sum_f(s, Cv, e2);
+    const float e = e1 + e2;
+    u_f = s;
+    const uint32_t bits = __float_as_uint(s);
+    const int E = (int)((bits >> 23) & 0xFFu) - 127;
+    const float M = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);
+    const float fE = (float)E;
+    ln_lo = fmaf(fE, 1.42860677e-6f, logf(M) + e / s);  // ln 2 = 0.693145752 + 1.42860677e-6
+    return fE * 0.693145752f;
+}
+
+// y = ln u - ln(1 - u) of the uniform as hi + lo, normalised (|lo| <= ulp(hi)/2); the complementary
+// integer for u >= 1/2
+__device__ __forceinline__ float logit_u52(uint32_t hi, uint32_t lo, float& y_lo) {
+    const uint32_t h20 = hi >> 12;
+    const bool upper = h20 >= 0x80000u;  // u >= 1/2: y = -(ln v - ln(1 - v)), v = 1 - u
+    float l_lo, uf;
+    const float l_hi = upper ? ln_u52(0xFFFFFu - h20, ~lo, l_lo, uf) : ln_u52(h20, lo, l_lo, uf);
+    float e;
+    const float y = two_sum_f(l_hi, l_lo - log1pf(-uf), e);
+    y_lo = upper ? -e : e;
+    return upper ? -y : y;
+}
+
+// one ICDF row at the cell (m, x) as hi + correction: the cubic through nodes m-1..m+2 (Newton form
+// about node m) on hi + lo entries; hi is row[m]'s hi part, the correction carries the rest
+__device__ __forceinline__ float icdf_row_ff(const float* __restrict__ rh, const float* __restrict__ rl, int m, float x,
+                                             float& corr) {
+    const float ah = rh[m - 1], bh = rh[m], ch = rh[m + 1], dh = rh[m + 2];
+    const float al = rl[m - 1], bl = rl[m], cl = rl[m + 1], dl = rl[m + 2];
+    const float d1 = (ch - bh) + (cl - bl);
+    const float d2 = 0.5f * (((ah - bh) + (ch - bh)) + ((al - bl) + (cl - bl)));
+    const float d3 = (((dh - ah) + 3.0f * (bh - ch)) + ((dl - al) + 3.0f * (bl - cl))) * (1.0f / 6.0f);
+    corr = bl + x * (d1 + (x - 1.0f) * (d2 + (x + 1.0f) * d3));
+    return bh;
+}
+
+// u' of the NLC ICDF of branch s at lnchi for the uniform of the 52 bits (hi, lo): returns false (and
+// nothing) when u' leaves the normal float range, where the caller takes the FP64 lookup
+__device__ __forceinline__ bool nlc_up_ff(const TabP<float>& T, int s, float lnchi, uint32_t whi, uint32_t wlo, float& up) {
+    float ylo;
+    const float yhi = logit_u52(whi, wlo, ylo);
+    // cell coordinate tt = (y - y_lo) inv_dy as hi + lo
+    float de;
+    const float dh = two_sum_f(yhi, -T.y_lo, de);
+    const float dl = de + ylo;
+    const float tp = dh * T.inv_dy;
+    float te;
+    const float th = two_sum_f(tp, fmaf(dh, T.inv_dy, -tp) + fmaf(dl, T.inv_dy, dh * T.inv_dy_lo), te);
+    const float tl = te;  // th + tl, normalised: the cell index comes from th
+    int i;
+    float f;
+    chi_coord(T, lnchi, i, f);
+    const size_t off = (size_t)s * T.n_chi * T.n_r;
+    const float* h0 = T.nlc_icdf + off + (size_t)i * T.n_r;
+    const float* l0 = T.nlc_icdf_lo + off + (size_t)i * T.n_r;
+    const float* h1 = h0 + T.n_r;
+    const float* l1 = l0 + T.n_r;
+    float base, c0, c1;
+    if (!(th + tl > 0.0f)) {  // below the grid: u' ~ r^3, ln u' = row[0] + 3 (y - y_lo)
+        const float s3 = 3.0f * dh;
+        const float s3e = fmaf(3.0f, dh, -s3);
+        float be;
+        base = two_sum_f(h0[0], s3, be);
+        c0 = be + l0[0] + s3e + 3.0f * dl;
+        c1 = (h1[0] - h0[0]) + (l1[0] - l0[0]);
+    } else if (th + tl >= (float)(T.n_r - 1)) {  // above the grid: the last entry
+        base = h0[T.n_r - 1];
+        c0 = l0[T.n_r - 1];
+        c1 = (h1[T.n_r - 1] - h0[T.n_r - 1]) + (l1[T.n_r - 1] - l0[T.n_r - 1]);
+    } else {
+        int m = (int)th;
+        if (m < 1) m = 1;
+        if (m > T.n_r - 3) m = T.n_r - 3;
+        const float x = (th - (float)m) + tl;
+        float k0, k1;
+        base = icdf_row_ff(h0, l0, m, x, k0);
+        const float b1 = icdf_row_ff(h1, l1, m, x, k1);
+        c0 = k0;
+        c1 = (b1 - base) + (k1 - k0);
+    }
+    const float corr = fmaf(f, c1, c0);
+    if (!(base + corr > -80.0f && base + corr < 80.0f)) return false;
+    up = expf(base) * expf(corr);
+    return true;
 }
 
 }  // namespace qed

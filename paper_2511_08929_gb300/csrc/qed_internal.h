@@ -19,6 +19,7 @@ struct qed_tables_s {
     double* icdf64;  // [4][n_chi][n_r]
     float* rate32;
     float* icdf32;
+    float* icdf32lo;  // icdf64 - icdf32 rounded to float: the two floats hold an ICDF entry to ~1e-14
     double* bes64;  // [3][kBesN] scaled Bessel values
     float* bes32;
 };
@@ -43,6 +44,8 @@ inline qed::TabP<R> tab_params(const qed_tables_s* t) {
     p.nbw_rate = rate + 2 * nc;
     p.nlc_icdf = icdf;
     p.nbw_icdf = icdf + 2 * nc * d.n_r;
+    p.nlc_icdf_lo = nullptr;
+    if constexpr (sizeof(R) == 4) p.nlc_icdf_lo = reinterpret_cast<const R*>(t->icdf32lo);
     const double dl = (std::log(d.chi_max) - std::log(d.chi_min)) / (d.n_chi - 1);
     p.lnchi_min = (R)std::log(d.chi_min);
     p.inv_dlnchi = (R)(1.0 / dl);
@@ -50,6 +53,7 @@ inline qed::TabP<R> tab_params(const qed_tables_s* t) {
     p.chi_max = (R)d.chi_max;
     p.y_lo = (R)d.y_lo;
     p.inv_dy = (R)((d.n_r - 1) / (d.y_hi - d.y_lo));
+    p.inv_dy_lo = (R)((d.n_r - 1) / (d.y_hi - d.y_lo) - (double)p.inv_dy);
     p.n_chi = d.n_chi;
     p.n_r = d.n_r;
     return p;

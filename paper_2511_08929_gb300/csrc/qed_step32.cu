@@ -32,7 +32,8 @@ template <bool PHOTON>
 __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float> T, const float* __restrict__ bes_g,
                                                                       FieldP<float> F, StepP S, float q, PartDev P,
                                                                       PartDev D1, PartDev D2, AppendState* A,
-                                                                      Tab64 X, qed_counters* ctr) {
+                                                                      Tab64 X, FieldP<double> F64p, qed_counters* ctr) {
+    const FieldP<double> F64 = F64p;  // the laser in FP64, for the events taken again in FP64
     extern __shared__ __align__(128) unsigned char smem[];
     const Shared32 sh = carve32(smem, T.n_chi);
     load_tables32(sh, bes_g, T);
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
         if (qn >= 32) {
             const int64_t je = wq[qn - 32 + lane];
             if (PHOTON) photon_events(C, X, je, P, D1, D2, A, ctr, c);
-            else lepton_events(C, X, je, P, D1, A, ctr, c);
+            else lepton_events(C, X, F64, je, P, D1, A, ctr, c);
             qn -= 32;
             __syncwarp();
         }
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
     if (qn > 0) {
         const int64_t je = lane < qn ? wq[lane] : -1;
         if (PHOTON) photon_events(C, X, je, P, D1, D2, A, ctr, c);
-        else lepton_events(C, X, je, P, D1, A, ctr, c);
+        else lepton_events(C, X, F64, je, P, D1, A, ctr, c);
     }
     flush_warp(c, ctr);
 }
@@ -156,7 +157,7 @@ void launch_lepton32(const qed_tables_s* t, const qed_field& f, const qed_step_d
     const void* k = (const void*)step32_kernel<false>;
     step32_kernel<false><<<blocks32(L->capacity, k, smem), kT32, smem, st>>>(
         tab_params<float>(t), t->bes32, field_params<float>(f), step_params(s, f), (float)L->charge, part_dev(L), g,
-        PartDev{}, G ? append_state(ctr) : nullptr, Tab64{tab_params<double>(t), t->bes64}, ctr);
+        PartDev{}, G ? append_state(ctr) : nullptr, Tab64{tab_params<double>(t), t->bes64}, field_params<double>(f), ctr);
 }
 
 void launch_photon32(const qed_tables_s* t, const qed_field& f, const qed_step_desc& s, const qed_particles* G,
@@ -171,5 +172,5 @@ void launch_photon32(const qed_tables_s* t, const qed_field& f, const qed_step_d
     const void* k = (const void*)step32_kernel<true>;
     step32_kernel<true><<<blocks32(G->capacity, k, smem), kT32, smem, st>>>(
         tab_params<float>(t), t->bes32, field_params<float>(f), step_params(s, f), 0.0f, part_dev(G), e, p,
-        (El && Po) ? append_state(ctr) : nullptr, Tab64{tab_params<double>(t), t->bes64}, ctr);
+        (El && Po) ? append_state(ctr) : nullptr, Tab64{tab_params<double>(t), t->bes64}, field_params<double>(f), ctr);
 }

@@ -385,13 +385,13 @@ __device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x
 // ------------------------------------------------------------------------------------------------
 // precision of the event passes
 // ------------------------------------------------------------------------------------------------
-// Events are a few per cent of the particle-steps and the FP64 pipe is idle there, so the quantities of an
-// event that FP32 cannot hold to 1e-5 relative are taken in FP64: the energy fraction (the ICDF rows and
-// the fraction from them: ln u' of a soft photon is ~ -40, whose FP32 rounding is ~4e-6 of u'), every
-// quantity of a pair (the j_e, j_p coefficients 1/(1 - lambda) - xi3/lambda and the like cancel), and the
-// photon's Stokes vector and the lepton's spin axis wherever the FP32 forms cancel (|F| or |g| small
-// against their terms).  Fields at events come from the accurate sine and cosine, so chi keeps its
-// relative precision next to a node of the carrier.
+// An event's outputs are held to FP32 relative precision without the narrow FP64 pipe of this GPU
+// wherever that can be done: fields from the accurate sine and cosine (chi keeps its relative precision
+// next to a node of the carrier) and the photon's energy fraction from the float-float ICDF lookup
+// (ln u' of a soft photon is ~ -40, whose plain FP32 rounding would be ~4e-6 of u').  FP64 is kept for
+// the rare parts that need it: every quantity of a pair (pairs are ~2 % of events; their spin
+// coefficients 1/(1 - lambda) - xi3/lambda and the like cancel), and the photon's Stokes vector and the
+// lepton's spin axis of the events whose FP32 forms cancel (|F| or |g| small against their terms).
 struct Tab64 {
     TabP<double> T;     // FP64 rate and ICDF tables
     const double* bes;  // FP64 scaled Bessel table [3][kBesN]
@@ -400,10 +400,11 @@ struct Tab64 {
 __device__ __forceinline__ V3<double> wide(const F3& v) { return V3<double>{v.x, v.y, v.z}; }
 __device__ __forceinline__ F3 narrow(const V3<double>& v) { return F3{(float)v.x, (float)v.y, (float)v.z}; }
 
-// The FP32 forms of g and F are recomputed in FP64 when |g| or |F| is below this fraction of the sum of
-// the absolute values of its terms (the FP32 rounding of the terms, ~1e-7 of that sum, would then move
-// the direction by more than ~1e-6)
-constexpr float kCancel = 0.2f;
+// An event is taken again in FP64 when |g| or |F| is below this fraction of the sum of the absolute
+// values of its terms.  The sum bounds the terms' FP32 rounding from above by a wide margin: measured, the
+// direction error of F is ~1e-8 of the sum over |F|, so at this threshold it stays near 1e-6, and only a
+// few events in 1e4 (chiefly spin flips against a polarized spin, where F0 = w - |g|) take the FP64 path.
+constexpr float kCancel = 0.01f;
 
 // sum over F1, F2, F3 of the absolute values of their terms (App. A.1 Eqs. F1-F3; the Bessel values are
 // positive)
@@ -425,62 +426,92 @@ __device__ __forceinline__ float nlc_stokes_scale(float lam, float one_m, const 
     return A1 + A2 + A3;
 }
 
-// The spin axis and the photon's Stokes vector of an NLC event in FP64 (App. A.1): SQA collapse with r3
-// (or the mean), then F with the final spin and PQA collapse with r4 (or the mean).  With do_spin false
-// the final spin sf is kept as given.
-static __device__ __noinline__ void nlc_spectra64(const Tab64& X, double lam, double one_m, double up, const F3& si,
-                                                 const F3& eps, const F3& beta, const F3& khat, uint32_t fl, bool do_spin,
-                                                 float r3, float r4, F3& sf, float xi[3]) {
+// An NLC event taken again in FP64 from the lepton's stored FP32 state (a, b, cc): fields, Boris push,
+// T-BMT precession, move, chi and basis, the energy fraction from the FP64 ICDF with the same uniform,
+// recoil, the SQA collapse of the spin with r3 and the PQA collapse of the photon's Stokes vector with
+// r4 (App. A.1), every flag as the FP64 path reads it.  The FP32 pass calls it for the events whose
+// spin axis or photon polarization is ill-conditioned (g or F far below its terms, as after a spin flip
+// against a polarized spin: F0 = w - |g|): there the FP32 rounding of the classical step alone, 1e-7 of
+// the spin and basis, would move the photon's Stokes vector by up to cond x 1e-7.  The branch (down) is
+// the FP32 pass's decision.  Outputs: the lepton's x, p, s and the photon's k and P, rounded to float.
+static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X, const FieldP<double>& F64,
+                                                  const float4& a, const float4& b, const float4& cc, bool down,
+                                                  const uint4& w1, const uint4& w2, F3& x_out, F3& p_out, F3& s_out,
+                                                  F3& k_out, F3& P_out) {
+    using V = V3<double>;
+    const uint32_t fl = C.S.flags;
+    const double dt = C.S.dt, q = (double)C.q;
+    V x{a.x, a.y, a.z}, p{a.w, b.x, b.y}, s{b.z, b.w, cc.x};
+    V E, B;
+    field_eval(F64, C.S.ph_hi, 0.0, x, E, B);
+    const V pold = p;
+    if (fl & QED_F_PUSH) p = boris(p, E, B, q, dt);
+    if (fl & QED_F_TBMT) s = rotate(s, tbmt_omega(0.5 * (pold + p), E, B, q, (fl & QED_F_TBMT_PAPER) != 0), dt);
+    const double gam = sqrt(1.0 + dot(p, p));
+    if (fl & QED_F_MOVE) x = x + v3(p.x / gam * dt, p.y / gam * dt, p.z / gam * dt);
+    const double chi = chi_of(F64.eta0, gam, p, E, B);
+    const double pn = sqrt(dot(p, p));
+    const V khat = v3(p.x / pn, p.y / pn, p.z / pn);
+    V eps{0, 0, 0}, beta{0, 0, 0};
+    make_basis(E, B, v3(p.x / gam, p.y / gam, p.z / gam), khat, -q, eps, beta);
+    const double r2 = uniform52(w1.x, w1.y), r3 = uniform52(w1.z, w1.w), r4 = uniform52(w2.x, w2.y);
+    const double up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
+    const double lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up);
+    const double one_m = 1.0 - lam;
+    const V k = lam * p;
+    V pf = p, sf = s, sfu{0, 0, 0}, si{0, 0, 0};
+    if (fl & QED_F_RECOIL) pf = one_m * p;
+    if (fl & QED_F_RESOLVED) si = s;
     double bb[3];
     bessel64(X.bes, up, bb);
-    const V3<double> s_i = wide(si), e = wide(eps), b = wide(beta), k = wide(khat);
-    double w;
-    V3<double> g;
-    nlc_wg(lam, one_m, bb, s_i, b, k, w, g);
-    V3<double> s_f = wide(sf);
-    if (do_spin && (fl & QED_F_SPIN_EVENT)) {
+    double xi[3] = {0.0, 0.0, 0.0};
+    double wv = 0.0;
+    V g{0, 0, 0};
+    if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, bb, si, beta, khat, wv, g);
+    if (fl & QED_F_SPIN_EVENT) {
         const double gn = sqrt(dot(g, g));
         if (fl & QED_F_SPIN_COLLAPSE) {
-            const double sg = (double)r3 < (w - gn) / (2.0 * w) ? -1.0 : 1.0;
-            s_f = gn > 0.0 ? (sg / gn) * g : V3<double>{0, 0, 0};
+            const double sg = r3 < (wv - gn) / (2.0 * wv) ? -1.0 : 1.0;
+            sf = gn > 0.0 ? v3(sg * g.x / gn, sg * g.y / gn, sg * g.z / gn) : v3(0.0, 0.0, 0.0);
         } else {
-            s_f = (1.0 / w) * g;
+            sf = v3(g.x / wv, g.y / wv, g.z / wv);
         }
-        sf = narrow(s_f);
+        sfu = sf;
     }
     if (fl & QED_F_POL_EVENT) {
-        const V3<double> sfu = (fl & QED_F_SPIN_EVENT) ? s_f : V3<double>{0, 0, 0};
         double Fv[4];
-        nlc_stokes(lam, one_m, bb, s_i, sfu, w, g, e, b, k, Fv);
+        nlc_stokes(lam, one_m, bb, si, sfu, wv, g, eps, beta, khat, Fv);
         const double Fn = sqrt(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
-        double iF;
         if (fl & QED_F_POL_COLLAPSE) {
-            const double sg = (double)r4 < (Fv[0] - Fn) / (2.0 * Fv[0]) ? -1.0 : 1.0;
-            iF = Fn > 0.0 ? sg / Fn : 0.0;
+            const double sg = r4 < (Fv[0] - Fn) / (2.0 * Fv[0]) ? -1.0 : 1.0;
+            for (int i = 0; i < 3; ++i) xi[i] = Fn > 0.0 ? sg * Fv[i + 1] / Fn : 0.0;
         } else {
-            iF = 1.0 / Fv[0];
+            for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] / Fv[0];
         }
-        for (int i = 0; i < 3; ++i) xi[i] = (float)(Fv[i + 1] * iF);
-    } else {
-        xi[0] = xi[1] = xi[2] = 0.0f;
     }
+    x_out = narrow(x);
+    p_out = narrow(pf);
+    s_out = narrow(sf);
+    k_out = narrow(k);
+    P_out = narrow(stokes_to_P(xi, eps, beta, khat));
 }
 
 // the event pass of one warp (all 32 lanes call it): a lane with j >= 0 takes particle j of buffer L,
 // whose step context is C and whose photons go to G through the reservation A (lanes may differ in all
 // three; A is NULL when the caller keeps no photons)
-static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, int64_t j, const PartDev& L,
-                                                 const PartDev& G, AppendState* A, qed_counters* ctr,
-                                                 unsigned long long* c) {
+static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, const FieldP<double>& F64, int64_t j,
+                                                 const PartDev& L, const PartDev& G, AppendState* A,
+                                                 qed_counters* ctr, unsigned long long* c) {
     // The lepton's outcome (energy fraction, recoil, spin) and the photon's polarization for every event,
     // then the photon's slot reservation: an event whose photon does not fit is not applied.
     const uint32_t fl = C.S.flags;
     bool want = false;
     LState st;
     uint64_t id = 0;
-    F3 k{0, 0, 0}, pf{0, 0, 0}, sf{0, 0, 0};
+    F3 k{0, 0, 0}, pf{0, 0, 0}, sf{0, 0, 0}, P{0, 0, 0};
     float xi[3] = {0.0f, 0.0f, 0.0f};
     double tau_kept = 0.0, tau_new = 0.0;
+    bool exact = false;  // the event was taken in FP64 (k, P and the lepton's x, p, s from lepton_event64)
     if (j >= 0) {
         const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
         lepton_classical<0, true>(C, a, b, cc, st, nullptr);  // the streaming pass's step, accurate fields
@@ -498,15 +529,26 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
         const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
         const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
         const float r3 = u52f(w1.z, w1.w), r4 = u52f(w2.x, w2.y);
-        // the energy fraction in FP64: the uniform's 52 bits, the FP64 ICDF rows, lambda and 1 - lambda
-        const double r2 = uniform52(w1.x, w1.y);
-        const double chi = (double)st.chi;
-        const double up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
-        const double den = 2.0 + 3.0 * chi * up;
-        const double lam64 = 3.0 * chi * up / den, om64 = 2.0 / den;
-        k = narrow(lam64 * wide(st.p));
-        if (fl & QED_F_RECOIL) pf = narrow(om64 * wide(st.p));
+        // the energy fraction to FP32 relative precision (float-float ICDF lookup); FP64 where u' leaves
+        // the float range (uniforms within ~1e-10 of 0 or 1)
+        float up32;
+        double up, lam64, om64;
+        if (nlc_up_ff(C.T, down ? 1 : 0, logf(st.chi), w1.x, w1.y, up32)) {
+            const float den = fmaf(3.0f * st.chi, up32, 2.0f);
+            const float iden = rcp_(den);
+            lam64 = (double)(3.0f * st.chi * up32 * iden);
+            om64 = (double)(2.0f * iden);
+            up = (double)up32;
+        } else {
+            const double r2 = uniform52(w1.x, w1.y), chi = (double)st.chi;
+            up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
+            const double den = 2.0 + 3.0 * chi * up;
+            lam64 = 3.0 * chi * up / den;
+            om64 = 2.0 / den;
+        }
         const float lam = (float)lam64, one_m = (float)om64;
+        k = lam * st.p;
+        if (fl & QED_F_RECOIL) pf = one_m * st.p;
         const F3 si = (fl & QED_F_RESOLVED) ? st.s : F3{0, 0, 0};
         if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) {
             float bb[3], wv;
@@ -519,7 +561,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
                              lam * u * (bb[1] + bb[2]) * fabsf(dot(si, st.khat));
             const float gn = sqrt_(dot(g, g));
             if (!(gn >= kCancel * gs) || !(wv > 0.0f) || !(up >= 1e-30)) {
-                nlc_spectra64(X, lam64, om64, up, si, st.eps, st.beta, st.khat, fl, true, r3, r4, sf, xi);
+                exact = true;
             } else {
                 F3 sfu{0, 0, 0};
                 if (fl & QED_F_SPIN_EVENT) {
@@ -537,10 +579,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
                     const float Fn = sqrt_(Fv[1] * Fv[1] + Fv[2] * Fv[2] + Fv[3] * Fv[3]);
                     const float Fs = nlc_stokes_scale(lam, one_m, bb, si, sfu, st.eps, st.beta, st.khat);
                     if (!(Fn >= kCancel * Fs)) {
-                        // the terms of F cancel (F0 = w - |g| after a spin flip is the usual case): F is
-                        // linear in s_f with coefficients far above |F|, so the final spin is taken again in
-                        // FP64 together with F
-                        nlc_spectra64(X, lam64, om64, up, si, st.eps, st.beta, st.khat, fl, true, r3, r4, sf, xi);
+                        exact = true;  // the terms of F cancel (F0 = w - |g| after a spin flip, typically)
                     } else if (fl & QED_F_POL_COLLAPSE) {
                         const float sg = r4 < div_(Fv[0] - Fn, 2.0f * Fv[0]) ? -1.0f : 1.0f;
                         const float iF = div_(sg, Fn);
@@ -552,6 +591,8 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
                 }
             }
         }
+        if (exact) lepton_event64(C, X, F64, a, b, cc, down, w1, w2, st.x, pf, sf, k, P);
+        else P = stokes_to_P(xi, st.eps, st.beta, st.khat);
         if (fl & QED_F_TAU) tau_new = exp_draw(w0.x, w0.y);
         want = sqrt_(dot(k, k)) >= C.S.store_min_f;
         if (!want) c[C_BELOW]++;
@@ -573,7 +614,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
         const int64_t slot = A->base[0] + ev;
         const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
         const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
-        store32(G, slot, st.x, k, stokes_to_P(xi, st.eps, st.beta, st.khat), st.w, birth_tau32(gid, C.S.seed));
+        store32(G, slot, st.x, k, P, st.w, birth_tau32(gid, C.S.seed));
         G.id[slot] = gid;
         c[C_STORED]++;
     }

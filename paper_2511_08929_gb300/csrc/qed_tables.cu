@@ -151,6 +151,15 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* b, size_t n
         b[i] = (float)a[i];
 }
 
+// a as the unevaluated float sum hi + lo (hi = a rounded to float, lo = the rest rounded to float)
+__global__ void split_float_kernel(const double* __restrict__ a, float* hi, float* lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float h = (float)a[i];
+        hi[i] = h;
+        lo[i] = (float)(a[i] - (double)h);
+    }
+}
+
 }  // namespace qed
 
 using namespace qed;
@@ -161,6 +170,7 @@ static void free_tables(qed_tables_s* t) {
     cudaFree(t->icdf64);
     cudaFree(t->rate32);
     cudaFree(t->icdf32);
+    cudaFree(t->icdf32lo);
     cudaFree(t->bes64);
     cudaFree(t->bes32);
     t->magic = 0;
@@ -185,6 +195,7 @@ extern "C" qed_status qed_tables_build(const qed_table_desc* desc, qed_tables_t*
               cudaMalloc(&t->icdf64, ni * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&t->rate32, nr * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&t->icdf32, ni * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&t->icdf32lo, ni * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&t->bes64, 3 * kBesN * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&t->bes32, 3 * kBesN * sizeof(float)) == cudaSuccess;
     if (!ok) {
@@ -201,7 +212,7 @@ extern "C" qed_status qed_tables_build(const qed_table_desc* desc, qed_tables_t*
     bessel_table_kernel<<<(kBesN + 127) / 128, 128, 0, st>>>(t->bes64, t->bes32);
     table_rows_kernel<<<4 * d.n_chi, 256, 0, st>>>(t->bes64, d, t->rate64, t->icdf64);
     to_float_kernel<<<64, 256, 0, st>>>(t->rate64, t->rate32, nr);
-    to_float_kernel<<<256, 256, 0, st>>>(t->icdf64, t->icdf32, ni);
+    split_float_kernel<<<256, 256, 0, st>>>(t->icdf64, t->icdf32, t->icdf32lo, ni);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
         free_tables(t);
         return QED_ERR_CUDA;
