@@ -62,18 +62,18 @@ enum {
 /* Species charge (qed_particles.charge). */
 enum { QED_ELECTRON = -1, QED_PHOTON = 0, QED_POSITRON = 1 };
 
-/* Physics switches (qed_step_desc.flags); the paper's "flexible switch" of Sec. 7.4.1. */
+/* Physics switches (qed_step_desc.flags); the paper's "flexible switch" of Sec. 8.5.1. */
 enum {
-    QED_F_TAU = 1u << 0,           /* optical-depth event decision (Sec. 3.1); else r1 < W dt per step */
-    QED_F_RECOIL = 1u << 1,        /* radiation reaction p_f = (1 - lambda) p_i (Sec. 4.1) */
-    QED_F_SPIN_COLLAPSE = 1u << 2, /* s_f = +-S_SQA (Sec. 4.1, 4.2); else the expectation value */
-    QED_F_POL_COLLAPSE = 1u << 3,  /* xi = +-Xi_PQA (Sec. 4.1); else xi = F/F0 */
-    QED_F_NONTRANSITION = 1u << 4, /* spin / polarization update without an event (Sec. 5) */
+    QED_F_TAU = 1u << 0,           /* optical-depth event decision (Sec. 4.1); else r1 < W dt per step */
+    QED_F_RECOIL = 1u << 1,        /* radiation reaction p_f = (1 - lambda) p_i (Sec. 5.1) */
+    QED_F_SPIN_COLLAPSE = 1u << 2, /* s_f = +-S_SQA (Sec. 5.1, 5.2); else the expectation value */
+    QED_F_POL_COLLAPSE = 1u << 3,  /* xi = +-Xi_PQA (Sec. 5.1); else xi = F/F0 */
+    QED_F_NONTRANSITION = 1u << 4, /* spin / polarization update without an event (Sec. 6) */
     QED_F_PUSH = 1u << 5,          /* Boris momentum push */
-    QED_F_TBMT = 1u << 6,          /* T-BMT spin precession (Sec. 7.3) */
+    QED_F_TBMT = 1u << 6,          /* T-BMT spin precession (Sec. 8.3) */
     QED_F_TBMT_PAPER = 1u << 7,    /* T-BMT v x E coefficient as printed, (a + 1/gamma) */
     QED_F_EMIT = 1u << 8,          /* QED events: NLC for leptons, NBW for photons */
-    QED_F_RESOLVED = 1u << 9,      /* rates and sampling depend on s.beta / xi3 (Sec. 4.1, 4.2) */
+    QED_F_RESOLVED = 1u << 9,      /* rates and sampling depend on s.beta / xi3 (Sec. 5.1, 5.2) */
     QED_F_MOVE = 1u << 10,         /* position advance */
     QED_F_SPIN_EVENT = 1u << 11,   /* lepton spin changes at emission; pair daughters get spins */
     QED_F_POL_EVENT = 1u << 12     /* emitted photons carry the Stokes vector of F (else unpolarized) */
@@ -82,7 +82,7 @@ enum {
     (QED_F_TAU | QED_F_RECOIL | QED_F_SPIN_COLLAPSE | QED_F_POL_COLLAPSE | QED_F_NONTRANSITION |       \
      QED_F_PUSH | QED_F_TBMT | QED_F_EMIT | QED_F_RESOLVED | QED_F_MOVE | QED_F_SPIN_EVENT | QED_F_POL_EVENT)
 
-/* Analytic fields that stand in for the PIC grid fields (Sec. 3). */
+/* Analytic fields that stand in for the PIC grid fields (Sec. 4). */
 enum {
     QED_FIELD_CONST = 0,     /* E = E0, B = B0 */
     QED_FIELD_LP = 1,        /* E = a0 g(phi) cos(phi) x, B = z x E, phi = t - z + phase */
@@ -100,8 +100,8 @@ typedef struct {
     double eta0;     /* hbar omega / (m c^2) of the laser that sets the units */
 } qed_field;
 
-/* Rate and inverse-CDF tables (Sec. 4.1: W_up/W_down and IntF^-1_up/down;
- * Sec. 4.2: W_+/W_- and IntG^-1_+/-).
+/* Rate and inverse-CDF tables (Sec. 5.1: W_up/W_down and IntF^-1_up/down;
+ * Sec. 5.2: W_+/W_- and IntG^-1_+/-).
  *   chi_i = exp(ln chi_min + i dlnchi), i < n_chi; y_m = y_lo + m dy, m < n_r, r_m = 1/(1 + e^-y_m).
  *   NLC rate  ln I_s(chi_i),  I_s = int_0^1 [-IntK13(u') + kappa K23(u') + s lambda K13(u')] d lambda
  *   NBW rate  ln(J_s(chi_i) e^{8/(3 chi_i)}),  J_s = int_0^1 [IntK13 + rho K23 - s K23](u~') d lambda
@@ -121,7 +121,7 @@ typedef struct {
 typedef struct qed_tables_s *qed_tables_t;
 
 /* One particle species in structure-of-arrays form.  For photons, (px, py, pz) is the
- * momentum hbar k and (sx, sy, sz) the polarization vector P of Sec. 2.2.
+ * momentum hbar k and (sx, sy, sz) the polarization vector P of Sec. 3.2.
  *   layout QED_FP64: x..w are eleven double arrays of `capacity` entries.
  *   layout QED_FP32: q0 = (x, y, z, px), q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi) are float4
  *                    arrays of `capacity` entries (16-byte aligned); tau is the FP64 optical depth stored
@@ -153,7 +153,7 @@ typedef struct {
     uint64_t seed;    /* xored into the Philox key */
     uint32_t flags;   /* QED_F_* */
     uint32_t pad;
-    double photon_store_min; /* emitted photons with |k| below this are not stored (Sec. 3.2); 0 keeps all */
+    double photon_store_min; /* emitted photons with |k| below this are not stored (Sec. 4.2); 0 keeps all */
     double chi_floor;        /* no QED event is considered below this chi */
 } qed_step_desc;
 
@@ -193,7 +193,7 @@ int32_t qed_abi_version(void);
 /* Human-readable name of a status code (static storage). */
 const char *qed_status_string(int32_t status);
 
-/* Build the FP64 tables on the current device (Sec. 4.1 and 4.2 rate and ICDF tables, from the
+/* Build the FP64 tables on the current device (Sec. 5.1 and 5.2 rate and ICDF tables, from the
  * Bessel-function forms of App. A).  All integrals are evaluated in FP64 to full precision; the FP32
  * path uses a float copy made here too.  Synchronizes `stream` before returning.
  * Errors: QED_ERR_ARG (bad desc or null out), QED_ERR_NOMEM, QED_ERR_CUDA. */
@@ -225,10 +225,10 @@ qed_status qed_tables_lookup(qed_tables_t t, int32_t precision, const double *ch
 #define QED_LOOKUP_COLS 8
 
 /* Optical depth at birth for particles [begin, *count): tau = -ln u(id, step = 2^64 - 1, slot 0)
- * (Sec. 3.1, optical-depth method). */
+ * (Sec. 4.1, optical-depth method). */
 qed_status qed_init_tau(qed_particles *p, uint64_t seed, int64_t begin, void *stream);
 
-/* One lepton step (Sec. 4.1 and its flow chart; Sec. 5 non-emission update): for every lepton in
+/* One lepton step (Sec. 5.1 and its flow chart; Sec. 6 non-emission update): for every lepton in
  * [0, *count at launch): fields at (x, t), Boris push, T-BMT precession, position advance, chi and the
  * (eps, beta, k) basis, W_s, optical depth; on emission lambda from the ICDF, recoil, SQA collapse of
  * the spin, PQA collapse of the photon Stokes vector, and a photon appended to `photons` (its P vector
@@ -239,7 +239,7 @@ qed_status qed_init_tau(qed_particles *p, uint64_t seed, int64_t begin, void *st
 qed_status qed_push_step(qed_tables_t t, const qed_field *field, const qed_step_desc *step, qed_particles *leptons,
                          qed_particles *photons, qed_counters *counters_dev, void *stream);
 
-/* One photon step (Sec. 4.2 and its flow chart; Sec. 5 non-pair update): ballistic move, chi_gamma,
+/* One photon step (Sec. 5.2 and its flow chart; Sec. 6 non-pair update): ballistic move, chi_gamma,
  * basis, Stokes from P, W_xi, optical depth; on conversion lambda from the folded ICDF, the four
  * correlated spin states of the pair, an electron and a positron appended (both at the photon's
  * position), and the photon flagged dead (appended to photons->dead); otherwise the non-pair update of
@@ -248,7 +248,7 @@ qed_status qed_pair_step(qed_tables_t t, const qed_field *field, const qed_step_
                          qed_particles *electrons, qed_particles *positrons, qed_counters *counters_dev,
                          void *stream);
 
-/* Remove the photons listed in photons->dead (Sec. 3.3: converted photons leave the simulation) by
+/* Remove the photons listed in photons->dead (Sec. 4.3: converted photons leave the simulation) by
  * moving live photons from the tail into the holes; the order of the survivors changes, their set does
  * not.  Resets *n_dead to 0.  workspace: device memory of at least qed_compact_workspace_bytes(capacity)
  * bytes (16-byte aligned), owned by the caller, zeroed (cudaMemset) before its first use; every call
@@ -288,7 +288,7 @@ qed_status qed_compact_noalloc(qed_particles *photons, void *stream);
  * buffers) advanced in lockstep.  One time step of the whole batch is: a planning kernel (alive counts
  * at step start, the tile list over all instances and species, each one's step context), one
  * persistent kernel that streams every tile of 32 particles of every instance (the lepton step of
- * Sec. 4.1 for electrons and positrons, the photon step of Sec. 4.2 for photons, each as qed_push_step /
+ * Sec. 5.1 for electrons and positrons, the photon step of Sec. 5.2 for photons, each as qed_push_step /
  * qed_pair_step do) and lists the particles whose optical depth ran out, an event kernel that runs the
  * emission / pair branch for the listed particles, and the photon compaction of every instance.  The step index and time live in device memory and advance on the
  * device, so a captured CUDA graph of one or more steps is replayed unchanged.  Results are the ones
@@ -363,7 +363,7 @@ qed_status qed_batch_tune(qed_batch_t b, int32_t steps_per_candidate, const char
 qed_status qed_batch_stats_read(qed_batch_t b, qed_batch_stats *out, void *stream);
 void qed_batch_destroy(qed_batch_t b);
 
-/* ---- Learned sampler (no counterpart code in the paper; Sec. 4.1 rejects a direct table in
+/* ---- Learned sampler (no counterpart code in the paper; Sec. 5.1 rejects a direct table in
  * (chi, r, s_beta) for its memory, and this network stands in for it) ----
  * Network 3 -> 64 -> 64 -> 64 -> 4 with SiLU.  Inputs ((ln chi - m)/h over chi in [1e-3, 1e2],
  * clamp(logit r, +-20)/10, s_beta).  Outputs: 100 x the corrections to the rate-weighted blend of the two
@@ -415,7 +415,7 @@ qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double *chi, const 
 
 /* *begin = *count for each of the n buffers (device-side copy; graph-capturable).  Call it at the start
  * of a time step that runs several step calls, so each call processes only the particles alive when the
- * step began (Sec. 3.3: an event's daughters join the simulation from the next step).  Buffers whose
+ * step began (Sec. 4.3: an event's daughters join the simulation from the next step).  Buffers whose
  * begin is NULL are skipped. */
 qed_status qed_snapshot_counts(qed_particles *const *buffers, int32_t n, void *stream);
 

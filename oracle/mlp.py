@@ -3,7 +3,7 @@ bench.py use it).
 
 The paper samples the emitted photon energy from the spin-resolved spectrum w(lambda; s_beta) with
 inverse-CDF tables and rejects a direct three-dimensional table in (chi, r, s_beta) for its memory
-(Sec. 4.1).  The learned sampler stands in for that table.  Since w is linear in s_beta, the exact
+(Sec. 5.1).  The learned sampler stands in for that table.  Since w is linear in s_beta, the exact
 r-quantile of the mixture lies between the quantiles of the two spin branches; the network predicts
 the correction to their rate-weighted blend:
 

@@ -91,7 +91,7 @@ void orc_uniform_pair(uint64_t id, uint64_t seed, uint64_t step, uint32_t slot, 
 #define ORC_SLOT_STOKES 2u      /* u0: r4 (Stokes collapse) */
 #define ORC_SLOT_CHILD 3u       /* words 0,1: first daughter id, words 2,3: second daughter id */
 
-/* Optical depth a particle starts with: tau = -ln u (Sec. 3.1, optical-depth method). */
+/* Optical depth a particle starts with: tau = -ln u (Sec. 4.1, optical-depth method). */
 double orc_birth_tau(uint64_t id, uint64_t seed)
 {
     double u[2];
@@ -191,7 +191,7 @@ static void cross3(const double a[3], const double b[3], double c[3])
 /* for scaled values whose ratios are the same).                              */
 /* ------------------------------------------------------------------------- */
 
-/* NLC, Eq. (w) of App. A.1 (and Sec. 2.1):
+/* NLC, Eq. (w) of App. A.1 (and Sec. 3.1):
  *   w = -IntK13(u') + kappa K23(u') + lambda (s_i . beta) K13(u'),
  *   g = u K13 beta + (-IntK13 + 2 K23) s_i + lambda u (-IntK13 + K23)(s_i . k) k,
  * with u = lambda/(1-lambda), u' = 2u/(3 chi), kappa = 1/(1-lambda) + (1-lambda).
@@ -245,7 +245,7 @@ void orc_nlc_stokes(double lam, const double bes[3], const double si[3], const d
            lu2 * K23 * sfk * sik;
 }
 
-/* NBW, App. A.2 / Sec. 2.1.  lambda = positron momentum fraction.
+/* NBW, App. A.2 / Sec. 3.1.  lambda = positron momentum fraction.
  *   w0  = IntK13(u~') + rho K23 - xi3 K23                                   (Eq. w0)
  *   j_e = (1/(1-l) - xi3/l) K13 beta + xi1 (1/l) K13 eps
  *         + xi2 ((1/(1-l)) IntK13 + rho~ K23) k                              (Eq. j_e)
@@ -342,7 +342,7 @@ static void gl_init(void)
 /* ------------------------------------------------------------------------- */
 /* Integrands of the rates in the substituted variables.                       */
 /* NLC: variable t with u' = t^3 (removes the lambda^{-2/3} infrared behaviour, */
-/*      Sec. 3.2), lambda = 3 chi u' / (2 + 3 chi u'), d lambda/du' = 6 chi /   */
+/*      Sec. 4.2), lambda = 3 chi u' / (2 + 3 chi u'), d lambda/du' = 6 chi /   */
 /*      (2 + 3 chi u')^2.  Integrand = w_sigma(lambda) d lambda/dt.             */
 /* NBW: folded positron spectrum (symmetric in lambda <-> 1-lambda); variable   */
 /*      t with u~' = u~'_min + t^2, u~'_min = 8/(3 chi); the density in t of     */
@@ -395,7 +395,7 @@ static double gl_segment(int nbw, double chi, int sigma, double a, double b)
 #define ORC_PANEL_W panel_w
 static double t_end(int nbw) { return nbw ? sqrt(80.0) : cbrt(80.0); }
 
-/* Rate integrals (Sec. 4.1 rate tabulation, App. A):
+/* Rate integrals (Sec. 5.1 rate tabulation, App. A):
  *   NLC: I_sigma(chi) = int_0^1 [-IntK13(u') + kappa K23(u') + sigma lambda K13(u')] d lambda,
  *        W_sigma = alpha/(sqrt3 pi eta0 gamma) * I_sigma  (per unit time 1/omega).
  *   NBW: J_sigma(chi) = int_0^1 [IntK13(u~') + rho K23(u~') - sigma K23(u~')] d lambda,
@@ -428,7 +428,7 @@ double orc_cdf_t(int nbw, double chi, int sigma, double t)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Tables (Sec. 4.1: rates W_up/W_down and ICDFs IntF^-1_up/down; Sec. 4.2:    */
+/* Tables (Sec. 5.1: rates W_up/W_down and ICDFs IntF^-1_up/down; Sec. 5.2:    */
 /* W_+/W_- and IntG^-1_+/-).                                                    */
 /*   chi grid:  chi_i = exp(ln chi_min + i * dlnchi), i < n_chi                 */
 /*   r grid:    y_m = y_lo + m * dy (logit of the cumulative probability r)     */
@@ -592,7 +592,7 @@ double orc_icdf_lookup(const orc_tables *t, int nbw, int s, double chi, double r
     return (1.0 - f) * v0 + f * v1;
 }
 
-/* NLC: lambda from u' (Sec. 4.1 definitions u = lambda/(1-lambda), u' = 2u/(3chi)). */
+/* NLC: lambda from u' (Sec. 5.1 definitions u = lambda/(1-lambda), u' = 2u/(3chi)). */
 double orc_nlc_lambda(double chi, double up) { return 3.0 * chi * up / (2.0 + 3.0 * chi * up); }
 
 /* NBW: positron fraction from the folded variable x and the uniform r
@@ -608,7 +608,7 @@ double orc_nbw_mu(double chi, double x)
 
 /* ------------------------------------------------------------------------- */
 /* Fields: analytic plane waves propagating along z (stand-in for the PIC      */
-/* grid fields of Sec. 3).  E, B in units of m c omega / e.                     */
+/* grid fields of Sec. 4).  E, B in units of m c omega / e.                     */
 /* ------------------------------------------------------------------------- */
 enum { ORC_FIELD_CONST = 0, ORC_FIELD_LP = 1, ORC_FIELD_CP = 2, ORC_FIELD_CP_COUNTER = 3 };
 typedef struct {
@@ -663,10 +663,10 @@ enum {
     ORC_F_RECOIL = 1u << 1,        /* radiation reaction: p <- (1 - lambda) p */
     ORC_F_SPIN_COLLAPSE = 1u << 2, /* s_f = +-S_SQA (else s_f = <s_f> = g/w) */
     ORC_F_POL_COLLAPSE = 1u << 3,  /* xi = +-Xi_PQA (else xi = F/F0) */
-    ORC_F_NONTRANSITION = 1u << 4, /* spin / polarization update when nothing happens (Sec. 5) */
+    ORC_F_NONTRANSITION = 1u << 4, /* spin / polarization update when nothing happens (Sec. 6) */
     ORC_F_PUSH = 1u << 5,          /* Boris momentum push */
     ORC_F_TBMT = 1u << 6,          /* T-BMT spin precession */
-    ORC_F_TBMT_PAPER = 1u << 7,    /* T-BMT coefficient as printed in Sec. 7.3 */
+    ORC_F_TBMT_PAPER = 1u << 7,    /* T-BMT coefficient as printed in Sec. 8.3 */
     ORC_F_EMIT = 1u << 8,          /* QED events (NLC for leptons, NBW for photons) */
     ORC_F_RESOLVED = 1u << 9,      /* rates and sampling depend on s.beta (leptons) / xi3 (photons) */
     ORC_F_MOVE = 1u << 10,         /* position advance */
@@ -708,7 +708,7 @@ static void push_particle(orc_particles *b, const double x[3], const double p[3]
 }
 
 /* Photon polarization vector P from Stokes xi in the basis (eps, beta, k),
- * Sec. 2.2: P = xi2 k + l (cos(dth) eps + sin(dth) beta), l = sqrt(xi1^2 + xi3^2),
+ * Sec. 3.2: P = xi2 k + l (cos(dth) eps + sin(dth) beta), l = sqrt(xi1^2 + xi3^2),
  * 2 dth = atan2(xi1, xi3) (the paper's unit-vector form, generalised to |xi| <= 1). */
 void orc_stokes_to_P(const double xi[3], const double eps[3], const double beta[3], const double k[3], double P[3])
 {
@@ -718,7 +718,7 @@ void orc_stokes_to_P(const double xi[3], const double eps[3], const double beta[
     for (int i = 0; i < 3; ++i) P[i] = xi[1] * k[i] + c * eps[i] + s * beta[i];
 }
 
-/* Stokes from P in the basis (eps, beta, k), Sec. 2.2 Eq. (P-vector/Stokes relation):
+/* Stokes from P in the basis (eps, beta, k), Sec. 3.2 Eq. (P-vector/Stokes relation):
  * xi1 = 2 P1 P2 / l, xi2 = P.k, xi3 = (P1^2 - P2^2)/l, l = sqrt(P1^2 + P2^2). */
 void orc_P_to_stokes(const double P[3], const double eps[3], const double beta[3], const double k[3], double xi[3])
 {
@@ -734,7 +734,7 @@ void orc_P_to_stokes(const double P[3], const double eps[3], const double beta[3
     }
 }
 
-/* Local basis (Sec. 2): k = direction of motion; eps along the component of the
+/* Local basis (Sec. 3): k = direction of motion; eps along the component of the
  * Lorentz-force field f perpendicular to k; beta = k x eps (right-handed).
  * Leptons: f = E + v x B, eps = -q f_perp/|f_perp| (q = charge); photons: f = E + k x B, eps = f_perp/|f_perp|.
  * Returns 0 if the basis is undefined. */
@@ -777,7 +777,7 @@ static void rotate(double s[3], const double n[3], double th)
 
 /* ------------------------------------------------------------------------- */
 /* Lepton step: Boris push, T-BMT precession, position advance, then the NLC  */
-/* module (Sec. 4.1 and its flow chart; non-emission update Sec. 5).           */
+/* module (Sec. 5.1 and its flow chart; non-emission update Sec. 6).           */
 /* ------------------------------------------------------------------------- */
 static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step *st, int q, orc_particles *L,
                        int64_t j, orc_result *res)
@@ -794,7 +794,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
     double E[3], B[3];
     orc_field_eval(fd, x, st->t, E, B);
 
-    /* Boris push (Sec. 4.1 "classical Lorentz pusher") */
+    /* Boris push (Sec. 5.1 "classical Lorentz pusher") */
     double pold[3] = {p[0], p[1], p[2]};
     if (fl & ORC_F_PUSH) {
         double h = 0.5 * q * dt;
@@ -812,7 +812,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
         for (int i = 0; i < 3; ++i) p[i] = pl[i] + h * E[i];
     }
 
-    /* T-BMT precession (Sec. 7.3): ds/dt = Omega x s, time-centred momentum */
+    /* T-BMT precession (Sec. 8.3): ds/dt = Omega x s, time-centred momentum */
     if (fl & ORC_F_TBMT) {
         double pb[3] = {0.5 * (pold[0] + p[0]), 0.5 * (pold[1] + p[1]), 0.5 * (pold[2] + p[2])};
         double gb = sqrt(1.0 + dot3(pb, pb));
@@ -863,13 +863,13 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
             res->clamped = cl;
             int resolved = (fl & ORC_F_RESOLVED) != 0;
             double sb = resolved ? dot3(s, beta) : 0.0;
-            /* Sec. 4.1: W_s = W_up (1 + s.beta)/2 + W_down (1 - s.beta)/2 */
+            /* Sec. 5.1: W_s = W_up (1 + s.beta)/2 + W_down (1 - s.beta)/2 */
             double Wup_part = Wu * (1.0 + sb) / 2.0, Wdn_part = Wd * (1.0 - sb) / 2.0;
             double Ws = Wup_part + Wdn_part;
             double u0[2];
             int down = 0;
             if (fl & ORC_F_TAU) {
-                /* optical depth (Sec. 3.1): tau_rem decreases by W dt, event when <= 0 */
+                /* optical depth (Sec. 4.1): tau_rem decreases by W dt, event when <= 0 */
                 tauf = tau - Ws * dt;
                 event = tauf <= 0.0;
                 if (event) {
@@ -878,7 +878,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                     down = u0[1] * Ws < Wdn_part;
                 }
             } else {
-                /* per-step probability (Sec. 3.1, 4.1): event if r1 < W_s dt; down if r1 < W_down (1-s.beta) dt/2 */
+                /* per-step probability (Sec. 4.1, 5.1): event if r1 < W_s dt; down if r1 < W_down (1-s.beta) dt/2 */
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_TAU_BRANCH, u0);
                 event = u0[0] < Ws * dt;
                 down = u0[0] < Wdn_part * dt;
@@ -891,10 +891,10 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 double u1[2], u2[2];
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_LAMBDA_SPIN, u1);
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_STOKES, u2);
-                /* lambda from the ICDF of the chosen branch (Sec. 4.1) */
+                /* lambda from the ICDF of the chosen branch (Sec. 5.1) */
                 double up = exp(orc_icdf_lookup(tb, 0, down ? 1 : 0, chi, u1[0]));
                 double lam = orc_nlc_lambda(chi, up);
-                /* photon and recoil (Sec. 4.1): hbar k = lambda p_i, p_f = (1 - lambda) p_i */
+                /* photon and recoil (Sec. 5.1): hbar k = lambda p_i, p_f = (1 - lambda) p_i */
                 double k[3] = {lam * p[0], lam * p[1], lam * p[2]};
                 if (fl & ORC_F_RECOIL)
                     for (int i = 0; i < 3; ++i) pf[i] = (1.0 - lam) * p[i];
@@ -907,7 +907,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                     orc_nlc_wg(lam, bes, si, eps, beta, khat, &w, g);
                     double gn = sqrt(dot3(g, g));
                     if (fl & ORC_F_SPIN_COLLAPSE) {
-                        /* SQA collapse (Sec. 4.1): s_f = -S if r3 < (w - |g|)/(2w), else +S */
+                        /* SQA collapse (Sec. 5.1): s_f = -S if r3 < (w - |g|)/(2w), else +S */
                         double sg = u1[1] < (w - gn) / (2.0 * w) ? -1.0 : 1.0;
                         for (int i = 0; i < 3; ++i) sf[i] = gn > 0.0 ? sg * g[i] / gn : 0.0;
                     } else {
@@ -916,7 +916,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                     for (int i = 0; i < 3; ++i) sfu[i] = sf[i];
                 }
                 if (fl & ORC_F_POL_EVENT) {
-                    /* photon Stokes given (s_i, s_f) (Sec. 4.1, App. A.1); s_f = 0 sums over final spins */
+                    /* photon Stokes given (s_i, s_f) (Sec. 5.1, App. A.1); s_f = 0 sums over final spins */
                     double F[4];
                     orc_nlc_stokes(lam, bes, si, sfu, eps, beta, khat, F);
                     double Fn = sqrt(F[1] * F[1] + F[2] * F[2] + F[3] * F[3]);
@@ -942,7 +942,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 res->tau0 = orc_birth_tau(cid[0], st->seed);
                 res->w0 = L->w[j];
             } else if ((fl & ORC_F_NONTRANSITION) && resolved) {
-                /* Sec. 5: s <- [s (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . s) dt],
+                /* Sec. 6: s <- [s (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . s) dt],
                  * <P> = (W_up + W_down)/2, P_i = ((W_up - W_down)/2) beta */
                 double W0 = 0.5 * (Wu + Wd), Pi = 0.5 * (Wu - Wd);
                 double D = 1.0 - (W0 + Pi * dot3(beta, s)) * dt;
@@ -997,8 +997,8 @@ int orc_lepton_step(const orc_tables *tb, const orc_field *fd, const orc_step *s
 }
 
 /* ------------------------------------------------------------------------- */
-/* Photon step: ballistic move and the NBW module (Sec. 4.2 and its flow chart;*/
-/* non-pair update Sec. 5).                                                    */
+/* Photon step: ballistic move and the NBW module (Sec. 5.2 and its flow chart;*/
+/* non-pair update Sec. 6).                                                    */
 /* ------------------------------------------------------------------------- */
 static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step *st, orc_particles *G, int64_t j,
                        orc_result *res)
@@ -1035,7 +1035,7 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
             double Wp = pref * orc_nbw_rate_lookup(tb, 0, chi, &cl);
             double Wm = pref * orc_nbw_rate_lookup(tb, 1, chi, NULL);
             res->clamped = cl;
-            /* Sec. 4.2: W_xi = W_- (1 - xi3)/2 + W_+ (1 + xi3)/2 */
+            /* Sec. 5.2: W_xi = W_- (1 - xi3)/2 + W_+ (1 + xi3)/2 */
             double Wm_part = Wm * (1.0 - xi[2]) / 2.0, Wp_part = Wp * (1.0 + xi[2]) / 2.0;
             double Wx = Wm_part + Wp_part;
             int event = 0, minus = 0;
@@ -1055,7 +1055,7 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
             if (event && Wx > 0.0) {
                 double u1[2];
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_LAMBDA_SPIN, u1);
-                /* lambda from the folded ICDF of the chosen branch (Sec. 4.2) */
+                /* lambda from the folded ICDF of the chosen branch (Sec. 5.2) */
                 double r = u1[0];
                 double rf = r < 0.5 ? 1.0 - 2.0 * r : 2.0 * r - 1.0;
                 double xv;
@@ -1079,7 +1079,7 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
                             Se[i] = jen > 0.0 ? je[i] / jen : 0.0;
                             Sp[i] = jpn > 0.0 ? jp[i] / jpn : 0.0;
                         }
-                        /* four correlated states (Sec. 4.2), order (--, -+, +-, ++), first sign = positron,
+                        /* four correlated states (Sec. 5.2), order (--, -+, +-, ++), first sign = positron,
                          * probabilities G_ab / (4 w0) */
                         double cum = 0.0;
                         int chosen = 3;
@@ -1116,7 +1116,7 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 res->tau1 = orc_birth_tau(cid[1], st->seed);
                 res->w0 = G->w[j];
             } else if (!event && (fl & ORC_F_NONTRANSITION) && resolved) {
-                /* Sec. 5 with Q = e3 in Stokes space: xi <- [xi (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . xi) dt],
+                /* Sec. 6 with Q = e3 in Stokes space: xi <- [xi (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . xi) dt],
                  * <P> = (W_+ + W_-)/2, P_i = ((W_+ - W_-)/2) e3 */
                 double W0 = 0.5 * (Wp + Wm), Pi = 0.5 * (Wp - Wm);
                 double D = 1.0 - (W0 + Pi * xi[2]) * dt;
@@ -1139,7 +1139,7 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
     G->tau[j] = tauf;
 }
 
-/* Photons that convert are removed (Sec. 3.3, 4.2); the surviving photons keep
+/* Photons that convert are removed (Sec. 4.3, 5.2); the surviving photons keep
  * their order, daughters are appended in parent order, electron then positron. */
 int orc_photon_step(const orc_tables *tb, const orc_field *fd, const orc_step *st, orc_particles *G,
                     orc_particles *el, orc_particles *po, orc_counters *ctr)
@@ -1186,7 +1186,7 @@ void orc_init_tau(orc_particles *b, uint64_t seed)
     for (int64_t j = 0; j < b->n; ++j) b->tau[j] = orc_birth_tau(b->id[j], seed);
 }
 
-/* Sokolov-Ternov / BKS functions (Sec. 7.1, 7.3), u'' = u^2/(1+u)^3, argument 2u/(3 chi):
+/* Sokolov-Ternov / BKS functions (Sec. 8.1, 8.3), u'' = u^2/(1+u)^3, argument 2u/(3 chi):
  *   psi1 = int u'' K23,  psi3 = int u'' K13,  psi2 = int u'' IntK13 - psi1.
  * which = 1, 2, 3.  Variable u = v^3 / (1 - v) style map not needed: substitute u = t^3
  * and integrate in t over panels until the integrand is negligible. */
@@ -1232,7 +1232,7 @@ void orc_set_num_threads(int n)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Target of the learned sampler.  Sec. 4.1 samples the photon energy from    */
+/* Target of the learned sampler.  Sec. 5.1 samples the photon energy from    */
 /* the spin-resolved spectrum w(lambda; s_beta) and notes that a direct table */
 /* in (chi, r, s_beta) costs memory; a small network stands in for that 3-D   */
 /* inverse CDF.  Its target, written out from the definition:                 */

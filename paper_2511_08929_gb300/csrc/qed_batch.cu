@@ -16,7 +16,7 @@
 //             the persistent kernel, whose registers then hold only the streaming pass: no calls, no
 //             spills);
 //   compact   head / classify / tail / move of every instance's photons (converted photons leave,
-//             Sec. 3.3), the last one also advancing the device step counter.
+//             Sec. 4.3), the last one also advancing the device step counter.
 // Daughters appended during a step sit beyond the counts taken by `plan`, so they are first stepped in
 // the next step (the begin snapshot of the single-buffer path).
 #include <cstdio>

@@ -1,5 +1,5 @@
 // qed_bessel.cuh -- modified Bessel functions of the App. A spectra and the table lookups
-// (Sec. 4.1, 4.2).  All Bessel values are scaled: e^x K_{1/3}(x), e^x K_{2/3}(x),
+// (Sec. 5.1, 5.2).  All Bessel values are scaled: e^x K_{1/3}(x), e^x K_{2/3}(x),
 // e^x int_x^inf K_{1/3} -- the factor cancels in every ratio the event sampling takes, and the
 // rate/CDF integrands put it back explicitly.
 //

@@ -66,7 +66,7 @@ __global__ void append_close_kernel(qed_counters* ctr, int64_t* c0, int64_t* c1)
     if (threadIdx.x == 0) append_close(append_state(ctr), c0, c1);
 }
 
-// ---- compaction (Sec. 3.3: converted photons leave the simulation) ----
+// ---- compaction (Sec. 4.3: converted photons leave the simulation) ----
 struct CompactWs {
     int64_t* holes;  // dead indices below n - D
     int64_t* live;   // live indices in the tail [n - D, n)

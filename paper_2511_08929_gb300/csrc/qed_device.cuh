@@ -110,7 +110,7 @@ __device__ __forceinline__ double birth_tau(uint64_t id, uint64_t seed) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// analytic plane-wave fields (stand-in for the grid fields of Sec. 3)
+// analytic plane-wave fields (stand-in for the grid fields of Sec. 4)
 // ---------------------------------------------------------------------------------------------
 template <class R>
 struct FieldP {
@@ -262,7 +262,7 @@ __device__ __forceinline__ V3<R> tbmt_omega(const V3<R>& pb, const V3<R>& E, con
     const R bB = dot(bb, B);
     const V3<R> bxE = cross(bb, E);
     const R c1 = ae + ig, c2 = div_(ae * gb, gb + R(1));
-    if (paper_form)  // (a + 1/gamma)(B - v x E) - (a gamma/(gamma+1))(v.B) v, as printed in Sec. 7.3
+    if (paper_form)  // (a + 1/gamma)(B - v x E) - (a gamma/(gamma+1))(v.B) v, as printed in Sec. 8.3
         return (-q) * axpy(-(c2 * bB), bb, c1 * (B - bxE));
     // standard form: (a + 1/gamma) B - (a gamma/(gamma+1))(beta.B) beta - (a + 1/(gamma+1)) beta x E
     const R c3 = ae + rcp_(gb + R(1));
@@ -380,7 +380,7 @@ __device__ __forceinline__ R nbw_G(R lam, R one_m, const R bes[3], const R xi[3]
     return G0 + xi[0] * G1 + xi[1] * G2 + xi[2] * G3;
 }
 
-// Stokes -> P (Sec. 2.2): P = xi2 k + l (cos dth eps + sin dth beta), l = |(xi1, xi3)|, 2 dth = atan2(xi1, xi3),
+// Stokes -> P (Sec. 3.2): P = xi2 k + l (cos dth eps + sin dth beta), l = |(xi1, xi3)|, 2 dth = atan2(xi1, xi3),
 // with half-angle identities: (l cos dth)^2 = l (l + xi3)/2, (l sin dth)^2 = l (l - xi3)/2 and
 // (l cos dth)(l sin dth) = l xi1 / 2.  The larger component comes from its square root (no cancellation),
 // the smaller one from the product; cos dth >= 0.

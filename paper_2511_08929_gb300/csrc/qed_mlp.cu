@@ -1,5 +1,5 @@
 // qed_mlp.cu -- the learned sampler: a 3-64-64-64-4 SiLU network standing in for the three-dimensional
-// inverse CDF in (chi, r, s_beta) that Sec. 4.1 rejects for its memory.
+// inverse CDF in (chi, r, s_beta) that Sec. 5.1 rejects for its memory.
 //
 // Target (the map the network learns, computed from the FP64 tables): the exact r-quantile ln u' of the
 // NLC spectrum for a continuous spin projection s (w is linear in s: the mixture CDF is the rate-weighted

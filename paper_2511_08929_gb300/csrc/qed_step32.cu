@@ -1,6 +1,6 @@
 // qed_step32.cu -- the FP32 fast path.
 //
-// Same algorithm as the FP64 path (Sec. 4.1, 4.2, 5), arithmetic split as follows: the Boris and T-BMT
+// Same algorithm as the FP64 path (Sec. 5.1, 5.2, 6), arithmetic split as follows: the Boris and T-BMT
 // pushers, chi, the basis, the rate lookups and all event sampling in FP32; the optical depth is
 // accumulated in FP64 and the excess |s|^2 - 1 of a spin / Stokes vector that leaves the unit ball is
 // computed in FP64.

@@ -1,7 +1,7 @@
 // qed_step32.cuh -- the per-particle arithmetic of the FP32 fast path, shared by the single-buffer step
 // kernels (qed_step32.cu) and the batched persistent kernel (qed_batch.cu).
 //
-// Arithmetic split (Sec. 4.1, 4.2, 5): the Boris and T-BMT pushers, chi, the basis, the rate lookups and
+// Arithmetic split (Sec. 5.1, 5.2, 6): the Boris and T-BMT pushers, chi, the basis, the rate lookups and
 // all event sampling in FP32; the optical depth is accumulated in FP64 and the excess |s|^2 - 1 of a
 // spin / Stokes vector that leaves the unit ball is computed in FP64.  Particles are three float4 planes
 // q0 = (x, y, z, p_x), q1 = (p_y, p_z, s_x, s_y), q2 = (s_z, w, tau_lo, tau_hi).
@@ -103,7 +103,7 @@ __device__ __forceinline__ double widen_pos(float v) {
 }
 
 // A spin or Stokes vector is renormalised when |s|^2 exceeds 1 by more than the FP32 rounding of the
-// update that produced it; below that the excess is rounding noise (the exact update of Sec. 5 raises
+// update that produced it; below that the excess is rounding noise (the exact update of Sec. 6 raises
 // |s|^2 by (P dt)^2 (1 - (s.beta)^2) / D^2, a real second-order excess, which still triggers it).
 constexpr float kRenormSlack = 0x1.0p-20f;
 
@@ -647,7 +647,7 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
     }
     F3 sf = st.s;
     if (st.qed && (fl & QED_F_NONTRANSITION) && (fl & QED_F_RESOLVED)) {
-        // Sec. 5: s <- [s (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . s) dt]
+        // Sec. 6: s <- [s (1 - <P> dt) - P_i dt] / [1 - (<P> + P_i . s) dt]
         const float W0 = 0.5f * (st.Wu + st.Wd), Pi = 0.5f * (st.Wu - st.Wd);
         const float D = 1.0f - (W0 + Pi * st.sb) * dt;
         if (D > 0.0f) {
@@ -845,7 +845,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
     }
     F3 Pf = st.P;
     if (st.qed && (fl & QED_F_NONTRANSITION) && (fl & QED_F_RESOLVED)) {
-        // Sec. 5 with Q = e3: xi <- [xi (1 - <P> dt) - P_i dt e3] / [1 - (<P> + P_i xi3) dt]
+        // Sec. 6 with Q = e3: xi <- [xi (1 - <P> dt) - P_i dt e3] / [1 - (<P> + P_i xi3) dt]
         const float W0 = 0.5f * (st.Wp + st.Wm), Pi = 0.5f * (st.Wp - st.Wm);
         const float D = 1.0f - (W0 + Pi * st.xi[2]) * dt;
         if (D > 0.0f) {

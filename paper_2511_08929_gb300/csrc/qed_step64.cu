@@ -1,6 +1,6 @@
 // qed_step64.cu -- the plain FP64 path: one thread per particle, every operation in double precision.
-// Lepton step: Sec. 4.1 (and its flow chart) with the non-emission update of Sec. 5.
-// Photon step: Sec. 4.2 (and its flow chart) with the non-pair update of Sec. 5.
+// Lepton step: Sec. 5.1 (and its flow chart) with the non-emission update of Sec. 6.
+// Photon step: Sec. 5.2 (and its flow chart) with the non-pair update of Sec. 6.
 #include "qed_bessel.cuh"
 #include "qed_internal.h"
 #include "qed_steps.h"

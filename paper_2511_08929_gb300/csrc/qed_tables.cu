@@ -1,9 +1,9 @@
-// qed_tables.cu -- FP64 construction of the rate and inverse-CDF tables of Sec. 4.1 (W_up, W_down,
-// IntF^-1_up/down) and Sec. 4.2 (W_+, W_-, IntG^-1_+/-), from the Bessel forms of App. A.
+// qed_tables.cu -- FP64 construction of the rate and inverse-CDF tables of Sec. 5.1 (W_up, W_down,
+// IntF^-1_up/down) and Sec. 5.2 (W_+, W_-, IntG^-1_+/-), from the Bessel forms of App. A.
 //
 // Every stored number is an exact (to FP64 rounding) value of a defined integral or of the root of a
 // monotone equation; the quadrature is only the means:
-//   NLC, variable t with u' = t^3 (removes the lambda^{-2/3} infrared behaviour noted in Sec. 3.2):
+//   NLC, variable t with u' = t^3 (removes the lambda^{-2/3} infrared behaviour noted in Sec. 4.2):
 //       density in t  = w_s(lambda) d lambda/dt,  lambda = 3 chi u'/(2 + 3 chi u'),
 //       d lambda/du' = 6 chi / (2 + 3 chi u')^2,  w_s = -IntK13 + kappa K23 + s lambda K13 at u'.
 //   NBW, spectrum folded about lambda = 1/2 (it is symmetric), variable t with u~' = 8/(3 chi) + t^2:

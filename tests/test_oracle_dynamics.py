@@ -1,7 +1,7 @@
 """Pins of the oracle's step functions: exact discrete dynamics (Boris, T-BMT), conservation at
 events, invariants, the ICDF against the exact CDF, and the paper's verification experiments
-reduced to 0-D with analytic fields: Sokolov-Ternov (Sec. 5 and 7.1) and the construction
-independence of unpolarized photon beams under the non-pair update (Sec. 5).  CPU only."""
+reduced to 0-D with analytic fields: Sokolov-Ternov (Sec. 6 and 8.1) and the construction
+independence of unpolarized photon beams under the non-pair update (Sec. 6).  CPU only."""
 import math
 
 import numpy as np
@@ -45,7 +45,7 @@ def test_boris_gyration_angle_exact(q, small_tables):
 
 def test_tbmt_precession_relative_to_momentum(small_tables):
     """Uniform B, p and s in the plane: s rotates by (a + 1/gamma_bar) B dt per step (gamma_bar from the
-    time-centred momentum), so s advances against p at a gamma omega_c to O(dt^2) (T-BMT, Sec. 7.3)."""
+    time-centred momentum), so s advances against p at a gamma omega_c to O(dt^2) (T-BMT, Sec. 8.3)."""
     g, Bz, dt, n = 50.0, 10.0, 0.05, 400
     pm = math.sqrt(g * g - 1)
     b = {"pos": np.zeros((1, 3)), "mom": np.array([[pm, 0, 0]]), "spin": np.array([[1.0, 0, 0]]),
@@ -71,7 +71,7 @@ def test_tbmt_precession_relative_to_momentum(small_tables):
 # conservation and invariants at events
 # ------------------------------------------------------------------------------------------
 def test_momentum_conservation_nlc_and_invariants(small_tables):
-    """No classical force: every emission satisfies p_i = p_f + hbar k exactly (Sec. 4.1), |s| <= 1,
+    """No classical force: every emission satisfies p_i = p_f + hbar k exactly (Sec. 5.1), |s| <= 1,
     |P| <= 1 for every particle after many steps."""
     b = I.random_states(400, seed=11)
     L = _particles(b, seed=5)
@@ -92,7 +92,7 @@ def test_momentum_conservation_nlc_and_invariants(small_tables):
 
 
 def test_nbw_momentum_conservation_and_spins(small_tables):
-    """p_e + p_p = hbar k for every pair (Sec. 4.2); daughters' spins are unit (four-state collapse)."""
+    """p_e + p_p = hbar k for every pair (Sec. 5.2); daughters' spins are unit (four-state collapse)."""
     eps_ = 4000.0
     P_list = [(0, 1, 0), (0, 0, 1), (1, 0, 0), (0, 0.7, 0.7)]
     b = I.photon_beam(2000, eps_, direction=(1, 0, 0), P_list=P_list, seed=3)
@@ -114,7 +114,7 @@ def test_nbw_momentum_conservation_and_spins(small_tables):
 
 
 # ------------------------------------------------------------------------------------------
-# sampling: the tabulated ICDF against the exact CDF (Sec. 3.2, 4.1, 4.2)
+# sampling: the tabulated ICDF against the exact CDF (Sec. 4.2, 5.1, 5.2)
 # ------------------------------------------------------------------------------------------
 @pytest.fixture(scope="module")
 def node_tables():
@@ -190,7 +190,7 @@ def test_sampled_spectrum_is_the_spin_mixture(small_tables):
 
 
 # ------------------------------------------------------------------------------------------
-# Sokolov-Ternov (Sec. 5 first example; Sec. 7.1)
+# Sokolov-Ternov (Sec. 6 first example; Sec. 8.1)
 # ------------------------------------------------------------------------------------------
 def _st_run(q, n, steps, dt, flags, tables, seed=21):
     p = math.sqrt(GAMMA_1GEV ** 2 - 1)
@@ -240,7 +240,7 @@ def test_sokolov_ternov_positrons_polarize_along_B(st_tables):
 
 
 # ------------------------------------------------------------------------------------------
-# unpolarized photon beams built three ways (Sec. 5, second example)
+# unpolarized photon beams built three ways (Sec. 6, second example)
 # ------------------------------------------------------------------------------------------
 def _nopair_run(construction, flags, tables, n=20000, steps=300, dt=0.1):
     eps_ = GAMMA_1GEV

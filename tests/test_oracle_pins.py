@@ -342,7 +342,7 @@ def test_quadrature_rule_converged():
 
 
 # ------------------------------------------------------------------------------------------
-# Sokolov-Ternov / BKS functions (Sec. 7.1, 7.3)
+# Sokolov-Ternov / BKS functions (Sec. 8.1, 8.3)
 # ------------------------------------------------------------------------------------------
 def _psi_scipy(chi, which):
     def f(u):
@@ -372,7 +372,7 @@ def test_psi_classical_ratios():
 
 
 # ------------------------------------------------------------------------------------------
-# Photon polarization vector P (Sec. 2.2)
+# Photon polarization vector P (Sec. 3.2)
 # ------------------------------------------------------------------------------------------
 def test_P_vector_round_trip_and_observation_rotation():
     rng = np.random.default_rng(8)

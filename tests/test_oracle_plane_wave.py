@@ -5,7 +5,7 @@ circular lasers, and drop the products by E_z and B_z in the Boris push and the 
 plane-wave kind.  These hold when the field is transverse (E_z = B_z = 0) and, for the reduced chi and
 f, when it is a single wave along +z (B = z x E):
 
-  chi = eta0 sqrt((e E + p x B)^2 - (p.E)^2)  =  eta0 |e - p_z| |E|          (Sec. 2, the invariant)
+  chi = eta0 sqrt((e E + p x B)^2 - (p.E)^2)  =  eta0 |e - p_z| |E|          (Sec. 1, the invariant)
   f   = E + v x B                              =  (1 - v_z) E + (v.E) z
 
 Here they are checked against the oracle's own field evaluation at random points and times, with the
