@@ -564,11 +564,14 @@ def native_batch(args):
     value = psteps_all / (tmax / 1e3)
 
     # roofline of the persistent kernel: algorithmic bytes per launch / its event-timed duration
-    # 88 B per lepton-step, 76 B per photon-step, 8 B (id) per event, 52 B per stored daughter
+    # lepton-step 88 B (read x, p, s, tau 44 B; write them 44 B); photon-step 56 B (read x, k, P, tau 44 B;
+    # write x 12 B) + 20 B (write P, tau) when the photon has a pair rate; 8 B (id) per event; 52 B per
+    # stored daughter
     peak, peak_kind = measured_peaks()
-    alg = 88.0 * (d_sp[0] + d_sp[1]) + 76.0 * d_sp[2] + 8.0 * ctr.events + 52.0 * ctr.stored
-    # the same with the survey's per-unit figures (id read every step): 96 B per lepton-step, 84 B per photon-step
-    alg_survey = 96.0 * (d_sp[0] + d_sp[1]) + 84.0 * d_sp[2] + 52.0 * ctr.stored
+    alg = 88.0 * (d_sp[0] + d_sp[1]) + 56.0 * d_sp[2] + 20.0 * ctr.rate_steps + 8.0 * ctr.events + 52.0 * ctr.stored
+    # the same with the survey's per-unit figures (the id read every step): 96 B per lepton-step, 64 B per
+    # photon-step + 20 B with a pair rate
+    alg_survey = 96.0 * (d_sp[0] + d_sp[1]) + 64.0 * d_sp[2] + 20.0 * ctr.rate_steps + 52.0 * ctr.stored
     tr = measured_traffic()
     traffic = None
     if tr is not None:  # ncu DRAM bytes per particle-step of a smaller capture, scaled to this launch
@@ -685,17 +688,26 @@ def mlp_leg(args, tables, torch):
 
 
 def _to_fp64(b32, b64, torch):
-    """Copy an FP32 buffer's [0, count) into an FP64 buffer (device-side repacking)."""
+    """Copy an FP32 buffer's [0, count) into an FP64 buffer (device-side repacking of the qed.h layouts;
+    planes of the FP64 buffer: x y z px py pz sx sy sz tau w)."""
+    from paper_2511_08929_gb300 import binding as B
     n = b32.count()
     q = b32.q[:, :n]
     P = b64.planes
     P[0:3, :n] = q[0, :, 0:3].T.double()
-    P[3, :n] = q[0, :, 3].double()
-    P[4:6, :n] = q[1, :, 0:2].T.double()
-    P[6:8, :n] = q[1, :, 2:4].T.double()
-    P[8, :n] = q[2, :, 0].double()
-    P[10, :n] = q[2, :, 1].double()
-    P[9, :n] = q[2, :, 2:4].contiguous().view(torch.float64).reshape(n)
+    if b32.charge == B.QED_PHOTON:
+        P[6, :n] = q[0, :, 3].double()
+        P[7:9, :n] = q[1, :, 0:2].T.double()
+        P[9, :n] = q[1, :, 2:4].contiguous().view(torch.float64).reshape(n)
+        P[3:6, :n] = q[2, :, 0:3].T.double()
+        P[10, :n] = q[2, :, 3].double()
+    else:
+        P[3, :n] = q[0, :, 3].double()
+        P[4:6, :n] = q[1, :, 0:2].T.double()
+        P[6:8, :n] = q[1, :, 2:4].T.double()
+        P[8, :n] = q[2, :, 0].double()
+        P[10, :n] = q[2, :, 1].double()
+        P[9, :n] = q[2, :, 2:4].contiguous().view(torch.float64).reshape(n)
     b64.ids[:n] = b32.ids[:n]
     b64.counts[:] = n
 
@@ -804,21 +816,11 @@ def _oracle_field(O, f):
     return O.field(f.kind, a0=f.a0, n_cycles=f.n_cycles, phase=f.phase, E0=tuple(f.E0), B0=tuple(f.B0), eta0=f.eta0)
 
 
-def _unpack32(q, ids):
-    """host FP64 arrays of FP32 particle rows q (3, m, 4) and ids (m,) (layout of qed.h)"""
-    m = q.shape[1]
-    pos = q[0, :, 0:3].astype(np.float64)
-    mom = np.column_stack([q[0, :, 3], q[1, :, 0], q[1, :, 1]]).astype(np.float64)
-    spin = np.column_stack([q[1, :, 2], q[1, :, 3], q[2, :, 0]]).astype(np.float64)
-    w = q[2, :, 1].astype(np.float64)
-    tau = np.ascontiguousarray(q[2, :, 2:4]).view(np.uint32).reshape(m, 2).copy().view(np.float64).reshape(m)
-    return {"pos": pos, "mom": mom, "spin": spin, "tau": tau, "w": w, "id": ids.view(np.uint64).copy()}
-
-
 def _gpu_rows(buf, idx, torch):
     """rows idx (device int64 tensor) of an FP32 particle buffer, as host FP64 arrays"""
-    q = buf.q[:, idx].cpu().numpy()
-    return _unpack32(q, buf.ids[idx].cpu().numpy())
+    from paper_2511_08929_gb300 import buffers as Q
+    pos, mom, spin, w, tau = Q.unpack32(buf.charge, buf.q[:, idx].cpu().numpy())
+    return {"pos": pos, "mom": mom, "spin": spin, "tau": tau, "w": w, "id": buf.ids[idx].cpu().numpy().view(np.uint64).copy()}
 
 
 def _gpu_find(buf, ids, torch):

@@ -123,9 +123,12 @@ typedef struct qed_tables_s *qed_tables_t;
 /* One particle species in structure-of-arrays form.  For photons, (px, py, pz) is the
  * momentum hbar k and (sx, sy, sz) the polarization vector P of Sec. 3.2.
  *   layout QED_FP64: x..w are eleven double arrays of `capacity` entries.
- *   layout QED_FP32: q0 = (x, y, z, px), q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi) are float4
- *                    arrays of `capacity` entries (16-byte aligned); tau is the FP64 optical depth stored
- *                    as the low and high 32-bit words of its bit pattern.
+ *   layout QED_FP32: three float4 arrays of `capacity` entries (16-byte aligned); tau is the FP64 optical
+ *                    depth stored as the low and high 32-bit words of its bit pattern.
+ *                    leptons: q0 = (x, y, z, px), q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi);
+ *                    photons: q0 = (x, y, z, sx), q1 = (sy, sz, tau_lo, tau_hi), q2 = (px, py, pz, w)
+ *                    (a photon step never changes k or w: it rewrites q0 and q1, or q0 alone when the
+ *                    photon has no pair rate).
  * id: uint64 array; the Philox key of each particle.  count: device int64, the live count, advanced
  * by the kernels that append daughters.  begin: optional device int64; when set, a step call processes
  * particles [0, *begin) instead of [0, *count at launch), so that daughters appended during the current
@@ -173,6 +176,8 @@ typedef struct {
     unsigned long long renormalised;     /* spin / Stokes vectors rescaled to unit length */
     unsigned long long below_store;      /* photons not stored because |k| < photon_store_min */
     unsigned long long nonfinite;        /* particles skipped because their state was not finite */
+    unsigned long long rate_steps;       /* FP32 paths: photon-steps with a nonzero pair rate (the others
+                                            only move, and write the position plane alone) */
     int32_t status;                      /* first device-side error (qed_status), 0 if none */
     int32_t pad;
     int64_t first_bad;                   /* particle index of the first device-side error, -1 if none */

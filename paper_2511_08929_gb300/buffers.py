@@ -12,9 +12,51 @@ from . import binding as B
 PLANES64 = ("x", "y", "z", "px", "py", "pz", "sx", "sy", "sz", "tau", "w")
 
 
+def pack32(charge: int, pos, mom, spin, w, tau) -> np.ndarray:
+    """(3, n, 4) float32 planes of the FP32 layout (qed.h): leptons q0 = (x, y, z, px),
+    q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi); photons q0 = (x, y, z, sx), q1 = (sy, sz, tau_lo,
+    tau_hi), q2 = (px, py, pz, w); tau as the two 32-bit words of its FP64 bit pattern."""
+    n = len(w)
+    host = np.zeros((3, n, 4), dtype=np.float32)
+    tw = np.asarray(tau, dtype=np.float64).view(np.uint32).reshape(n, 2).view(np.float32)
+    host[0, :, 0:3] = pos
+    if charge == B.QED_PHOTON:
+        host[0, :, 3] = spin[:, 0]
+        host[1, :, 0:2] = spin[:, 1:3]
+        host[1, :, 2:4] = tw
+        host[2, :, 0:3] = mom
+        host[2, :, 3] = w
+    else:
+        host[0, :, 3] = mom[:, 0]
+        host[1, :, 0:2] = mom[:, 1:3]
+        host[1, :, 2:4] = spin[:, 0:2]
+        host[2, :, 0] = spin[:, 2]
+        host[2, :, 1] = w
+        host[2, :, 2:4] = tw
+    return host
+
+
+def unpack32(charge: int, h: np.ndarray):
+    """(pos, mom, spin, w, tau) as FP64 arrays from (3, n, 4) planes of the FP32 layout"""
+    n = h.shape[1]
+    pos = h[0, :, 0:3].astype(np.float64)
+    if charge == B.QED_PHOTON:
+        spin = np.column_stack([h[0, :, 3], h[1, :, 0], h[1, :, 1]]).astype(np.float64)
+        mom = h[2, :, 0:3].astype(np.float64)
+        w = h[2, :, 3].astype(np.float64)
+        tw = h[1, :, 2:4]
+    else:
+        mom = np.column_stack([h[0, :, 3], h[1, :, 0], h[1, :, 1]]).astype(np.float64)
+        spin = np.column_stack([h[1, :, 2], h[1, :, 3], h[2, :, 0]]).astype(np.float64)
+        w = h[2, :, 1].astype(np.float64)
+        tw = h[2, :, 2:4]
+    tau = np.ascontiguousarray(tw).view(np.uint32).reshape(n, 2).copy().view(np.float64).reshape(n)
+    return pos, mom, spin, w, tau
+
+
 class ParticleBuffer:
-    """One species in the layout qed.h describes: QED_FP64 (eleven double planes) or QED_FP32
-    (q0 = (x, y, z, px), q1 = (py, pz, sx, sy), q2 = (sz, w, tau_lo, tau_hi) float4 planes)."""
+    """One species in the layout qed.h describes: QED_FP64 (eleven double planes) or QED_FP32 (three
+    float4 planes; see pack32)."""
 
     def __init__(self, capacity: int, layout: int, charge: int, device="cuda", photons: bool = False,
                  use_begin: bool = False):
@@ -66,15 +108,7 @@ class ParticleBuffer:
             host[10] = w
             self.planes[:, :n].copy_(torch.from_numpy(host))
         else:
-            host = np.zeros((3, n, 4), dtype=np.float32)
-            host[0, :, 0:3] = pos
-            host[0, :, 3] = mom[:, 0]
-            host[1, :, 0:2] = mom[:, 1:3]
-            host[1, :, 2:4] = spin[:, 0:2]
-            host[2, :, 0] = spin[:, 2]
-            host[2, :, 1] = w
-            host[2, :, 2:4] = tau.astype(np.float64).view(np.uint32).reshape(n, 2).view(np.float32)
-            self.q[:, :n].copy_(torch.from_numpy(host))
+            self.q[:, :n].copy_(torch.from_numpy(pack32(self.charge, pos, mom, spin, w, tau)))
         self.ids[:n].copy_(torch.from_numpy(np.asarray(ids, dtype=np.uint64).view(np.int64)))
         self.counts.copy_(torch.tensor([n, n], dtype=torch.int64))
         if hasattr(self, "n_dead"):
@@ -93,12 +127,7 @@ class ParticleBuffer:
             h = self.planes[:, :n].cpu().numpy()
             pos, mom, spin, tau, w = h[0:3].T.copy(), h[3:6].T.copy(), h[6:9].T.copy(), h[9].copy(), h[10].copy()
         else:
-            h = self.q[:, :n].cpu().numpy()
-            pos = h[0, :, 0:3].astype(np.float64)
-            mom = np.column_stack([h[0, :, 3], h[1, :, 0], h[1, :, 1]]).astype(np.float64)
-            spin = np.column_stack([h[1, :, 2], h[1, :, 3], h[2, :, 0]]).astype(np.float64)
-            w = h[2, :, 1].astype(np.float64)
-            tau = np.ascontiguousarray(h[2, :, 2:4]).view(np.uint32).reshape(n, 2).copy().view(np.float64).reshape(n)
+            pos, mom, spin, w, tau = unpack32(self.charge, self.q[:, :n].cpu().numpy())
         ids = self.ids[:n].cpu().numpy().view(np.uint64).copy()
         return {"pos": pos, "mom": mom, "spin": spin, "tau": tau, "w": w, "id": ids}
 

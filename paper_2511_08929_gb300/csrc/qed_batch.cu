@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     Tl.nlc_rate = sh.rates;
     Tl.nbw_rate = sh.rates + 2 * T.n_chi;
     const int W2 = 2 * gridDim.x * WARPS;
-    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[C_N] = {};
     int2* ring = s_chunks + warp * kChunkRing;
     // the copy walk (warp-uniform): tile pt of a chunk ending at pe, the chunks put in the ring (pk), the
     // prefetched take (ns, nsz; lane 0 adds, the warp shares the result)
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
                                                                    const ClockDev* __restrict__ clk, Tab64 X64,
                                                                    qed_counters* ctr) {
     const unsigned long long n = clk->n_events;
-    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[C_N] = {};
     const int lane = threadIdx.x & 31;
     const unsigned long long warps = (unsigned long long)gridDim.x * (kEventThreads / 32);
     for (unsigned long long k = ((unsigned long long)blockIdx.x * (kEventThreads / 32) + (threadIdx.x >> 5)) * 32; k < n;

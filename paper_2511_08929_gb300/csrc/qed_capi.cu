@@ -29,7 +29,7 @@ extern "C" const char* qed_status_string(int32_t s) {
 
 namespace qed {
 
-__global__ void init_tau_kernel(PartDev P, int layout, uint64_t seed, int64_t begin) {
+__global__ void init_tau_kernel(PartDev P, int layout, bool photon, uint64_t seed, int64_t begin) {
     const int64_t n = min(*P.count, P.capacity);
     for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double tau = birth_tau(P.id[i], seed);
@@ -37,10 +37,11 @@ __global__ void init_tau_kernel(PartDev P, int layout, uint64_t seed, int64_t be
             P.tau[i] = tau;
         } else {
             const long long b = __double_as_longlong(tau);
-            float4 q = P.q2[i];
+            float4* plane = photon ? P.q1 : P.q2;  // FP32 photons keep tau in q1, leptons in q2
+            float4 q = plane[i];
             q.z = __int_as_float((int)(unsigned)(b & 0xffffffffll));
             q.w = __int_as_float((int)(unsigned)((unsigned long long)b >> 32));
-            P.q2[i] = q;
+            plane[i] = q;
         }
     }
 }
@@ -149,7 +150,8 @@ static bool valid_step(const qed_step_desc* s) {
 
 extern "C" qed_status qed_init_tau(qed_particles* p, uint64_t seed, int64_t begin, void* stream) {
     if (check_particles(p, false) != QED_OK || begin < 0) return QED_ERR_ARG;
-    init_tau_kernel<<<launch_blocks(p->capacity, 256), 256, 0, (cudaStream_t)stream>>>(part_dev(p), p->layout, seed, begin);
+    init_tau_kernel<<<launch_blocks(p->capacity, 256), 256, 0, (cudaStream_t)stream>>>(part_dev(p), p->layout,
+                                                                                       p->charge == QED_PHOTON, seed, begin);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 

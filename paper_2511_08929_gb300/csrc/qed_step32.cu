@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kT32, QED_MIN_BLOCKS) step32_kernel(TabP<float
     C.F = F;
     C.S = S;
     C.q = q;
-    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[C_N] = {};
     if (lane == 0)
         for (int s = 0; s < kStages; ++s) ts.issue(s);
     int qn = 0;  // queued event indices (warp-uniform)

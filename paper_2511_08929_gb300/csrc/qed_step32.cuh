@@ -3,8 +3,10 @@
 //
 // Arithmetic split (Sec. 5.1, 5.2, 6): the Boris and T-BMT pushers, chi, the basis, the rate lookups and
 // all event sampling in FP32; the optical depth is accumulated in FP64 and the excess |s|^2 - 1 of a
-// spin / Stokes vector that leaves the unit ball is computed in FP64.  Particles are three float4 planes
-// q0 = (x, y, z, p_x), q1 = (p_y, p_z, s_x, s_y), q2 = (s_z, w, tau_lo, tau_hi).
+// spin / Stokes vector that leaves the unit ball is computed in FP64.  Particles are three float4 planes:
+// leptons q0 = (x, y, z, p_x), q1 = (p_y, p_z, s_x, s_y), q2 = (s_z, w, tau_lo, tau_hi); photons
+// q0 = (x, y, z, P_x), q1 = (P_y, P_z, tau_lo, tau_hi), q2 = (k_x, k_y, k_z, w), so that a photon step,
+// which never changes k or w, writes two planes (one when the photon has no pair rate).
 #pragma once
 #include "qed_bessel.cuh"
 #include "qed_internal.h"
@@ -146,6 +148,21 @@ __device__ __forceinline__ bool finite_state(const float4& a, const float4& b, c
     return z == 0.0f;
 }
 
+// the same test for a photon's planes: x and P_x (q0), P_y and P_z (q1), k and w (q2)
+__device__ __forceinline__ bool finite_photon(const float4& a, const float4& b, const float4& cc) {
+    float z = 0.0f * a.x;
+    z = fmaf(0.0f, a.y, z);
+    z = fmaf(0.0f, a.z, z);
+    z = fmaf(0.0f, a.w, z);
+    z = fmaf(0.0f, b.x, z);
+    z = fmaf(0.0f, b.y, z);
+    z = fmaf(0.0f, cc.x, z);
+    z = fmaf(0.0f, cc.y, z);
+    z = fmaf(0.0f, cc.z, z);
+    z = fmaf(0.0f, cc.w, z);
+    return z == 0.0f;
+}
+
 // ------------------------------------------------------------------------------------------------
 // shared memory
 // ------------------------------------------------------------------------------------------------
@@ -185,7 +202,7 @@ __device__ __forceinline__ void load_tables32(const Shared32& sh, const float* _
     }
 }
 
-enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_N };
+enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_RATE_STEPS, C_N };
 
 // per-warp counter flush (no block barrier: warps finish at different times)
 __device__ __forceinline__ void flush_warp(unsigned long long (&c)[C_N], qed_counters* ctr) {
@@ -380,6 +397,24 @@ __device__ __forceinline__ void store32(const PartDev& L, int64_t j, const F3& x
     L.q0[j] = make_float4(x.x, x.y, x.z, p.x);
     L.q1[j] = make_float4(p.y, p.z, s.x, s.y);
     L.q2[j] = make_float4(s.z, w, lo, hi);
+}
+
+// a photon: every plane (a new photon, or one that converted)
+__device__ __forceinline__ void store_photon32(const PartDev& G, int64_t j, const F3& x, const F3& k, const F3& P, float w,
+                                               double tau) {
+    float lo, hi;
+    tau_split(tau, lo, hi);
+    G.q0[j] = make_float4(x.x, x.y, x.z, P.x);
+    G.q1[j] = make_float4(P.y, P.z, lo, hi);
+    G.q2[j] = make_float4(k.x, k.y, k.z, w);
+}
+
+// a photon step: position, polarization and optical depth (k and w are unchanged)
+__device__ __forceinline__ void store_photon32_step(const PartDev& G, int64_t j, const F3& x, const F3& P, double tau) {
+    float lo, hi;
+    tau_split(tau, lo, hi);
+    G.q0[j] = make_float4(x.x, x.y, x.z, P.x);
+    G.q1[j] = make_float4(P.y, P.z, lo, hi);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -614,7 +649,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
         const int64_t slot = A->base[0] + ev;
         const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
         const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
-        store32(G, slot, st.x, k, P, st.w, birth_tau32(gid, C.S.seed));
+        store_photon32(G, slot, st.x, k, P, st.w, birth_tau32(gid, C.S.seed));
         G.id[slot] = gid;
         c[C_STORED]++;
     }
@@ -679,9 +714,9 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
                                                  const TabP<float>* Tp = nullptr) {
     const TabP<float>& T = Tp ? *Tp : C.T;  // the caller may hand the tables over from its parameters
     const F3 xold{a.x, a.y, a.z};
-    st.k = F3{a.w, b.x, b.y};
-    st.P = F3{b.z, b.w, cc.x};
-    st.w = cc.y;
+    st.k = F3{cc.x, cc.y, cc.z};
+    st.P = F3{a.w, b.x, b.y};
+    st.w = cc.w;
     field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const float en2 = dot(st.k, st.k);
     st.en = sqrt_(en2);
@@ -727,7 +762,7 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, 
         k = st.k;
         P = st.P;
         w = st.w;
-        tauf = tau_join(cc.z, cc.w);
+        tauf = tau_join(b.z, b.w);
         if (fl & QED_F_TAU) tauf -= widen_pos(st.Wx * C.S.dt_f);
         const uint64_t id = G.id[j];
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
@@ -811,11 +846,11 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, 
         if (ok) {
             c[C_EVENTS]++;
             c[C_STORED] += 2;
-            store32(G, j, x, F3{0, 0, 0}, P, 0.0f, tauf);  // converted: inert until compaction
+            store_photon32(G, j, x, F3{0, 0, 0}, P, 0.0f, tauf);  // converted: inert until compaction
         } else {
             c[C_DROPPED]++;
             if (have) record_error(ctr, QED_ERR_CAPACITY, j);
-            store32(G, j, x, k, P, w, tauf);  // survives and retries next step
+            store_photon32_step(G, j, x, P, tauf);  // survives and retries next step
         }
     }
 }
@@ -825,14 +860,21 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
                                                   const float4& cc, qed_counters* ctr, unsigned long long* c, const TabP<float>* Tp = nullptr) {
     const uint32_t fl = flags_of<FIX>(C);
     const float dt = C.S.dt_f;
-    if (!finite_state(a, b, cc)) {
+    if (!finite_photon(a, b, cc)) {
         c[C_NONFINITE]++;
         record_error(ctr, QED_ERR_NAN, j);
         return false;
     }
     PState st;
     photon_classical<FIX>(C, a, b, cc, st, c, Tp);
-    const double tau = tau_join(cc.z, cc.w);
+    if (!st.qed || (st.Wp == 0.0f && st.Wm == 0.0f)) {
+        // no pair rate here (outside the pulse, or W_+ and W_- below the float range): the optical depth
+        // stays, the non-pair update is the identity and P, k, w do not change, so only the position
+        // plane is written (16 of the photon's 48 bytes)
+        G.q0[j] = make_float4(st.x.x, st.x.y, st.x.z, a.w);
+        return false;
+    }
+    const double tau = tau_join(b.z, b.w);
     double tauf = tau;
     if (st.qed && st.Wx > 0.0f) {
         if (fl & QED_F_TAU) {
@@ -861,7 +903,8 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
             Pf = stokes_to_P(xn, st.eps, st.beta, st.khat);
         }
     }
-    store32(G, j, st.x, st.k, Pf, st.w, tauf);
+    store_photon32_step(G, j, st.x, Pf, tauf);
+    c[C_RATE_STEPS]++;
     return false;
 }
 

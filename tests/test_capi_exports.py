@@ -19,8 +19,8 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     # the ABI version and status strings need no device
     assert lib.qed_abi_version() == 2
-    # qed_counters: seven 64-bit counters, status, pad, first_bad, and the call's reservation block
-    assert ctypes.sizeof(B.QedCounters) == 7 * 8 + 8 + 8 + 4 * 8
+    # qed_counters: eight 64-bit counters, status, pad, first_bad, and the call's reservation block
+    assert ctypes.sizeof(B.QedCounters) == 8 * 8 + 8 + 8 + 4 * 8
     lib.qed_status_string.restype = ctypes.c_char_p
     assert lib.qed_status_string(-3) == b"particle buffer capacity exhausted"
 

@@ -193,8 +193,10 @@ def test_photon_pairs_and_compaction(gpu_tables, ora_tables):
     torch.cuda.synchronize()
     assert octr.events > 200 and ctr.read().status == 0
     # photons are held to the n-step bar, and so are their daughters: a pair made at step k inherits its
-    # photon's k-step state (pairs made from the same state in one step: test_gpu_overflow, at 1e-5)
-    f1, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons")
+    # photon's k-step state (pairs made from the same state in one step: test_gpu_overflow, at 1e-5).
+    # P is compared headless: a photon without pair rate keeps its P as loaded, the oracle rewrites it in
+    # its own representative (P and -P_perp are the same Stokes vector)
+    f1, _ = compare_with_flips(gG.read(), oG.view(), 1e-5 * steps, "photons", P_headless=True)
     f2, _ = compare_with_flips(gE.read(), oE.view(), 1e-5 * steps, "electrons")
     f3, _ = compare_with_flips(gP.read(), oP.view(), 1e-5 * steps, "positrons")
     assert f1 + f2 + f3 <= max(1, 1e-5 * 4000 * steps), (f1, f2, f3)
