@@ -430,9 +430,24 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
                                                                    const long long* __restrict__ ev,
                                                                    const ClockDev* __restrict__ clk, Tab64 X64,
                                                                    qed_counters* ctr) {
+    __shared__ ExactQ eq[kEventThreads / 32];  // per warp: the events taken again in FP64
     const unsigned long long n = clk->n_events;
     unsigned long long c[C_N] = {};
     const int lane = threadIdx.x & 31;
+    ExactQ& q = eq[threadIdx.x >> 5];
+    if (lane == 0) q.n = 0;
+    __syncwarp();
+    // lanes take queued entries [from, from + cnt), each with the context of its own segment
+    auto drain = [&](int from, int cnt) {
+        if (lane < cnt) {
+            const int key = q.key[from + lane];
+            const SegCtx& X = ctx[key & 0x3FFFFFFF];
+            const InstDev& I = inst[X.ii];
+            lepton_exact_one(X.C, X64, I.F64, I.sp[X.sp], I.sp[2], q.j[from + lane], q.slot[from + lane],
+                             (key >> 30) & 1);
+        }
+        __syncwarp();
+    };
     const unsigned long long warps = (unsigned long long)gridDim.x * (kEventThreads / 32);
     for (unsigned long long k = ((unsigned long long)blockIdx.x * (kEventThreads / 32) + (threadIdx.x >> 5)) * 32; k < n;
          k += warps * 32) {
@@ -445,10 +460,17 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
         const bool ph = X.sp == 2;
         // both passes are warp-collective; a lane takes part in the one of its species with its particle
         if (__ballot_sync(0xffffffffu, j >= 0 && !ph))
-            lepton_events(X.C, X64, I.F64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c);
+            lepton_events(X.C, X64, I.F64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c, &q, s);
         if (__ballot_sync(0xffffffffu, j >= 0 && ph))
             photon_events(X.C, X64, ph ? j : -1, I.sp[2], I.sp[0], I.sp[1], &I.app[1], ctr, c);
+        const int qn = q.n;
+        if (qn >= 32) {  // 32 queued events in FP64 with every lane busy
+            drain(qn - 32, 32);
+            if (lane == 0) q.n = qn - 32;
+            __syncwarp();
+        }
     }
+    drain(0, q.n);
     flush_warp(c, ctr);
 }
 

@@ -531,12 +531,48 @@ static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X,
     P_out = narrow(stokes_to_P(xi, eps, beta, khat));
 }
 
+// Events to be taken again in FP64, queued per warp so that the FP64 code runs with all 32 lanes busy
+// (one ill-conditioned lane would otherwise make its whole warp run it).  An entry names the lepton, the
+// photon's reserved slot (-1: no photon stored) and the caller's context key with the branch in bit 30.
+constexpr int kExactQ = 64;  // entries per warp; drained 32 at a time
+struct ExactQ {
+    int64_t j[kExactQ];
+    int64_t slot[kExactQ];
+    int key[kExactQ];
+    int n;
+};
+
+// One queued event in FP64 (per lane, not warp-collective): the lepton's stored state is still the one
+// the step began with; its event outcome and its photon (in the reserved slot) are written here.
+static __device__ __noinline__ void lepton_exact_one(const Ctx& C, const Tab64& X, const FieldP<double>& F64,
+                                                    const PartDev& L, const PartDev& G, int64_t j, int64_t slot,
+                                                    bool down) {
+    const uint32_t fl = C.S.flags;
+    const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
+    const uint64_t id = L.id[j];
+    const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
+    const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
+    const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
+    F3 x, pf, sf, k, P;
+    lepton_event64(C, X, F64, a, b, cc, down, w1, w2, x, pf, sf, k, P);
+    const double tau_new = (fl & QED_F_TAU) ? exp_draw(w0.x, w0.y) : tau_join(cc.z, cc.w);
+    store32(L, j, x, pf, sf, cc.y, tau_new);
+    if (slot >= 0) {
+        const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
+        const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
+        store_photon32(G, slot, x, k, P, cc.y, birth_tau32(gid, C.S.seed));
+        G.id[slot] = gid;
+    }
+}
+
 // the event pass of one warp (all 32 lanes call it): a lane with j >= 0 takes particle j of buffer L,
 // whose step context is C and whose photons go to G through the reservation A (lanes may differ in all
-// three; A is NULL when the caller keeps no photons)
+// three; A is NULL when the caller keeps no photons).  q (may be NULL): the warp's queue for the events
+// taken again in FP64, with the lane's context key; without it they are taken here.
 static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, const FieldP<double>& F64, int64_t j,
                                                  const PartDev& L, const PartDev& G, AppendState* A,
-                                                 qed_counters* ctr, unsigned long long* c) {
+                                                 qed_counters* ctr, unsigned long long* c, ExactQ* q = nullptr,
+                                                 int key = 0) {
     // The lepton's outcome (energy fraction, recoil, spin) and the photon's polarization for every event,
     // then the photon's slot reservation: an event whose photon does not fit is not applied.
     const uint32_t fl = C.S.flags;
@@ -546,7 +582,8 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
     F3 k{0, 0, 0}, pf{0, 0, 0}, sf{0, 0, 0}, P{0, 0, 0};
     float xi[3] = {0.0f, 0.0f, 0.0f};
     double tau_kept = 0.0, tau_new = 0.0;
-    bool exact = false;  // the event was taken in FP64 (k, P and the lepton's x, p, s from lepton_event64)
+    bool exact = false;  // the event is taken in FP64 (k, P and the lepton's x, p, s from lepton_event64)
+    bool down = false;
     if (j >= 0) {
         const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
         lepton_classical<0, true>(C, a, b, cc, st, nullptr);  // the streaming pass's step, accurate fields
@@ -558,7 +595,6 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
         tau_kept = (fl & QED_F_TAU) ? tau0 - widen_pos(st.Ws * C.S.dt_f) : tau0;
         tau_new = tau_kept;
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
-        bool down;
         if (fl & QED_F_TAU) down = u52f(w0.z, w0.w) * st.Ws < st.Wdn;
         else down = u52f(w0.x, w0.y) < st.Wdn * C.S.dt_f;
         const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
@@ -626,32 +662,48 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
                 }
             }
         }
-        if (exact) lepton_event64(C, X, F64, a, b, cc, down, w1, w2, st.x, pf, sf, k, P);
-        else P = stokes_to_P(xi, st.eps, st.beta, st.khat);
+        if (exact && q == nullptr) lepton_event64(C, X, F64, a, b, cc, down, w1, w2, st.x, pf, sf, k, P);
+        else if (!exact) P = stokes_to_P(xi, st.eps, st.beta, st.khat);
         if (fl & QED_F_TAU) tau_new = exp_draw(w0.x, w0.y);
         want = sqrt_(dot(k, k)) >= C.S.store_min_f;
         if (!want) c[C_BELOW]++;
     }
     const long long ev = reserve_event(A, want);
     const bool keep = want && A != nullptr && ev < A->budget;
+    const bool refused = want && A != nullptr && !keep;
+    const bool queued = j >= 0 && exact && q != nullptr && !refused;  // stored by lepton_exact_one later
     if (j >= 0) {
-        if (want && A != nullptr && !keep) {  // no room for the photon: the event is not applied
+        if (refused) {  // no room for the photon: the event is not applied
             c[C_DROPPED]++;
             record_error(ctr, QED_ERR_CAPACITY, j);
             store32(L, j, st.x, st.p, st.s, st.w, tau_kept);
         } else {
             c[C_EVENTS]++;
             if (want && A == nullptr) c[C_DROPPED]++;  // the caller keeps no photons
-            store32(L, j, st.x, pf, sf, st.w, tau_new);
+            if (!queued) store32(L, j, st.x, pf, sf, st.w, tau_new);
         }
     }
     if (keep) {
-        const int64_t slot = A->base[0] + ev;
-        const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
-        const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
-        store_photon32(G, slot, st.x, k, P, st.w, birth_tau32(gid, C.S.seed));
-        G.id[slot] = gid;
         c[C_STORED]++;
+        if (!queued) {
+            const int64_t slot = A->base[0] + ev;
+            const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
+            const uint64_t gid = (uint64_t)wc.x | ((uint64_t)wc.y << 32);
+            store_photon32(G, slot, st.x, k, P, st.w, birth_tau32(gid, C.S.seed));
+            G.id[slot] = gid;
+        }
+    }
+    if (q != nullptr) {  // warp-uniform
+        const unsigned m = __ballot_sync(0xffffffffu, queued);
+        if (queued) {
+            const int e = q->n + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+            q->j[e] = j;
+            q->slot[e] = keep ? A->base[0] + ev : -1;
+            q->key[e] = key | (down ? (1 << 30) : 0);
+        }
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) q->n += __popc(m);
+        __syncwarp();
     }
 }
 
@@ -727,13 +779,16 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     if (!(flags_of<FIX>(C) & QED_F_EMIT) || !(en2 > 0.0f)) return;
     st.chi = chi32(C, st.en, st.k, st.E, st.B);
     if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
+    st.lnchi = __logf(st.chi);
+    if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
+    nbw_rates(T, st.chi, st.lnchi, st.Wp, st.Wm);
+    // most photons are too soft, or in too weak a field, for a pair rate in the float range: nothing of
+    // the basis or the Stokes vector is needed for them (the caller moves them and stops)
+    if (st.Wp == 0.0f && st.Wm == 0.0f) return;
     if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
     if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
-    st.lnchi = __logf(st.chi);
-    if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
-    nbw_rates(T, st.chi, st.lnchi, st.Wp, st.Wm);
     const float pref = (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0 * st.en);
     st.Wp *= pref;
     st.Wm *= pref;
@@ -867,7 +922,7 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
     }
     PState st;
     photon_classical<FIX>(C, a, b, cc, st, c, Tp);
-    if (!st.qed || (st.Wp == 0.0f && st.Wm == 0.0f)) {
+    if (!st.qed) {
         // no pair rate here (outside the pulse, or W_+ and W_- below the float range): the optical depth
         // stays, the non-pair update is the identity and P, k, w do not change, so only the position
         // plane is written (16 of the photon's 48 bytes)
