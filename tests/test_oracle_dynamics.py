@@ -271,3 +271,101 @@ def test_unpolarized_photon_beams_evolve_identically(st_tables):
     # without the non-pair update the circular construction cannot move
     m2 = {c: _nopair_run(c, fl & ~O.F_NONTRANSITION, st_tables) for c in ("linear", "circular")}
     assert abs(m2["circular"][0]) < 0.01 and m2["linear"][0] > 0.02
+
+
+# ------------------------------------------------------------------------------------------
+# buffer overflow: an event whose daughters find no slot is not applied (Sec. 4.3, reading R2)
+# ------------------------------------------------------------------------------------------
+def test_overflow_emission_not_applied(small_tables):
+    """No classical force, every lepton close to its optical-depth crossing.  One step with room for
+    every photon (run A) against one with room for half of them (run B): the first half of the
+    emitters (parent order) end as in A; each refused emitter keeps its initial momentum and spin, which
+    is A's recoiled momentum plus A's photon (p_i = p_f + hbar k, Sec. 5.1), and a spent optical depth,
+    so it emits in the next step.  A rule that applied the recoil or discarded the photon fails here."""
+    b = I.random_states(400, seed=21)
+    tau0 = np.full(400, 1e-4)
+    f = O.field(O.FIELD_CONST, E0=(0, 0, 0), B0=(30.0, 10.0, 0.0), eta0=ETA0)
+    fl = O.F_FULL & ~O.F_PUSH & ~O.F_TBMT
+    st = O.step_desc(0.05, 0.0, 0, 9, fl)
+
+    def run(cap):
+        L = O.Particles.from_arrays(400, b["pos"], b["mom"], b["spin"], b["w"], b["id"], tau=tau0)
+        G = O.Particles(cap)
+        return L, G, O.lepton_step(small_tables, f, st, -1, L, G)
+
+    LA, GA, cA = run(100000)
+    va, ga = LA.view(), GA.view()
+    emit = np.flatnonzero(np.any(va["mom"] != b["mom"], axis=1))
+    nA = len(emit)
+    assert cA.events == nA == GA.n and nA > 50 and cA.dropped_capacity == 0
+    c = nA // 2
+    LB, GB, cB = run(c)
+    vb, gb = LB.view(), GB.view()
+    assert cB.events == c and cB.dropped_capacity == nA - c and GB.n == c
+    # the photons that fit and their emitters are those of run A
+    for k in ("pos", "mom", "spin", "tau", "id"):
+        np.testing.assert_array_equal(gb[k], ga[k][:c])
+    applied, refused = emit[:c], emit[c:]
+    quiet = np.setdiff1d(np.arange(400), emit)
+    for k in ("pos", "mom", "spin", "tau"):
+        np.testing.assert_array_equal(vb[k][applied], va[k][applied])
+        np.testing.assert_array_equal(vb[k][quiet], va[k][quiet])
+    # refused emitters: the pre-event state, equal to A's recoil plus A's photon
+    np.testing.assert_array_equal(vb["mom"][refused], b["mom"][refused])
+    np.testing.assert_array_equal(vb["spin"][refused], b["spin"][refused])
+    pk = va["mom"][refused] + ga["mom"][c:]
+    np.testing.assert_allclose(pk, vb["mom"][refused], rtol=0,
+                               atol=1e-12 * np.abs(vb["mom"][refused]).max())
+    assert np.all(vb["tau"][refused] <= 0.0) and np.all(va["tau"][applied] > 0.0)
+    # with room in the next step every refused emitter emits
+    G2 = O.Particles(100000)
+    O.lepton_step(small_tables, f, O.step_desc(0.05, 0.05, 1, 9, fl), -1, LB, G2)
+    v2 = LB.view()
+    assert np.all(np.any(v2["mom"][refused] != b["mom"][refused], axis=1))
+
+
+def test_overflow_pair_not_applied(small_tables):
+    """Photons at chi_gamma = 3, each close to its optical-depth crossing, with room for half of the
+    pairs: the first half of the converting photons (parent order) are removed and their pairs carry
+    k (p_e + p_p = hbar k, Sec. 5.2); every other converting photon survives with its k and P unchanged
+    and a spent optical depth, and converts in the next step once there is room.  No pair is split."""
+    eps_ = 4000.0
+    b = I.photon_beam(600, eps_, direction=(1, 0, 0), P_list=[(0, 1, 0), (0, 0, 1)], seed=5)
+    Bz = 3.0 / (ETA0 * eps_)
+    f = O.field(O.FIELD_CONST, B0=(0, 0, Bz), eta0=ETA0)
+    st = O.step_desc(0.2, 0.0, 0, 7)
+    tau0 = np.full(600, 1e-6)
+
+    def run(cap_e, cap_p):
+        G = O.Particles.from_arrays(600, b["pos"], b["mom"], b["spin"], b["w"], b["id"], tau=tau0)
+        el, po = O.Particles(cap_e), O.Particles(cap_p)
+        return G, el, po, O.photon_step(small_tables, f, st, G, el, po)
+
+    GA, elA, poA, cA = run(5000, 5000)
+    nA = cA.events
+    assert nA > 50 and elA.n == poA.n == nA and GA.n == 600 - nA
+    c = nA // 2
+    GB, elB, poB, cB = run(5000, c)  # the positron buffer is the short one
+    assert cB.events == c and cB.dropped_capacity == nA - c and elB.n == poB.n == c
+    gav, gbv = GA.view(), GB.view()
+    ea, eb, pa, pb = elA.view(), elB.view(), poA.view(), poB.view()
+    for k in ("pos", "mom", "spin", "tau", "id"):
+        np.testing.assert_array_equal(eb[k], ea[k][:c])
+        np.testing.assert_array_equal(pb[k], pa[k][:c])
+    np.testing.assert_allclose(eb["mom"] + pb["mom"], np.tile([eps_, 0, 0], (c, 1)), rtol=1e-14, atol=1e-9)
+    # the photons of run A's second half of pairs survive in B, unchanged but for x and tau
+    gone_a = set(int(i) for i in b["id"]) - set(int(i) for i in gav["id"])
+    left_b = {int(i): j for j, i in enumerate(gbv["id"])}
+    refused = [i for i in gone_a if i in left_b]
+    assert len(refused) == nA - c and GB.n == 600 - c
+    row = {int(i): j for j, i in enumerate(b["id"])}
+    for i in refused:
+        jb, j0 = left_b[i], row[i]
+        np.testing.assert_array_equal(gbv["mom"][jb], b["mom"][j0])
+        np.testing.assert_array_equal(gbv["spin"][jb], b["spin"][j0])
+        assert gbv["tau"][jb] <= 0.0
+    el2, po2 = O.Particles(5000), O.Particles(5000)
+    c2 = O.photon_step(small_tables, f, O.step_desc(0.2, 0.2, 1, 7), GB, el2, po2)
+    assert c2.events >= len(refused)
+    left2 = set(int(i) for i in GB.view()["id"])
+    assert not (set(refused) & left2)
