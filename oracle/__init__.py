@@ -40,6 +40,9 @@ F_RESOLVED = 1 << 9
 F_MOVE = 1 << 10
 F_SPIN_EVENT = 1 << 11
 F_POL_EVENT = 1 << 12
+F_AMM = 1 << 13
+F_LOOP = 1 << 14
+F_G2 = 1 << 15
 F_FULL = (F_TAU | F_RECOIL | F_SPIN_COLLAPSE | F_POL_COLLAPSE | F_NONTRANSITION | F_PUSH | F_TBMT | F_EMIT
           | F_RESOLVED | F_MOVE | F_SPIN_EVENT | F_POL_EVENT)
 
@@ -64,7 +67,8 @@ class TableDesc(C.Structure):
 
 class _Tables(C.Structure):
     _fields_ = [("d", TableDesc), ("nlc_rate", C.POINTER(C.c_double)), ("nbw_rate", C.POINTER(C.c_double)),
-                ("nlc_icdf", C.POINTER(C.c_double)), ("nbw_icdf", C.POINTER(C.c_double))]
+                ("nlc_icdf", C.POINTER(C.c_double)), ("nbw_icdf", C.POINTER(C.c_double)),
+                ("amm", C.POINTER(C.c_double))]
 
 
 class Field(C.Structure):
@@ -126,6 +130,13 @@ def lib():
             for fn in ("orc_nlc_rate_lookup", "orc_nbw_rate_lookup"):
                 getattr(L, fn).restype = _D
                 getattr(L, fn).argtypes = [_P(_Tables), C.c_int, _D, _P(C.c_int)]
+            L.orc_airy_scorer.argtypes = [_D, _P(_D)]
+            L.orc_amm.restype = _D
+            L.orc_amm.argtypes = [_D]
+            L.orc_amm_build.restype = C.c_int
+            L.orc_amm_build.argtypes = [_P(TableDesc), _P(_D)]
+            L.orc_amm_lookup.restype = _D
+            L.orc_amm_lookup.argtypes = [_P(_Tables), _D]
             L.orc_icdf_lookup.restype = _D
             L.orc_icdf_lookup.argtypes = [_P(_Tables), C.c_int, C.c_int, _D, _D]
             L.orc_nlc_lambda.restype = _D
@@ -262,6 +273,18 @@ def mlp_cdf(chi: float, s: float, ln_up: float) -> float:
     return lib().orc_mlp_cdf(float(chi), float(s), float(ln_up))
 
 
+def airy_scorer(z: float):
+    """(Ai(z), Gi(z)) for z >= 0 from the integral definition (App. A.1)."""
+    out = np.zeros(2)
+    lib().orc_airy_scorer(float(z), _dp(out))
+    return float(out[0]), float(out[1])
+
+
+def amm(chi: float) -> float:
+    """Field-dependent anomalous moment a(chi) (one-loop Scorer term), by quadrature."""
+    return lib().orc_amm(float(chi))
+
+
 def nlc_lambda(chi, up):
     return lib().orc_nlc_lambda(chi, up)
 
@@ -299,7 +322,21 @@ class Tables:
         if rc != 0:
             raise ValueError("bad table description")
         self._s = _Tables(self.desc, _dp(self.nlc_rate), _dp(self.nbw_rate), _dp(self.nlc_icdf),
-                          _dp(self.nbw_icdf))
+                          _dp(self.nbw_icdf), None)
+        self.amm = None
+
+    def ensure_amm(self):
+        """Build the ln a(chi) table on the rate grid (needed by the F_AMM and F_LOOP steps)."""
+        if self.amm is None:
+            amm = np.zeros(self.desc.n_chi)
+            if lib().orc_amm_build(C.byref(self.desc), _dp(amm)) != 0:
+                raise ValueError("bad table description")
+            self.amm = amm
+            self._s.amm = _dp(self.amm)
+        return self
+
+    def amm_lookup(self, chi):
+        return lib().orc_amm_lookup(self.ref, chi)
 
     @property
     def ref(self):
@@ -415,6 +452,8 @@ def lepton_step(tb: Tables, f: Field, st: Step, charge: int, leptons: Particles,
     ctr = ctr if ctr is not None else Counters()
     rc = lib().orc_lepton_step(tb.ref, C.byref(f), C.byref(st), int(charge), leptons.ref,
                                photons.ref if photons is not None else None, C.byref(ctr))
+    if rc == -2:
+        raise ValueError("flags need the a(chi) table (Tables.ensure_amm) or contradict each other")
     if rc != 0:
         raise MemoryError("oracle lepton step failed")
     return ctr

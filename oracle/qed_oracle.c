@@ -448,6 +448,7 @@ typedef struct {
     double *nbw_rate; /* [2][n_chi] */
     double *nlc_icdf; /* [2][n_chi][n_r] */
     double *nbw_icdf; /* [2][n_chi][n_r] */
+    double *amm;      /* [n_chi] ln a(chi_i), the field-dependent anomalous moment; NULL if not built */
 } orc_tables;
 
 /* Solve c(t) = r for t by bisection on the panel that brackets r, followed by
@@ -607,6 +608,94 @@ double orc_nbw_mu(double chi, double x)
 }
 
 /* ------------------------------------------------------------------------- */
+/* One-loop self-energy terms (App. A.1) and the field-dependent anomalous     */
+/* moment g(chi) = 2 + 2 a(chi) (Sec. 8.6.2).                                  */
+/*                                                                            */
+/* Airy and Scorer functions from their integral definition (App. A.1):       */
+/*   Ai(z) + i Gi(z) = (1/pi) int_0^inf exp(i (z t + t^3/3)) dt.               */
+/* For z >= 0 the integrand is analytic and bounded in the sector             */
+/* 0 <= arg t <= pi/6 (there Re(i t^3) <= 0 and Re(i z t) <= 0), so by Cauchy  */
+/* the ray t = e^{i pi/6} s gives the same integral, now absolutely convergent:*/
+/*   Ai + i Gi = (e^{i pi/6}/pi) int_0^inf exp(-s^3/3 - z s/2)                 */
+/*                                   exp(i sqrt(3) z s / 2) ds.               */
+/* Gauss-Legendre panels on [0, S], S where the exponent reaches -45.  Gi has  */
+/* no cancellation (Gi ~ 1/(pi z) for large z); Ai does (it decays like        */
+/* exp(-2 z^{3/2}/3) from terms of size 1/z), so Ai is accurate to ~1e-16 in   */
+/* absolute terms only.                                                       */
+/* ------------------------------------------------------------------------- */
+void orc_airy_scorer(double z, double out[2])
+{
+    gl_init();
+    double S = fmin(cbrt(135.0), 90.0 / fmax(z, 1e-300));
+    const int np = 48;
+    double h = S / np, c = 0.0, sn = 0.0;
+    double w = 0.5 * ORC_SQRT3 * z;
+    for (int p = 0; p < np; ++p) {
+        double a = p * h, r = 0.5 * h;
+        for (int k = 0; k < gl_n; ++k) {
+            double s = a + r + r * gl_x[k];
+            double e = exp(-s * s * s / 3.0 - 0.5 * z * s) * gl_w[k] * r;
+            c += e * cos(w * s);
+            sn += e * sin(w * s);
+        }
+    }
+    /* e^{i pi/6} = (sqrt(3)/2, 1/2) */
+    out[0] = (0.5 * ORC_SQRT3 * c - 0.5 * sn) / ORC_PI; /* Ai */
+    out[1] = (0.5 * c + 0.5 * ORC_SQRT3 * sn) / ORC_PI; /* Gi */
+}
+
+/* Field-dependent anomalous moment from the Scorer term of the loop (App. A.1, the Gi(z)/sqrt(z) part of
+ * R_if), with z = (u/chi)^{2/3}, u = lambda/(1 - lambda):
+ *   a(chi) = (alpha/chi) int_0^1 dlambda lambda Gi(z)/sqrt(z)
+ *          = (alpha/chi) int_0^inf du u/(1+u)^3 Gi(z)/sqrt(z).
+ * Normalised so that chi -> 0 gives Schwinger's alpha/(2 pi) (Gi(z) -> 1/(pi z)).  With u = chi v^3
+ * (z = v^2) and v = e^t:  a(chi) = 3 alpha chi int v^5 Gi(v^2)/(1 + chi v^3)^3 dt, a smooth integrand on
+ * t in [ln(1e-3 m), ln(1e3 M)], m = min(1, chi^{-1/3}), M = max(1, chi^{-1/3}) (the ends contribute below
+ * 1e-15 of the result); Gauss-Legendre panels of width 1/8 in t. */
+double orc_amm(double chi)
+{
+    gl_init();
+    double c3 = cbrt(1.0 / chi);
+    double t0 = log(1e-3 * fmin(1.0, c3)), t1 = log(1e3 * fmax(1.0, c3));
+    int np = (int)ceil((t1 - t0) * 8.0);
+    double h = (t1 - t0) / np, acc = 0.0;
+    for (int p = 0; p < np; ++p) {
+        double a = t0 + p * h, r = 0.5 * h;
+        for (int k = 0; k < gl_n; ++k) {
+            double t = a + r + r * gl_x[k];
+            double v = exp(t);
+            double ag[2];
+            orc_airy_scorer(v * v, ag);
+            double d = 1.0 + chi * v * v * v;
+            acc += gl_w[k] * r * pow(v, 5.0) * ag[1] / (d * d * d);
+        }
+    }
+    return 3.0 * ORC_ALPHA * chi * acc;
+}
+
+/* Table of ln a(chi_i) on the rate grid (one entry per chi node). */
+int orc_amm_build(const orc_table_desc *d, double *amm)
+{
+    if (d->n_chi < 2 || !(d->chi_min > 0) || !(d->chi_max > d->chi_min)) return -1;
+    gl_init();
+    double dl = (log(d->chi_max) - log(d->chi_min)) / (d->n_chi - 1);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < d->n_chi; ++i) amm[i] = log(orc_amm(exp(log(d->chi_min) + i * dl)));
+    return 0;
+}
+
+/* a(chi) from the table: linear in (ln chi, ln a) between nodes, the end values outside the grid
+ * (below chi_min a(chi) differs from alpha/(2 pi) by less than 1e-6 of it).  Returns the zero-field value
+ * alpha/(2 pi) if no table was built. */
+double orc_amm_lookup(const orc_tables *t, double chi)
+{
+    if (!t->amm) return ORC_ALPHA / (2.0 * ORC_PI);
+    int i; double f;
+    chi_coord(&t->d, chi > 0.0 ? chi : t->d.chi_min, &i, &f);
+    return exp((1.0 - f) * t->amm[i] + f * t->amm[i + 1]);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Fields: analytic plane waves propagating along z (stand-in for the PIC      */
 /* grid fields of Sec. 4).  E, B in units of m c omega / e.                     */
 /* ------------------------------------------------------------------------- */
@@ -671,7 +760,10 @@ enum {
     ORC_F_RESOLVED = 1u << 9,      /* rates and sampling depend on s.beta (leptons) / xi3 (photons) */
     ORC_F_MOVE = 1u << 10,         /* position advance */
     ORC_F_SPIN_EVENT = 1u << 11,   /* lepton spin changes at emission; pair daughters get spins */
-    ORC_F_POL_EVENT = 1u << 12     /* emitted photons get the Stokes vector of F (else unpolarized) */
+    ORC_F_POL_EVENT = 1u << 12,    /* emitted photons get the Stokes vector of F (else unpolarized) */
+    ORC_F_AMM = 1u << 13,          /* T-BMT with the field-dependent a(chi) (Sec. 8.6.2) instead of alpha/(2 pi) */
+    ORC_F_LOOP = 1u << 14,         /* Scorer term of the loop in the no-emission update; T-BMT with g = 2 */
+    ORC_F_G2 = 1u << 15            /* T-BMT with g = 2 (a = 0), the comparison run of Sec. 8.6.2 */
 };
 
 typedef struct {
@@ -821,14 +913,19 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
         double bxE[3];
         cross3(bb, E, bxE);
         double Om[3];
+        /* anomalous moment: alpha/(2 pi); g(chi) with chi of the time-centred momentum (Sec. 8.6.2);
+         * none (g = 2) for the comparison run, or when the loop's Scorer term carries it */
+        double aT = aE;
+        if (fl & (ORC_F_G2 | ORC_F_LOOP)) aT = 0.0;
+        else if (fl & ORC_F_AMM) aT = orc_amm_lookup(tb, chi_of(fd->eta0, gb, pb, E, B));
         if (fl & ORC_F_TBMT_PAPER) {
             /* as printed: (a + 1/gamma)(B - v x E) - (a gamma/(gamma+1))(v.B) v */
             for (int i = 0; i < 3; ++i)
-                Om[i] = -q * ((aE + 1.0 / gb) * (B[i] - bxE[i]) - (aE * gb / (gb + 1.0)) * bB * bb[i]);
+                Om[i] = -q * ((aT + 1.0 / gb) * (B[i] - bxE[i]) - (aT * gb / (gb + 1.0)) * bB * bb[i]);
         } else {
             /* standard (Jackson 11.170): (a + 1/gamma) B - (a gamma/(gamma+1))(beta.B) beta - (a + 1/(gamma+1)) beta x E */
             for (int i = 0; i < 3; ++i)
-                Om[i] = -q * ((aE + 1.0 / gb) * B[i] - (aE * gb / (gb + 1.0)) * bB * bb[i] - (aE + 1.0 / (gb + 1.0)) * bxE[i]);
+                Om[i] = -q * ((aT + 1.0 / gb) * B[i] - (aT * gb / (gb + 1.0)) * bB * bb[i] - (aT + 1.0 / (gb + 1.0)) * bxE[i]);
         }
         double om = sqrt(dot3(Om, Om));
         if (om > 0.0) {
@@ -956,6 +1053,22 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                     }
                 }
             }
+            if (!event && (fl & ORC_F_LOOP)) {
+                /* Scorer term of the loop Mueller matrix (App. A.1, R_if): the antisymmetric part in the
+                 * (k, eps) plane turns the spin about the rest-frame magnetic field, at a(chi) times the
+                 * rest-frame field chi/eta0, in the lepton's proper time (1/gamma per unit lab time), with
+                 * the T-BMT sense (-q).  B' = gamma (B - v x E) - gamma^2/(gamma+1) (v.B) v. */
+                double v[3] = {p[0] / gam, p[1] / gam, p[2] / gam};
+                double vxE[3];
+                cross3(v, E, vxE);
+                double vB = dot3(v, B), Bp[3];
+                for (int i = 0; i < 3; ++i) Bp[i] = gam * (B[i] - vxE[i]) - gam * gam / (gam + 1.0) * vB * v[i];
+                double nb = sqrt(dot3(Bp, Bp));
+                if (nb > 0.0) {
+                    double n[3] = {-q * Bp[0] / nb, -q * Bp[1] / nb, -q * Bp[2] / nb};
+                    rotate(sf, n, orc_amm_lookup(tb, chi) * chi / (fd->eta0 * gam) * dt);
+                }
+            }
         }
     }
     L->x[j] = x[0]; L->y[j] = x[1]; L->z[j] = x[2];
@@ -968,6 +1081,10 @@ int orc_lepton_step(const orc_tables *tb, const orc_field *fd, const orc_step *s
                     orc_particles *L, orc_particles *ph, orc_counters *ctr)
 {
     int64_t n = L->n;
+    /* g(chi) and the loop term need the a(chi) table; a(chi) in T-BMT and the loop's Scorer term are the
+     * same anomalous moment, and g = 2 excludes both */
+    if ((st->flags & (ORC_F_AMM | ORC_F_LOOP)) && !tb->amm) return -2;
+    if ((st->flags & ORC_F_AMM) && (st->flags & (ORC_F_LOOP | ORC_F_G2))) return -2;
     orc_result *res = (orc_result *)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_result));
     if (!res) return -1;
 #pragma omp parallel for schedule(static)
