@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define QED_ABI_VERSION 2
+#define QED_ABI_VERSION 3
 
 typedef enum {
     QED_OK = 0,
@@ -76,7 +76,16 @@ enum {
     QED_F_RESOLVED = 1u << 9,      /* rates and sampling depend on s.beta / xi3 (Sec. 5.1, 5.2) */
     QED_F_MOVE = 1u << 10,         /* position advance */
     QED_F_SPIN_EVENT = 1u << 11,   /* lepton spin changes at emission; pair daughters get spins */
-    QED_F_POL_EVENT = 1u << 12     /* emitted photons carry the Stokes vector of F (else unpolarized) */
+    QED_F_POL_EVENT = 1u << 12,    /* emitted photons carry the Stokes vector of F (else unpolarized) */
+    /* The anomalous moment in the spin precession (Sec. 8.6.2, App. A.1 one-loop terms).  Default: the
+     * zero-field a = alpha/(2 pi) in T-BMT.  QED_F_AMM: T-BMT with the field-dependent a(chi) of the loop's
+     * Scorer term, chi taken at the time-centred momentum.  QED_F_LOOP: T-BMT with g = 2, and the loop's
+     * Scorer term applied in the no-emission update instead (a turn about the rest-frame magnetic field
+     * by a(chi) chi dt / (eta0 gamma); needs QED_F_EMIT).  QED_F_G2: T-BMT with g = 2 and no loop term
+     * (the paper's g = 2 comparison).  QED_F_AMM with QED_F_LOOP or QED_F_G2 is QED_ERR_ARG. */
+    QED_F_AMM = 1u << 13,
+    QED_F_LOOP = 1u << 14,
+    QED_F_G2 = 1u << 15
 };
 #define QED_F_FULL                                                                                     \
     (QED_F_TAU | QED_F_RECOIL | QED_F_SPIN_COLLAPSE | QED_F_POL_COLLAPSE | QED_F_NONTRANSITION |       \
@@ -209,6 +218,11 @@ qed_status qed_tables_build(const qed_table_desc *desc, qed_tables_t *out, void 
 qed_status qed_tables_export(qed_tables_t t, double *host_nlc_rate, double *host_nbw_rate, double *host_nlc_icdf,
                              double *host_nbw_icdf);
 
+/* Copy the table of the field-dependent anomalous moment to the host: ln a(chi_i) on the rate grid,
+ * double[n_chi] (one-loop Scorer term of App. A.1, a(chi) = (alpha/chi) int_0^1 dlambda lambda Gi(z)/sqrt(z),
+ * z = (lambda/(chi (1 - lambda)))^{2/3}, built in FP64 with the other tables).  Synchronous. */
+qed_status qed_tables_export_amm(qed_tables_t t, double *host_ln_a);
+
 /* Free the tables.  Synchronizes the device. */
 qed_status qed_tables_destroy(qed_tables_t t);
 
@@ -226,8 +240,9 @@ qed_status qed_tables_lookup(qed_tables_t t, int32_t precision, const double *ch
                              double *out_dev, int64_t n, void *stream);
 /* out_dev row layout of qed_tables_lookup: [0] I_up(chi), [1] I_down(chi), [2] J_+(chi), [3] J_-(chi)
  * (unscaled), [4] ln u' from the up ICDF, [5] ln u' from the down ICDF, [6] ln x from the + ICDF,
- * [7] ln x from the - ICDF (NBW rows take r as the folded coordinate). */
-#define QED_LOOKUP_COLS 8
+ * [7] ln x from the - ICDF (NBW rows take r as the folded coordinate), [8] a(chi), the field-dependent
+ * anomalous moment (linear in (ln chi, ln a) between nodes, the end values outside the grid). */
+#define QED_LOOKUP_COLS 9
 
 /* Optical depth at birth for particles [begin, *count): tau = -ln u(id, step = 2^64 - 1, slot 0)
  * (Sec. 4.1, optical-depth method). */

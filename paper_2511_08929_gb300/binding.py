@@ -22,7 +22,7 @@ QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_RANGE, QED_ERR_NAN,
 QED_FP64, QED_FP32 = 0, 1
 QED_ELECTRON, QED_PHOTON, QED_POSITRON = -1, 0, 1
 QED_FIELD_CONST, QED_FIELD_LP, QED_FIELD_CP, QED_FIELD_CP_COUNTER = 0, 1, 2, 3
-QED_LOOKUP_COLS = 8
+QED_LOOKUP_COLS = 9
 QED_COMPACT_NOALLOC_MAX_CAPACITY = int(re.search(r"#define QED_COMPACT_NOALLOC_MAX_CAPACITY (\d+)",
                                                  open(HEADER).read()).group(1))
 
@@ -31,7 +31,7 @@ def _flags_from_header():
     """Physics switch values, read from include/qed.h so the binding cannot drift from the ABI."""
     flags = {}
     txt = open(HEADER).read()
-    for name, shift in re.findall(r"(QED_F_[A-Z_]+) = 1u << (\d+)", txt):
+    for name, shift in re.findall(r"(QED_F_[A-Z0-9_]+) = 1u << (\d+)", txt):
         flags[name] = 1 << int(shift)
     return flags
 
@@ -123,6 +123,7 @@ def lib():
                 "qed_status_string": (C.c_char_p, [i32]),
                 "qed_tables_build": (i32, [P(QedTableDesc), P(vp), vp]),
                 "qed_tables_export": (i32, [vp, vp, vp, vp, vp]),
+                "qed_tables_export_amm": (i32, [vp, vp]),
                 "qed_tables_destroy": (i32, [vp]),
                 "qed_bessel_eval": (i32, [vp, i32, vp, vp, i64, vp]),
                 "qed_tables_lookup": (i32, [vp, i32, vp, vp, vp, i64, vp]),
@@ -190,6 +191,13 @@ def qed_tables_export(handle: int, desc: QedTableDesc):
            "nbw_icdf": np.zeros((2, nc, nr))}
     ptr = [out[k].ctypes.data for k in ("nlc_rate", "nbw_rate", "nlc_icdf", "nbw_icdf")]
     _check(lib().qed_tables_export(handle, *ptr), "qed_tables_export")
+    return out
+
+
+def qed_tables_export_amm(handle: int, desc: QedTableDesc):
+    """ln a(chi_i) on the rate grid, double[n_chi]."""
+    out = np.zeros(desc.n_chi)
+    _check(lib().qed_tables_export_amm(handle, out.ctypes.data), "qed_tables_export_amm")
     return out
 
 

@@ -722,8 +722,7 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
     *out = nullptr;
     if (!valid_tables(t)) return QED_ERR_STATE;
     if (!instances || n_inst < 1 || n_inst > QED_BATCH_MAX_INSTANCES || !desc || !counters_dev) return QED_ERR_ARG;
-    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER;
-    if (!(desc->dt > 0.0) || !std::isfinite(desc->dt) || !std::isfinite(desc->t0) || (desc->flags & ~known) != 0 ||
+    if (!(desc->dt > 0.0) || !std::isfinite(desc->dt) || !std::isfinite(desc->t0) || !valid_flags(desc->flags) ||
         !(desc->photon_store_min >= 0.0) || !(desc->chi_floor >= 0.0))
         return QED_ERR_ARG;
     for (int i = 0; i < n_inst; ++i)

@@ -148,6 +148,7 @@ struct TabP {
     const R* nlc_icdf;  // [2][n_chi][n_r]
     const R* nbw_icdf;  // [2][n_chi][n_r]
     const R* nlc_icdf_lo;  // FP32 only: nlc_icdf's rounding remainders (entry = nlc_icdf + nlc_icdf_lo)
+    const R* amm;       // [n_chi] ln a(chi), the field-dependent anomalous moment
     R lnchi_min, inv_dlnchi, chi_min, chi_max;
     R y_lo, inv_dy, inv_dy_lo;  // inv_dy + inv_dy_lo: (n_r - 1)/(y_hi - y_lo) to twice the precision of R
     int n_chi, n_r;
@@ -178,6 +179,40 @@ __device__ __forceinline__ void nlc_rates(const TabP<R>& T, R chi, R lnchi, R& I
     chi_coord(T, lnchi, i, f);
     Iu = exp_(fma_(f, T.nlc_rate[i + 1] - T.nlc_rate[i], T.nlc_rate[i]));
     Id = exp_(fma_(f, T.nlc_rate[T.n_chi + i + 1] - T.nlc_rate[T.n_chi + i], T.nlc_rate[T.n_chi + i]));
+}
+
+// field-dependent anomalous moment a(chi) (one-loop Scorer term, App. A.1; Sec. 8.6.2): linear in
+// (ln chi, ln a) between nodes, the end values outside the grid (chi <= 0 reads the first node)
+template <class R>
+__device__ __forceinline__ R amm_lookup(const TabP<R>& T, R chi) {
+    int i; R f;
+    chi_coord(T, chi > R(0) ? log_(chi) : T.lnchi_min, i, f);
+    return exp_(fma_(f, T.amm[i + 1] - T.amm[i], T.amm[i]));
+}
+
+// the anomalous moment T-BMT precesses with: alpha/(2 pi); a(chi) at the time-centred momentum pb
+// (QED_F_AMM); zero for g = 2 (QED_F_G2) and when the loop's Scorer term carries it (QED_F_LOOP)
+template <class R>
+__device__ __forceinline__ R tbmt_a(uint32_t fl, const TabP<R>& T, R eta0, const V3<R>& pb, const V3<R>& E,
+                                    const V3<R>& B) {
+    if (fl & (QED_F_G2 | QED_F_LOOP)) return R(0);
+    if (fl & QED_F_AMM) return amm_lookup(T, chi_of(eta0, sqrt_(R(1) + dot(pb, pb)), pb, E, B));
+    return R(kAlpha / (2.0 * kPi));
+}
+
+// the loop's Scorer term in the no-emission update (QED_F_LOOP; App. A.1 R_if): a turn about the
+// rest-frame magnetic field B' = gamma (B - v x E) - gamma^2/(gamma+1) (v.B) v by a(chi) chi dt/(eta0 gamma),
+// in the T-BMT sense (-q).  Returned as the vector Omega with s <- rotate(s, Omega, dt).
+template <class R>
+__device__ __forceinline__ V3<R> loop_omega(const TabP<R>& T, R eta0, R chi, R gam, const V3<R>& p, const V3<R>& E,
+                                            const V3<R>& B, R q) {
+    const R ig = rcp_(gam);
+    const V3<R> v = ig * p;
+    const V3<R> Bp = axpy(-(div_(gam * gam, gam + R(1)) * dot(v, B)), v, gam * (B - cross(v, E)));
+    const R nb2 = dot(Bp, Bp);
+    if (!(nb2 > R(0))) return V3<R>{R(0), R(0), R(0)};
+    const R rate = amm_lookup(T, chi) * div_(chi, eta0) * ig;
+    return ((-q) * rate * rsqrt_(nb2)) * Bp;
 }
 
 // NBW rate integrals J_+, J_- at chi (zero below chi_min)

@@ -143,8 +143,7 @@ __global__ void compact_move_kernel(PartDev G, int layout, CompactWs w) {
 }  // namespace qed
 
 static bool valid_step(const qed_step_desc* s) {
-    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER;
-    return s && s->dt > 0.0 && std::isfinite(s->dt) && std::isfinite(s->t) && (s->flags & ~known) == 0 &&
+    return s && s->dt > 0.0 && std::isfinite(s->dt) && std::isfinite(s->t) && valid_flags(s->flags) &&
            s->photon_store_min >= 0.0 && s->chi_floor >= 0.0;
 }
 

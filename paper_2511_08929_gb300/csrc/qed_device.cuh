@@ -253,9 +253,9 @@ __device__ __forceinline__ V3<R> boris(const V3<R>& p, const V3<R>& E, const V3<
 }
 
 // T-BMT precession vector Omega (ds/dt = Omega x s) with the time-centred momentum pb.
+// ae: the anomalous moment (alpha/(2 pi), a(chi), or 0 for g = 2).
 template <class R>
-__device__ __forceinline__ V3<R> tbmt_omega(const V3<R>& pb, const V3<R>& E, const V3<R>& B, R q, bool paper_form) {
-    const R ae = R(kAlpha / (2.0 * kPi));
+__device__ __forceinline__ V3<R> tbmt_omega(const V3<R>& pb, const V3<R>& E, const V3<R>& B, R q, bool paper_form, R ae) {
     const R gb = sqrt_(R(1) + dot(pb, pb));
     const R ig = rcp_(gb);
     const V3<R> bb = ig * pb;

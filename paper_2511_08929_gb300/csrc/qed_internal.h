@@ -22,6 +22,8 @@ struct qed_tables_s {
     float* icdf32lo;  // icdf64 - icdf32 rounded to float: the two floats hold an ICDF entry to ~1e-14
     double* bes64;  // [3][kBesN] scaled Bessel values
     float* bes32;
+    double* amm64;  // [n_chi] ln a(chi_i), the field-dependent anomalous moment
+    float* amm32;
 };
 
 inline bool valid_tables(const qed_tables_s* t) { return t != nullptr && t->magic == kTablesMagic; }
@@ -46,6 +48,8 @@ inline qed::TabP<R> tab_params(const qed_tables_s* t) {
     p.nbw_icdf = icdf + 2 * nc * d.n_r;
     p.nlc_icdf_lo = nullptr;
     if constexpr (sizeof(R) == 4) p.nlc_icdf_lo = reinterpret_cast<const R*>(t->icdf32lo);
+    if constexpr (sizeof(R) == 8) p.amm = reinterpret_cast<const R*>(t->amm64);
+    else p.amm = reinterpret_cast<const R*>(t->amm32);
     const double dl = (std::log(d.chi_max) - std::log(d.chi_min)) / (d.n_chi - 1);
     p.lnchi_min = (R)std::log(d.chi_min);
     p.inv_dlnchi = (R)(1.0 / dl);
@@ -92,6 +96,14 @@ inline PartDev part_dev(const qed_particles* p) {
 // the reservation state of a step call: the append_* fields at the end of the caller's counters
 __host__ __device__ inline qed::AppendState* append_state(qed_counters* ctr) {
     return reinterpret_cast<qed::AppendState*>(&ctr->append_base[0]);
+}
+
+// the switches a step accepts: every flag of the header, without the contradictory anomalous-moment
+// pairs (a(chi) in T-BMT and the loop's Scorer term are the same moment; g = 2 excludes both)
+inline bool valid_flags(uint32_t f) {
+    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER | QED_F_AMM | QED_F_LOOP | QED_F_G2;
+    if (f & ~known) return false;
+    return !((f & QED_F_AMM) && (f & (QED_F_LOOP | QED_F_G2)));
 }
 
 // validation of a particle buffer for a given layout

@@ -318,8 +318,7 @@ __device__ __forceinline__ F3 boris_t(const F3& p, const F3& E, const F3& B, flo
     return F3{fma_(h, E.x, pl.x), fma_(h, E.y, pl.y), pl.z};
 }
 
-__device__ __forceinline__ F3 tbmt_omega_t(const F3& pb, const F3& E, const F3& B, float q, bool paper_form) {
-    const float ae = (float)(kAlpha / (2.0 * kPi));
+__device__ __forceinline__ F3 tbmt_omega_t(const F3& pb, const F3& E, const F3& B, float q, bool paper_form, float ae) {
     const float gb = sqrt_(1.0f + dot(pb, pb));
     const float ig = rcp_(gb);
     const F3 bb = ig * pb;
@@ -363,7 +362,11 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     if (fl & QED_F_TBMT) {
         const F3 pb = 0.5f * (pold + st.p);
         const bool paper = (fl & QED_F_TBMT_PAPER) != 0;
-        st.s = rotate(st.s, transverse ? tbmt_omega_t(pb, st.E, st.B, C.q, paper) : tbmt_omega(pb, st.E, st.B, C.q, paper), dt);
+        // the anomalous moment: alpha/(2 pi), a(chi) at pb, or none (tbmt_a; chi32 takes the plane-wave form)
+        float ae = (float)(kAlpha / (2.0 * kPi));
+        if (fl & (QED_F_G2 | QED_F_LOOP)) ae = 0.0f;
+        else if (fl & QED_F_AMM) ae = amm_lookup(T, chi32(C, sqrt_(1.0f + dot(pb, pb)), pb, st.E, st.B));
+        st.s = rotate(st.s, transverse ? tbmt_omega_t(pb, st.E, st.B, C.q, paper, ae) : tbmt_omega(pb, st.E, st.B, C.q, paper, ae), dt);
     }
     st.gam = sqrt_(1.0f + dot(st.p, st.p));
     const float rg = rcp_(st.gam);
@@ -481,7 +484,10 @@ static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X,
     field_eval(F64, C.S.ph_hi, 0.0, x, E, B);
     const V pold = p;
     if (fl & QED_F_PUSH) p = boris(p, E, B, q, dt);
-    if (fl & QED_F_TBMT) s = rotate(s, tbmt_omega(0.5 * (pold + p), E, B, q, (fl & QED_F_TBMT_PAPER) != 0), dt);
+    if (fl & QED_F_TBMT) {
+        const V pb = 0.5 * (pold + p);
+        s = rotate(s, tbmt_omega(pb, E, B, q, (fl & QED_F_TBMT_PAPER) != 0, tbmt_a(fl, X.T, F64.eta0, pb, E, B)), dt);
+    }
     const double gam = sqrt(1.0 + dot(p, p));
     if (fl & QED_F_MOVE) x = x + v3(p.x / gam * dt, p.y / gam * dt, p.z / gam * dt);
     const double chi = chi_of(F64.eta0, gam, p, E, B);
@@ -745,6 +751,11 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
                 c[C_RENORM]++;
             }
         }
+    }
+    if (st.qed && (fl & QED_F_LOOP)) {
+        // the loop's Scorer term (App. A.1): a turn about the rest-frame magnetic field
+        const TabP<float>& T = Tp ? *Tp : C.T;
+        sf = rotate(sf, loop_omega(T, C.F.eta0, st.chi, st.gam, st.p, st.E, st.B, C.q), dt);
     }
     store32(L, j, st.x, st.p, sf, st.w, tauf);
     return false;

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                 if (fl & QED_F_PUSH) p = boris(p, E, B, q, dt);
                 if (fl & QED_F_TBMT) {
                     const V pb = 0.5 * (pold + p);
-                    s = rotate(s, tbmt_omega(pb, E, B, q, (fl & QED_F_TBMT_PAPER) != 0), dt);
+                    s = rotate(s, tbmt_omega(pb, E, B, q, (fl & QED_F_TBMT_PAPER) != 0, tbmt_a(fl, T, F.eta0, pb, E, B)), dt);
                 }
                 const double gam = sqrt(1.0 + dot(p, p));
                 if (fl & QED_F_MOVE) x = x + v3(p.x / gam * dt, p.y / gam * dt, p.z / gam * dt);
@@ -169,6 +169,8 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                                 }
                             }
                         }
+                        // the loop's Scorer term (App. A.1): a turn about the rest-frame magnetic field
+                        if (!event && (fl & QED_F_LOOP)) sf = rotate(sf, loop_omega(T, F.eta0, chi, gam, p, E, B, q), dt);
                     }
                 }
                 st_do = true;

@@ -160,6 +160,67 @@ __global__ void split_float_kernel(const double* __restrict__ a, float* hi, floa
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// field-dependent anomalous moment (the one-loop Scorer term of App. A.1; g(chi) of Sec. 8.6.2)
+// ------------------------------------------------------------------------------------------------
+// Scorer function for z >= 0 from its defining integral pi Gi(z) = Im int_0^inf exp(i(z t + t^3/3)) dt,
+// taken along the ray t = e^{i pi/6} s (the integrand is analytic and bounded between the two rays):
+//   pi Gi(z) = int_0^inf exp(-s^3/3 - z s/2) sin(sqrt(3) z s/2 + pi/6) ds,
+// a decaying integrand with at most ~13 oscillations before the exponential falls below e^-46:
+// 40 panels of 12-point Gauss-Legendre on [0, min(5.2, 92/z)].
+__device__ double scorer_gi(double z) {
+    const double S = fmin(5.2, 92.0 / fmax(z, 1e-300));
+    constexpr int np = 40;
+    const double h = S / np, w = 0.86602540378443864676 * z, r = 0.5 * h;
+    double acc = 0.0;
+    for (int p = 0; p < np; ++p) {
+        const double m = (p + 0.5) * h;
+        double ps = 0.0;
+        for (int i = 0; i < kGL; ++i) {
+            const double t = m + r * c_gl_x[i];
+            ps += c_gl_w[i] * exp(-t * t * t / 3.0 - 0.5 * z * t) * sin(w * t + kPi / 6.0);
+        }
+        acc += ps * r;
+    }
+    return acc / kPi;
+}
+
+// One block per chi node: a(chi) = (alpha/chi) int_0^inf du u/(1+u)^3 Gi(z)/sqrt(z), z = (u/chi)^{2/3}
+// (= (alpha/chi) int_0^1 dlambda lambda Gi(z)/sqrt(z) with u = lambda/(1-lambda)), integrated in x = ln u
+// on [min(ln chi, 0) - 21, max(ln chi, 0) + 21] (the ends add below 1e-17 of the result) with panels of
+// width 1/4, one per thread, summed in a fixed tree order.  Stores ln a.
+__global__ void __launch_bounds__(256) amm_table_kernel(qed_table_desc d, double* amm64, float* amm32) {
+    __shared__ double part[256];
+    const int i = blockIdx.x;
+    const double dl = (log(d.chi_max) - log(d.chi_min)) / (d.n_chi - 1);
+    const double lnchi = log(d.chi_min) + i * dl, chi = exp(lnchi);
+    const double x0 = fmin(lnchi, 0.0) - 21.0, x1 = fmax(lnchi, 0.0) + 21.0;
+    const int np = (int)ceil((x1 - x0) * 4.0);
+    const double h = (x1 - x0) / np, r = 0.5 * h;
+    double acc = 0.0;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const double m = x0 + (p + 0.5) * h;
+        for (int k = 0; k < kGL; ++k) {
+            const double x = m + r * c_gl_x[k];
+            const double u = exp(x);
+            const double sz = exp((x - lnchi) / 3.0);  // sqrt(z) = (u/chi)^{1/3}
+            const double q = 1.0 / (1.0 + u);
+            acc += c_gl_w[k] * r * u * u * q * q * q * scorer_gi(sz * sz) / sz;
+        }
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double la = log(kAlpha / chi * part[0]);
+        amm64[i] = la;
+        amm32[i] = (float)la;
+    }
+}
+
 }  // namespace qed
 
 using namespace qed;
@@ -173,6 +234,8 @@ static void free_tables(qed_tables_s* t) {
     cudaFree(t->icdf32lo);
     cudaFree(t->bes64);
     cudaFree(t->bes32);
+    cudaFree(t->amm64);
+    cudaFree(t->amm32);
     t->magic = 0;
     delete t;
 }
@@ -197,7 +260,9 @@ extern "C" qed_status qed_tables_build(const qed_table_desc* desc, qed_tables_t*
               cudaMalloc(&t->icdf32, ni * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&t->icdf32lo, ni * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&t->bes64, 3 * kBesN * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&t->bes32, 3 * kBesN * sizeof(float)) == cudaSuccess;
+              cudaMalloc(&t->bes32, 3 * kBesN * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&t->amm64, d.n_chi * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&t->amm32, d.n_chi * sizeof(float)) == cudaSuccess;
     if (!ok) {
         free_tables(t);
         return QED_ERR_NOMEM;
@@ -213,6 +278,7 @@ extern "C" qed_status qed_tables_build(const qed_table_desc* desc, qed_tables_t*
     table_rows_kernel<<<4 * d.n_chi, 256, 0, st>>>(t->bes64, d, t->rate64, t->icdf64);
     to_float_kernel<<<64, 256, 0, st>>>(t->rate64, t->rate32, nr);
     split_float_kernel<<<256, 256, 0, st>>>(t->icdf64, t->icdf32, t->icdf32lo, ni);
+    amm_table_kernel<<<d.n_chi, 256, 0, st>>>(d, t->amm64, t->amm32);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
         free_tables(t);
         return QED_ERR_CUDA;
@@ -232,6 +298,14 @@ extern "C" qed_status qed_tables_export(qed_tables_t t, double* nlc_rate, double
     if (nlc_icdf && e == cudaSuccess) e = cudaMemcpy(nlc_icdf, t->icdf64, ni * sizeof(double), cudaMemcpyDeviceToHost);
     if (nbw_icdf && e == cudaSuccess) e = cudaMemcpy(nbw_icdf, t->icdf64 + ni, ni * sizeof(double), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+extern "C" qed_status qed_tables_export_amm(qed_tables_t t, double* ln_a) {
+    if (!valid_tables(t)) return QED_ERR_STATE;
+    if (!ln_a) return QED_ERR_ARG;
+    return cudaMemcpy(ln_a, t->amm64, t->desc.n_chi * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess
+               ? QED_OK
+               : QED_ERR_CUDA;
 }
 
 extern "C" qed_status qed_tables_destroy(qed_tables_t t) {
@@ -278,6 +352,7 @@ __global__ void lookup_kernel(TabP<R> T, const double* chi, const double* r, dou
         o[5] = icdf_lookup(T, false, 1, lc, y);
         o[6] = icdf_lookup(T, true, 0, lc, y);
         o[7] = icdf_lookup(T, true, 1, lc, y);
+        o[8] = amm_lookup(T, c);
     }
 }
 }  // namespace qed

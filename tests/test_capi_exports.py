@@ -18,7 +18,7 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
     # the ABI version and status strings need no device
-    assert lib.qed_abi_version() == 2
+    assert lib.qed_abi_version() == 3
     # qed_counters: eight 64-bit counters, status, pad, first_bad, and the call's reservation block
     assert ctypes.sizeof(B.QedCounters) == 8 * 8 + 8 + 8 + 4 * 8
     lib.qed_status_string.restype = ctypes.c_char_p
@@ -32,7 +32,7 @@ def test_binding_flags_match_oracle_flags():
     pairs = {"TAU": O.F_TAU, "RECOIL": O.F_RECOIL, "SPIN_COLLAPSE": O.F_SPIN_COLLAPSE, "POL_COLLAPSE": O.F_POL_COLLAPSE,
              "NONTRANSITION": O.F_NONTRANSITION, "PUSH": O.F_PUSH, "TBMT": O.F_TBMT, "TBMT_PAPER": O.F_TBMT_PAPER,
              "EMIT": O.F_EMIT, "RESOLVED": O.F_RESOLVED, "MOVE": O.F_MOVE, "SPIN_EVENT": O.F_SPIN_EVENT,
-             "POL_EVENT": O.F_POL_EVENT}
+             "POL_EVENT": O.F_POL_EVENT, "AMM": O.F_AMM, "LOOP": O.F_LOOP, "G2": O.F_G2}
     for k, v in pairs.items():
         assert getattr(B, "QED_F_" + k) == v, k
     assert B.QED_F_FULL == O.F_FULL

@@ -91,7 +91,7 @@ def test_lookups_match_oracle(gpu_tables, ora_tables):
             assert g[i, 2] == 0 and g[i, 3] == 0
         ic = [ora_tables.icdf(False, 0, chi[i], r[i]), ora_tables.icdf(False, 1, chi[i], r[i]),
               ora_tables.icdf(True, 0, chi[i], r[i]), ora_tables.icdf(True, 1, chi[i], r[i])]
-        np.testing.assert_allclose(g[i, 4:], ic, rtol=0, atol=1e-12 * max(1.0, np.abs(ic).max()))
+        np.testing.assert_allclose(g[i, 4:8], ic, rtol=0, atol=1e-12 * max(1.0, np.abs(ic).max()))
 
 
 # ------------------------------------------------------------------------------------------------
