@@ -43,10 +43,11 @@ F_POL_EVENT = 1 << 12
 F_AMM = 1 << 13
 F_LOOP = 1 << 14
 F_G2 = 1 << 15
+F_BETA_BASIS = 1 << 16
 F_FULL = (F_TAU | F_RECOIL | F_SPIN_COLLAPSE | F_POL_COLLAPSE | F_NONTRANSITION | F_PUSH | F_TBMT | F_EMIT
           | F_RESOLVED | F_MOVE | F_SPIN_EVENT | F_POL_EVENT)
 
-FIELD_CONST, FIELD_LP, FIELD_CP, FIELD_CP_COUNTER = 0, 1, 2, 3
+FIELD_CONST, FIELD_LP, FIELD_CP, FIELD_CP_COUNTER, FIELD_ROT_B = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:

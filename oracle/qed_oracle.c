@@ -699,7 +699,7 @@ double orc_amm_lookup(const orc_tables *t, double chi)
 /* Fields: analytic plane waves propagating along z (stand-in for the PIC      */
 /* grid fields of Sec. 4).  E, B in units of m c omega / e.                     */
 /* ------------------------------------------------------------------------- */
-enum { ORC_FIELD_CONST = 0, ORC_FIELD_LP = 1, ORC_FIELD_CP = 2, ORC_FIELD_CP_COUNTER = 3 };
+enum { ORC_FIELD_CONST = 0, ORC_FIELD_LP = 1, ORC_FIELD_CP = 2, ORC_FIELD_CP_COUNTER = 3, ORC_FIELD_ROT_B = 4 };
 typedef struct {
     int32_t kind;
     int32_t pad;
@@ -720,6 +720,16 @@ void orc_field_eval(const orc_field *f, const double x[3], double t, double E[3]
     for (int i = 0; i < 3; ++i) { E[i] = 0.0; B[i] = 0.0; }
     if (f->kind == ORC_FIELD_CONST) {
         for (int i = 0; i < 3; ++i) { E[i] = f->E0[i]; B[i] = f->B0[i]; }
+        return;
+    }
+    if (f->kind == ORC_FIELD_ROT_B) {
+        /* a magnetic field of constant strength |B0_z| that turns from z to y (the rotating-field test of
+         * Sec. 8.3): angle (pi/2) clamp((t + phase) / (2 pi n_cycles), 0, 1), uniform in space, E = 0 */
+        double u = (t + f->phase) / (2.0 * ORC_PI * f->n_cycles);
+        u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+        double th = 0.5 * ORC_PI * u;
+        B[1] = f->B0[2] * sin(th);
+        B[2] = f->B0[2] * cos(th);
         return;
     }
     double phi = t - x[2] + f->phase;
@@ -763,7 +773,8 @@ enum {
     ORC_F_POL_EVENT = 1u << 12,    /* emitted photons get the Stokes vector of F (else unpolarized) */
     ORC_F_AMM = 1u << 13,          /* T-BMT with the field-dependent a(chi) (Sec. 8.6.2) instead of alpha/(2 pi) */
     ORC_F_LOOP = 1u << 14,         /* Scorer term of the loop in the no-emission update; T-BMT with g = 2 */
-    ORC_F_G2 = 1u << 15            /* T-BMT with g = 2 (a = 0), the comparison run of Sec. 8.6.2 */
+    ORC_F_G2 = 1u << 15,           /* T-BMT with g = 2 (a = 0), the comparison run of Sec. 8.6.2 */
+    ORC_F_BETA_BASIS = 1u << 16    /* spins resolved along +-beta instead of the SQA (Sec. 8.3 comparison) */
 };
 
 typedef struct {
@@ -1003,7 +1014,17 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                     double w, g[3];
                     orc_nlc_wg(lam, bes, si, eps, beta, khat, &w, g);
                     double gn = sqrt(dot3(g, g));
-                    if (fl & ORC_F_SPIN_COLLAPSE) {
+                    if (fl & ORC_F_BETA_BASIS) {
+                        /* beta basis (Sec. 8.3): the final spin resolved along +-beta only; the probability
+                         * of -beta is (w - g.beta)/(2w), the expectation (g.beta/w) beta */
+                        double gb = dot3(g, beta);
+                        if (fl & ORC_F_SPIN_COLLAPSE) {
+                            double sg = u1[1] < (w - gb) / (2.0 * w) ? -1.0 : 1.0;
+                            for (int i = 0; i < 3; ++i) sf[i] = sg * beta[i];
+                        } else {
+                            for (int i = 0; i < 3; ++i) sf[i] = gb / w * beta[i];
+                        }
+                    } else if (fl & ORC_F_SPIN_COLLAPSE) {
                         /* SQA collapse (Sec. 5.1): s_f = -S if r3 < (w - |g|)/(2w), else +S */
                         double sg = u1[1] < (w - gn) / (2.0 * w) ? -1.0 : 1.0;
                         for (int i = 0; i < 3; ++i) sf[i] = gn > 0.0 ? sg * g[i] / gn : 0.0;
@@ -1196,6 +1217,9 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
                             Se[i] = jen > 0.0 ? je[i] / jen : 0.0;
                             Sp[i] = jpn > 0.0 ? jp[i] / jpn : 0.0;
                         }
+                        /* beta basis: both axes beta (the four G_ab still sum to 4 w0 for any axes) */
+                        if (fl & ORC_F_BETA_BASIS)
+                            for (int i = 0; i < 3; ++i) { Se[i] = beta[i]; Sp[i] = beta[i]; }
                         /* four correlated states (Sec. 5.2), order (--, -+, +-, ++), first sign = positron,
                          * probabilities G_ab / (4 w0) */
                         double cum = 0.0;
@@ -1212,6 +1236,9 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
                         }
                         double sa = (chosen & 2) ? 1.0 : -1.0, sbb = (chosen & 1) ? 1.0 : -1.0;
                         for (int i = 0; i < 3; ++i) { sp[i] = sa * Sp[i]; se[i] = sbb * Se[i]; }
+                    } else if (fl & ORC_F_BETA_BASIS) {
+                        double eb = dot3(je, beta) / w0, pb = dot3(jp, beta) / w0;
+                        for (int i = 0; i < 3; ++i) { se[i] = eb * beta[i]; sp[i] = pb * beta[i]; }
                     } else {
                         for (int i = 0; i < 3; ++i) { se[i] = je[i] / w0; sp[i] = jp[i] / w0; }
                     }
