@@ -85,7 +85,12 @@ enum {
      * (the paper's g = 2 comparison).  QED_F_AMM with QED_F_LOOP or QED_F_G2 is QED_ERR_ARG. */
     QED_F_AMM = 1u << 13,
     QED_F_LOOP = 1u << 14,
-    QED_F_G2 = 1u << 15
+    QED_F_G2 = 1u << 15,
+    /* Spins resolved along +-beta (the rest-frame magnetic direction) instead of the spin quantization
+     * axis (Sec. 8.3 compares the two): an emitting lepton ends at -beta with probability
+     * (w - g.beta)/(2w), else +beta (expectation mode: (g.beta/w) beta); pair daughters take the four
+     * states along (+-beta, +-beta) with probabilities G_ab/(4 w0) (expectation: (j.beta/w0) beta). */
+    QED_F_BETA_BASIS = 1u << 16
 };
 #define QED_F_FULL                                                                                     \
     (QED_F_TAU | QED_F_RECOIL | QED_F_SPIN_COLLAPSE | QED_F_POL_COLLAPSE | QED_F_NONTRANSITION |       \
@@ -96,7 +101,10 @@ enum {
     QED_FIELD_CONST = 0,     /* E = E0, B = B0 */
     QED_FIELD_LP = 1,        /* E = a0 g(phi) cos(phi) x, B = z x E, phi = t - z + phase */
     QED_FIELD_CP = 2,        /* E = a0 g(phi) (cos phi, sin phi, 0), B = z x E */
-    QED_FIELD_CP_COUNTER = 3 /* CP plus a CP wave along -z with phi2 = t + z + phase, B2 = -z x E2 */
+    QED_FIELD_CP_COUNTER = 3, /* CP plus a CP wave along -z with phi2 = t + z + phase, B2 = -z x E2 */
+    QED_FIELD_ROT_B = 4       /* E = 0, B = B0[2] (0, sin th, cos th), th = (pi/2) clamp((t + phase) /
+                                 (2 pi n_cycles), 0, 1): a uniform field turning from z to y (the
+                                 rotating-field test of Sec. 8.3) */
 };
 
 typedef struct {

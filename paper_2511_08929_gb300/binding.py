@@ -21,7 +21,7 @@ QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_RANGE, QED_ERR_NAN,
     QED_ERR_NOMEM, QED_ERR_TOO_LARGE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 QED_FP64, QED_FP32 = 0, 1
 QED_ELECTRON, QED_PHOTON, QED_POSITRON = -1, 0, 1
-QED_FIELD_CONST, QED_FIELD_LP, QED_FIELD_CP, QED_FIELD_CP_COUNTER = 0, 1, 2, 3
+QED_FIELD_CONST, QED_FIELD_LP, QED_FIELD_CP, QED_FIELD_CP_COUNTER, QED_FIELD_ROT_B = 0, 1, 2, 3, 4
 QED_LOOKUP_COLS = 9
 QED_COMPACT_NOALLOC_MAX_CAPACITY = int(re.search(r"#define QED_COMPACT_NOALLOC_MAX_CAPACITY (\d+)",
                                                  open(HEADER).read()).group(1))

@@ -200,6 +200,14 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
         B = v3(f.B0x, f.B0y, f.B0z);
         return;
     }
+    if (f.kind == QED_FIELD_ROT_B) {  // |B| = B0z turning from z to y as t + phase runs over [0, phimax]
+        R u = div_(ph_hi + ph_lo, f.phimax);
+        u = u < R(0) ? R(0) : (u > R(1) ? R(1) : u);
+        const R th = R(0.5 * kPi) * u;
+        E = v3(R(0), R(0), R(0));
+        B = v3(R(0), f.B0z * sin(th), f.B0z * cos(th));
+        return;
+    }
     // phase t + phase - z: the rounding error of the subtraction is recovered exactly and added to the
     // reduced argument, so the FP32 carrier keeps the phase to ~1e-7 however large it is
     R e1;

@@ -101,7 +101,7 @@ __host__ __device__ inline qed::AppendState* append_state(qed_counters* ctr) {
 // the switches a step accepts: every flag of the header, without the contradictory anomalous-moment
 // pairs (a(chi) in T-BMT and the loop's Scorer term are the same moment; g = 2 excludes both)
 inline bool valid_flags(uint32_t f) {
-    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER | QED_F_AMM | QED_F_LOOP | QED_F_G2;
+    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER | QED_F_AMM | QED_F_LOOP | QED_F_G2 | QED_F_BETA_BASIS;
     if (f & ~known) return false;
     return !((f & QED_F_AMM) && (f & (QED_F_LOOP | QED_F_G2)));
 }
@@ -137,7 +137,7 @@ inline qed::FieldP<R> field_params(const qed_field& f) {
 }
 
 inline bool valid_field(const qed_field* f) {
-    return f && f->kind >= QED_FIELD_CONST && f->kind <= QED_FIELD_CP_COUNTER && std::isfinite(f->a0) &&
+    return f && f->kind >= QED_FIELD_CONST && f->kind <= QED_FIELD_ROT_B && std::isfinite(f->a0) &&
            std::isfinite(f->phase) && f->eta0 > 0.0 && std::isfinite(f->eta0) &&
            (f->kind == QED_FIELD_CONST || f->n_cycles > 0.0);
 }

@@ -511,7 +511,10 @@ static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X,
     if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, bb, si, beta, khat, wv, g);
     if (fl & QED_F_SPIN_EVENT) {
         const double gn = sqrt(dot(g, g));
-        if (fl & QED_F_SPIN_COLLAPSE) {
+        if (fl & QED_F_BETA_BASIS) {  // resolved along +-beta (Sec. 8.3 comparison)
+            const double gb = dot(g, beta);
+            sf = (fl & QED_F_SPIN_COLLAPSE) ? (r3 < (wv - gb) / (2.0 * wv) ? -1.0 : 1.0) * beta : (gb / wv) * beta;
+        } else if (fl & QED_F_SPIN_COLLAPSE) {
             const double sg = r3 < (wv - gn) / (2.0 * wv) ? -1.0 : 1.0;
             sf = gn > 0.0 ? v3(sg * g.x / gn, sg * g.y / gn, sg * g.z / gn) : v3(0.0, 0.0, 0.0);
         } else {
@@ -642,7 +645,11 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
             } else {
                 F3 sfu{0, 0, 0};
                 if (fl & QED_F_SPIN_EVENT) {
-                    if (fl & QED_F_SPIN_COLLAPSE) {
+                    if (fl & QED_F_BETA_BASIS) {  // resolved along +-beta (Sec. 8.3 comparison)
+                        const float gb = dot(g, st.beta);
+                        sf = (fl & QED_F_SPIN_COLLAPSE) ? (r3 < div_(wv - gb, 2.0f * wv) ? -1.0f : 1.0f) * st.beta
+                                                        : div_(gb, wv) * st.beta;
+                    } else if (fl & QED_F_SPIN_COLLAPSE) {
                         const float sg = r3 < div_(wv - gn, 2.0f * wv) ? -1.0f : 1.0f;
                         sf = gn > 0.0f ? div_(sg, gn) * g : F3{0, 0, 0};
                     } else {
@@ -866,8 +873,9 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, 
             nbw_j(lam, one_m, bb, xi, eps, beta, kh, w0v, je, jp);
             if (fl & QED_F_SPIN_COLLAPSE) {
                 const double jen = sqrt(dot(je, je)), jpn = sqrt(dot(jp, jp));
-                const V3<double> Se = jen > 0.0 ? (1.0 / jen) * je : V3<double>{0, 0, 0};
-                const V3<double> Sp = jpn > 0.0 ? (1.0 / jpn) * jp : V3<double>{0, 0, 0};
+                V3<double> Se = jen > 0.0 ? (1.0 / jen) * je : V3<double>{0, 0, 0};
+                V3<double> Sp = jpn > 0.0 ? (1.0 / jpn) * jp : V3<double>{0, 0, 0};
+                if (fl & QED_F_BETA_BASIS) Se = Sp = beta;  // the G_ab sum to 4 w0 on any axes
                 // four correlated states, order (--, -+, +-, ++), first sign = positron
                 double cum = 0.0;
                 int chosen = 3;
@@ -882,6 +890,9 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, 
                 const double sa = (chosen & 2) ? 1.0 : -1.0, sbb = (chosen & 1) ? 1.0 : -1.0;
                 sp = narrow(sa * Sp);
                 se = narrow(sbb * Se);
+            } else if (fl & QED_F_BETA_BASIS) {
+                se = narrow((dot(je, beta) / w0v) * beta);
+                sp = narrow((dot(jp, beta) / w0v) * beta);
             } else {
                 se = narrow((1.0 / w0v) * je);
                 sp = narrow((1.0 / w0v) * jp);

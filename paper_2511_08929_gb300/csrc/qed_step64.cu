@@ -122,7 +122,11 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                             if (fl & (QED_F_SPIN_EVENT | QED_F_POL_EVENT)) nlc_wg(lam, one_m, b, si, beta, khat, wv, g);
                             if (fl & QED_F_SPIN_EVENT) {
                                 const double gn = sqrt(dot(g, g));
-                                if (fl & QED_F_SPIN_COLLAPSE) {
+                                if (fl & QED_F_BETA_BASIS) {  // resolved along +-beta (Sec. 8.3 comparison)
+                                    const double gb = dot(g, beta);
+                                    sf = (fl & QED_F_SPIN_COLLAPSE) ? (r3 < (wv - gb) / (2.0 * wv) ? -1.0 : 1.0) * beta
+                                                                    : (gb / wv) * beta;
+                                } else if (fl & QED_F_SPIN_COLLAPSE) {
                                     const double sg = r3 < (wv - gn) / (2.0 * wv) ? -1.0 : 1.0;
                                     sf = gn > 0.0 ? v3(sg * g.x / gn, sg * g.y / gn, sg * g.z / gn) : v3(0.0, 0.0, 0.0);
                                 } else {
@@ -295,8 +299,9 @@ __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const dou
                                 nbw_j(lam, one_m, b, xi, eps, beta, khat, w0v, je, jp);
                                 if (fl & QED_F_SPIN_COLLAPSE) {
                                     const double jen = sqrt(dot(je, je)), jpn = sqrt(dot(jp, jp));
-                                    const V Se = jen > 0.0 ? v3(je.x / jen, je.y / jen, je.z / jen) : v3(0.0, 0.0, 0.0);
-                                    const V Sp = jpn > 0.0 ? v3(jp.x / jpn, jp.y / jpn, jp.z / jpn) : v3(0.0, 0.0, 0.0);
+                                    V Se = jen > 0.0 ? v3(je.x / jen, je.y / jen, je.z / jen) : v3(0.0, 0.0, 0.0);
+                                    V Sp = jpn > 0.0 ? v3(jp.x / jpn, jp.y / jpn, jp.z / jpn) : v3(0.0, 0.0, 0.0);
+                                    if (fl & QED_F_BETA_BASIS) Se = Sp = beta;  // the G_ab sum to 4 w0 on any axes
                                     // four correlated states, order (--, -+, +-, ++), first sign = positron
                                     double cum = 0.0;
                                     int chosen = 3;
@@ -311,6 +316,9 @@ __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const dou
                                     const double sa = (chosen & 2) ? 1.0 : -1.0, sbb = (chosen & 1) ? 1.0 : -1.0;
                                     sp = sa * Sp;
                                     se = sbb * Se;
+                                } else if (fl & QED_F_BETA_BASIS) {
+                                    se = (dot(je, beta) / w0v) * beta;
+                                    sp = (dot(jp, beta) / w0v) * beta;
                                 } else {
                                     se = v3(je.x / w0v, je.y / w0v, je.z / w0v);
                                     sp = v3(jp.x / w0v, jp.y / w0v, jp.z / w0v);

@@ -32,7 +32,8 @@ def test_binding_flags_match_oracle_flags():
     pairs = {"TAU": O.F_TAU, "RECOIL": O.F_RECOIL, "SPIN_COLLAPSE": O.F_SPIN_COLLAPSE, "POL_COLLAPSE": O.F_POL_COLLAPSE,
              "NONTRANSITION": O.F_NONTRANSITION, "PUSH": O.F_PUSH, "TBMT": O.F_TBMT, "TBMT_PAPER": O.F_TBMT_PAPER,
              "EMIT": O.F_EMIT, "RESOLVED": O.F_RESOLVED, "MOVE": O.F_MOVE, "SPIN_EVENT": O.F_SPIN_EVENT,
-             "POL_EVENT": O.F_POL_EVENT, "AMM": O.F_AMM, "LOOP": O.F_LOOP, "G2": O.F_G2}
+             "POL_EVENT": O.F_POL_EVENT, "AMM": O.F_AMM, "LOOP": O.F_LOOP, "G2": O.F_G2,
+             "BETA_BASIS": O.F_BETA_BASIS}
     for k, v in pairs.items():
         assert getattr(B, "QED_F_" + k) == v, k
     assert B.QED_F_FULL == O.F_FULL

@@ -175,7 +175,8 @@ def _photon_inputs(n, seed, energy=3000.0):
             "id": np.arange(n, dtype=np.uint64) * 104729 + 1}
 
 
-def test_photon_pairs_and_compaction(gpu_tables, ora_tables):
+@pytest.mark.parametrize("flags", [None, B.QED_F_FULL | B.QED_F_BETA_BASIS])
+def test_photon_pairs_and_compaction(gpu_tables, ora_tables, flags):
     b = _photon_inputs(4000, seed=21)
     f = Q.field(B.QED_FIELD_CP, a0=200.0, n_cycles=4.0, eta0=ETA0)
     of = as_oracle_field(f)
@@ -186,7 +187,7 @@ def test_photon_pairs_and_compaction(gpu_tables, ora_tables):
     ctr, octr = Q.Counters(), O.Counters()
     steps = 20
     for s in range(steps):
-        st = Q.step_desc(0.2, 6.0 + 0.2 * s, s, 4)
+        st = Q.step_desc(0.2, 6.0 + 0.2 * s, s, 4, flags)
         B.qed_pair_step(gpu_tables.handle, f, st, gG.s, gE.s, gP.s, ctr.ptr)
         B.qed_compact(gG.s, ws.ptr, ws.bytes)
         O.photon_step(ora_tables, of, as_oracle_step(st), oG, oE, oP, octr)
