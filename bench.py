@@ -14,6 +14,11 @@ counted on the device.  The particle state (several GB) is far larger than L2: n
 --workload headon: the single-buffer entry points on one collision (1e7 electrons, gamma 4000, spin +z,
 CP a0 = 150, 20 cycles).
 
+--workload cascade: 2e8 electrons (gamma 1000) where two CP pulses (a0 = 500, 1 um, 15 cycles) collide,
+the whole 3000-step run through the batched path as one instance: the pair cascade multiplies the
+leptons, compaction every step; photons below 300 m c^2 are not stored.  Timed: all 3000 steps, in
+graph launches of 500 steps; the error leg runs three extra (untimed) steps after step 1000.
+
 Multi-GPU (torchrun): every rank runs an independent replica with its own seeds (particles never
 interact across ranks; there is no data-path collective): weak scaling.
 
@@ -45,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "headon"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "headon", "cascade"])
     ap.add_argument("--electrons", type=int, default=10_000_000, help="headon workload only")
     ap.add_argument("--advance", type=int, default=None,
                     help="untimed steps before warm-up (into the interaction; default 450 batched, 620 headon)")
@@ -54,6 +59,7 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="batched: fixed launch shape 'variant,blocks_per_sm,chunk' instead of the autotuner")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-sampler leg")
+    ap.add_argument("--cascade-steps", type=int, default=None, help="cascade: steps of the run (default 3000)")
     ap.add_argument("--mlp-train", type=float, default=5e7, help="learned sampler: training samples")
     ap.add_argument("--mlp-eval", type=float, default=1e8, help="learned sampler: evaluated events")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -208,7 +214,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args) if args.workload == "headon" else reference_arm_batch(args)
-    out = native(args) if args.workload == "headon" else native_batch(args)
+    run = {"headon": native, "cascade": native_cascade}.get(args.workload, native_batch)
+    out = run(args)
     if out is not None:
         print(json.dumps(out))
 
@@ -408,7 +415,8 @@ def growth_capacities(Q, B, tables, wl, insts, fields, seeds, end_step, device, 
     import torch
     fac = [8.0, 8.0, 400.0]
     for _attempt in range(3):
-        subs = [_subsample(wl.beam(k, x), min(x["n"], max(min_sub, x["n"] // sub))) for k, x in enumerate(insts)]
+        subs = [wl.sample(k, x, min(x["n"], max(min_sub, x["n"] // sub))) if hasattr(wl, "sample") else
+                _subsample(wl.beam(k, x), min(x["n"], max(min_sub, x["n"] // sub))) for k, x in enumerate(insts)]
         caps = [tuple(max(4096, int(f * len(b["id"]))) for f in fac) for b in subs]
         bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
                      device=device)
@@ -625,6 +633,157 @@ def native_batch(args):
     if rank != 0:
         return None
     return out
+
+
+def native_cascade(args):
+    """The large cascade (one instance of the batched path): every step of the run timed."""
+    import torch
+    from paper_2511_08929_gb300 import binding as B
+    from paper_2511_08929_gb300 import build as bld
+    from paper_2511_08929_gb300 import buffers as Q
+    from paper_2511_08929_gb300 import inputs as I
+    import dataclasses
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = f"cuda:{local if world > 1 else 0}"
+    bld.build()
+    wl = I.CASCADE_2E8
+    if args.scale != 1.0:
+        wl = dataclasses.replace(wl, name=f"{wl.name}_x{args.scale:g}", n_electrons=int(wl.n_electrons * args.scale))
+    steps = wl.steps if args.cascade_steps is None else args.cascade_steps
+    SEG = min(500, steps)
+    ERR_STEPS, ERR_AT = 3, min(1000, steps)
+    extras_on = not args.no_extras and rank == 0
+    t0 = time.time()
+    tables = Q.Tables(1e-4, 1e3, 256, 256)
+    torch.cuda.synchronize()
+    t_tables = time.time() - t0
+    seeds = [wl.seed + 1000 * rank]
+    id_offset = np.uint64(rank << 48)
+    insts = wl.instances()
+    fields = [Q.laser_field(wl.laser())]
+    t0 = time.time()
+    caps, sizing = growth_capacities(Q, B, tables, wl, insts, fields, seeds, steps + ERR_STEPS + 8, device,
+                                     sub=1024, min_sub=4096)
+    sizing["seconds"] = round(time.time() - t0, 2)
+    bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
+                 device=device)
+    e = bt.buffers()[0][0]
+    t0 = time.time()
+    done = 0
+    for c in range(wl.n_chunks()):
+        b = wl.chunk_beam(c)
+        if done + len(b["id"]) > wl.n_electrons:
+            b = {k: v[:wl.n_electrons - done] for k, v in b.items()}
+        e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"] + id_offset, offset=done)
+        done += len(b["id"])
+    e.init_tau(seeds[0])
+    torch.cuda.synchronize()
+    t_load = time.time() - t0
+    v, bps, ch = (int(x) for x in (args.tuning or "0,3,16").split(","))
+    B.qed_batch_set_tuning(bt.handle, B.QedBatchTuning(v, bps, ch, SEG))
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(SEG)]
+    bt.set_kernel_events(kev)
+    stream = torch.cuda.current_stream().cuda_stream
+    bt.step(0, stream)  # capture and instantiate outside the timed region
+    bt.ctr.zero()
+    torch.cuda.synchronize()
+    stop = threading.Event()
+    clock_lines = []
+    th = threading.Thread(target=clocks_sampler, args=(stop, clock_lines, local), daemon=True)
+    th.start()
+    time.sleep(0.5)
+    ms, tk, psteps = 0.0, 0.0, 0.0
+    d_sp = np.zeros(3)
+    tot = {"events": 0, "stored": 0, "rate_steps": 0, "renormalised": 0, "chi_clamped": 0, "below_store": 0}
+    growth, extras, timed = [], {}, 0
+    s_first = bt.stats(stream)
+    while timed < steps:
+        n = min(SEG, steps - timed)
+        s0 = bt.stats(stream)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        bt.step(n, stream)
+        z.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(z)
+        if n == SEG:
+            tk += sum(x.elapsed_time(y) for x, y in kev)
+        s1 = bt.stats(stream)
+        c = bt.ctr.read()
+        if c.status != 0:
+            raise SystemExit(f"bench: cascade steps ended with status {c.status} ({B.status_string(c.status)}), "
+                             f"{c.dropped_capacity} daughters dropped: no valid measurement")
+        for k in tot:
+            tot[k] += int(getattr(c, k))
+        psteps += float(s1.particle_steps - s0.particle_steps)
+        d_sp += [float(s1.species_steps[i] - s0.species_steps[i]) for i in range(3)]
+        bt.ctr.zero()
+        timed += n
+        growth.append({"step": int(s1.step), "electrons": int(s1.alive[0]), "positrons": int(s1.alive[1]),
+                       "photons": int(s1.alive[2])})
+        if extras_on and timed == ERR_AT:  # accuracy mid-cascade (untimed; the batch moves on ERR_STEPS steps)
+            alive = int(sum(s1.alive))
+            err, cpu = error_leg(bt, wl, fields, seeds, torch, ERR_STEPS, stride=max(16, alive // 200000))
+            extras["error"], extras["cpu_baseline"] = err, cpu
+            c = bt.ctr.read()
+            if c.status != 0:
+                raise SystemExit("bench: the error leg's steps overflowed")
+            bt.ctr.zero()
+    stop.set()
+    th.join(timeout=5)
+    tmax, psteps_all = ms, psteps
+    if dist is not None:
+        tmax, psteps_all = reduce_over_ranks(ms, psteps, dist, device)
+    value = psteps_all / (tmax / 1e3)
+    peak, peak_kind = measured_peaks()
+    alg = 88.0 * (d_sp[0] + d_sp[1]) + 56.0 * d_sp[2] + 20.0 * tot["rate_steps"] + 8.0 * tot["events"] + \
+        52.0 * tot["stored"]
+    full = steps // SEG * SEG  # steps whose kernels were event-timed (whole graph launches)
+    roof = {"kernel": "batch_step_kernel+batch_event_kernel", "bound": "hbm", "peak": peak, "unit": "GB/s",
+            "peak_source": peak_kind, "traffic": None,
+            "algorithmic_bytes_per_launch": alg / steps}
+    if tk > 0:
+        achieved = alg * (full / steps) / (tk / 1e3) / 1e9
+        roof.update({"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+                     "ms_per_launch": round(tk / full, 4), "share_of_step": round(tk / (ms * full / steps), 4)})
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": 0,
+        "ms_per_step": tmax / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "electrons_initial": wl.n_electrons, "gamma": wl.gamma,
+                   "laser": f"two colliding CP pulses a0={wl.a0:g}, {wl.wavelength_um:g} um, {wl.n_cycles:g} cycles",
+                   "photon_store_min_mc2": wl.photon_store_min, "sizing": sizing,
+                   "buffers": {"electrons": caps[0][0], "positrons": caps[0][1], "photons": caps[0][2]},
+                   "timed": f"all {steps} steps from step 0, graph launches of {SEG} steps",
+                   "launch": {"variant": v, "blocks_per_sm": bps, "chunk": ch, "graph_steps": SEG},
+                   "parallelism": f"replicas x{world}", "l2": "state > L2 (no flush needed)",
+                   "load_s": round(t_load, 1), "tables": "256 chi x 256 r, FP64-built"},
+        "roofline": roof,
+        "clocks": summarize_clocks(clock_lines),
+        "gpu_launches": 7 * steps,
+        "growth": growth,
+        "particle_steps_timed": {"electrons": d_sp[0], "positrons": d_sp[1], "photons": d_sp[2]},
+        "counters": tot,
+        "table_build_s": round(t_tables, 2),
+    }
+    out.update(extras)
+    bt.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
 
 
 def mlp_leg(args, tables, torch):

@@ -91,10 +91,11 @@ class ParticleBuffer:
             self.s.n_dead = self.n_dead.data_ptr()
 
     # ---- host <-> device marshalling -----------------------------------------------------
-    def load(self, pos, mom, spin, w, ids, tau=None):
-        """Copy host arrays (n, 3), (n, 3), (n, 3), (n,), (n,) [and tau (n,)] into [0, n) and set the count."""
+    def load(self, pos, mom, spin, w, ids, tau=None, offset=0):
+        """Copy host arrays (n, 3), (n, 3), (n, 3), (n,), (n,) [and tau (n,)] into [offset, offset + n) and
+        set the count to offset + n (loading a beam in chunks: offset = particles already loaded)."""
         n = len(ids)
-        if n > self.capacity:
+        if offset < 0 or offset + n > self.capacity:
             raise ValueError("capacity")
         pos, mom, spin = (np.asarray(a, dtype=np.float64).reshape(n, 3) for a in (pos, mom, spin))
         w = np.asarray(w, dtype=np.float64).reshape(n)
@@ -106,11 +107,11 @@ class ParticleBuffer:
             host[6:9] = spin.T
             host[9] = tau
             host[10] = w
-            self.planes[:, :n].copy_(torch.from_numpy(host))
+            self.planes[:, offset:offset + n].copy_(torch.from_numpy(host))
         else:
-            self.q[:, :n].copy_(torch.from_numpy(pack32(self.charge, pos, mom, spin, w, tau)))
-        self.ids[:n].copy_(torch.from_numpy(np.asarray(ids, dtype=np.uint64).view(np.int64)))
-        self.counts.copy_(torch.tensor([n, n], dtype=torch.int64))
+            self.q[:, offset:offset + n].copy_(torch.from_numpy(pack32(self.charge, pos, mom, spin, w, tau)))
+        self.ids[offset:offset + n].copy_(torch.from_numpy(np.asarray(ids, dtype=np.uint64).view(np.int64)))
+        self.counts.copy_(torch.tensor([offset + n, offset + n], dtype=torch.int64))
         if hasattr(self, "n_dead"):
             self.n_dead.zero_()
 

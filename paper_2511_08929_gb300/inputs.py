@@ -217,3 +217,56 @@ def batched_instances(n_inst: int = 96, seed: int = 3, n_min: float = 1e3, n_max
 # gamma ~ U[500, 8000], partially polarized spins, LP / CP alternating, 0.8 um, 10 cycles, 2000 steps,
 # NLC + NBW, buffers 4x per species.
 BATCHED_96 = BatchWorkload("batched96_n1e3-2e6_a10-300_g500-8000", 96, 1e3, 2e6)
+
+
+@dataclasses.dataclass
+class CascadeWorkload:
+    """Electrons seeded where two circularly polarized pulses collide head on (the plane-wave stand-in for
+    the rotating-field cascade of Sec. 8.6.5): gamma 1000, directions uniform in the x-y plane (across the
+    laser axis), z ~ U[-lambda/4, lambda/4] about the point where the two pulse fronts meet at t = 0,
+    unpolarized (random unit spins).  Both pulses: a0 per component, 1 um, n_cycles sin^2 envelopes
+    (field kind CP_COUNTER, phase 0).  NLC and NBW both resolved; photons below photon_store_min (m c^2)
+    are not stored.  The beam is generated in chunks of `chunk` electrons, chunk c with seed + c and ids
+    c * chunk + i + 1, so any chunk can be made alone."""
+    name: str = "cascade_cp2_a500_g1000_n2e8"
+    n_electrons: int = 200_000_000
+    gamma: float = 1000.0
+    a0: float = 500.0
+    wavelength_um: float = 1.0
+    n_cycles: float = 15.0
+    steps: int = 3000
+    dt: float = 2.0 * math.pi / 100.0
+    photon_store_min: float = 300.0
+    seed: int = 5
+    chunk: int = 10_000_000
+
+    def instances(self):
+        return [{"n": self.n_electrons, "seed": self.seed}]
+
+    def laser(self, inst=None) -> Laser:
+        return Laser("CP_COUNTER", self.a0, self.wavelength_um, self.n_cycles, 0.0)
+
+    def chunk_beam(self, c: int, n=None) -> dict:
+        """Chunk c of the beam (its first n electrons if n is given)."""
+        m = min(self.chunk, self.n_electrons - c * self.chunk) if n is None else n
+        rng = np.random.default_rng([self.seed, c])
+        pm = math.sqrt(self.gamma * self.gamma - 1.0)
+        ph = rng.uniform(0.0, 2.0 * math.pi, m)
+        lam = 2.0 * math.pi
+        pos = np.zeros((m, 3))
+        pos[:, 2] = rng.uniform(-0.25 * lam, 0.25 * lam, m)
+        return {"pos": pos, "mom": np.column_stack([pm * np.cos(ph), pm * np.sin(ph), np.zeros(m)]),
+                "spin": _unit_vectors(rng, m), "w": np.ones(m),
+                "id": np.arange(m, dtype=np.uint64) + np.uint64(c * self.chunk + 1)}
+
+    def n_chunks(self) -> int:
+        return (self.n_electrons + self.chunk - 1) // self.chunk
+
+    def sample(self, k: int, inst, m: int) -> dict:
+        """m electrons drawn as the beam's are (the growth of a subsample stands for the beam's)."""
+        return self.chunk_beam(0, min(m, self.n_electrons))
+
+
+# 2e8 electrons, gamma 1000, two colliding CP pulses a0 = 500, 1 um, 15 cycles, 3000 steps, NLC + NBW,
+# compaction every step, FP32 path; photons below 300 m c^2 not stored.
+CASCADE_2E8 = CascadeWorkload()
