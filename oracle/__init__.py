@@ -131,6 +131,8 @@ def lib():
             for fn in ("orc_nlc_rate_lookup", "orc_nbw_rate_lookup"):
                 getattr(L, fn).restype = _D
                 getattr(L, fn).argtypes = [_P(_Tables), C.c_int, _D, _P(C.c_int)]
+            L.orc_chi.restype = _D
+            L.orc_chi.argtypes = [_D, _D, _P(_D), _P(_D), _P(_D)]
             L.orc_airy_scorer.argtypes = [_D, _P(_D)]
             L.orc_amm.restype = _D
             L.orc_amm.argtypes = [_D]
@@ -272,6 +274,11 @@ def mlp_target(chi: float, r: float, s: float):
 def mlp_cdf(chi: float, s: float, ln_up: float) -> float:
     """Exact mixture CDF of the NLC spectrum with spin projection s at u' = exp(ln_up)."""
     return lib().orc_mlp_cdf(float(chi), float(s), float(ln_up))
+
+
+def chi(eta0, e, p, E, B):
+    """chi of a particle of energy e, momentum p in E, B, as the step functions evaluate it."""
+    return lib().orc_chi(float(eta0), float(e), _dp(_v3(p)), _dp(_v3(E)), _dp(_v3(B)))
 
 
 def airy_scorer(z: float):

@@ -868,6 +868,12 @@ static double chi_of(double eta0, double e, const double p[3], const double E[3]
     return eta0 * sqrt(v > 0.0 ? v : 0.0);
 }
 
+/* chi_of for tests */
+double orc_chi(double eta0, double e, const double p[3], const double E[3], const double B[3])
+{
+    return chi_of(eta0, e, p, E, B);
+}
+
 /* Rodrigues rotation of s about the unit axis n by angle th. */
 static void rotate(double s[3], const double n[3], double th)
 {

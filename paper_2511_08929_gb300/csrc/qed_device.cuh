@@ -73,6 +73,8 @@ __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
 __device__ __forceinline__ double exp_(double v) { return exp(v); }
 __device__ __forceinline__ float exp_(float v) { return expf(v); }
+__device__ __forceinline__ void sincospi_(double v, double* s, double* c) { sincospi(v, s, c); }
+__device__ __forceinline__ void sincospi_(float v, float* s, float* c) { sincospif(v, s, c); }
 __device__ __forceinline__ double log_(double v) { return log(v); }
 __device__ __forceinline__ float log_(float v) { return logf(v); }
 __device__ __forceinline__ void sincos_(double v, double* s, double* c) { sincos(v, s, c); }
@@ -193,8 +195,17 @@ __device__ __forceinline__ R envelope_acc(R ps, R dp, const FieldP<R>& f) {
 
 // phase_t = t + phase (split by the caller for the FP32 path as hi + lo).  ACC: the accurate sine and
 // cosine (event passes of the FP32 path); otherwise the fast ones.
+// the transverse E of the forward and of the backward wave of QED_FIELD_CP_COUNTER, so that a caller can
+// form E + v x B wave by wave (B1 = z x E1, B2 = -z x E2)
+template <class R>
+struct Waves {
+    R e1x, e1y, e2x, e2y;
+};
+
+// waves: filled for QED_FIELD_CP_COUNTER only (optional)
 template <class R, bool ACC = false>
-__device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x, V3<R>& E, V3<R>& B) {
+__device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x, V3<R>& E, V3<R>& B,
+                                           Waves<R>* waves = nullptr) {
     if (f.kind == QED_FIELD_CONST) {
         E = v3(f.E0x, f.E0y, f.E0z);
         B = v3(f.B0x, f.B0y, f.B0z);
@@ -203,9 +214,10 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
     if (f.kind == QED_FIELD_ROT_B) {  // |B| = B0z turning from z to y as t + phase runs over [0, phimax]
         R u = div_(ph_hi + ph_lo, f.phimax);
         u = u < R(0) ? R(0) : (u > R(1) ? R(1) : u);
-        const R th = R(0.5 * kPi) * u;
+        R sn, cs;
+        sincospi_(R(0.5) * u, &sn, &cs);  // angle (pi/2) u, u in [0, 1]: no large-argument reduction
         E = v3(R(0), R(0), R(0));
-        B = v3(R(0), f.B0z * sin(th), f.B0z * cos(th));
+        B = v3(R(0), f.B0z * sn, f.B0z * cs);
         return;
     }
     // phase t + phase - z: the rounding error of the subtraction is recovered exactly and added to the
@@ -226,6 +238,7 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
         B = v3(-ey, ex, R(0));  // forward wave: B = z x E
     }
     if (f.kind == QED_FIELD_CP_COUNTER) {
+        if (waves) *waves = Waves<R>{E.x, E.y, R(0), R(0)};
         R e2;
         const R ps2 = two_sum(ph_hi, x.z, e2);
         const R dp2 = e2 + ph_lo;
@@ -236,6 +249,10 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
             if (ACC) phase_sincos_acc(ps2, dp2, &s2, &c2);
             else phase_sincos(ps2, &s2, &c2, dp2);
             const R ex2 = a2 * c2, ey2 = a2 * s2;
+            if (waves) {
+                waves->e2x = ex2;
+                waves->e2y = ey2;
+            }
             E.x += ex2;
             E.y += ey2;
             B.x += ey2;  // backward wave: B = -z x E

@@ -267,25 +267,56 @@ __device__ __forceinline__ uint32_t flags_of(const Ctx& C) {
     return FIX ? FIX : C.S.flags;
 }
 
-// chi and the basis vector f = E + v x B for the FP32 path.  In a single plane wave travelling along +z
-// (the linear and circular lasers: E transverse, B = z x E) the invariant reduces exactly to
-// chi = eta0 |e - p_z| |E| (free of the cancellation of the general form) and f to
-// (1 - v_z) E + (v . E) z; other fields take the general forms.
+// chi and the basis vector f = E + v x B for the FP32 path, in forms free of the cancellation that the
+// general ones suffer for a particle moving with a wave (there e E and p x B nearly cancel, and the
+// general forms lose ~1/theta^2 of relative precision at an angle theta to the wave).  With
+// e - p_z and e + p_z from e_minus_pz / e_plus_pz (no difference of nearly equal numbers):
+//   a single wave along +z (the linear and circular lasers; E transverse, B = z x E):
+//     chi = eta0 (e - p_z) |E|,   f = ((e - p_z) E + (p.E) z) / e;
+//   the counter-propagating pair (E1 forward with B1 = z x E1, E2 backward with B2 = -z x E2):
+//     chi^2 = eta0^2 (|(e - p_z) E1 + (e + p_z) E2|^2 - 4 (p.E1)(p.E2)),
+//     f = ((e - p_z) E1 + (e + p_z) E2 + (p.E1 - p.E2) z) / e;
+// both are e E + p x B and the invariant chi^2 = eta0^2 ((e E + p x B)^2 - (p.E)^2) written out for
+// these fields.  Other fields take the general forms.
 __device__ __forceinline__ bool single_wave(const Ctx& C) {
     return C.F.kind == QED_FIELD_LP || C.F.kind == QED_FIELD_CP;
 }
 
-__device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B) {
-    if (single_wave(C)) return C.F.eta0 * fabsf(e - p.z) * sqrt_(fma_(E.x, E.x, E.y * E.y));
+__device__ __forceinline__ bool two_wave(const Ctx& C) { return C.F.kind == QED_FIELD_CP_COUNTER; }
+
+// e - p_z and e + p_z of a particle with e^2 = m2 + p^2 (m2 = 1 lepton, 0 photon): the one whose terms
+// would cancel is taken as (m2 + p_x^2 + p_y^2) / (the other)
+__device__ __forceinline__ float e_minus_pz(float e, const F3& p, float m2) {
+    return p.z > 0.0f ? div_(fma_(p.x, p.x, fma_(p.y, p.y, m2)), e + p.z) : e - p.z;
+}
+__device__ __forceinline__ float e_plus_pz(float e, const F3& p, float m2) {
+    return p.z < 0.0f ? div_(fma_(p.x, p.x, fma_(p.y, p.y, m2)), e - p.z) : e + p.z;
+}
+
+// w: the two waves' transverse E (field_eval's `waves`), read for the counter-propagating pair only
+__device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B, float m2,
+                                      const Waves<float>& w) {
+    if (single_wave(C)) return C.F.eta0 * e_minus_pz(e, p, m2) * sqrt_(fma_(E.x, E.x, E.y * E.y));
+    if (two_wave(C)) {
+        const float em = e_minus_pz(e, p, m2), ep = e_plus_pz(e, p, m2);
+        const float tx = fma_(em, w.e1x, ep * w.e2x), ty = fma_(em, w.e1y, ep * w.e2y);
+        const float pe1 = fma_(p.x, w.e1x, p.y * w.e1y), pe2 = fma_(p.x, w.e2x, p.y * w.e2y);
+        const float v = fma_(-4.0f * pe1, pe2, fma_(tx, tx, ty * ty));
+        return C.F.eta0 * sqrt_(v > 0.0f ? v : 0.0f);
+    }
     return chi_of(C.F.eta0, e, p, E, B);
 }
 
 __device__ __forceinline__ bool basis32(const Ctx& C, const F3& E, const F3& B, const F3& v, const F3& khat, float sign,
-                                       F3& eps, F3& beta) {
+                                       F3& eps, F3& beta, float e, const F3& p, float m2, const Waves<float>& w) {
     F3 f;
     if (single_wave(C)) {
-        const float g = 1.0f - v.z;
+        const float g = div_(e_minus_pz(e, p, m2), e);
         f = F3{g * E.x, g * E.y, fma_(v.x, E.x, v.y * E.y)};
+    } else if (two_wave(C)) {
+        const float em = e_minus_pz(e, p, m2), ep = e_plus_pz(e, p, m2), ie = rcp_(e);
+        f = F3{ie * fma_(em, w.e1x, ep * w.e2x), ie * fma_(em, w.e1y, ep * w.e2y),
+               ie * (fma_(p.x, w.e1x, p.y * w.e1y) - fma_(p.x, w.e2x, p.y * w.e2y))};
     } else {
         f = E + cross(v, B);
     }
@@ -354,7 +385,8 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     st.p = F3{a.w, b.x, b.y};
     st.s = F3{b.z, b.w, cc.x};
     st.w = cc.y;
-    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
+    Waves<float> w{0.0f, 0.0f, 0.0f, 0.0f};  // the two waves of the counter-propagating field
+    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B, &w);
     const F3 pold = st.p;
     // the field kinds known to have E_z = B_z = 0; any other kind takes the general forms
     const bool transverse = C.F.kind >= QED_FIELD_LP && C.F.kind <= QED_FIELD_CP_COUNTER;
@@ -365,7 +397,7 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
         // the anomalous moment: alpha/(2 pi), a(chi) at pb, or none (tbmt_a; chi32 takes the plane-wave form)
         float ae = (float)(kAlpha / (2.0 * kPi));
         if (fl & (QED_F_G2 | QED_F_LOOP)) ae = 0.0f;
-        else if (fl & QED_F_AMM) ae = amm_lookup(T, chi32(C, sqrt_(1.0f + dot(pb, pb)), pb, st.E, st.B));
+        else if (fl & QED_F_AMM) ae = amm_lookup(T, chi32(C, sqrt_(1.0f + dot(pb, pb)), pb, st.E, st.B, 1.0f, w));
         st.s = rotate(st.s, transverse ? tbmt_omega_t(pb, st.E, st.B, C.q, paper, ae) : tbmt_omega(pb, st.E, st.B, C.q, paper, ae), dt);
     }
     st.gam = sqrt_(1.0f + dot(st.p, st.p));
@@ -376,12 +408,12 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     }
     st.qed = false;
     if (!(fl & QED_F_EMIT)) return;
-    st.chi = chi32(C, st.gam, st.p, st.E, st.B);
+    st.chi = chi32(C, st.gam, st.p, st.E, st.B, 1.0f, w);
     const float pn2 = dot(st.p, st.p);
     if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.khat = rsqrtf(pn2) * st.p;
     const F3 v = rg * st.p;
-    if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta)) return;
+    if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta, st.gam, st.p, 1.0f, w)) return;
     st.qed = true;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
@@ -787,7 +819,8 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.k = F3{cc.x, cc.y, cc.z};
     st.P = F3{a.w, b.x, b.y};
     st.w = cc.w;
-    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
+    Waves<float> w{0.0f, 0.0f, 0.0f, 0.0f};  // the two waves of the counter-propagating field
+    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B, &w);
     const float en2 = dot(st.k, st.k);
     st.en = sqrt_(en2);
     st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
@@ -795,7 +828,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     if (flags_of<FIX>(C) & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;
     if (!(flags_of<FIX>(C) & QED_F_EMIT) || !(en2 > 0.0f)) return;
-    st.chi = chi32(C, st.en, st.k, st.E, st.B);
+    st.chi = chi32(C, st.en, st.k, st.E, st.B, 0.0f, w);
     if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
@@ -803,7 +836,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     // most photons are too soft, or in too weak a field, for a pair rate in the float range: nothing of
     // the basis or the Stokes vector is needed for them (the caller moves them and stops)
     if (st.Wp == 0.0f && st.Wm == 0.0f) return;
-    if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta)) return;
+    if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta, st.en, st.k, 0.0f, w)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
     if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;

@@ -87,12 +87,15 @@ def oracle_full_step(tb, f, st, leptons, photons, el=None, po=None, ctr=None):
 
 
 def compare_with_flips(gpu: dict, ora: dict, rtol: float, what: str, P_headless: bool = False, pos_floor=1.0,
-                       diverged=0.1, frac_ok=0.0, hard=None):
+                       diverged=0.1, frac_ok=0.0, hard=None, spin_scale=None):
     """FP32-vs-FP64 comparison, matched by id.  A decision taken in FP32 next to its threshold (an event,
     a collapse sign) can go the other way: it leaves one daughter id on one side only and one on the
     other; such unmatched ids, and particles whose state moved apart by more than `diverged`, are flips.
     Every other particle must be within rtol, except that a fraction `frac_ok` of them may reach `hard`
-    (ill-conditioned directions, see the FP32 tests).  Returns (flipped decisions, error quantiles)."""
+    (ill-conditioned directions, see the FP32 tests).  spin_scale = (ids, factors >= 1): the spin (or
+    P) and optical-depth bars of those particles are rtol x factor (a step whose own condition number is
+    that factor: the optical depth depends on the turned spin through W(s.beta)).
+    Returns (flipped decisions, error quantiles)."""
     g, o = by_id(gpu), by_id(ora)
     common, gi, oi = np.intersect1d(g["id"], o["id"], assume_unique=False, return_indices=True)
     only = (len(g["id"]) - len(common)) + (len(o["id"]) - len(common))
@@ -107,8 +110,18 @@ def compare_with_flips(gpu: dict, ora: dict, rtol: float, what: str, P_headless:
         flip = (gperp * operp).sum(1) < 0
         sg = np.where(flip[:, None], gpar - gperp, sg)
     e["spin"] = np.linalg.norm(sg - so, axis=1)
+    if spin_scale is not None:
+        sid, fac = np.asarray(spin_scale[0], dtype=np.uint64), np.asarray(spin_scale[1], dtype=np.float64)
+        o_ = np.argsort(sid)
+        sid, fac = sid[o_], fac[o_]
+        ix = np.clip(np.searchsorted(sid, gg["id"]), 0, max(len(sid) - 1, 0))
+        hit = (sid[ix] == gg["id"]) if len(sid) else np.zeros(len(gg["id"]), bool)
+        div_ = np.where(hit, np.maximum(fac[ix] if len(sid) else 1.0, 1.0), 1.0)
+        e["spin"] = e["spin"] / div_
+    else:
+        div_ = 1.0
     fin = np.isfinite(oo["tau"]) & np.isfinite(gg["tau"])
-    e["tau"] = np.where(fin, np.abs(gg["tau"] - oo["tau"]) / np.maximum(np.abs(oo["tau"]), 1.0), 0.0)
+    e["tau"] = np.where(fin, np.abs(gg["tau"] - oo["tau"]) / np.maximum(np.abs(oo["tau"]), 1.0), 0.0) / div_
     e["w"] = np.abs(gg["w"] - oo["w"]) / np.maximum(np.abs(oo["w"]), 1e-300)
     worst_each = np.max(np.stack([e["pos"], e["mom"], e["spin"], e["tau"]]), axis=0)
     div = worst_each > diverged

@@ -31,14 +31,41 @@ def test_workload_generator_chunks():
     assert np.all(a["mom"][:, 2] == 0) and np.all(np.abs(a["pos"][:, 2]) <= np.pi / 2)
 
 
+AE = 7.2973525693e-3 / (2 * np.pi)
+
+
+def _tbmt_angle(st: dict, of, t: float, dt: float, q: float) -> np.ndarray:
+    """The T-BMT turn |Omega| dt of each lepton's step (FP64: Boris push from the step's start, the
+    time-centred momentum, the standard T-BMT vector)."""
+    out = np.zeros(len(st["id"]))
+    for i in range(len(st["id"])):
+        E, B = (np.asarray(v) for v in O.field_eval(of, st["pos"][i], t))
+        p = st["mom"][i]
+        h = 0.5 * q * dt
+        pm = p + h * E
+        tv = h * B / np.sqrt(1 + pm @ pm)
+        pl = pm + np.cross(pm + np.cross(pm, tv), 2 * tv / (1 + tv @ tv))
+        pb = 0.5 * (p + pl + h * E)
+        g = np.sqrt(1 + pb @ pb)
+        b = pb / g
+        Om = (AE + 1 / g) * B - (AE * g / (g + 1)) * (b @ B) * b - (AE + 1 / (g + 1)) * np.cross(b, E)
+        out[i] = np.linalg.norm(Om) * dt
+    return out
+
+
 @pytest.mark.gpu
 def test_cascade_subset_against_oracle():
+    """Five steps inside the cascade, each from the GPU's state.  Low-energy leptons at the magnetic
+    antinodes of the standing wave turn their spin by up to ~30 rad in one step (gamma ~ 6 in |B| ~ 900):
+    such a step is ill-conditioned (a 1e-7 relative change of its inputs moves the spin by up to ~1e-5),
+    so the spin bar of a lepton (and of the photon it emits) is 1e-5 x max(1, its turn angle)."""
     from paper_2511_08929_gb300 import build as bld
     bld.build()
     wl = dataclasses.replace(I.CASCADE_2E8, n_electrons=4000, chunk=4000)
     gt = Q.Tables(**DESC)
     ot = O.tables(*DESC.values())
     f = Q.laser_field(wl.laser())
+    of = as_oracle_field(f)
     caps = (200000, 200000, 400000)
     bt = Q.Batch(gt, [f], [wl.seed], [caps], wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min)
     e = bt.buffers()[0][0]
@@ -49,27 +76,36 @@ def test_cascade_subset_against_oracle():
     bt.step(start)
     torch.cuda.synchronize()
     bufs = bt.buffers()[0]
-    st0 = [x.read() for x in bufs]
-    assert len(st0[1]["id"]) > 1000 and len(st0[2]["id"]) > 1000, [len(x["id"]) for x in st0]
-    ora = [O.Particles.from_arrays(c, r["pos"], r["mom"], r["spin"], r["w"], r["id"], tau=r["tau"])
-           for c, r in zip(caps, st0)]
-    steps = 10
-    bt.step(steps)
-    of = as_oracle_field(f)
-    ctr = O.Counters()
-    for s in range(steps):
-        st = Q.step_desc(wl.dt, float(start + s) * wl.dt, start + s, wl.seed, photon_store_min=wl.photon_store_min)
-        oracle_full_step(ot, of, as_oracle_step(st), [(ora[0], -1), (ora[1], 1)], ora[2], ora[0], ora[1], ctr)
-    torch.cuda.synchronize()
+    flips, psteps, events, worst_turn = 0, 0, 0, 0.0
+    for s in range(5):
+        step = start + s
+        pre = [x.read() for x in bufs]
+        if s == 0:
+            assert len(pre[1]["id"]) > 1000 and len(pre[2]["id"]) > 1000, [len(x["id"]) for x in pre]
+        ora = [O.Particles.from_arrays(c, r["pos"], r["mom"], r["spin"], r["w"], r["id"], tau=r["tau"])
+               for c, r in zip(caps, pre)]
+        bt.step(1)
+        st = Q.step_desc(wl.dt, float(step) * wl.dt, step, wl.seed, photon_store_min=wl.photon_store_min)
+        ctr = oracle_full_step(ot, of, as_oracle_step(st), [(ora[0], -1), (ora[1], 1)], ora[2], ora[0], ora[1])
+        torch.cuda.synchronize()
+        events += ctr.events
+        # each lepton's turn angle, and the same factor for the photon it emitted this step
+        ids, fac = [], []
+        for r, q in ((pre[0], -1.0), (pre[1], 1.0)):
+            ang = _tbmt_angle(r, of, float(step) * wl.dt, wl.dt, q)
+            worst_turn = max(worst_turn, float(ang.max(initial=0.0)))
+            ids.append(r["id"])
+            fac.append(ang)
+            kids = np.array([O.child_ids(int(i), wl.seed, step)[0] for i in r["id"]], dtype=np.uint64)
+            ids.append(kids)
+            fac.append(ang)
+        scale = (np.concatenate(ids), np.concatenate(fac))
+        for buf, o, name, ph in zip(bufs, ora, ("electrons", "positrons", "photons"), (False, False, True)):
+            fl, _ = compare_with_flips(buf.read(), o.view(), 1e-5, name, P_headless=ph, spin_scale=scale)
+            flips += fl
+        psteps += sum(len(x["id"]) for x in pre)
     assert bt.ctr.read().status == 0
-    assert ctr.events > 500  # emissions and pairs in the window
-    assert ora[1].n > len(st0[1]["id"])  # positrons were made
-    tol = 1e-5 * steps
-    flips = 0
-    psteps = steps * sum(len(x["id"]) for x in st0)
-    for buf, o, name, ph in zip(bufs, ora, ("electrons", "positrons", "photons"), (False, False, True)):
-        fl, _ = compare_with_flips(buf.read(), o.view(), tol, name, P_headless=ph)
-        flips += fl
+    assert events > 1000 and worst_turn > 10.0
     assert flips <= max(3, 1e-5 * psteps), (flips, psteps)
     bt.close()
     gt.close()

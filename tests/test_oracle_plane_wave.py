@@ -94,3 +94,48 @@ def test_reduced_chi_fails_for_the_counter_propagating_field():
         red = ETA0 * abs(e - p[2]) * np.hypot(E[0], E[1])
         worst = max(worst, abs(red - chi) / max(chi, 1e-300))
     assert worst > 1e-3
+
+
+def _chi_mp(e, p, E, B, m2):
+    """The invariant of Sec. 1 in 60-digit arithmetic from the same (double) inputs; e recomputed from p."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    P = [mp.mpf(float(x)) for x in p]
+    Ev = [mp.mpf(float(x)) for x in E]
+    Bv = [mp.mpf(float(x)) for x in B]
+    ee = mp.sqrt(m2 + sum(x * x for x in P))
+    pxB = [P[1] * Bv[2] - P[2] * Bv[1], P[2] * Bv[0] - P[0] * Bv[2], P[0] * Bv[1] - P[1] * Bv[0]]
+    a = [ee * Ev[i] + pxB[i] for i in range(3)]
+    pe = sum(P[i] * Ev[i] for i in range(3))
+    return float(ETA0 * mp.sqrt(sum(x * x for x in a) - pe * pe))
+
+
+@pytest.mark.parametrize("kind", [O.FIELD_CP, O.FIELD_CP_COUNTER])
+def test_chi_evaluation_against_60_digits(kind):
+    """The oracle's chi against the invariant in 60-digit arithmetic from the same inputs: generic
+    directions to 1e-13; leptons and photons moving with the forward wave (angles 1e-4 .. 1e-2 to it,
+    gamma 1e2 .. 1e4) to 4e-16 x the cancellation factor (e|E| + |p||B|)^2 / (chi/eta0)^2 of the formula
+    (both inside e E + p x B and in the difference of squares), which for an angle theta to the wave grows
+    like 16/theta^4: the invariant itself is that ill-conditioned for such particles in double."""
+    rng = np.random.default_rng(11 + kind)
+    f = O.field(kind, a0=200.0, n_cycles=4.0, phase=0.7)
+    n_checked = 0
+    for xi, ti in zip(*_points(rng, 200)):
+        E, B = O.field_eval(f, xi, ti)
+        if not np.any(E):
+            continue
+        for m2 in (1.0, 0.0):
+            p = rng.normal(size=3) * rng.uniform(1.0, 5000.0)  # generic
+            e = np.sqrt(m2 + p @ p)
+            assert O.chi(ETA0, e, p, E, B) == pytest.approx(_chi_mp(e, p, E, B, m2), rel=1e-13)
+            th = 10 ** rng.uniform(-4, -2)  # co-moving with the forward wave
+            g = 10 ** rng.uniform(2, 4)
+            ph = rng.uniform(0, 2 * np.pi)
+            p = g * np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+            e = np.sqrt(m2 + p @ p)
+            ref = _chi_mp(e, p, E, B, m2)
+            kappa = (e * np.linalg.norm(E) + np.linalg.norm(p) * np.linalg.norm(B)) ** 2 / max((ref / ETA0) ** 2, 1e-300)
+            got = O.chi(ETA0, e, p, E, B)
+            assert abs(got - ref) <= 4e-16 * kappa * ref + 1e-300, (got, ref, kappa)
+            n_checked += 1
+    assert n_checked > 50
