@@ -284,22 +284,34 @@ __device__ __forceinline__ bool single_wave(const Ctx& C) {
 
 __device__ __forceinline__ bool two_wave(const Ctx& C) { return C.F.kind == QED_FIELD_CP_COUNTER; }
 
-// e - p_z and e + p_z of a particle with e^2 = m2 + p^2 (m2 = 1 lepton, 0 photon): the one whose terms
-// would cancel is taken as (m2 + p_x^2 + p_y^2) / (the other)
-__device__ __forceinline__ float e_minus_pz(float e, const F3& p, float m2) {
-    return p.z > 0.0f ? div_(fma_(p.x, p.x, fma_(p.y, p.y, m2)), e + p.z) : e - p.z;
-}
-__device__ __forceinline__ float e_plus_pz(float e, const F3& p, float m2) {
-    return p.z < 0.0f ? div_(fma_(p.x, p.x, fma_(p.y, p.y, m2)), e - p.z) : e + p.z;
+// e - p_z and e + p_z of a particle with e^2 = m2 + p^2 (m2 = 1 lepton, 0 photon), for the single wave
+// (e - p_z only) and the counter-propagating pair (both): the one whose terms would cancel is taken as
+// (m2 + p_x^2 + p_y^2) / (the other).  Computed once per particle step, for chi and the basis.
+struct LightCone {
+    float em, ep;
+};
+
+__device__ __forceinline__ LightCone light_cone(const Ctx& C, float e, const F3& p, float m2) {
+    LightCone lc{0.0f, 0.0f};
+    if (single_wave(C) || two_wave(C)) {
+        const float q = fma_(p.x, p.x, fma_(p.y, p.y, m2));
+        if (p.z > 0.0f) {
+            lc.ep = e + p.z;
+            lc.em = div_(q, lc.ep);
+        } else {
+            lc.em = e - p.z;
+            if (two_wave(C)) lc.ep = div_(q, lc.em);
+        }
+    }
+    return lc;
 }
 
 // w: the two waves' transverse E (field_eval's `waves`), read for the counter-propagating pair only
-__device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B, float m2,
+__device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B, const LightCone& lc,
                                       const Waves<float>& w) {
-    if (single_wave(C)) return C.F.eta0 * e_minus_pz(e, p, m2) * sqrt_(fma_(E.x, E.x, E.y * E.y));
+    if (single_wave(C)) return C.F.eta0 * lc.em * sqrt_(fma_(E.x, E.x, E.y * E.y));
     if (two_wave(C)) {
-        const float em = e_minus_pz(e, p, m2), ep = e_plus_pz(e, p, m2);
-        const float tx = fma_(em, w.e1x, ep * w.e2x), ty = fma_(em, w.e1y, ep * w.e2y);
+        const float tx = fma_(lc.em, w.e1x, lc.ep * w.e2x), ty = fma_(lc.em, w.e1y, lc.ep * w.e2y);
         const float pe1 = fma_(p.x, w.e1x, p.y * w.e1y), pe2 = fma_(p.x, w.e2x, p.y * w.e2y);
         const float v = fma_(-4.0f * pe1, pe2, fma_(tx, tx, ty * ty));
         return C.F.eta0 * sqrt_(v > 0.0f ? v : 0.0f);
@@ -307,15 +319,16 @@ __device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const
     return chi_of(C.F.eta0, e, p, E, B);
 }
 
+// ie = 1/e
 __device__ __forceinline__ bool basis32(const Ctx& C, const F3& E, const F3& B, const F3& v, const F3& khat, float sign,
-                                       F3& eps, F3& beta, float e, const F3& p, float m2, const Waves<float>& w) {
+                                       F3& eps, F3& beta, float ie, const F3& p, const LightCone& lc,
+                                       const Waves<float>& w) {
     F3 f;
     if (single_wave(C)) {
-        const float g = div_(e_minus_pz(e, p, m2), e);
+        const float g = lc.em * ie;
         f = F3{g * E.x, g * E.y, fma_(v.x, E.x, v.y * E.y)};
     } else if (two_wave(C)) {
-        const float em = e_minus_pz(e, p, m2), ep = e_plus_pz(e, p, m2), ie = rcp_(e);
-        f = F3{ie * fma_(em, w.e1x, ep * w.e2x), ie * fma_(em, w.e1y, ep * w.e2y),
+        f = F3{ie * fma_(lc.em, w.e1x, lc.ep * w.e2x), ie * fma_(lc.em, w.e1y, lc.ep * w.e2y),
                ie * (fma_(p.x, w.e1x, p.y * w.e1y) - fma_(p.x, w.e2x, p.y * w.e2y))};
     } else {
         f = E + cross(v, B);
@@ -397,7 +410,10 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
         // the anomalous moment: alpha/(2 pi), a(chi) at pb, or none (tbmt_a; chi32 takes the plane-wave form)
         float ae = (float)(kAlpha / (2.0 * kPi));
         if (fl & (QED_F_G2 | QED_F_LOOP)) ae = 0.0f;
-        else if (fl & QED_F_AMM) ae = amm_lookup(T, chi32(C, sqrt_(1.0f + dot(pb, pb)), pb, st.E, st.B, 1.0f, w));
+        else if (fl & QED_F_AMM) {
+            const float gb = sqrt_(1.0f + dot(pb, pb));
+            ae = amm_lookup(T, chi32(C, gb, pb, st.E, st.B, light_cone(C, gb, pb, 1.0f), w));
+        }
         st.s = rotate(st.s, transverse ? tbmt_omega_t(pb, st.E, st.B, C.q, paper, ae) : tbmt_omega(pb, st.E, st.B, C.q, paper, ae), dt);
     }
     st.gam = sqrt_(1.0f + dot(st.p, st.p));
@@ -408,12 +424,13 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     }
     st.qed = false;
     if (!(fl & QED_F_EMIT)) return;
-    st.chi = chi32(C, st.gam, st.p, st.E, st.B, 1.0f, w);
+    const LightCone lc = light_cone(C, st.gam, st.p, 1.0f);
+    st.chi = chi32(C, st.gam, st.p, st.E, st.B, lc, w);
     const float pn2 = dot(st.p, st.p);
     if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.khat = rsqrtf(pn2) * st.p;
     const F3 v = rg * st.p;
-    if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta, st.gam, st.p, 1.0f, w)) return;
+    if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta, rg, st.p, lc, w)) return;
     st.qed = true;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
@@ -828,7 +845,8 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     if (flags_of<FIX>(C) & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;
     if (!(flags_of<FIX>(C) & QED_F_EMIT) || !(en2 > 0.0f)) return;
-    st.chi = chi32(C, st.en, st.k, st.E, st.B, 0.0f, w);
+    const LightCone lc = light_cone(C, st.en, st.k, 0.0f);
+    st.chi = chi32(C, st.en, st.k, st.E, st.B, lc, w);
     if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
@@ -836,7 +854,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     // most photons are too soft, or in too weak a field, for a pair rate in the float range: nothing of
     // the basis or the Stokes vector is needed for them (the caller moves them and stops)
     if (st.Wp == 0.0f && st.Wm == 0.0f) return;
-    if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta, st.en, st.k, 0.0f, w)) return;
+    if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta, rsqrtf(en2), st.k, lc, w)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
     if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
