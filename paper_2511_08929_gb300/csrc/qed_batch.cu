@@ -556,6 +556,7 @@ struct qed_batch_s {
     int device, sms;
     const qed_tables_s* tables;
     int n_inst;
+    bool plane_waves;  // every instance a single plane wave (LP or CP): the fixed-flag kernels may run it
     qed_batch_desc desc;
     qed_counters* ctr;
     InstDev* d_inst;
@@ -603,7 +604,7 @@ static void launch_variant(const qed_batch_s* b, int grid, cudaStream_t st) {
 static const BatchVariant kVariants[2][QED_BATCH_VARIANTS] = {QED_VARIANTS(0u), QED_VARIANTS(QED_F_FULL)};
 
 static const BatchVariant& variant_of(const qed_batch_s* b, int v) {
-    return kVariants[b->desc.flags == QED_F_FULL ? 1 : 0][v];
+    return kVariants[b->desc.flags == QED_F_FULL && b->plane_waves ? 1 : 0][v];
 }
 
 static size_t variant_smem(const qed_batch_s* b, int v) {
@@ -733,6 +734,10 @@ extern "C" qed_status qed_batch_create(qed_tables_t t, const qed_instance* insta
     b->tables = t;
     b->n_inst = n_inst;
     b->desc = *desc;
+    b->plane_waves = true;
+    for (int i = 0; i < n_inst; ++i)
+        b->plane_waves = b->plane_waves &&
+                         (instances[i].field.kind == QED_FIELD_LP || instances[i].field.kind == QED_FIELD_CP);
     b->ctr = counters_dev;
     bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess;

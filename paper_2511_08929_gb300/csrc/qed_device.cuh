@@ -195,23 +195,15 @@ __device__ __forceinline__ R envelope_acc(R ps, R dp, const FieldP<R>& f) {
 
 // phase_t = t + phase (split by the caller for the FP32 path as hi + lo).  ACC: the accurate sine and
 // cosine (event passes of the FP32 path); otherwise the fast ones.
-// the transverse E of the forward and of the backward wave of QED_FIELD_CP_COUNTER, so that a caller can
-// form E + v x B wave by wave (B1 = z x E1, B2 = -z x E2)
-template <class R>
-struct Waves {
-    R e1x, e1y, e2x, e2y;
-};
-
-// waves: filled for QED_FIELD_CP_COUNTER only (optional)
-template <class R, bool ACC = false>
-__device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x, V3<R>& E, V3<R>& B,
-                                           Waves<R>* waves = nullptr) {
-    if (f.kind == QED_FIELD_CONST) {
+// PW: the caller knows the field is a single plane wave (QED_FIELD_LP or QED_FIELD_CP)
+template <class R, bool ACC = false, bool PW = false>
+__device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x, V3<R>& E, V3<R>& B) {
+    if (!PW && f.kind == QED_FIELD_CONST) {
         E = v3(f.E0x, f.E0y, f.E0z);
         B = v3(f.B0x, f.B0y, f.B0z);
         return;
     }
-    if (f.kind == QED_FIELD_ROT_B) {  // |B| = B0z turning from z to y as t + phase runs over [0, phimax]
+    if (!PW && f.kind == QED_FIELD_ROT_B) {  // |B| = B0z turning from z to y as t + phase runs over [0, phimax]
         R u = div_(ph_hi + ph_lo, f.phimax);
         u = u < R(0) ? R(0) : (u > R(1) ? R(1) : u);
         R sn, cs;
@@ -237,8 +229,7 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
         E = v3(ex, ey, R(0));
         B = v3(-ey, ex, R(0));  // forward wave: B = z x E
     }
-    if (f.kind == QED_FIELD_CP_COUNTER) {
-        if (waves) *waves = Waves<R>{E.x, E.y, R(0), R(0)};
+    if (!PW && f.kind == QED_FIELD_CP_COUNTER) {
         R e2;
         const R ps2 = two_sum(ph_hi, x.z, e2);
         const R dp2 = e2 + ph_lo;
@@ -249,16 +240,48 @@ __device__ __forceinline__ void field_eval(const FieldP<R>& f, R ph_hi, R ph_lo,
             if (ACC) phase_sincos_acc(ps2, dp2, &s2, &c2);
             else phase_sincos(ps2, &s2, &c2, dp2);
             const R ex2 = a2 * c2, ey2 = a2 * s2;
-            if (waves) {
-                waves->e2x = ex2;
-                waves->e2y = ey2;
-            }
             E.x += ex2;
             E.y += ey2;
             B.x += ey2;  // backward wave: B = -z x E
             B.y += -ex2;
         }
     }
+}
+
+// The two waves of QED_FIELD_CP_COUNTER separately: the transverse E of the forward wave (B1 = z x E1) and
+// of the backward wave (B2 = -z x E2), the same numbers field_eval adds up, so that a caller can form
+// e E + p x B wave by wave.
+template <class R>
+struct Waves {
+    R e1x, e1y, e2x, e2y;
+};
+
+template <class R, bool ACC = false>
+__device__ __forceinline__ Waves<R> field_waves(const FieldP<R>& f, R ph_hi, R ph_lo, const V3<R>& x) {
+    Waves<R> w{R(0), R(0), R(0), R(0)};
+    R e1;
+    const R ps = two_sum(ph_hi, -x.z, e1);
+    const R dp = e1 + ph_lo;
+    const R a = f.a0 * (ACC ? envelope_acc(ps, dp, f) : envelope(ps + dp, f));
+    if (a != R(0)) {
+        R s, c;
+        if (ACC) phase_sincos_acc(ps, dp, &s, &c);
+        else phase_sincos(ps, &s, &c, dp);
+        w.e1x = a * c;
+        w.e1y = a * s;
+    }
+    R e2;
+    const R ps2 = two_sum(ph_hi, x.z, e2);
+    const R dp2 = e2 + ph_lo;
+    const R a2 = f.a0 * (ACC ? envelope_acc(ps2, dp2, f) : envelope(ps2 + dp2, f));
+    if (a2 != R(0)) {
+        R s2, c2;
+        if (ACC) phase_sincos_acc(ps2, dp2, &s2, &c2);
+        else phase_sincos(ps2, &s2, &c2, dp2);
+        w.e2x = a2 * c2;
+        w.e2y = a2 * s2;
+    }
+    return w;
 }
 
 // ---------------------------------------------------------------------------------------------

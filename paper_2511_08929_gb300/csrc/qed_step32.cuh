@@ -284,52 +284,64 @@ __device__ __forceinline__ bool single_wave(const Ctx& C) {
 
 __device__ __forceinline__ bool two_wave(const Ctx& C) { return C.F.kind == QED_FIELD_CP_COUNTER; }
 
-// e - p_z and e + p_z of a particle with e^2 = m2 + p^2 (m2 = 1 lepton, 0 photon), for the single wave
-// (e - p_z only) and the counter-propagating pair (both): the one whose terms would cancel is taken as
-// (m2 + p_x^2 + p_y^2) / (the other).  Computed once per particle step, for chi and the basis.
-struct LightCone {
-    float em, ep;
+// The batched kernels built for a fixed flag set (FIX != 0) run only batches whose instances are all
+// single plane waves (the linear and circular lasers); the host picks them so.  They carry no code for
+// the other field kinds.
+template <uint32_t FIX>
+__device__ __forceinline__ constexpr bool plane_waves_only() {
+    return FIX != 0;
+}
+
+// e - p_z of a particle with e^2 = m2 + p^2 (m2 = 1 lepton, 0 photon): where it moves with the forward
+// wave (p_z > 0) e and p_z nearly cancel, and it is taken as (m2 + p_x^2 + p_y^2) / (e + p_z)
+__device__ __forceinline__ float e_minus_pz(float e, const F3& p, float m2) {
+    return p.z > 0.0f ? div_(fma_(p.x, p.x, fma_(p.y, p.y, m2)), e + p.z) : e - p.z;
+}
+
+// chi and f = E + v x B of the counter-propagating pair from its two waves (the forms above)
+struct ChiF {
+    float chi;
+    F3 f;
 };
 
-__device__ __forceinline__ LightCone light_cone(const Ctx& C, float e, const F3& p, float m2) {
-    LightCone lc{0.0f, 0.0f};
-    if (single_wave(C) || two_wave(C)) {
-        const float q = fma_(p.x, p.x, fma_(p.y, p.y, m2));
-        if (p.z > 0.0f) {
-            lc.ep = e + p.z;
-            lc.em = div_(q, lc.ep);
-        } else {
-            lc.em = e - p.z;
-            if (two_wave(C)) lc.ep = div_(q, lc.em);
-        }
+__device__ __forceinline__ ChiF two_wave_chi(const Waves<float>& w, float eta0, float e, const F3& p, float m2) {
+    const float q = fma_(p.x, p.x, fma_(p.y, p.y, m2));
+    float em, ep;
+    if (p.z > 0.0f) {
+        ep = e + p.z;
+        em = div_(q, ep);
+    } else {
+        em = e - p.z;
+        ep = div_(q, em);
     }
-    return lc;
+    const float tx = fma_(em, w.e1x, ep * w.e2x), ty = fma_(em, w.e1y, ep * w.e2y);
+    const float pe1 = fma_(p.x, w.e1x, p.y * w.e1y), pe2 = fma_(p.x, w.e2x, p.y * w.e2y);
+    const float ie = rcp_(e);
+    const float v = fma_(-4.0f * pe1, pe2, fma_(tx, tx, ty * ty));
+    return ChiF{eta0 * sqrt_(v > 0.0f ? v : 0.0f), F3{ie * tx, ie * ty, ie * (pe1 - pe2)}};
 }
 
-// w: the two waves' transverse E (field_eval's `waves`), read for the counter-propagating pair only
-__device__ __forceinline__ float chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B, const LightCone& lc,
-                                      const Waves<float>& w) {
-    if (single_wave(C)) return C.F.eta0 * lc.em * sqrt_(fma_(E.x, E.x, E.y * E.y));
-    if (two_wave(C)) {
-        const float tx = fma_(lc.em, w.e1x, lc.ep * w.e2x), ty = fma_(lc.em, w.e1y, lc.ep * w.e2y);
-        const float pe1 = fma_(p.x, w.e1x, p.y * w.e1y), pe2 = fma_(p.x, w.e2x, p.y * w.e2y);
-        const float v = fma_(-4.0f * pe1, pe2, fma_(tx, tx, ty * ty));
-        return C.F.eta0 * sqrt_(v > 0.0f ? v : 0.0f);
-    }
-    return chi_of(C.F.eta0, e, p, E, B);
+// xold: where the fields were evaluated (the counter-propagating field is evaluated again there, wave by
+// wave); the result's f is set for that kind only (basis32 takes it from there)
+template <bool ACC, bool PW>
+__device__ __forceinline__ ChiF chi32(const Ctx& C, float e, const F3& p, const F3& E, const F3& B, float m2,
+                                     const F3& xold) {
+    if (PW || single_wave(C)) return ChiF{C.F.eta0 * e_minus_pz(e, p, m2) * sqrt_(fma_(E.x, E.x, E.y * E.y)), F3{0, 0, 0}};
+    if (two_wave(C))
+        return two_wave_chi(field_waves<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold), C.F.eta0, e, p, m2);
+    return ChiF{chi_of(C.F.eta0, e, p, E, B), F3{0, 0, 0}};
 }
 
-// ie = 1/e
+// ie = 1/e; f2w: f of the counter-propagating field from chi32
+template <bool PW>
 __device__ __forceinline__ bool basis32(const Ctx& C, const F3& E, const F3& B, const F3& v, const F3& khat, float sign,
-                                       F3& eps, F3& beta, float ie, const F3& p, const LightCone& lc,
-                                       const Waves<float>& w) {
+                                       F3& eps, F3& beta, float ie, const F3& p, float m2, const F3& f2w) {
     F3 f;
-    if (single_wave(C)) {
-        const float g = lc.em * ie;
+    if (PW || single_wave(C)) {
+        const float g = e_minus_pz(1.0f / ie, p, m2) * ie;
         f = F3{g * E.x, g * E.y, fma_(v.x, E.x, v.y * E.y)};
     } else if (two_wave(C)) {
-        f = F3{ie * fma_(lc.em, w.e1x, lc.ep * w.e2x), ie * fma_(lc.em, w.e1y, lc.ep * w.e2y),
-               ie * (fma_(p.x, w.e1x, p.y * w.e1y) - fma_(p.x, w.e2x, p.y * w.e2y))};
+        f = f2w;
     } else {
         f = E + cross(v, B);
     }
@@ -398,11 +410,11 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     st.p = F3{a.w, b.x, b.y};
     st.s = F3{b.z, b.w, cc.x};
     st.w = cc.y;
-    Waves<float> w{0.0f, 0.0f, 0.0f, 0.0f};  // the two waves of the counter-propagating field
-    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B, &w);
+    constexpr bool PW = plane_waves_only<FIX>();
+    field_eval<float, ACC, PW>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const F3 pold = st.p;
     // the field kinds known to have E_z = B_z = 0; any other kind takes the general forms
-    const bool transverse = C.F.kind >= QED_FIELD_LP && C.F.kind <= QED_FIELD_CP_COUNTER;
+    const bool transverse = PW || (C.F.kind >= QED_FIELD_LP && C.F.kind <= QED_FIELD_CP_COUNTER);
     if (fl & QED_F_PUSH) st.p = transverse ? boris_t(st.p, st.E, st.B, C.q, dt) : boris(st.p, st.E, st.B, C.q, dt);
     if (fl & QED_F_TBMT) {
         const F3 pb = 0.5f * (pold + st.p);
@@ -410,10 +422,7 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
         // the anomalous moment: alpha/(2 pi), a(chi) at pb, or none (tbmt_a; chi32 takes the plane-wave form)
         float ae = (float)(kAlpha / (2.0 * kPi));
         if (fl & (QED_F_G2 | QED_F_LOOP)) ae = 0.0f;
-        else if (fl & QED_F_AMM) {
-            const float gb = sqrt_(1.0f + dot(pb, pb));
-            ae = amm_lookup(T, chi32(C, gb, pb, st.E, st.B, light_cone(C, gb, pb, 1.0f), w));
-        }
+        else if (fl & QED_F_AMM) ae = amm_lookup(T, chi32<ACC, PW>(C, sqrt_(1.0f + dot(pb, pb)), pb, st.E, st.B, 1.0f, xold).chi);
         st.s = rotate(st.s, transverse ? tbmt_omega_t(pb, st.E, st.B, C.q, paper, ae) : tbmt_omega(pb, st.E, st.B, C.q, paper, ae), dt);
     }
     st.gam = sqrt_(1.0f + dot(st.p, st.p));
@@ -424,13 +433,13 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     }
     st.qed = false;
     if (!(fl & QED_F_EMIT)) return;
-    const LightCone lc = light_cone(C, st.gam, st.p, 1.0f);
-    st.chi = chi32(C, st.gam, st.p, st.E, st.B, lc, w);
+    const ChiF cf = chi32<ACC, PW>(C, st.gam, st.p, st.E, st.B, 1.0f, xold);
+    st.chi = cf.chi;
     const float pn2 = dot(st.p, st.p);
     if (!(pn2 > 0.0f) || !(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.khat = rsqrtf(pn2) * st.p;
     const F3 v = rg * st.p;
-    if (!basis32(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta, rg, st.p, lc, w)) return;
+    if (!basis32<PW>(C, st.E, st.B, v, st.khat, -C.q, st.eps, st.beta, rg, st.p, 1.0f, cf.f)) return;
     st.qed = true;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
@@ -836,8 +845,8 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.k = F3{cc.x, cc.y, cc.z};
     st.P = F3{a.w, b.x, b.y};
     st.w = cc.w;
-    Waves<float> w{0.0f, 0.0f, 0.0f, 0.0f};  // the two waves of the counter-propagating field
-    field_eval<float, ACC>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B, &w);
+    constexpr bool PW = plane_waves_only<FIX>();
+    field_eval<float, ACC, PW>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
     const float en2 = dot(st.k, st.k);
     st.en = sqrt_(en2);
     st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
@@ -845,8 +854,8 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     if (flags_of<FIX>(C) & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;
     if (!(flags_of<FIX>(C) & QED_F_EMIT) || !(en2 > 0.0f)) return;
-    const LightCone lc = light_cone(C, st.en, st.k, 0.0f);
-    st.chi = chi32(C, st.en, st.k, st.E, st.B, lc, w);
+    const ChiF cf = chi32<ACC, PW>(C, st.en, st.k, st.E, st.B, 0.0f, xold);
+    st.chi = cf.chi;
     if (!(st.chi > 0.0f) || st.chi < C.S.chi_floor_f) return;
     st.lnchi = __logf(st.chi);
     if (c && st.chi > T.chi_max) c[C_CLAMPED]++;
@@ -854,7 +863,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     // most photons are too soft, or in too weak a field, for a pair rate in the float range: nothing of
     // the basis or the Stokes vector is needed for them (the caller moves them and stops)
     if (st.Wp == 0.0f && st.Wm == 0.0f) return;
-    if (!basis32(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta, rsqrtf(en2), st.k, lc, w)) return;
+    if (!basis32<PW>(C, st.E, st.B, st.khat, st.khat, 1.0f, st.eps, st.beta, rsqrtf(en2), st.k, 0.0f, cf.f)) return;
     st.qed = true;
     P_to_stokes(st.P, st.eps, st.beta, st.khat, st.xi);
     if (!(flags_of<FIX>(C) & QED_F_RESOLVED)) st.xi[0] = st.xi[1] = st.xi[2] = 0.0f;
