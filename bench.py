@@ -975,6 +975,15 @@ def _oracle_field(O, f):
     return O.field(f.kind, a0=f.a0, n_cycles=f.n_cycles, phase=f.phase, E0=tuple(f.E0), B0=tuple(f.B0), eta0=f.eta0)
 
 
+def _step_condition(O, f, pre: dict, t: float, dt: float) -> np.ndarray:
+    """A lepton step's condition number max(1, dt (|E| + |B|) / |p|) at its start (the field impulse over
+    the momentum; for a low-energy lepton it also bounds the spin's turn angle per step, ~ dt |B| / gamma):
+    FP32 field rounding, relative to the field's amplitude, reaches the outputs multiplied by it."""
+    E, B = O.field_eval_n(_oracle_field(O, f), pre["pos"], t)
+    pn = np.maximum(np.linalg.norm(pre["mom"], axis=1), 1e-300)
+    return np.maximum(1.0, dt * (np.linalg.norm(E, axis=1) + np.linalg.norm(B, axis=1)) / pn)
+
+
 def _gpu_rows(buf, idx, torch):
     """rows idx (device int64 tensor) of an FP32 particle buffer, as host FP64 arrays"""
     from paper_2511_08929_gb300 import buffers as Q
@@ -1029,7 +1038,7 @@ def error_leg(bt, wl, fields, seeds, torch, steps, stride=16, diverged=1e-3):
     baseline (the oracle as it stands, all host cores)."""
     import oracle as O
     tb = O.tables(1e-4, 1e3, 256, 256)
-    acc = {"lepton": {}, "photon": {}, "daughter": {}}
+    acc = {"lepton": {}, "lepton_conditioned": {}, "photon": {}, "daughter": {}}
     n_ps, flips, t_or, ps_or = 0, 0, 0.0, 0
     spec_g, spec_o = [], []
     for _ in range(steps):
@@ -1070,6 +1079,11 @@ def error_leg(bt, wl, fields, seeds, torch, steps, stride=16, diverged=1e-3):
                 flips += int(bad.sum())
                 for kk, v in er.items():
                     acc[kind].setdefault(kk, []).append(v[~bad])
+                if kind == "lepton":  # the same errors over the step's condition number
+                    pm, _ = _match(prev, oo)
+                    kap = _step_condition(O, fields[k], pm, float(step) * wl.dt, wl.dt)
+                    for kk, v in er.items():
+                        acc["lepton_conditioned"].setdefault(kk, []).append((v / kap)[~bad])
                 gn, on = _match(g_new, o_new)
                 er = _errors(gn, on, kind == "photon")  # the buffer's new particles: daughters of its kind
                 bad = np.max(np.stack(list(er.values())), axis=0) > diverged

@@ -147,6 +147,7 @@ def lib():
             L.orc_nbw_mu.restype = _D
             L.orc_nbw_mu.argtypes = [_D, _D]
             L.orc_field_eval.argtypes = [_P(Field), _P(_D), _D, _P(_D), _P(_D)]
+            L.orc_field_eval_n.argtypes = [_P(Field), C.c_int64, _P(_D), _D, _P(_D), _P(_D)]
             L.orc_stokes_to_P.argtypes = [_P(_D)] * 5
             L.orc_P_to_stokes.argtypes = [_P(_D)] * 5
             L.orc_lepton_step.restype = C.c_int
@@ -385,6 +386,15 @@ def field_eval(f: Field, x, t):
     E = np.zeros(3)
     B = np.zeros(3)
     lib().orc_field_eval(C.byref(f), _dp(_v3(x)), float(t), _dp(E), _dp(B))
+    return E, B
+
+
+def field_eval_n(f: Field, x, t):
+    """Fields at the rows of x (n, 3) at time t: (E, B), each (n, 3)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
+    E = np.zeros_like(x)
+    B = np.zeros_like(x)
+    lib().orc_field_eval_n(C.byref(f), len(x), _dp(x), float(t), _dp(E), _dp(B))
     return E, B
 
 

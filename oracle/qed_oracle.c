@@ -748,6 +748,12 @@ void orc_field_eval(const orc_field *f, const double x[3], double t, double E[3]
     }
 }
 
+/* Fields at n points (x: [n][3]; E, B: [n][3]), for tests and diagnostics. */
+void orc_field_eval_n(const orc_field *f, int64_t n, const double *x, double t, double *E, double *B)
+{
+    for (int64_t i = 0; i < n; ++i) orc_field_eval(f, x + 3 * i, t, E + 3 * i, B + 3 * i);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Particles (structure of arrays, FP64) and step parameters                    */
 /* ------------------------------------------------------------------------- */

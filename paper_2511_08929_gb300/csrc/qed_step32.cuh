@@ -362,16 +362,43 @@ __device__ __forceinline__ F3 cross_t(const F3& a, const F3& b) {  // b.z = 0
     return F3{-(a.z * b.y), a.z * b.x, fma_(a.x, b.y, -(a.y * b.x))};
 }
 
-__device__ __forceinline__ F3 boris_t(const F3& p, const F3& E, const F3& B, float q, float dt) {
+// The Boris rotation of p- by t = (q dt/2) B / gamma- in closed form,
+//   p+ = c p- + s (p- x t) + s (t.p-) t,   s = 2/(1 + t^2), c = s - 1 = (1 - t^2)/(1 + t^2),
+// which is the textbook p+ = p- + (p- + p- x t) x s t written out: every term is bounded by |p-|
+// (2|t|/(1 + t^2) <= 1), so the FP32 rounding stays at a few ulp of |p| where a step turns the momentum by
+// a large angle (|t| >> 1: low-energy leptons in strong fields), where the textbook form's intermediate
+// p- x t is |t| times larger than the result.  pb receives the time-centred momentum (p_old + p_new)/2 =
+// (p- + p+)/2 = (s/2)(p- + p- x t + (t.p-) t), free of the cancellation of the average of two momenta a
+// large turn apart.
+__device__ __forceinline__ F3 boris_t(const F3& p, const F3& E, const F3& B, float q, float dt, F3& pb) {
     const float h = 0.5f * q * dt;
     const F3 pm{fma_(h, E.x, p.x), fma_(h, E.y, p.y), p.z};
     const float ig = rsqrt_(1.0f + dot(pm, pm));
     const float hi = h * ig;
     const F3 t{hi * B.x, hi * B.y, 0.0f};
-    const float sfac = div_(2.0f, 1.0f + fma_(t.x, t.x, t.y * t.y));
-    const F3 pp = pm + cross_t(pm, t);
-    const F3 pl = pm + cross_t(pp, F3{sfac * t.x, sfac * t.y, 0.0f});
+    const float sf = div_(2.0f, 1.0f + fma_(t.x, t.x, t.y * t.y));
+    const float c = sf - 1.0f, stp = sf * fma_(t.x, pm.x, t.y * pm.y);
+    const F3 x = cross_t(pm, t);
+    const F3 pl{fma_(c, pm.x, fma_(sf, x.x, stp * t.x)), fma_(c, pm.y, fma_(sf, x.y, stp * t.y)), fma_(c, pm.z, sf * x.z)};
+    const float hs = 0.5f * sf, hstp = 0.5f * stp;
+    pb = F3{fma_(hs, pm.x + x.x, hstp * t.x), fma_(hs, pm.y + x.y, hstp * t.y), hs * (pm.z + x.z)};
     return F3{fma_(h, E.x, pl.x), fma_(h, E.y, pl.y), pl.z};
+}
+
+// the same for fields with E_z or B_z nonzero
+__device__ __forceinline__ F3 boris32(const F3& p, const F3& E, const F3& B, float q, float dt, F3& pb) {
+    const float h = 0.5f * q * dt;
+    const F3 pm = axpy(h, E, p);
+    const float ig = rsqrt_(1.0f + dot(pm, pm));
+    const F3 t = (h * ig) * B;
+    const float sf = div_(2.0f, 1.0f + dot(t, t));
+    const float c = sf - 1.0f, stp = sf * dot(t, pm);
+    const F3 x = cross(pm, t);
+    const F3 pl{fma_(c, pm.x, fma_(sf, x.x, stp * t.x)), fma_(c, pm.y, fma_(sf, x.y, stp * t.y)),
+                fma_(c, pm.z, fma_(sf, x.z, stp * t.z))};
+    const float hs = 0.5f * sf, hstp = 0.5f * stp;
+    pb = F3{fma_(hs, pm.x + x.x, hstp * t.x), fma_(hs, pm.y + x.y, hstp * t.y), fma_(hs, pm.z + x.z, hstp * t.z)};
+    return axpy(h, E, pl);
 }
 
 __device__ __forceinline__ F3 tbmt_omega_t(const F3& pb, const F3& E, const F3& B, float q, bool paper_form, float ae) {
@@ -412,12 +439,11 @@ __device__ __forceinline__ void lepton_classical(const Ctx& C, const float4& a, 
     st.w = cc.y;
     constexpr bool PW = plane_waves_only<FIX>();
     field_eval<float, ACC, PW>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
-    const F3 pold = st.p;
+    F3 pb = st.p;  // the time-centred momentum (the push replaces it by its own, cancellation-free form)
     // the field kinds known to have E_z = B_z = 0; any other kind takes the general forms
     const bool transverse = PW || (C.F.kind >= QED_FIELD_LP && C.F.kind <= QED_FIELD_CP_COUNTER);
-    if (fl & QED_F_PUSH) st.p = transverse ? boris_t(st.p, st.E, st.B, C.q, dt) : boris(st.p, st.E, st.B, C.q, dt);
+    if (fl & QED_F_PUSH) st.p = transverse ? boris_t(st.p, st.E, st.B, C.q, dt, pb) : boris32(st.p, st.E, st.B, C.q, dt, pb);
     if (fl & QED_F_TBMT) {
-        const F3 pb = 0.5f * (pold + st.p);
         const bool paper = (fl & QED_F_TBMT_PAPER) != 0;
         // the anomalous moment: alpha/(2 pi), a(chi) at pb, or none (tbmt_a; chi32 takes the plane-wave form)
         float ae = (float)(kAlpha / (2.0 * kPi));

@@ -92,9 +92,9 @@ def compare_with_flips(gpu: dict, ora: dict, rtol: float, what: str, P_headless:
     a collapse sign) can go the other way: it leaves one daughter id on one side only and one on the
     other; such unmatched ids, and particles whose state moved apart by more than `diverged`, are flips.
     Every other particle must be within rtol, except that a fraction `frac_ok` of them may reach `hard`
-    (ill-conditioned directions, see the FP32 tests).  spin_scale = (ids, factors >= 1): the spin (or
-    P) and optical-depth bars of those particles are rtol x factor (a step whose own condition number is
-    that factor: the optical depth depends on the turned spin through W(s.beta)).
+    (ill-conditioned directions, see the FP32 tests).  spin_scale = (ids, factors >= 1): the momentum,
+    spin (or P) and optical-depth bars of those particles are rtol x factor (a step whose own condition
+    number is that factor; the optical depth depends on the turned spin through W(s.beta)).
     Returns (flipped decisions, error quantiles)."""
     g, o = by_id(gpu), by_id(ora)
     common, gi, oi = np.intersect1d(g["id"], o["id"], assume_unique=False, return_indices=True)
@@ -118,6 +118,7 @@ def compare_with_flips(gpu: dict, ora: dict, rtol: float, what: str, P_headless:
         hit = (sid[ix] == gg["id"]) if len(sid) else np.zeros(len(gg["id"]), bool)
         div_ = np.where(hit, np.maximum(fac[ix] if len(sid) else 1.0, 1.0), 1.0)
         e["spin"] = e["spin"] / div_
+        e["mom"] = e["mom"] / div_
     else:
         div_ = 1.0
     fin = np.isfinite(oo["tau"]) & np.isfinite(gg["tau"])

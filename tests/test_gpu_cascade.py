@@ -34,10 +34,19 @@ def test_workload_generator_chunks():
 AE = 7.2973525693e-3 / (2 * np.pi)
 
 
-def _tbmt_angle(st: dict, of, t: float, dt: float, q: float) -> np.ndarray:
-    """The T-BMT turn |Omega| dt of each lepton's step (FP64: Boris push from the step's start, the
-    time-centred momentum, the standard T-BMT vector)."""
+def _condition(st: dict, of, wl, t: float, dt: float, q: float) -> np.ndarray:
+    """The condition number of each lepton's step: max(1, its T-BMT turn |Omega| dt, its field impulse
+    dt (|E1| + |E2|) / |p|), with |E1|, |E2| the amplitudes of the two waves at the particle.  FP32 fields
+    carry rounding relative to each wave's amplitude; a step whose impulse is several times the momentum,
+    or that turns the spin by many radians, passes that rounding on multiplied (FP64 Boris push from the
+    step's start, time-centred momentum, standard T-BMT vector)."""
     out = np.zeros(len(st["id"]))
+    n2 = 2 * np.pi * wl.n_cycles
+
+    def env(ph):
+        return np.where((ph >= 0) & (ph <= n2), np.sin(ph / (2 * wl.n_cycles)) ** 2, 0.0)
+
+    amp = wl.a0 * (env(t - st["pos"][:, 2]) + env(t + st["pos"][:, 2]))
     for i in range(len(st["id"])):
         E, B = (np.asarray(v) for v in O.field_eval(of, st["pos"][i], t))
         p = st["mom"][i]
@@ -49,16 +58,17 @@ def _tbmt_angle(st: dict, of, t: float, dt: float, q: float) -> np.ndarray:
         g = np.sqrt(1 + pb @ pb)
         b = pb / g
         Om = (AE + 1 / g) * B - (AE * g / (g + 1)) * (b @ B) * b - (AE + 1 / (g + 1)) * np.cross(b, E)
-        out[i] = np.linalg.norm(Om) * dt
+        out[i] = max(1.0, np.linalg.norm(Om) * dt, dt * amp[i] / max(np.linalg.norm(p), 1e-300))
     return out
 
 
 @pytest.mark.gpu
 def test_cascade_subset_against_oracle():
-    """Five steps inside the cascade, each from the GPU's state.  Low-energy leptons at the magnetic
-    antinodes of the standing wave turn their spin by up to ~30 rad in one step (gamma ~ 6 in |B| ~ 900):
-    such a step is ill-conditioned (a 1e-7 relative change of its inputs moves the spin by up to ~1e-5),
-    so the spin bar of a lepton (and of the photon it emits) is 1e-5 x max(1, its turn angle)."""
+    """Five steps inside the cascade, each from the GPU's state.  Low-energy leptons at the nodes of the
+    standing wave turn their spin by up to ~30 rad in one step (gamma ~ 6 in |B| ~ 900) and receive field
+    impulses several times their momentum: such a step is ill-conditioned (a 1e-7 relative change of its
+    inputs moves the spin by up to ~1e-5), so the bar of a lepton (and of the photon it emits) is
+    1e-5 x its step's condition number (_condition); every other particle is held to 1e-5."""
     from paper_2511_08929_gb300 import build as bld
     bld.build()
     wl = dataclasses.replace(I.CASCADE_2E8, n_electrons=4000, chunk=4000)
@@ -92,7 +102,7 @@ def test_cascade_subset_against_oracle():
         # each lepton's turn angle, and the same factor for the photon it emitted this step
         ids, fac = [], []
         for r, q in ((pre[0], -1.0), (pre[1], 1.0)):
-            ang = _tbmt_angle(r, of, float(step) * wl.dt, wl.dt, q)
+            ang = _condition(r, of, wl, float(step) * wl.dt, wl.dt, q)
             worst_turn = max(worst_turn, float(ang.max(initial=0.0)))
             ids.append(r["id"])
             fac.append(ang)
