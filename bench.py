@@ -976,12 +976,24 @@ def _oracle_field(O, f):
 
 
 def _step_condition(O, f, pre: dict, t: float, dt: float) -> np.ndarray:
-    """A lepton step's condition number max(1, dt (|E| + |B|) / |p|) at its start (the field impulse over
-    the momentum; for a low-energy lepton it also bounds the spin's turn angle per step, ~ dt |B| / gamma):
-    FP32 field rounding, relative to the field's amplitude, reaches the outputs multiplied by it."""
+    """A lepton step's condition number: max(1, its T-BMT turn |Omega| dt, its field impulse dt (|E| + |B|)
+    / |p|), from its state at the step's start (FP64 Boris push, time-centred momentum, standard T-BMT
+    vector).  FP32 field rounding, relative to the field's amplitude, reaches the outputs multiplied by
+    it: low-energy leptons in strong fields turn their spin by tens of radians in one step."""
+    ae = 7.2973525693e-3 / (2.0 * np.pi)
     E, B = O.field_eval_n(_oracle_field(O, f), pre["pos"], t)
-    pn = np.maximum(np.linalg.norm(pre["mom"], axis=1), 1e-300)
-    return np.maximum(1.0, dt * (np.linalg.norm(E, axis=1) + np.linalg.norm(B, axis=1)) / pn)
+    p = pre["mom"]
+    h = 0.5 * dt  # the turn's size does not depend on the sign of the charge
+    pm = p + h * E
+    tv = h * B / np.sqrt(1.0 + (pm * pm).sum(1))[:, None]
+    pl = pm + np.cross(pm + np.cross(pm, tv), 2.0 * tv / (1.0 + (tv * tv).sum(1))[:, None])
+    pb = 0.5 * (p + pl + h * E)
+    g = np.sqrt(1.0 + (pb * pb).sum(1))[:, None]
+    b = pb / g
+    om = (ae + 1.0 / g) * B - (ae * g / (g + 1.0)) * (b * B).sum(1)[:, None] * b - (ae + 1.0 / (g + 1.0)) * np.cross(b, E)
+    pn = np.maximum(np.linalg.norm(p, axis=1), 1e-300)
+    imp = dt * (np.linalg.norm(E, axis=1) + np.linalg.norm(B, axis=1)) / pn
+    return np.maximum(1.0, np.maximum(np.linalg.norm(om, axis=1) * dt, imp))
 
 
 def _gpu_rows(buf, idx, torch):
