@@ -834,7 +834,13 @@ def mlp_leg(args, tables, torch):
     e1.record()
     torch.cuda.synchronize()
     t_tab = e0.elapsed_time(e1) / 1e3
-    net_rate, tab_rate = total / t_net, chi.shape[0] / t_tab
+    smp.sample(tables, chi, r, s, branch_table=True)  # warm-up
+    e0.record()
+    smp.sample(tables, chi, r, s, branch_table=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_br = e0.elapsed_time(e1) / 1e3
+    net_rate, tab_rate, br_rate = total / t_net, chi.shape[0] / t_tab, chi.shape[0] / t_br
     smp.close()
     labels = ["<1e-7", "1e-7..1e-6", "1e-6..1e-5", "1e-5..1e-4", "1e-4..1e-3", ">1e-3"]
     return {"train_samples": steps * batch, "train_steps": steps, "train_s": round(train_s, 2),
@@ -842,7 +848,11 @@ def mlp_leg(args, tables, torch):
             "eval_events": total, "samples_per_s": net_rate, "fallback_fraction": n_fb / total,
             "network_cdf_error_hist": {k: float(v / total) for k, v in zip(labels, hist)},
             "table_path_samples_per_s": tab_rate, "table_path_events": int(chi.shape[0]),
-            "gain_over_table_path": net_rate / tab_rate, "tolerance": 1e-4,
+            "table_path": "the checked sampler's own fallback: the mixture quantile by bisection of its CDF",
+            "gain_over_table_path": net_rate / tab_rate,
+            "branch_table_samples_per_s": br_rate,
+            "branch_table": "the step's sampler: spin branch by W_down(1-s)/(2W_s), one float-float ICDF row",
+            "gain_over_branch_table": net_rate / br_rate, "tolerance": 1e-4,
             "parameters": 8836, "weights_bytes_bf16": 2 * (192 + 4096 + 4096 + 256)}
 
 

@@ -401,6 +401,10 @@ void qed_batch_destroy(qed_batch_t b);
  * W3[64][64] b3[64] W4[4][64] b4[4] (weights row = output unit). */
 #define QED_MLP_PARAMS 8836
 #define QED_MLP_ALWAYS_TABLE 1 /* qed_mlp_sample flag: skip the network (the table path, for comparison) */
+/* qed_mlp_sample flag: instead of the network, the sampler the step's event pass runs (Sec. 5.1): the spin
+ * branch chosen with probability W_down (1 - s)/(2 W_s), the uniform rescaled within it, one row of that
+ * branch's ICDF (float-float), xi3 at the sampled u'; out4 = (ln u', 0, 0, xi3), no check, no fallback */
+#define QED_MLP_BRANCH_TABLE 2
 
 typedef struct qed_mlp_s *qed_mlp_t;
 

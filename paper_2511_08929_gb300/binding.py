@@ -309,6 +309,7 @@ def qed_batch_destroy(batch: int):
 
 QED_MLP_PARAMS = int(re.search(r"#define QED_MLP_PARAMS (\d+)", open(HEADER).read()).group(1))
 QED_MLP_ALWAYS_TABLE = 1
+QED_MLP_BRANCH_TABLE = 2
 
 
 def qed_mlp_create(max_batch: int, init_params) -> int:

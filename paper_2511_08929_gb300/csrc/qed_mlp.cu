@@ -638,6 +638,44 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
     tc_teardown(S.tmem);
 }
 
+// The method the network would replace, as the step's event pass runs it (Sec. 5.1): the spin branch
+// taken with probability W_down (1 - s)/(2 W_s), the uniform rescaled within the chosen branch (the pair
+// gives the mixture w(lambda; s) exactly, reading C4), one row of that branch's ICDF in float-float
+// (nlc_up_ff, the FP64 row where u' leaves the float range), and xi3 at the sampled u' from the float
+// Bessel table.  out4 = (ln u', 0, 0, xi3).
+__global__ void branch_table_kernel(TabP<float> T, TabP<double> T64, const float* __restrict__ bes32,
+                                    const double* __restrict__ chi_in, const double* __restrict__ r_in,
+                                    const double* __restrict__ s_in, int64_t n, float* __restrict__ out4) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float chi = (float)chi_in[i], s = (float)s_in[i];
+        const double r = r_in[i];
+        const float lnchi = logf(chi);
+        float Iu, Id;
+        nlc_rates(T, chi, lnchi, Iu, Id);
+        const double wd = (double)Id * (1.0 - s) * 0.5, wu = (double)Iu * (1.0 + s) * 0.5;
+        const double pd = wd / (wu + wd);
+        const bool down = r < pd;
+        double rr = down ? r / pd : (r - pd) / (1.0 - pd);
+        rr = fmin(fmax(rr, 0x1.0p-53), 1.0 - 0x1.0p-53);
+        uint64_t m = (uint64_t)(rr * 0x1.0p52);
+        if (m > (1ull << 52) - 1ull) m = (1ull << 52) - 1ull;
+        const uint32_t whi = (uint32_t)(m >> 32) << 12, wlo = (uint32_t)m;
+        float up;
+        if (!nlc_up_ff(T, down ? 1 : 0, lnchi, whi, wlo, up)) {
+            const double u = uniform52(whi, wlo);
+            up = (float)exp(icdf_lookup(T64, false, down ? 1 : 0, (double)lnchi, log(u) - log(1.0 - u)));
+        }
+        const float den = fmaf(3.0f * chi, up, 2.0f), lam = 3.0f * chi * up / den, one_m = 2.0f / den;
+        float b[3];
+        bessel32(bes32, up, b);
+        const float u = lam / one_m, kappa = 1.0f / one_m + one_m;
+        out4[4 * i] = logf(up);
+        out4[4 * i + 1] = 0.0f;
+        out4[4 * i + 2] = 0.0f;
+        out4[4 * i + 3] = (b[1] + u * s * b[0]) / (-b[2] + kappa * b[1] + lam * s * b[0]);
+    }
+}
+
 }  // namespace qed
 
 // ---- host side -------------------------------------------------------------------------------------
@@ -829,8 +867,17 @@ extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* 
                                      float* err_out, unsigned long long* n_fallback, void* stream) {
     if (!valid_mlp(m)) return QED_ERR_STATE;
     if (!valid_tables(t)) return QED_ERR_STATE;
-    if (n < 0 || (n > 0 && (!chi || !r || !s || !out4)) || !(tol >= 0.0) || (flags & ~QED_MLP_ALWAYS_TABLE)) return QED_ERR_ARG;
+    if (n < 0 || (n > 0 && (!chi || !r || !s || !out4)) || !(tol >= 0.0) ||
+        (flags & ~(QED_MLP_ALWAYS_TABLE | QED_MLP_BRANCH_TABLE)))
+        return QED_ERR_ARG;
     if (n == 0) return QED_OK;
+    if (flags & QED_MLP_BRANCH_TABLE) {
+        const int threads = 256;
+        const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
+        branch_table_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(tab_params<float>(t), tab_params<double>(t),
+                                                                          t->bes32, chi, r, s, n, out4);
+        return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+    }
     // persistent grid (one resident wave): each warp streams many 32-sample rows, so its fallback queue
     // drains full
     const int blocks = tc_blocks(n, (const void*)mlp_sample_kernel);

@@ -79,16 +79,19 @@ class Sampler:
         B.qed_mlp_adamw(self.handle, g.data_ptr(), lr, weight_decay, stream)
 
     def sample(self, tables, chi, r, s, tol: float = 1e-4, table_only: bool = False, stream: int = 0,
-               with_error: bool = False):
+               with_error: bool = False, branch_table: bool = False):
         """(out4 = (ln u', xi1, xi2, xi3), fell_back mask, number of fallbacks[, network CDF errors]) for
-        device double arrays chi, r, s."""
+        device double arrays chi, r, s.  table_only: the checked sampler's own fallback (the mixture
+        quantile by bisection) for every sample; branch_table: the step's sampler (branch, then one ICDF
+        row) instead of the network."""
         n = chi.shape[0]
         out = torch.empty((n, 4), dtype=torch.float32, device=self.device)
         fell = torch.zeros(n, dtype=torch.uint8, device=self.device)
         nf = torch.zeros(1, dtype=torch.int64, device=self.device)
         err = torch.empty(n, dtype=torch.float32, device=self.device) if with_error else None
         B.qed_mlp_sample(self.handle, tables.handle, chi.data_ptr(), r.data_ptr(), s.data_ptr(), n, tol,
-                         B.QED_MLP_ALWAYS_TABLE if table_only else 0, out.data_ptr(), fell.data_ptr(), nf.data_ptr(),
+                         (B.QED_MLP_ALWAYS_TABLE if table_only else 0) | (B.QED_MLP_BRANCH_TABLE if branch_table else 0),
+                         out.data_ptr(), fell.data_ptr(), nf.data_ptr(),
                          stream, err.data_ptr() if with_error else 0)
         return (out, fell, nf, err) if with_error else (out, fell, nf)
 
