@@ -44,6 +44,7 @@ F_AMM = 1 << 13
 F_LOOP = 1 << 14
 F_G2 = 1 << 15
 F_BETA_BASIS = 1 << 16
+F_REJECT = 1 << 17
 F_FULL = (F_TAU | F_RECOIL | F_SPIN_COLLAPSE | F_POL_COLLAPSE | F_NONTRANSITION | F_PUSH | F_TBMT | F_EMIT
           | F_RESOLVED | F_MOVE | F_SPIN_EVENT | F_POL_EVENT)
 
@@ -85,7 +86,8 @@ class Step(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("events", C.c_int64), ("stored", C.c_int64), ("dropped_capacity", C.c_int64),
-                ("chi_clamped", C.c_int64), ("renormalised", C.c_int64), ("below_store", C.c_int64)]
+                ("chi_clamped", C.c_int64), ("renormalised", C.c_int64), ("below_store", C.c_int64),
+                ("bound_exceeded", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

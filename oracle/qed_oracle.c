@@ -780,7 +780,8 @@ enum {
     ORC_F_AMM = 1u << 13,          /* T-BMT with the field-dependent a(chi) (Sec. 8.6.2) instead of alpha/(2 pi) */
     ORC_F_LOOP = 1u << 14,         /* Scorer term of the loop in the no-emission update; T-BMT with g = 2 */
     ORC_F_G2 = 1u << 15,           /* T-BMT with g = 2 (a = 0), the comparison run of Sec. 8.6.2 */
-    ORC_F_BETA_BASIS = 1u << 16    /* spins resolved along +-beta instead of the SQA (Sec. 8.3 comparison) */
+    ORC_F_BETA_BASIS = 1u << 16,   /* spins resolved along +-beta instead of the SQA (Sec. 8.3 comparison) */
+    ORC_F_REJECT = 1u << 17        /* table-free decision and sampling by rejection (Sec. 4.2) */
 };
 
 typedef struct {
@@ -794,6 +795,7 @@ typedef struct {
 
 typedef struct {
     int64_t events, stored, dropped_capacity, chi_clamped, renormalised, below_store;
+    int64_t bound_exceeded; /* rejection steps whose acceptance probability exceeded 1 */
 } orc_counters;
 
 /* result record of one particle's step, appended serially afterwards */
@@ -802,7 +804,7 @@ typedef struct {
     double d0[3], k0[3], P0[3], tau0, w0;      /* daughter 0 (photon / electron) */
     double d1k[3], s1[3], tau1;                /* daughter 1 (positron) */
     uint64_t id0, id1;
-    int clamped, renorm;
+    int clamped, renorm, bound;
     double kept_p[3], kept_s[3], kept_tau;     /* lepton state if its event is not applied */
 } orc_result;
 
@@ -988,7 +990,22 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
             double Ws = Wup_part + Wdn_part;
             double u0[2];
             int down = 0;
-            if (fl & ORC_F_TAU) {
+            double rej_up = 0.0;
+            if (fl & ORC_F_REJECT) {
+                /* table-free (Sec. 4.2): rejection with the proposal f = r^3.  The candidate energy
+                 * fraction lambda = r1^3 is accepted if r2 < 3 r1^2 (dW/dlambda)(lambda) dt, with
+                 * dW/dlambda = pref w(lambda; s.beta) the spin-resolved density (App. A.1); the
+                 * acceptance must stay below 1 (counted when it does not); no optical depth */
+                orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_TAU_BRANCH, u0);
+                double lc = u0[0] * u0[0] * u0[0], om = 1.0 - lc;
+                rej_up = 2.0 * lc / (3.0 * chi * om);
+                double b[3];
+                orc_bessel(rej_up, b);
+                double wl = -b[2] + (1.0 / om + om) * b[1] + lc * sb * b[0];
+                double acc = 3.0 * u0[0] * u0[0] * pref * wl * dt;
+                res->bound = acc > 1.0;
+                event = u0[1] < acc;
+            } else if (fl & ORC_F_TAU) {
                 /* optical depth (Sec. 4.1): tau_rem decreases by W dt, event when <= 0 */
                 tauf = tau - Ws * dt;
                 event = tauf <= 0.0;
@@ -1011,8 +1028,8 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 double u1[2], u2[2];
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_LAMBDA_SPIN, u1);
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_STOKES, u2);
-                /* lambda from the ICDF of the chosen branch (Sec. 5.1) */
-                double up = exp(orc_icdf_lookup(tb, 0, down ? 1 : 0, chi, u1[0]));
+                /* lambda from the ICDF of the chosen branch (Sec. 5.1), or the accepted candidate */
+                double up = (fl & ORC_F_REJECT) ? rej_up : exp(orc_icdf_lookup(tb, 0, down ? 1 : 0, chi, u1[0]));
                 double lam = orc_nlc_lambda(chi, up);
                 /* photon and recoil (Sec. 5.1): hbar k = lambda p_i, p_f = (1 - lambda) p_i */
                 double k[3] = {lam * p[0], lam * p[1], lam * p[2]};
@@ -1061,7 +1078,7 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 double P[3];
                 orc_stokes_to_P(xi, eps, beta, khat, P);
                 /* new optical depth for the emitter */
-                if (fl & ORC_F_TAU) tauf = -log(u0[0]);
+                if ((fl & ORC_F_TAU) && !(fl & ORC_F_REJECT)) tauf = -log(u0[0]);
                 res->event = 1;
                 double kn = sqrt(dot3(k, k));
                 res->store = kn >= st->photon_store_min;
@@ -1128,6 +1145,7 @@ int orc_lepton_step(const orc_tables *tb, const orc_field *fd, const orc_step *s
     for (int64_t j = 0; j < n; ++j) {
         if (res[j].clamped) ctr->chi_clamped++;
         if (res[j].renorm) ctr->renormalised++;
+        if (res[j].bound) ctr->bound_exceeded++;
         if (!res[j].event) continue;
         if (!res[j].store) { ctr->events++; ctr->below_store++; continue; }
         if (ph == NULL) { ctr->events++; ctr->dropped_capacity++; continue; }
@@ -1190,7 +1208,22 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
             double Wx = Wm_part + Wp_part;
             int event = 0, minus = 0;
             double u0[2];
-            if (fl & ORC_F_TAU) {
+            double rej_lam = 0.0, rej_ut = 0.0;
+            if (fl & ORC_F_REJECT) {
+                /* table-free (Sec. 4.2): the pair spectrum is bounded, so the candidate positron fraction
+                 * is lambda = r1 itself, accepted if r2 < (dW/dlambda)(lambda) dt = pref w0(lambda; xi3) dt
+                 * (App. A.2); no optical depth */
+                orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_TAU_BRANCH, u0);
+                double lc = u0[0], om = 1.0 - u0[0];
+                rej_lam = lc;
+                rej_ut = 2.0 / (3.0 * chi * lc * om);
+                double b[3];
+                orc_bessel(rej_ut, b);
+                double w0 = b[2] + (om / lc + lc / om) * b[1] - xi[2] * b[1];
+                double acc = pref * w0 * dt;
+                res->bound = acc > 1.0;
+                event = u0[1] < acc;
+            } else if (fl & ORC_F_TAU) {
                 tauf = tau - Wx * dt;
                 event = tauf <= 0.0;
                 if (event) {
@@ -1202,18 +1235,24 @@ static void photon_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 event = u0[0] < Wx * dt;
                 minus = u0[0] < Wm_part * dt;
             }
-            if (event && Wx > 0.0) {
+            if (event && ((fl & ORC_F_REJECT) || Wx > 0.0)) {
                 double u1[2];
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_LAMBDA_SPIN, u1);
-                /* lambda from the folded ICDF of the chosen branch (Sec. 5.2) */
-                double r = u1[0];
-                double rf = r < 0.5 ? 1.0 - 2.0 * r : 2.0 * r - 1.0;
-                double xv;
-                if (rf > 0.0) xv = exp(orc_icdf_lookup(tb, 1, minus ? 1 : 0, chi, rf));
-                else xv = 0.0;
-                double mu = orc_nbw_mu(chi, xv);
-                double lam = r < 0.5 ? mu : 1.0 - mu;
-                double ut = 8.0 / (3.0 * chi) + xv;
+                double lam, ut;
+                if (fl & ORC_F_REJECT) {
+                    lam = rej_lam;
+                    ut = rej_ut;
+                } else {
+                    /* lambda from the folded ICDF of the chosen branch (Sec. 5.2) */
+                    double r = u1[0];
+                    double rf = r < 0.5 ? 1.0 - 2.0 * r : 2.0 * r - 1.0;
+                    double xv;
+                    if (rf > 0.0) xv = exp(orc_icdf_lookup(tb, 1, minus ? 1 : 0, chi, rf));
+                    else xv = 0.0;
+                    double mu = orc_nbw_mu(chi, xv);
+                    lam = r < 0.5 ? mu : 1.0 - mu;
+                    ut = 8.0 / (3.0 * chi) + xv;
+                }
                 double bes[3];
                 orc_bessel_scaled(ut, bes);
                 double pe[3], pp[3];
@@ -1309,6 +1348,7 @@ int orc_photon_step(const orc_tables *tb, const orc_field *fd, const orc_step *s
     for (int64_t j = 0; j < n; ++j) {
         if (res[j].clamped) ctr->chi_clamped++;
         if (res[j].renorm) ctr->renormalised++;
+        if (res[j].bound) ctr->bound_exceeded++;
         int dead = 0;
         if (res[j].event) {
             if (el == NULL || po == NULL || el->n >= el->capacity || po->n >= po->capacity) {

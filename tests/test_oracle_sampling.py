@@ -297,6 +297,61 @@ def test_probability_mode_photon_frequency_and_branch(xi3, P, tb):
 
 
 # ------------------------------------------------------------------------------------------
+# table-free rejection sampling (Sec. 4.2, the f = r^3 proposal): frequency and spectrum
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("sbeta", [1.0, -0.4])
+def test_rejection_lepton_frequency_and_spectrum(sbeta, tb):
+    """Candidates lambda = r1^3 accepted with probability 3 r1^2 (dW/dlambda) dt: the event frequency is
+    W_s dt and the accepted fractions follow w(lambda; s.beta), with no table involved in either."""
+    chi, gamma = 4.0, 2000.0
+    n = 100000
+    s_up = Spectrum(lambda l: nlc_density(l, chi, 1.0), cube=True).total_lambda()
+    s_dn = Spectrum(lambda l: nlc_density(l, chi, -1.0), cube=True).total_lambda()
+    Ws = PREF_NLC / gamma * (s_up * (1 + sbeta) / 2 + s_dn * (1 - sbeta) / 2)
+    dt = 0.05 / Ws
+    L, f, pm = _electrons(chi, sbeta * BETA, gamma=gamma, n=n, seed=8, tau=1.0)
+    G = O.Particles(n)
+    ctr = O.lepton_step(tb, f, O.step_desc(dt, 0.0, 0, 16, (FL_EMIT & ~O.F_TAU) | O.F_REJECT), -1, L, G)
+    assert ctr.bound_exceeded == 0
+    p = Ws * dt
+    assert abs(ctr.events / n - p) < 4 * math.sqrt(p * (1 - p) / n), (ctr.events / n, p)
+    lam = G.view()["mom"][:, 0] / pm
+    assert ks_p(lam, Spectrum(lambda l: nlc_density(l, chi, sbeta), cube=True)) > P_MIN
+    if sbeta == 1.0:
+        assert ks_p(lam, Spectrum(lambda l: nlc_density(l, chi, -1.0), cube=True)) < 1e-6
+    assert np.all(L.view()["tau"] == 1.0)  # no optical depth in this mode
+
+
+@pytest.mark.parametrize("xi3,P", [(1.0, (0.0, 1.0, 0.0)), (-1.0, (0.0, 0.0, 1.0))])
+def test_rejection_photon_frequency_and_spectrum(xi3, P, tb):
+    """Candidate positron fractions lambda = r1 accepted with probability (dW/dlambda) dt."""
+    chi, energy = 1.0, 2000.0
+    n = 100000
+    J = Spectrum(lambda l: nbw_density(l, chi, xi3)).total_lambda()
+    W = ALPHA / (math.sqrt(3.0) * math.pi * ETA0 * energy) * J
+    dt = 0.05 / W
+    G, f = _photons(chi, P, energy, n=n, seed=9)
+    G.a["tau"][:n] = 1.0
+    el, po = O.Particles(n), O.Particles(n)
+    ctr = O.photon_step(tb, f, O.step_desc(dt, 0.0, 0, 17, (O.F_FULL & ~O.F_MOVE & ~O.F_TAU) | O.F_REJECT), G, el, po)
+    assert ctr.bound_exceeded == 0
+    p = W * dt
+    assert abs(ctr.events / n - p) < 4 * math.sqrt(p * (1 - p) / n), (ctr.events / n, p)
+    lam = po.view()["mom"][:, 0] / energy
+    assert ks_p(lam, Spectrum(lambda l: nbw_density(l, chi, xi3))) > P_MIN
+
+
+def test_rejection_bound_is_counted(tb):
+    """A step so long that 3 r^2 (dW/dlambda) dt exceeds 1 for some candidates is counted (the method's
+    requirement, Sec. 4.2); then the accepted spectrum is distorted, which the counter reports."""
+    chi, gamma = 4.0, 2000.0
+    L, f, pm = _electrons(chi, BETA, gamma=gamma, n=20000, seed=10, tau=1.0)
+    dt = 5.0 / (PREF_NLC / gamma)
+    ctr = O.lepton_step(tb, f, O.step_desc(dt, 0.0, 0, 18, (FL_EMIT & ~O.F_TAU) | O.F_REJECT), -1, L, None)
+    assert ctr.bound_exceeded > 0
+
+
+# ------------------------------------------------------------------------------------------
 # T-BMT in a Wien filter (Sec. 8.3): both forms against their closed forms
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("q", [-1, 1])
