@@ -90,7 +90,14 @@ enum {
      * axis (Sec. 8.3 compares the two): an emitting lepton ends at -beta with probability
      * (w - g.beta)/(2w), else +beta (expectation mode: (g.beta/w) beta); pair daughters take the four
      * states along (+-beta, +-beta) with probabilities G_ab/(4 w0) (expectation: (j.beta/w0) beta). */
-    QED_F_BETA_BASIS = 1u << 16
+    QED_F_BETA_BASIS = 1u << 16,
+    /* Table-free decision and sampling by rejection (Sec. 4.2): per step a candidate energy fraction
+     * lambda = r1^3 (emission; the f = r^3 proposal) or lambda = r1 (pair, positron fraction) is accepted
+     * if r2 < 3 r1^2 (dW/dlambda) dt (emission) or r2 < (dW/dlambda) dt (pair), with dW/dlambda the
+     * spin- (polarization-) resolved density of App. A; the ICDF tables and the optical depth are not
+     * used (the 1-D rate tables still serve the no-emission update).  Steps whose acceptance exceeds 1
+     * (dt too long for the method) are counted in bound_exceeded. */
+    QED_F_REJECT = 1u << 17
 };
 #define QED_F_FULL                                                                                     \
     (QED_F_TAU | QED_F_RECOIL | QED_F_SPIN_COLLAPSE | QED_F_POL_COLLAPSE | QED_F_NONTRANSITION |       \
@@ -195,6 +202,7 @@ typedef struct {
     unsigned long long nonfinite;        /* particles skipped because their state was not finite */
     unsigned long long rate_steps;       /* FP32 paths: photon-steps with a nonzero pair rate (the others
                                             only move, and write the position plane alone) */
+    unsigned long long bound_exceeded;   /* QED_F_REJECT: particle-steps whose acceptance exceeded 1 */
     int32_t status;                      /* first device-side error (qed_status), 0 if none */
     int32_t pad;
     int64_t first_bad;                   /* particle index of the first device-side error, -1 if none */

@@ -97,7 +97,8 @@ class QedBatchStats(C.Structure):
 class QedCounters(C.Structure):
     _fields_ = [("events", C.c_ulonglong), ("stored", C.c_ulonglong), ("dropped_capacity", C.c_ulonglong),
                 ("chi_clamped", C.c_ulonglong), ("renormalised", C.c_ulonglong), ("below_store", C.c_ulonglong),
-                ("nonfinite", C.c_ulonglong), ("rate_steps", C.c_ulonglong), ("status", C.c_int32),
+                ("nonfinite", C.c_ulonglong), ("rate_steps", C.c_ulonglong), ("bound_exceeded", C.c_ulonglong),
+                ("status", C.c_int32),
                 ("pad", C.c_int32), ("first_bad", C.c_int64),
                 ("append_base", C.c_int64 * 2), ("append_budget", C.c_int64), ("append_next", C.c_ulonglong)]
 

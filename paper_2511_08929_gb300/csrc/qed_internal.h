@@ -101,7 +101,8 @@ __host__ __device__ inline qed::AppendState* append_state(qed_counters* ctr) {
 // the switches a step accepts: every flag of the header, without the contradictory anomalous-moment
 // pairs (a(chi) in T-BMT and the loop's Scorer term are the same moment; g = 2 excludes both)
 inline bool valid_flags(uint32_t f) {
-    const uint32_t known = QED_F_FULL | QED_F_TBMT_PAPER | QED_F_AMM | QED_F_LOOP | QED_F_G2 | QED_F_BETA_BASIS;
+    const uint32_t known =
+        QED_F_FULL | QED_F_TBMT_PAPER | QED_F_AMM | QED_F_LOOP | QED_F_G2 | QED_F_BETA_BASIS | QED_F_REJECT;
     if (f & ~known) return false;
     return !((f & QED_F_AMM) && (f & (QED_F_LOOP | QED_F_G2)));
 }

@@ -202,7 +202,7 @@ __device__ __forceinline__ void load_tables32(const Shared32& sh, const float* _
     }
 }
 
-enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_RATE_STEPS, C_N };
+enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_RATE_STEPS, C_BOUND, C_N };
 
 // per-warp counter flush (no block barrier: warps finish at different times)
 __device__ __forceinline__ void flush_warp(unsigned long long (&c)[C_N], qed_counters* ctr) {
@@ -555,11 +555,46 @@ __device__ __forceinline__ float nlc_stokes_scale(float lam, float one_m, const 
 // spin axis or photon polarization is ill-conditioned (g or F far below its terms, as after a spin flip
 // against a polarized spin: F0 = w - |g|): there the FP32 rounding of the classical step alone, 1e-7 of
 // the spin and basis, would move the photon's Stokes vector by up to cond x 1e-7.  The branch (down) is
+
+// Table-free decision by rejection (QED_F_REJECT, Sec. 4.2).  Emission: the candidate lambda = r1^3 is
+// accepted with probability 3 r1^2 (dW/dlambda) dt, dW/dlambda = pref w(lambda; s.beta) (App. A.1); pair:
+// the candidate positron fraction lambda = r1 with probability (dW/dlambda) dt = pref w0(lambda; xi3) dt
+// (App. A.2).  The Bessel values come from the float table (scaled by e^x, unscaled here); beyond x = 80
+// the density is below the float range.  A step whose acceptance exceeds 1 is counted (the method needs
+// it below 1).
+__device__ __forceinline__ bool reject_nlc(const Ctx& C, const uint4& w0, float chi, float gam, float sb,
+                                           unsigned long long* c) {
+    const float r1 = u52f(w0.x, w0.y), r2 = u52f(w0.z, w0.w);
+    const float lc = r1 * r1 * r1, om = 1.0f - lc;
+    const float up = div_(2.0f * lc, 3.0f * chi * om);
+    if (!(up < 80.0f)) return false;
+    float b[3];
+    bessel32(C.bes, up, b);
+    const float wl = (-b[2] + (rcp_(om) + om) * b[1] + lc * sb * b[0]) * __expf(-up);
+    const float acc = 3.0f * r1 * r1 * (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0 * gam) * wl * C.S.dt_f;
+    if (c && acc > 1.0f) c[C_BOUND]++;
+    return r2 < acc;
+}
+
+__device__ __forceinline__ bool reject_nbw(const Ctx& C, const uint4& w0, float chi, float en, float xi3,
+                                           unsigned long long* c) {
+    const float r1 = u52f(w0.x, w0.y), r2 = u52f(w0.z, w0.w);
+    const float om = 1.0f - r1;
+    const float ut = div_(2.0f, 3.0f * chi * r1 * om);
+    if (!(ut < 80.0f)) return false;
+    float b[3];
+    bessel32(C.bes, ut, b);
+    const float w0r = (b[2] + (div_(om, r1) + div_(r1, om)) * b[1] - xi3 * b[1]) * __expf(-ut);
+    const float acc = (float)(kAlpha / (kSqrt3 * kPi)) * rcp_(C.F.eta0 * en) * w0r * C.S.dt_f;
+    if (c && acc > 1.0f) c[C_BOUND]++;
+    return r2 < acc;
+}
+
 // the FP32 pass's decision.  Outputs: the lepton's x, p, s and the photon's k and P, rounded to float.
 static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X, const FieldP<double>& F64,
                                                   const float4& a, const float4& b, const float4& cc, bool down,
-                                                  const uint4& w1, const uint4& w2, F3& x_out, F3& p_out, F3& s_out,
-                                                  F3& k_out, F3& P_out) {
+                                                  const uint4& w0, const uint4& w1, const uint4& w2, F3& x_out,
+                                                  F3& p_out, F3& s_out, F3& k_out, F3& P_out) {
     using V = V3<double>;
     const uint32_t fl = C.S.flags;
     const double dt = C.S.dt, q = (double)C.q;
@@ -580,9 +615,17 @@ static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X,
     V eps{0, 0, 0}, beta{0, 0, 0};
     make_basis(E, B, v3(p.x / gam, p.y / gam, p.z / gam), khat, -q, eps, beta);
     const double r2 = uniform52(w1.x, w1.y), r3 = uniform52(w1.z, w1.w), r4 = uniform52(w2.x, w2.y);
-    const double up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
-    const double lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up);
-    const double one_m = 1.0 - lam;
+    double lam, one_m, up;
+    if (fl & QED_F_REJECT) {  // the accepted candidate lambda = r1^3
+        const double r1 = uniform52(w0.x, w0.y);
+        lam = r1 * r1 * r1;
+        one_m = 1.0 - lam;
+        up = 2.0 * lam / (3.0 * chi * one_m);
+    } else {
+        up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
+        lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up);
+        one_m = 1.0 - lam;
+    }
     const V k = lam * p;
     V pf = p, sf = s, sfu{0, 0, 0}, si{0, 0, 0};
     if (fl & QED_F_RECOIL) pf = one_m * p;
@@ -647,8 +690,8 @@ static __device__ __noinline__ void lepton_exact_one(const Ctx& C, const Tab64& 
     const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
     const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
     F3 x, pf, sf, k, P;
-    lepton_event64(C, X, F64, a, b, cc, down, w1, w2, x, pf, sf, k, P);
-    const double tau_new = (fl & QED_F_TAU) ? exp_draw(w0.x, w0.y) : tau_join(cc.z, cc.w);
+    lepton_event64(C, X, F64, a, b, cc, down, w0, w1, w2, x, pf, sf, k, P);
+    const double tau_new = ((fl & QED_F_TAU) && !(fl & QED_F_REJECT)) ? exp_draw(w0.x, w0.y) : tau_join(cc.z, cc.w);
     store32(L, j, x, pf, sf, cc.y, tau_new);
     if (slot >= 0) {
         const uint4 wc = draw(id, C.S.seed, C.S.step, kSlotChild);
@@ -685,7 +728,8 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
         sf = st.s;
         // the optical depth as the streaming pass left it (spent), kept if the event is not applied
         const double tau0 = tau_join(cc.z, cc.w);
-        tau_kept = (fl & QED_F_TAU) ? tau0 - widen_pos(st.Ws * C.S.dt_f) : tau0;
+        const bool rej = (fl & QED_F_REJECT) != 0;
+        tau_kept = ((fl & QED_F_TAU) && !rej) ? tau0 - widen_pos(st.Ws * C.S.dt_f) : tau0;
         tau_new = tau_kept;
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
         if (fl & QED_F_TAU) down = u52f(w0.z, w0.w) * st.Ws < st.Wdn;
@@ -697,7 +741,12 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
         // the float range (uniforms within ~1e-10 of 0 or 1)
         float up32;
         double up, lam64, om64;
-        if (nlc_up_ff(C.T, down ? 1 : 0, logf(st.chi), w1.x, w1.y, up32)) {
+        if (rej) {  // the accepted candidate lambda = r1^3 (Sec. 4.2)
+            const double r1 = uniform52(w0.x, w0.y);
+            lam64 = r1 * r1 * r1;
+            om64 = 1.0 - lam64;
+            up = 2.0 * lam64 / (3.0 * (double)st.chi * om64);
+        } else if (nlc_up_ff(C.T, down ? 1 : 0, logf(st.chi), w1.x, w1.y, up32)) {
             const float den = fmaf(3.0f * st.chi, up32, 2.0f);
             const float iden = rcp_(den);
             lam64 = (double)(3.0f * st.chi * up32 * iden);
@@ -759,9 +808,9 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
                 }
             }
         }
-        if (exact && q == nullptr) lepton_event64(C, X, F64, a, b, cc, down, w1, w2, st.x, pf, sf, k, P);
+        if (exact && q == nullptr) lepton_event64(C, X, F64, a, b, cc, down, w0, w1, w2, st.x, pf, sf, k, P);
         else if (!exact) P = stokes_to_P(xi, st.eps, st.beta, st.khat);
-        if (fl & QED_F_TAU) tau_new = exp_draw(w0.x, w0.y);
+        if ((fl & QED_F_TAU) && !rej) tau_new = exp_draw(w0.x, w0.y);
         want = sqrt_(dot(k, k)) >= C.S.store_min_f;
         if (!want) c[C_BELOW]++;
     }
@@ -821,7 +870,9 @@ __device__ __forceinline__ bool lepton_stream_one(const Ctx& C, const PartDev& L
     const double tau = tau_join(cc.z, cc.w);
     double tauf = tau;
     if (st.qed) {
-        if (fl & QED_F_TAU) {
+        if (fl & QED_F_REJECT) {
+            if (reject_nlc(C, draw(L.id[j], C.S.seed, C.S.step, kSlotTauBranch), st.chi, st.gam, st.sb, c)) return true;
+        } else if (fl & QED_F_TAU) {
             tauf = tau - widen_pos(st.Ws * dt);
             if (tau_spent(tauf)) return true;
         } else {
@@ -922,7 +973,8 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, 
         P = st.P;
         w = st.w;
         tauf = tau_join(b.z, b.w);
-        if (fl & QED_F_TAU) tauf -= widen_pos(st.Wx * C.S.dt_f);
+        const bool rej = (fl & QED_F_REJECT) != 0;
+        if ((fl & QED_F_TAU) && !rej) tauf -= widen_pos(st.Wx * C.S.dt_f);
         const uint64_t id = G.id[j];
         const uint4 w0 = draw(id, C.S.seed, C.S.step, kSlotTauBranch);
         bool minus;
@@ -938,14 +990,21 @@ static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, 
         const uint64_t dm = low ? half - 1ull - m : m - half;
         const double rf = ((double)dm + 0.5) * 0x1.0p-51, rfc = ((double)((half - 1ull) - dm) + 0.5) * 0x1.0p-51;
         const double chi = (double)st.chi;
-        const double xv = exp(icdf_lookup(X.T, true, minus ? 1 : 0, log(chi), log(rf) - log(rfc)));
-        const double umin = (8.0 / 3.0) / chi;
-        const double ut = umin + xv;
-        // mu (1 - mu) = q = 2/(3 chi u~'), so 1 - 4q = x/u~' exactly and mu = (1 - sqrt(x/u~'))/2
-        // = u~'_min / (2 u~' (1 + sqrt(x/u~'))), free of cancellation near the centre
-        const double mu = 0.5 * (umin / ut) / (1.0 + sqrt(xv / ut));
-        const double lam = low ? mu : 1.0 - mu;
-        const double one_m = low ? 1.0 - mu : mu;
+        double ut, lam, one_m;
+        if (rej) {  // the accepted candidate positron fraction lambda = r1 (Sec. 4.2)
+            lam = uniform52(w0.x, w0.y);
+            one_m = 1.0 - lam;
+            ut = 2.0 / (3.0 * chi * lam * one_m);
+        } else {
+            const double xv = exp(icdf_lookup(X.T, true, minus ? 1 : 0, log(chi), log(rf) - log(rfc)));
+            const double umin = (8.0 / 3.0) / chi;
+            ut = umin + xv;
+            // mu (1 - mu) = q = 2/(3 chi u~'), so 1 - 4q = x/u~' exactly and mu = (1 - sqrt(x/u~'))/2
+            // = u~'_min / (2 u~' (1 + sqrt(x/u~'))), free of cancellation near the centre
+            const double mu = 0.5 * (umin / ut) / (1.0 + sqrt(xv / ut));
+            lam = low ? mu : 1.0 - mu;
+            one_m = low ? 1.0 - mu : mu;
+        }
         const V3<double> k64 = wide(st.k);
         pp = narrow(lam * k64);
         pe = narrow(one_m * k64);
@@ -1039,7 +1098,9 @@ __device__ __forceinline__ bool photon_stream_one(const Ctx& C, const PartDev& G
     }
     const double tau = tau_join(b.z, b.w);
     double tauf = tau;
-    if (st.qed && st.Wx > 0.0f) {
+    if (st.qed && (fl & QED_F_REJECT)) {
+        if (reject_nbw(C, draw(G.id[j], C.S.seed, C.S.step, kSlotTauBranch), st.chi, st.en, st.xi[2], c)) return true;
+    } else if (st.qed && st.Wx > 0.0f) {
         if (fl & QED_F_TAU) {
             tauf = tau - widen_pos(st.Wx * dt);
             if (tau_spent(tauf)) return true;

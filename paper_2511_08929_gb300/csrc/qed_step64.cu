@@ -19,7 +19,7 @@ __device__ __forceinline__ void store_particle64(const PartDev& B, int64_t k, co
 
 __device__ __forceinline__ bool finite3(const V& a) { return isfinite(a.x) && isfinite(a.y) && isfinite(a.z); }
 
-enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_N };
+enum { C_EVENTS, C_STORED, C_DROPPED, C_CLAMPED, C_RENORM, C_BELOW, C_NONFINITE, C_RATE_STEPS, C_BOUND, C_N };
 
 __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const double* __restrict__ bes, FieldP<double> F,
                                                        StepP S, double q, PartDev L, PartDev G, AppendState* A,
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
     const int64_t n = min(L.begin ? *L.begin : *L.count, L.capacity);
     const uint32_t fl = S.flags;
     const double dt = S.dt;
-    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[C_N] = {};
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n; w0 += stride) {
@@ -82,9 +82,22 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                         const double Wup = Wu * (1.0 + sb) / 2.0, Wdn = Wd * (1.0 - sb) / 2.0;
                         const double Ws = Wup + Wdn;
                         bool event = false, down = false;
-                        double u0a = 0.0;
+                        double u0a = 0.0, rej_up = 0.0;
                         const uint64_t id = L.id[j];
-                        if (fl & QED_F_TAU) {
+                        if (fl & QED_F_REJECT) {
+                            // table-free (Sec. 4.2): candidate lambda = r1^3, accepted with probability
+                            // 3 r1^2 (dW/dlambda) dt, dW/dlambda = pref w(lambda; s.beta) (App. A.1)
+                            const uint4 w = draw(id, S.seed, S.step, kSlotTauBranch);
+                            const double r1 = uniform52(w.x, w.y), r2 = uniform52(w.z, w.w);
+                            const double lc = r1 * r1 * r1, om = 1.0 - lc;
+                            rej_up = 2.0 * lc / (3.0 * chi * om);
+                            double b[3] = {0.0, 0.0, 0.0};
+                            if (rej_up < 700.0) bessel64(bes, rej_up, b);  // scaled by e^{u'}; beyond, w ~ 0
+                            const double wl = (-b[2] + (1.0 / om + om) * b[1] + lc * sb * b[0]) * exp(-rej_up);
+                            const double acc = 3.0 * r1 * r1 * pref * wl * dt;
+                            if (acc > 1.0) c[C_BOUND]++;
+                            event = r2 < acc;
+                        } else if (fl & QED_F_TAU) {
                             tauf = tau - Ws * dt;
                             event = tauf <= 0.0;
                             if (event) {
@@ -107,7 +120,7 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                             const uint4 w2 = draw(id, S.seed, S.step, kSlotStokes);
                             const double r2 = uniform52(w1.x, w1.y), r3 = uniform52(w1.z, w1.w), r4 = uniform52(w2.x, w2.y);
                             const double y = log(r2) - log(1.0 - r2);
-                            const double up = exp(icdf_lookup(T, false, down ? 1 : 0, lnchi, y));
+                            const double up = (fl & QED_F_REJECT) ? rej_up : exp(icdf_lookup(T, false, down ? 1 : 0, lnchi, y));
                             const double lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up);
                             const double one_m = 1.0 - lam;
                             const V k = lam * p;
@@ -145,7 +158,7 @@ __global__ void __launch_bounds__(256) lepton64_kernel(TabP<double> T, const dou
                                     for (int i = 0; i < 3; ++i) xi[i] = Fv[i + 1] / Fv[0];
                                 }
                             }
-                            if (fl & QED_F_TAU) tauf = -log(u0a);
+                            if ((fl & QED_F_TAU) && !(fl & QED_F_REJECT)) tauf = -log(u0a);
                             const uint4 wc = draw(id, S.seed, S.step, kSlotChild);
                             const double kn = sqrt(dot(k, k));
                             if (kn >= S.store_min) {
@@ -217,7 +230,7 @@ __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const dou
     const int64_t n = min(G.begin ? *G.begin : *G.count, G.capacity);
     const uint32_t fl = S.flags;
     const double dt = S.dt;
-    unsigned long long c[C_N] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[C_N] = {};
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool have_daughters = El.count != nullptr && Po.count != nullptr;
@@ -264,8 +277,23 @@ __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const dou
                         const double Wmp = Wm * (1.0 - xi[2]) / 2.0, Wpp = Wp * (1.0 + xi[2]) / 2.0;
                         const double Wx = Wmp + Wpp;
                         bool event = false, minus = false;
+                        double rej_lam = 0.0, rej_ut = 0.0;
                         const uint64_t id = G.id[j];
-                        if (fl & QED_F_TAU) {
+                        if (fl & QED_F_REJECT) {
+                            // table-free (Sec. 4.2): candidate positron fraction lambda = r1, accepted with
+                            // probability (dW/dlambda) dt = pref w0(lambda; xi3) dt (App. A.2)
+                            const uint4 w = draw(id, S.seed, S.step, kSlotTauBranch);
+                            const double r1 = uniform52(w.x, w.y), r2 = uniform52(w.z, w.w);
+                            const double om = 1.0 - r1;
+                            rej_lam = r1;
+                            rej_ut = 2.0 / (3.0 * chi * r1 * om);
+                            double b[3] = {0.0, 0.0, 0.0};
+                            if (rej_ut < 700.0) bessel64(bes, rej_ut, b);  // scaled by e^{u~'}; beyond, w0 ~ 0
+                            const double w0r = (b[2] + (om / r1 + r1 / om) * b[1] - xi[2] * b[1]) * exp(-rej_ut);
+                            const double acc = pref * w0r * dt;
+                            if (acc > 1.0) c[C_BOUND]++;
+                            event = r2 < acc;
+                        } else if (fl & QED_F_TAU) {
                             tauf = tau - Wx * dt;
                             event = tauf <= 0.0;
                             if (event) {
@@ -278,16 +306,22 @@ __global__ void __launch_bounds__(256) photon64_kernel(TabP<double> T, const dou
                             event = r1 < Wx * dt;
                             minus = r1 < Wmp * dt;
                         }
-                        if (event && Wx > 0.0) {
+                        if (event && ((fl & QED_F_REJECT) || Wx > 0.0)) {
                             const uint4 w1 = draw(id, S.seed, S.step, kSlotLambdaSpin);
                             const double r = uniform52(w1.x, w1.y), r3 = uniform52(w1.z, w1.w);
-                            const double rf = r < 0.5 ? 1.0 - 2.0 * r : 2.0 * r - 1.0;
-                            double xv = 0.0;
-                            if (rf > 0.0) xv = exp(icdf_lookup(T, true, minus ? 1 : 0, lnchi, log(rf) - log(1.0 - rf)));
-                            const double ut = 8.0 / (3.0 * chi) + xv;
-                            const double qq = 2.0 / (3.0 * chi * ut);
-                            const double mu = 0.5 * (1.0 - sqrt(1.0 - 4.0 * qq));
-                            const double lam = r < 0.5 ? mu : 1.0 - mu;
+                            double ut, lam;
+                            if (fl & QED_F_REJECT) {
+                                ut = rej_ut;
+                                lam = rej_lam;
+                            } else {
+                                const double rf = r < 0.5 ? 1.0 - 2.0 * r : 2.0 * r - 1.0;
+                                double xv = 0.0;
+                                if (rf > 0.0) xv = exp(icdf_lookup(T, true, minus ? 1 : 0, lnchi, log(rf) - log(1.0 - rf)));
+                                ut = 8.0 / (3.0 * chi) + xv;
+                                const double qq = 2.0 / (3.0 * chi * ut);
+                                const double mu = 0.5 * (1.0 - sqrt(1.0 - 4.0 * qq));
+                                lam = r < 0.5 ? mu : 1.0 - mu;
+                            }
                             const double one_m = 1.0 - lam;
                             double b[3];
                             bessel64(bes, ut, b);

@@ -20,7 +20,7 @@ def test_library_exports_every_declared_symbol():
     # the ABI version and status strings need no device
     assert lib.qed_abi_version() == 3
     # qed_counters: eight 64-bit counters, status, pad, first_bad, and the call's reservation block
-    assert ctypes.sizeof(B.QedCounters) == 8 * 8 + 8 + 8 + 4 * 8
+    assert ctypes.sizeof(B.QedCounters) == 9 * 8 + 8 + 8 + 4 * 8
     lib.qed_status_string.restype = ctypes.c_char_p
     assert lib.qed_status_string(-3) == b"particle buffer capacity exhausted"
 
@@ -33,7 +33,7 @@ def test_binding_flags_match_oracle_flags():
              "NONTRANSITION": O.F_NONTRANSITION, "PUSH": O.F_PUSH, "TBMT": O.F_TBMT, "TBMT_PAPER": O.F_TBMT_PAPER,
              "EMIT": O.F_EMIT, "RESOLVED": O.F_RESOLVED, "MOVE": O.F_MOVE, "SPIN_EVENT": O.F_SPIN_EVENT,
              "POL_EVENT": O.F_POL_EVENT, "AMM": O.F_AMM, "LOOP": O.F_LOOP, "G2": O.F_G2,
-             "BETA_BASIS": O.F_BETA_BASIS}
+             "BETA_BASIS": O.F_BETA_BASIS, "REJECT": O.F_REJECT}
     for k, v in pairs.items():
         assert getattr(B, "QED_F_" + k) == v, k
     assert B.QED_F_FULL == O.F_FULL
