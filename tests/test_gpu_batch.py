@@ -173,7 +173,7 @@ def test_batch_matches_single_buffer_path(gpu_tables):
 @pytest.mark.parametrize("flags", [B.QED_F_FULL | B.QED_F_TBMT_PAPER,
                                    B.QED_F_FULL & ~(B.QED_F_POL_COLLAPSE | B.QED_F_SPIN_COLLAPSE),
                                    B.QED_F_FULL | B.QED_F_AMM, B.QED_F_FULL | B.QED_F_LOOP,
-                                   B.QED_F_FULL | B.QED_F_BETA_BASIS])
+                                   B.QED_F_FULL | B.QED_F_BETA_BASIS, B.QED_F_FULL | B.QED_F_REJECT])
 def test_batch_matches_single_buffer_path_other_flags(gpu_tables, flags):
     """A flag set other than the full one runs the batched kernels that read the flags at run time."""
     specs = _specs()

@@ -175,7 +175,7 @@ def _photon_inputs(n, seed, energy=3000.0):
             "id": np.arange(n, dtype=np.uint64) * 104729 + 1}
 
 
-@pytest.mark.parametrize("flags", [None, B.QED_F_FULL | B.QED_F_BETA_BASIS])
+@pytest.mark.parametrize("flags", [None, B.QED_F_FULL | B.QED_F_BETA_BASIS, B.QED_F_FULL | B.QED_F_REJECT])
 def test_photon_pairs_and_compaction(gpu_tables, ora_tables, flags):
     b = _photon_inputs(4000, seed=21)
     f = Q.field(B.QED_FIELD_CP, a0=200.0, n_cycles=4.0, eta0=ETA0)

@@ -228,7 +228,8 @@ def _photon_inputs(n, seed, energy=3000.0):
 
 @pytest.mark.parametrize("flags", [None, B.QED_F_FULL & ~B.QED_F_SPIN_COLLAPSE, B.QED_F_FULL & ~B.QED_F_TAU,
                                    B.QED_F_FULL | B.QED_F_BETA_BASIS,
-                                   (B.QED_F_FULL & ~B.QED_F_SPIN_COLLAPSE) | B.QED_F_BETA_BASIS])
+                                   (B.QED_F_FULL & ~B.QED_F_SPIN_COLLAPSE) | B.QED_F_BETA_BASIS,
+                                   B.QED_F_FULL | B.QED_F_REJECT])
 def test_photon_steps_pairs_and_compaction(gpu_tables, ora_tables, flags):
     fl = B.QED_F_FULL if flags is None else flags
     b = _photon_inputs(2500, seed=21)
