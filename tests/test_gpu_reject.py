@@ -67,8 +67,9 @@ def test_fp64_rejection_lepton_steps(gpu_tables, ora_tables, q):
     assert c.bound_exceeded == oc.bound_exceeded
     compare_sets(gL.read(), oL.view(), steps * 1e-12, "leptons")
     compare_sets(gG.read(), oG.view(), steps * 1e-12, "photons", P_headless=True)
-    # the optical depth is not used in this mode
-    np.testing.assert_array_equal(np.sort(gL.read()["tau"]), np.sort(oL.view()["tau"]))
+    # the optical depth is not used in this mode: both sides keep their birth values (-ln u, equal but
+    # for the last bit of the two logarithms)
+    np.testing.assert_allclose(np.sort(gL.read()["tau"]), np.sort(oL.view()["tau"]), rtol=4e-16, atol=0)
 
 
 def test_fp32_rejection_lepton_steps(gpu_tables, ora_tables):
