@@ -60,6 +60,8 @@ def parse():
                     help="batched: fixed launch shape 'variant,blocks_per_sm,chunk' instead of the autotuner")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-sampler leg")
     ap.add_argument("--cascade-steps", type=int, default=None, help="cascade: steps of the run (default 3000)")
+    ap.add_argument("--flags", default="full", choices=["full", "reject"],
+                    help="batched: the full flag set, or with the table-free rejection sampler (QED_F_REJECT)")
     ap.add_argument("--mlp-train", type=float, default=5e7, help="learned sampler: training samples")
     ap.add_argument("--mlp-eval", type=float, default=1e8, help="learned sampler: evaluated events")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -406,7 +408,8 @@ def _subsample(beam: dict, m: int) -> dict:
     return {k: v[ix] for k, v in beam.items()}
 
 
-def growth_capacities(Q, B, tables, wl, insts, fields, seeds, end_step, device, sub=64, min_sub=256, margin=1.25):
+def growth_capacities(Q, B, tables, wl, insts, fields, seeds, end_step, device, sub=64, min_sub=256, margin=1.25,
+                      flags=None):
     """Buffer capacities from a measured growth curve.  A strided subsample of every instance (1/sub of
     its electrons, at least min_sub) is stepped on the GPU through end_step steps with generous buffers,
     and each species' largest count per initial electron is recorded; the batch then gets
@@ -419,7 +422,7 @@ def growth_capacities(Q, B, tables, wl, insts, fields, seeds, end_step, device, 
                 _subsample(wl.beam(k, x), min(x["n"], max(min_sub, x["n"] // sub))) for k, x in enumerate(insts)]
         caps = [tuple(max(4096, int(f * len(b["id"]))) for f in fac) for b in subs]
         bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
-                     device=device)
+                     device=device, flags=flags)
         bt.set_tuning(0, 0, 16, 25)
         for k, ((e, _, _), b) in enumerate(zip(bt.buffers(), subs)):
             b = z_order(b)
@@ -447,14 +450,14 @@ def growth_capacities(Q, B, tables, wl, insts, fields, seeds, end_step, device, 
     raise RuntimeError("buffer sizing pass overflowed three times")
 
 
-def batch_setup(Q, B, I, tables, rank, device, scale=1.0, caps=None):
+def batch_setup(Q, B, I, tables, rank, device, scale=1.0, caps=None, flags=None):
     wl = batch_workload(I, scale)
     insts, seeds, id_offset = replica_plan(wl, rank)
     fields = [Q.laser_field(wl.laser(x)) for x in insts]
     if caps is None:
         caps = [tuple(max(4096, int(wl.capacity_factor * x["n"])) for _ in range(3)) for x in insts]
     bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, photon_store_min=wl.photon_store_min,
-                 device=device)
+                 device=device, flags=flags)
     for k, (x, (e, p, g)) in enumerate(zip(insts, bt.buffers())):
         b = z_order(wl.beam(k, x))
         b["id"] = b["id"] + id_offset
@@ -495,9 +498,10 @@ def native_batch(args):
     insts0, seeds0, _ = replica_plan(wl0, rank)
     fields0 = [Q.laser_field(wl0.laser(x)) for x in insts0]
     t0 = time.time()
-    caps, sizing = growth_capacities(Q, B, tables, wl0, insts0, fields0, seeds0, end_step, device)
+    flags = {"full": None, "reject": B.QED_F_FULL | B.QED_F_REJECT}[args.flags]
+    caps, sizing = growth_capacities(Q, B, tables, wl0, insts0, fields0, seeds0, end_step, device, flags=flags)
     sizing["seconds"] = round(time.time() - t0, 2)
-    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device, args.scale, caps=caps)
+    wl, insts, fields, seeds, caps, bt = batch_setup(Q, B, I, tables, rank, device, args.scale, caps=caps, flags=flags)
     stream = torch.cuda.current_stream().cuda_stream
 
     # untimed advance into the interaction; the autotuner times its candidates on real steps near its end
@@ -611,7 +615,8 @@ def native_batch(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": wl.name, "instances": len(insts), "electrons_per_gpu": n_el,
+        "config": {"workload": wl.name + ("" if args.flags == "full" else "_reject"), "instances": len(insts),
+                   "electrons_per_gpu": n_el, "flags": args.flags,
                    "laser": "LP/CP alternating 0.8um 10 cycles, a0 U[10,300]", "gamma": "U[500,8000]",
                    "buffers": "sized from a measured growth curve (no daughter dropped)", "sizing": sizing,
                    "layout": "FP32 float4 SoA",
@@ -904,7 +909,7 @@ def fp64_leg(bt, wl, fields, seeds, tables, Q, B, torch, stream, steps=3):
         counts.append(torch.stack([torch.stack([b.counts[0] for b in x[:3]]).sum() for x in bufs64]).sum())
         s = step0 + k
         for (e64, p64, g64, ws), f, sd in zip(bufs64, fields, seeds):
-            d = Q.step_desc(wl.dt, float(s) * wl.dt, s, sd, B.QED_F_FULL, wl.photon_store_min)
+            d = Q.step_desc(wl.dt, float(s) * wl.dt, s, sd, int(bt.desc.flags), wl.photon_store_min)
             B.qed_snapshot_counts([e64.s, p64.s, g64.s], stream)
             B.qed_pair_step(tables.handle, f, d, g64.s, e64.s, p64.s, ctr64.ptr, stream)
             B.qed_push_step(tables.handle, f, d, e64.s, g64.s, ctr64.ptr, stream)
@@ -1079,7 +1084,7 @@ def error_leg(bt, wl, fields, seeds, torch, steps, stride=16, diverged=1e-3):
             caps = (2 * (n0[0] + n0[2]) + 64, 2 * (n0[1] + n0[2]) + 64, n0[2] + 2 * (n0[0] + n0[1]) + 64)
             E, P, G = (O.Particles.from_arrays(c, d["pos"], d["mom"], d["spin"], d["w"], d["id"], tau=d["tau"])
                        for c, d in zip(caps, (pe, pp, pg)))
-            st = O.step_desc(wl.dt, float(step) * wl.dt, step, seeds[k], O.F_FULL, wl.photon_store_min)
+            st = O.step_desc(wl.dt, float(step) * wl.dt, step, seeds[k], int(bt.desc.flags), wl.photon_store_min)
             t0 = time.perf_counter()
             _oracle_batch_step(O, tb, _oracle_field(O, fields[k]), st, E, P, G)
             t_or += time.perf_counter() - t0
