@@ -14,6 +14,11 @@ counted on the device.  The particle state (several GB) is far larger than L2: n
 --workload headon: the single-buffer entry points on one collision (1e7 electrons, gamma 4000, spin +z,
 CP a0 = 150, 20 cycles).
 
+--workload helicity: the plane-wave analogues of the helicity-transfer benchmarks (10 GeV electrons of
+helicity +1 against an LP a0 = 50 pulse and a CP a0 = 100 pulse, 1e6 electrons each, two instances of one
+batch), the whole crossing timed, with the photons' circular polarization and the positrons' longitudinal
+polarization against energy.
+
 --workload cascade: 2e8 electrons (gamma 1000) where two CP pulses (a0 = 500, 1 um, 15 cycles) collide,
 the whole 3000-step run through the batched path as one instance: the pair cascade multiplies the
 leptons, compaction every step; photons below 300 m c^2 are not stored.  Timed: all 3000 steps, in
@@ -50,7 +55,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "headon", "cascade"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "headon", "cascade", "helicity"])
     ap.add_argument("--electrons", type=int, default=10_000_000, help="headon workload only")
     ap.add_argument("--advance", type=int, default=None,
                     help="untimed steps before warm-up (into the interaction; default 450 batched, 620 headon)")
@@ -216,7 +221,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args) if args.workload == "headon" else reference_arm_batch(args)
-    run = {"headon": native, "cascade": native_cascade}.get(args.workload, native_batch)
+    run = {"headon": native, "cascade": native_cascade, "helicity": native_helicity}.get(args.workload, native_batch)
     out = run(args)
     if out is not None:
         print(json.dumps(out))
@@ -789,6 +794,105 @@ def native_cascade(args):
     if dist is not None:
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+class _Workloads:
+    """Several head-on workloads as the instances of one batch (the interface growth_capacities reads)."""
+
+    def __init__(self, wls, scale=1.0):
+        self.wls = wls
+        self.scale = scale
+        self.dt = wls[0].dt
+        self.photon_store_min = wls[0].photon_store_min
+
+    def instances(self):
+        return [{"n": max(1, int(w.n_electrons * self.scale)), "seed": w.seed} for w in self.wls]
+
+    def laser(self, inst):
+        return self.wls[self.instances().index(inst)].laser
+
+    def beam(self, k, inst, n=None):
+        b = self.wls[k].beam(inst["n"] if n is None else n)
+        b["id"] = b["id"] + np.uint64(k << 40)
+        return b
+
+    def sample(self, k, inst, m):
+        return self.beam(k, inst, m)
+
+
+def native_helicity(args):
+    """The helicity-transfer analogues: both collisions in one batch, every step of the crossing timed."""
+    import torch
+    from paper_2511_08929_gb300 import binding as B
+    from paper_2511_08929_gb300 import build as bld
+    from paper_2511_08929_gb300 import buffers as Q
+    from paper_2511_08929_gb300 import diagnostics as D
+    from paper_2511_08929_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    device = "cuda:0"
+    bld.build()
+    tables = Q.Tables(1e-4, 1e3, 256, 256)
+    wl = _Workloads([I.HELICITY_LP_X14, I.HELICITY_CP_X15], args.scale)
+    insts = wl.instances()
+    seeds = [x["seed"] for x in insts]
+    fields = [Q.laser_field(w.laser) for w in wl.wls]
+    steps = max(w.crossing_steps() for w in wl.wls)
+    t0 = time.time()
+    caps, sizing = growth_capacities(Q, B, tables, wl, insts, fields, seeds, steps + 8, device, sub=64, min_sub=4096)
+    sizing["seconds"] = round(time.time() - t0, 2)
+    bt = Q.Batch(tables, fields, seeds, caps, wl.dt, t0=0.0, step0=0, device=device)
+    for k, (x, (e, p, g)) in enumerate(zip(insts, bt.buffers())):
+        b = z_order(wl.beam(k, x))
+        e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"])
+        e.init_tau(seeds[k])
+    v, bps, ch = (int(x) for x in (args.tuning or "0,3,16").split(","))
+    SEG = 100
+    B.qed_batch_set_tuning(bt.handle, B.QedBatchTuning(v, bps, ch, SEG))
+    stream = torch.cuda.current_stream().cuda_stream
+    bt.step(0, stream)
+    bt.ctr.zero()
+    torch.cuda.synchronize()
+    stop = threading.Event()
+    clock_lines = []
+    th = threading.Thread(target=clocks_sampler, args=(stop, clock_lines, 0), daemon=True)
+    th.start()
+    time.sleep(0.5)
+    s0 = bt.stats(stream)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    bt.step(steps, stream)
+    z.record()
+    torch.cuda.synchronize()
+    stop.set()
+    th.join(timeout=5)
+    ms = a.elapsed_time(z)
+    s1 = bt.stats(stream)
+    c = bt.ctr.read()
+    if c.status != 0:
+        raise SystemExit(f"bench: helicity run ended with status {c.status} ({B.status_string(c.status)})")
+    psteps = float(s1.particle_steps - s0.particle_steps)
+    gev = 1e9 / I.ME_EV
+    edges = [i * gev for i in range(0, 11)]
+    diag = {}
+    for name, (e, p, g) in zip(("x14_lp_photons_xi2", "x15_cp_positrons_longitudinal"), bt.buffers()):
+        diag[name] = D.polarization_vs_energy(g if name.startswith("x14") else p, edges)
+    diag["energy_unit"] = "m c^2 (bins of 1 GeV)"
+    out = {"metric": METRIC, "value": psteps / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 0,
+           "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "helicity_transfer_x14_x15", "instances": [w.name for w in wl.wls],
+                      "electrons": [x["n"] for x in insts], "sizing": sizing,
+                      "timed": f"all {steps} steps of the crossing, graph launches of {SEG} steps",
+                      "launch": {"variant": v, "blocks_per_sm": bps, "chunk": ch}},
+           "clocks": summarize_clocks(clock_lines), "gpu_launches": 7 * steps,
+           "counters": {k: int(x) for k, x in c.as_dict().items()},
+           "particles_at_end": {"electrons": [int(bt.buffers()[k][0].count()) for k in range(2)],
+                                "positrons": [int(bt.buffers()[k][1].count()) for k in range(2)],
+                                "photons": [int(bt.buffers()[k][2].count()) for k in range(2)]},
+           "diagnostics": diag}
+    bt.close()
+    return out
 
 
 def mlp_leg(args, tables, torch):

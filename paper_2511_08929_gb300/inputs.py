@@ -146,13 +146,18 @@ class Workload:
     n_r: int = 256
     seed: int = 1
     photon_store_min: float = 0.0
+    z_cycles: float = 10.0  # beam length in wavelengths (electrons at z in [lambda, (1 + z_cycles) lambda])
 
     def beam(self, n=None, seed=None):
         n = self.n_electrons if n is None else n
         lam = 2.0 * math.pi  # wavelength in c/omega
         return lepton_beam(n, self.gamma, rel_spread=self.rel_spread, ang_sigma=self.ang_sigma,
-                           direction=(0.0, 0.0, -1.0), z_range=(lam, 11.0 * lam), spin=self.spin,
+                           direction=(0.0, 0.0, -1.0), z_range=(lam, (1.0 + self.z_cycles) * lam), spin=self.spin,
                            spin_dir=self.spin_dir, seed=self.seed if seed is None else seed)
+
+    def crossing_steps(self) -> int:
+        """Steps for the whole beam to cross the whole pulse (closing speed 2c) and leave it."""
+        return int(math.ceil((self.laser.n_cycles + self.z_cycles + 1.0) * 2.0 * math.pi / 2.0 / self.dt)) + 20
 
 
 # 1e4 electrons, gamma 2000 (1 % spread, 1 mrad), random unit spins, LP a0=50, 0.8 um, 10 cycles,
@@ -162,6 +167,19 @@ HEADON_LP_SMALL = Workload("headon_lp_a50_g2000_n1e4", 10_000, 2000.0, Laser("LP
 # 1e7 electrons, gamma 4000, s = +z, CP a0=150, 20 cycles, 4000 steps, NLC + NBW, buffers 4x.
 HEADON_CP_LARGE = Workload("headon_cp_a150_g4000_n1e7", 10_000_000, 4000.0, Laser("CP", 150.0, 0.8, 20.0), 4000,
                            spin="fixed", spin_dir=(0.0, 0.0, 1.0), pairs=True, capacity_factor=4.0, seed=2)
+
+
+# Plane-wave analogues of the helicity-transfer benchmarks of Sec. 8.6.3 and 8.6.4 (focused pulses there):
+# 10 GeV electrons (6 % spread), fully longitudinally polarized with helicity +1 (spin along the momentum,
+# -z), a 2-wavelength bunch, against
+#   X14: a linearly polarized pulse a0 = 50, 1 um, 12 cycles: circularly polarized photons;
+#   X15: a circularly polarized pulse a0 = 100, 1 um, 5 cycles: longitudinally polarized positrons.
+HELICITY_LP_X14 = Workload("helicity_lp_a50_10GeV", 1_000_000, 10e9 / ME_EV, Laser("LP", 50.0, 1.0, 12.0), 0,
+                           rel_spread=0.06, spin="fixed", spin_dir=(0.0, 0.0, -1.0), pairs=True, seed=14,
+                           z_cycles=2.0)
+HELICITY_CP_X15 = Workload("helicity_cp_a100_10GeV", 1_000_000, 10e9 / ME_EV, Laser("CP", 100.0, 1.0, 5.0), 0,
+                           rel_spread=0.06, spin="fixed", spin_dir=(0.0, 0.0, -1.0), pairs=True, seed=15,
+                           z_cycles=2.0)
 
 
 @dataclasses.dataclass
