@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="batched: fixed launch shape 'variant,blocks_per_sm,chunk' instead of the autotuner")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-sampler leg")
+    ap.add_argument("--no-headon", action="store_true", help="batched: skip the config-2 head-on leg")
     ap.add_argument("--cascade-steps", type=int, default=None, help="cascade: steps of the run (default 3000)")
     ap.add_argument("--flags", default="full", choices=["full", "reject"],
                     help="batched: the full flag set, or with the table-free rejection sampler (QED_F_REJECT)")
@@ -324,11 +325,11 @@ def native(args):
     # roofline of the dominant kernel: algorithmic bytes per launch / its event-timed duration
     # electron step: 88 B per lepton-step (read x, p, s, tau 44 B; write x, p, s, tau 44 B)
     #                + 8 B id per emission + 52 B per stored photon (x, k, P 36 + tau 8 + id 8)
-    # photon step:   76 B per photon-step (read x, k, P, tau 44 B; write x, P, tau 32 B)
-    #                + 8 B id per conversion + 104 B per stored pair
+    # photon step:   56 B per photon-step (read x, k, P, tau 44 B; write x 12 B) + 20 B (write P, tau)
+    #                per photon-step with a pair rate, + 8 B id per conversion + 104 B per stored pair
     peak, peak_kind = measured_peaks()
-    push_bytes = 88.0 * n_el + 60.0 * (ctr.events)  # events of all species counted together (upper bound)
-    pair_bytes = 76.0 * n_ph
+    push_bytes = 88.0 * (n_el + n_po) + 60.0 * (ctr.events)  # events of all species counted together (upper bound)
+    pair_bytes = 56.0 * n_ph + 20.0 * ctr.rate_steps
     bw_push = push_bytes / (t_push / 1e3) / 1e9 if t_push > 0 else 0.0
     bw_pair = pair_bytes / (t_pair / 1e3) / 1e9 if t_pair > 0 else 0.0
     dominant = "photon_step" if t_pair >= t_push else "electron_step"
@@ -344,6 +345,8 @@ def native(args):
     extras = {}
     if not args.no_extras and rank == 0:
         extras = extra_legs(args, sim, Q, B, I, wl, tables, device, torch)
+    elif getattr(args, "fp64_leg", False) and rank == 0:
+        extras = extra_legs(args, sim, Q, B, I, wl, tables, device, torch, legs=("fp64",))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -615,6 +618,10 @@ def native_batch(args):
         bt.close()
         torch.cuda.empty_cache()
         extras["mlp"] = mlp_leg(args, tables, torch)
+    if extras_on and not args.no_headon:
+        bt.close()
+        torch.cuda.empty_cache()
+        extras["config2_headon"] = headon_leg(args)
     n_el = sum(x["n"] for x in insts)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -893,6 +900,23 @@ def native_helicity(args):
            "diagnostics": diag}
     bt.close()
     return out
+
+
+def headon_leg(args):
+    """Config 2 beside the headline: 1e7 electrons (gamma 4000, spin +z) in the CP a0 = 150 pulse through
+    the single-buffer FP32 entry points (20 timed steps inside the interaction, buffers sized by the
+    growth pass, status 0), and the plain FP64 path on the same state."""
+    import copy
+    a = copy.copy(args)
+    a.workload, a.steps, a.warmup, a.advance, a.electrons = "headon", 20, 3, 620, 10_000_000
+    a.no_extras, a.fp64_leg = True, True
+    o = native(a)
+    v64 = o.get("fp64_plain", {}).get("value")
+    return {"workload": o["config"]["workload"], "value": o["value"], "unit": UNIT, "ms_per_step": o["ms_per_step"],
+            "roofline": {k: o["roofline"].get(k) for k in ("kernel", "achieved", "frac", "peak")},
+            "fp64_plain": o.get("fp64_plain"), "fp32_over_fp64": (o["value"] / v64) if v64 else None,
+            "status": o["counters"]["status"], "particles_at_start": o["particles_at_start"],
+            "clocks": o["clocks"]}
 
 
 def mlp_leg(args, tables, torch):
@@ -1311,7 +1335,7 @@ def reference_arm_batch(args):
     return 0
 
 
-def extra_legs(args, sim, Q, B, I, wl, tables, device, torch):
+def extra_legs(args, sim, Q, B, I, wl, tables, device, torch, legs=("fp64", "e2e", "cpu")):
     """e2e through the C ABI with host buffers, the plain FP64 path on the same state, and the oracle
     on a bounded sample of the same state (CPU baseline)."""
     out = {}
@@ -1338,6 +1362,8 @@ def extra_legs(args, sim, Q, B, I, wl, tables, device, torch):
     out["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": K64, "ms_per_step": s_.elapsed_time(e_) / K64}
     del sim64
     torch.cuda.empty_cache()
+    if "e2e" not in legs:
+        return out
 
     # ---- e2e: host-resident particle state, copied in and out through pinned memory every step ----
     Ke = 3
