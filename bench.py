@@ -499,9 +499,11 @@ def native_batch(args):
     t_tables = time.time() - t0
     extras_on = not args.no_extras and rank == 0
     E2E_STEPS, ERR_STEPS = 3, 3
-    # every step the run takes on the FP32 batch: advance, warm-up, e2e, timed, error legs (+ slack)
+    MLP_STEPS = 4 * MLP_WINDOW if extras_on and not args.no_mlp and args.flags == "full" else 0
+    # every step the run takes on the FP32 batch: advance, warm-up, e2e, timed, error legs, the learned
+    # sampler's windows (+ slack)
     end_step = args.advance + args.warmup + (E2E_STEPS if extras_on else 0) + args.steps + \
-        (ERR_STEPS if extras_on else 0) + 16
+        (ERR_STEPS if extras_on else 0) + MLP_STEPS + 16
     wl0 = batch_workload(I, args.scale)
     insts0, seeds0, _ = replica_plan(wl0, rank)
     fields0 = [Q.laser_field(wl0.laser(x)) for x in insts0]
@@ -615,9 +617,9 @@ def native_batch(args):
         extras["cpu_baseline"] = cpu
         extras["fp64_plain"] = fp64_leg(bt, wl, fields, seeds, tables, Q, B, torch, stream)
     if extras_on and not args.no_mlp:
+        extras["mlp"] = mlp_leg(args, tables, torch, bt if MLP_STEPS else None, stream)
         bt.close()
         torch.cuda.empty_cache()
-        extras["mlp"] = mlp_leg(args, tables, torch)
     if extras_on and not args.no_headon:
         bt.close()
         torch.cuda.empty_cache()
@@ -919,10 +921,54 @@ def headon_leg(args):
             "clocks": o["clocks"]}
 
 
-def mlp_leg(args, tables, torch):
+MLP_WINDOW = 8  # steps per timed window of the learned sampler on the batch's event path
+
+
+def mlp_event_path(bt, smp, torch, stream, tol=1e-4):
+    """The learned sampler inside the batched step (qed_batch_set_mlp) on the timed workload's state:
+    four consecutive graph launches of MLP_WINDOW steps each, tables / network / tables / network (the
+    alternation cancels the drift of the populations), each captured outside its timed launch."""
+    from paper_2511_08929_gb300 import binding as B
+    tn = bt.tuning()
+    ms = {"tables": 0.0, "network": 0.0}
+    ev = {"tables": 0, "network": 0}
+    ps = {"tables": 0.0, "network": 0.0}
+    fb = 0
+    for mode in ("tables", "network", "tables", "network"):
+        bt.set_sampler(smp if mode == "network" else None, tol)  # resets the fallback count
+        B.qed_batch_set_tuning(bt.handle, B.QedBatchTuning(tn.variant, tn.blocks_per_sm, tn.chunk, MLP_WINDOW))
+        bt.step(0, stream)  # capture outside the timed launch
+        torch.cuda.synchronize()
+        c0, s0 = bt.ctr.read().events, bt.stats(stream).particle_steps
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        bt.step(MLP_WINDOW, stream)
+        b.record()
+        torch.cuda.synchronize()
+        ms[mode] += a.elapsed_time(b)
+        ev[mode] += bt.ctr.read().events - c0
+        ps[mode] += float(bt.stats(stream).particle_steps - s0)
+        if mode == "network":
+            fb += bt.sampler_last(0)[1]
+    bt.set_sampler(None)
+    status = int(bt.ctr.read().status)
+    n = 2 * MLP_WINDOW
+    return {"steps_per_mode": n, "status": status, "tolerance": tol,
+            "ms_per_step_tables": ms["tables"] / n, "ms_per_step_network": ms["network"] / n,
+            "events_per_step_tables": ev["tables"] / n, "events_per_step_network": ev["network"] / n,
+            "particle_steps_per_s_tables": ps["tables"] / (ms["tables"] / 1e3),
+            "particle_steps_per_s_network": ps["network"] / (ms["network"] / 1e3),
+            "step_time_ratio_network_over_tables": ms["network"] / ms["tables"],
+            "fallback_fraction": fb / max(1, ev["network"]),
+            "note": "events counted by the counters (leptons' emissions and photons' pairs); the sampler runs "
+                    "on every listed event, pairs with placeholder inputs"}
+
+
+def mlp_leg(args, tables, torch, bt=None, stream=0):
     """The learned sampler: 3-64-64-64-4 SiLU, BF16 weights and activations with FP32 accumulation on
     tensor cores, trained on table samples at chi in [1e-3, 1e2], evaluated on events with the table
-    fallback wherever the network's CDF error (or Stokes error) exceeds 1e-4; the table path beside it."""
+    fallback wherever the network's CDF error (or Stokes error) exceeds 1e-4; the table path beside it;
+    with bt, also inside the batched step on its state (mlp_event_path)."""
     from paper_2511_08929_gb300 import mlp as GM
     batch = 4096
     steps = int(math.ceil(args.mlp_train / batch))
@@ -974,19 +1020,24 @@ def mlp_leg(args, tables, torch):
     torch.cuda.synchronize()
     t_br = e0.elapsed_time(e1) / 1e3
     net_rate, tab_rate, br_rate = total / t_net, chi.shape[0] / t_tab, chi.shape[0] / t_br
+    n_tab = int(chi.shape[0])
+    del first, chi, r, s
+    torch.cuda.empty_cache()
+    event_path = mlp_event_path(bt, smp, torch, stream) if bt is not None else None
     smp.close()
     labels = ["<1e-7", "1e-7..1e-6", "1e-6..1e-5", "1e-5..1e-4", "1e-4..1e-3", ">1e-3"]
     return {"train_samples": steps * batch, "train_steps": steps, "train_s": round(train_s, 2),
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-100:].mean()),
             "eval_events": total, "samples_per_s": net_rate, "fallback_fraction": n_fb / total,
             "network_cdf_error_hist": {k: float(v / total) for k, v in zip(labels, hist)},
-            "table_path_samples_per_s": tab_rate, "table_path_events": int(chi.shape[0]),
+            "table_path_samples_per_s": tab_rate, "table_path_events": n_tab,
             "table_path": "the checked sampler's own fallback: the mixture quantile by bisection of its CDF",
             "gain_over_table_path": net_rate / tab_rate,
             "branch_table_samples_per_s": br_rate,
             "branch_table": "the step's sampler: spin branch by W_down(1-s)/(2W_s), one float-float ICDF row",
             "gain_over_branch_table": net_rate / br_rate, "tolerance": 1e-4,
-            "parameters": 8836, "weights_bytes_bf16": 2 * (192 + 4096 + 4096 + 256)}
+            "parameters": 8836, "weights_bytes_bf16": 2 * (192 + 4096 + 4096 + 256),
+            "event_path": event_path}
 
 
 def _to_fp64(b32, b64, torch):

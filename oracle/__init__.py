@@ -45,6 +45,7 @@ F_LOOP = 1 << 14
 F_G2 = 1 << 15
 F_BETA_BASIS = 1 << 16
 F_REJECT = 1 << 17
+F_MIX_QUANTILE = 1 << 18  # oracle only: emission u' the exact quantile of the spin mixture at r2
 F_FULL = (F_TAU | F_RECOIL | F_SPIN_COLLAPSE | F_POL_COLLAPSE | F_NONTRANSITION | F_PUSH | F_TBMT | F_EMIT
           | F_RESOLVED | F_MOVE | F_SPIN_EVENT | F_POL_EVENT)
 

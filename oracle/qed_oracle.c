@@ -781,8 +781,11 @@ enum {
     ORC_F_LOOP = 1u << 14,         /* Scorer term of the loop in the no-emission update; T-BMT with g = 2 */
     ORC_F_G2 = 1u << 15,           /* T-BMT with g = 2 (a = 0), the comparison run of Sec. 8.6.2 */
     ORC_F_BETA_BASIS = 1u << 16,   /* spins resolved along +-beta instead of the SQA (Sec. 8.3 comparison) */
-    ORC_F_REJECT = 1u << 17        /* table-free decision and sampling by rejection (Sec. 4.2) */
+    ORC_F_REJECT = 1u << 17,       /* table-free decision and sampling by rejection (Sec. 4.2) */
+    ORC_F_MIX_QUANTILE = 1u << 18  /* emission's u' the exact quantile of the spin mixture at r2 (oracle only) */
 };
+
+void orc_mlp_target(double chi, double r, double s, double out[4]); /* defined with the sampler's target */
 
 typedef struct {
     double dt, t;         /* step length, time at the start of the step */
@@ -1028,8 +1031,19 @@ static void lepton_one(const orc_tables *tb, const orc_field *fd, const orc_step
                 double u1[2], u2[2];
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_LAMBDA_SPIN, u1);
                 orc_uniform_pair(id, st->seed, st->step, ORC_SLOT_STOKES, u2);
-                /* lambda from the ICDF of the chosen branch (Sec. 5.1), or the accepted candidate */
-                double up = (fl & ORC_F_REJECT) ? rej_up : exp(orc_icdf_lookup(tb, 0, down ? 1 : 0, chi, u1[0]));
+                /* lambda from the ICDF of the chosen branch (Sec. 5.1), or the accepted candidate, or
+                 * (the learned sampler's target) the exact quantile of the mixture w(lambda; s.beta) at
+                 * the same r2: the branch pair samples that mixture, so both draw one distribution */
+                double up;
+                if (fl & ORC_F_REJECT) {
+                    up = rej_up;
+                } else if (fl & ORC_F_MIX_QUANTILE) {
+                    double o[4];
+                    orc_mlp_target(chi, u1[0], sb, o);
+                    up = exp(o[0]);
+                } else {
+                    up = exp(orc_icdf_lookup(tb, 0, down ? 1 : 0, chi, u1[0]));
+                }
                 double lam = orc_nlc_lambda(chi, up);
                 /* photon and recoil (Sec. 5.1): hbar k = lambda p_i, p_f = (1 - lambda) p_i */
                 double k[3] = {lam * p[0], lam * p[1], lam * p[2]};

@@ -155,6 +155,8 @@ def lib():
                 "qed_mlp_train": (i32, [vp, vp, i64, i64, u64, i64, C.c_float, C.c_float, C.c_float, vp, vp]),
                 "qed_mlp_forward": (i32, [vp, vp, i64, vp, vp]),
                 "qed_mlp_sample": (i32, [vp, vp, vp, vp, vp, i64, C.c_double, i32, vp, vp, vp, vp, vp]),
+                "qed_batch_set_mlp": (i32, [vp, vp, C.c_double]),
+                "qed_batch_mlp_last": (i32, [vp, i64, vp, vp, vp, vp, vp, P(i64), P(C.c_ulonglong)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -376,3 +378,23 @@ def declared_entry_points():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(qed_[a-z0-9_]+)\s*\(", txt)))
+
+
+def qed_batch_set_mlp(batch: int, m: int, tol: float):
+    """m = 0 (None) restores the tables on the batch's event path."""
+    _check(lib().qed_batch_set_mlp(batch, m or None, tol), "qed_batch_set_mlp")
+
+
+def qed_batch_mlp_last(batch: int, n_max: int):
+    """The last step's sampler inputs and outputs of its first n_max events: (n_events, n_fallback_total,
+    dict of chi, r, s_beta (float64), out4 (float32, n x 4), is_lepton (bool)) trimmed to the events."""
+    n_max = int(n_max)
+    chi, r, sb = (np.zeros(n_max) for _ in range(3))
+    out4 = np.zeros((n_max, 4), dtype=np.float32)
+    lep = np.zeros(n_max, dtype=np.uint8)
+    n, fb = C.c_int64(0), C.c_ulonglong(0)
+    _check(lib().qed_batch_mlp_last(batch, n_max, chi.ctypes.data, r.ctypes.data, sb.ctypes.data, out4.ctypes.data,
+                                    lep.ctypes.data, C.byref(n), C.byref(fb)), "qed_batch_mlp_last")
+    k = min(n_max, n.value)
+    return n.value, fb.value, {"chi": chi[:k], "r": r[:k], "s_beta": sb[:k], "out4": out4[:k],
+                               "is_lepton": lep[:k].astype(bool)}

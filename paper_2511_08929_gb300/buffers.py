@@ -270,6 +270,17 @@ class Batch:
     def stats(self, stream: int = 0):
         return B.qed_batch_stats_read(self.handle, stream)
 
+    def set_sampler(self, sampler=None, tol: float = 1e-4):
+        """Draw every emission's energy fraction with the learned sampler (an mlp.Sampler, kept alive by
+        this batch while it is set), checked at tol with the tables as fallback; None restores the
+        tables."""
+        B.qed_batch_set_mlp(self.handle, sampler.handle if sampler is not None else None, tol)
+        self._sampler = sampler
+
+    def sampler_last(self, n_max: int):
+        """The last step's sampler inputs and outputs (see binding.qed_batch_mlp_last)."""
+        return B.qed_batch_mlp_last(self.handle, n_max)
+
     def buffers(self):
         return [(self.el[k], self.po[k], self.ph[k]) for k in range(len(self))]
 

@@ -429,7 +429,8 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
                                                                    const SegCtx* __restrict__ ctx,
                                                                    const long long* __restrict__ ev,
                                                                    const ClockDev* __restrict__ clk, Tab64 X64,
-                                                                   qed_counters* ctr) {
+                                                                   qed_counters* ctr,
+                                                                   const float* __restrict__ lnup = nullptr) {
     __shared__ ExactQ eq[kEventThreads / 32];  // per warp: the events taken again in FP64
     const unsigned long long n = clk->n_events;
     unsigned long long c[C_N] = {};
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
             const SegCtx& X = ctx[key & 0x3FFFFFFF];
             const InstDev& I = inst[X.ii];
             lepton_exact_one(X.C, X64, I.F64, I.sp[X.sp], I.sp[2], q.j[from + lane], q.slot[from + lane],
-                             (key >> 30) & 1);
+                             (key >> 30) & 1, lnup != nullptr, q.lnu[from + lane]);
         }
         __syncwarp();
     };
@@ -458,9 +459,11 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
         const SegCtx& X = ctx[s];
         const InstDev& I = inst[X.ii];
         const bool ph = X.sp == 2;
+        const float lnu = lnup != nullptr && e >= 0 ? lnup[4 * (k + lane)] : 0.0f;  // the learned sampler's ln u'
         // both passes are warp-collective; a lane takes part in the one of its species with its particle
         if (__ballot_sync(0xffffffffu, j >= 0 && !ph))
-            lepton_events(X.C, X64, I.F64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c, &q, s);
+            lepton_events(X.C, X64, I.F64, ph ? -1 : j, I.sp[ph ? 0 : X.sp], I.sp[2], &I.app[0], ctr, c, &q, s,
+                          lnup != nullptr, lnu);
         if (__ballot_sync(0xffffffffu, j >= 0 && ph))
             photon_events(X.C, X64, ph ? j : -1, I.sp[2], I.sp[0], I.sp[1], &I.app[1], ctr, c);
         const int qn = q.n;
@@ -472,6 +475,42 @@ __global__ void __launch_bounds__(kEventThreads, 2) batch_event_kernel(const Ins
     }
     drain(0, q.n);
     flush_warp(c, ctr);
+}
+
+// ------------------------------------------------------------------------------------------------
+// the learned sampler's inputs for every listed event (Sec. 5.1): a lepton's (chi, r2, s.beta) as its
+// event will see them (the streaming pass's classical step with accurate fields; r2 the uniform of its
+// energy-fraction draw, which the ICDF row would take); a pair event gets placeholders (chi 1, r 1/2,
+// s 0) and lep 0, so that list position k is sample k
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) batch_mlp_prep_kernel(const InstDev* __restrict__ inst,
+                                                             const SegCtx* __restrict__ ctx,
+                                                             const long long* __restrict__ ev,
+                                                             const ClockDev* __restrict__ clk, double* chi, double* r,
+                                                             double* sb, uint8_t* lep) {
+    const unsigned long long n = clk->n_events;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const long long e = ev[k];
+        const SegCtx& X = ctx[(int)(e >> 32)];
+        if (X.sp == 2) {
+            chi[k] = 1.0;
+            r[k] = 0.5;
+            sb[k] = 0.0;
+            lep[k] = 0;
+            continue;
+        }
+        const int64_t j = (int64_t)(uint32_t)e;
+        const PartDev& L = inst[X.ii].sp[X.sp];
+        const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
+        LState st;
+        lepton_classical<0, true>(X.C, a, b, cc, st, nullptr);
+        const uint4 w1 = draw(L.id[j], X.C.S.seed, X.C.S.step, kSlotLambdaSpin);
+        chi[k] = (double)st.chi;
+        r[k] = uniform52(w1.x, w1.y);
+        sb[k] = (double)st.sb;
+        lep[k] = 1;
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -577,6 +616,15 @@ struct qed_batch_s {
     int exec_steps;
     std::vector<cudaEvent_t> kev;  // caller's event pairs around the persistent kernel (may be empty)
     long long direct_steps;        // directly launched steps (event pair index of the next one)
+    // the learned sampler on the event path (mlp NULL: the tables): per listed event its inputs, the
+    // sampler's outputs and whether it is a lepton's; the fallback count since the network was set
+    qed_mlp_t mlp;
+    double mlp_tol;
+    int mlp_grid;
+    double *d_mchi, *d_mr, *d_ms;
+    float* d_mout;
+    uint8_t* d_mlep;
+    unsigned long long* d_mfb;
 };
 
 template <int WARPS, int STAGES, int MINB, uint32_t FIX>
@@ -637,9 +685,15 @@ static void launch_batch_step(const qed_batch_s* b, cudaStream_t st, cudaEvent_t
                                                   tab_params<float>(b->tables), b->tables->bes32, P);
     if (e0) cudaEventRecordWithFlags(e0, st, rec);
     variant_of(b, b->tuning.variant).launch(b, b->grid, st);
+    if (b->mlp) {  // the learned sampler draws every listed emission's energy fraction
+        batch_mlp_prep_kernel<<<b->sms * 8, 256, 0, st>>>(b->d_inst, b->d_ctx, b->d_ev, b->d_clk, b->d_mchi, b->d_mr,
+                                                          b->d_ms, b->d_mlep);
+        mlp_sample_listed(b->mlp, b->tables, b->d_mchi, b->d_mr, b->d_ms, b->capacity_total, &b->d_clk->n_events,
+                          b->mlp_tol, b->d_mout, b->d_mfb, b->mlp_grid, st);
+    }
     batch_event_kernel<<<b->ev_grid, kEventThreads, 0, st>>>(b->d_inst, b->d_ctx, b->d_ev, b->d_clk,
                                                              Tab64{tab_params<double>(b->tables), b->tables->bes64},
-                                                             b->ctr);
+                                                             b->ctr, b->mlp ? b->d_mout : nullptr);
     if (e1) cudaEventRecordWithFlags(e1, st, rec);
     batch_compact_head<<<(b->n_inst + 255) / 256, 256, 0, st>>>(b->d_inst, b->n_inst);
     const dim3 g(kCompactBlocks, b->n_inst);
@@ -713,6 +767,12 @@ extern "C" void qed_batch_destroy(qed_batch_t b) {
     cudaFree(b->d_hdr);
     cudaFree(b->d_app);
     cudaFree(b->d_ws);
+    cudaFree(b->d_mchi);
+    cudaFree(b->d_mr);
+    cudaFree(b->d_ms);
+    cudaFree(b->d_mout);
+    cudaFree(b->d_mlep);
+    cudaFree(b->d_mfb);
     b->magic = 0;
     delete b;
 }
@@ -865,6 +925,68 @@ extern "C" qed_status qed_batch_set_kernel_events(qed_batch_t b, void* const* ev
     b->kev.assign((cudaEvent_t*)events, (cudaEvent_t*)events + 2 * n_pairs);
     b->direct_steps = 0;
     return QED_OK;
+}
+
+extern "C" qed_status qed_batch_set_mlp(qed_batch_t b, qed_mlp_t m, double tol) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (m && !mlp_valid(m)) return QED_ERR_STATE;
+    if (m && (!(tol > 0.0) || !(tol < 1.0) || (b->desc.flags & QED_F_REJECT))) return QED_ERR_ARG;
+    drop_graph(b);
+    if (!m) {
+        b->mlp = nullptr;
+        return QED_OK;
+    }
+    if (!b->d_mout) {
+        const size_t n = (size_t)std::max<int64_t>(1, b->capacity_total);
+        const bool ok = cudaMalloc(&b->d_mchi, 8 * n) == cudaSuccess && cudaMalloc(&b->d_mr, 8 * n) == cudaSuccess &&
+                        cudaMalloc(&b->d_ms, 8 * n) == cudaSuccess && cudaMalloc(&b->d_mout, 16 * n) == cudaSuccess &&
+                        cudaMalloc(&b->d_mlep, n) == cudaSuccess &&
+                        cudaMalloc(&b->d_mfb, sizeof(unsigned long long)) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            cudaFree(b->d_mchi);
+            cudaFree(b->d_mr);
+            cudaFree(b->d_ms);
+            cudaFree(b->d_mout);
+            cudaFree(b->d_mlep);
+            cudaFree(b->d_mfb);
+            b->d_mchi = b->d_mr = b->d_ms = nullptr;
+            b->d_mout = nullptr;
+            b->d_mlep = nullptr;
+            b->d_mfb = nullptr;
+            return QED_ERR_NOMEM;
+        }
+    }
+    if (cudaMemset(b->d_mfb, 0, sizeof(unsigned long long)) != cudaSuccess) return QED_ERR_CUDA;
+    b->mlp = m;
+    b->mlp_tol = tol;
+    b->mlp_grid = mlp_listed_grid(std::max<int64_t>(1, b->capacity_total));
+    return QED_OK;
+}
+
+extern "C" qed_status qed_batch_mlp_last(qed_batch_t b, int64_t n_max, double* chi, double* r, double* s_beta,
+                                         float* out4, uint8_t* is_lepton, int64_t* n_out,
+                                         unsigned long long* n_fallback_total) {
+    if (!valid_batch(b)) return QED_ERR_STATE;
+    if (!b->d_mout) return QED_ERR_STATE;  // no network was ever set
+    if (n_max < 0) return QED_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QED_ERR_CUDA;
+    ClockDev clk;
+    unsigned long long fb = 0;
+    if (cudaMemcpy(&clk, b->d_clk, sizeof(ClockDev), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&fb, b->d_mfb, sizeof(fb), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return QED_ERR_CUDA;
+    if (n_out) *n_out = (int64_t)clk.n_events;
+    if (n_fallback_total) *n_fallback_total = fb;
+    const size_t n = (size_t)std::min<int64_t>(n_max, (int64_t)clk.n_events);
+    if (n == 0) return QED_OK;
+    bool ok = true;
+    if (chi) ok = ok && cudaMemcpy(chi, b->d_mchi, 8 * n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (r) ok = ok && cudaMemcpy(r, b->d_mr, 8 * n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (s_beta) ok = ok && cudaMemcpy(s_beta, b->d_ms, 8 * n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (out4) ok = ok && cudaMemcpy(out4, b->d_mout, 16 * n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (is_lepton) ok = ok && cudaMemcpy(is_lepton, b->d_mlep, n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    return ok ? QED_OK : QED_ERR_CUDA;
 }
 
 extern "C" qed_status qed_batch_stats_read(qed_batch_t b, qed_batch_stats* out, void* stream) {

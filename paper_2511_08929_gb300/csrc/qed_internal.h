@@ -154,3 +154,13 @@ inline int launch_blocks(int64_t work, int threads) {
     const int64_t need = (work + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
 }
+
+// The learned sampler inside the batched step (defined with the network in qed_mlp.cu): the network's
+// validity check, the persistent grid of its sampling kernel for up to n_max samples, and that kernel
+// over the first min(n_max, *n_dev) samples (n_dev a count on the device, written by an earlier kernel
+// of the same stream), checked at tol with the tables' mixture quantile as fallback.
+bool mlp_valid(qed_mlp_t m);
+int mlp_listed_grid(int64_t n_max);
+qed_status mlp_sample_listed(qed_mlp_t m, const qed_tables_s* t, const double* chi, const double* r, const double* s,
+                             int64_t n_max, const unsigned long long* n_dev, double tol, float* out4,
+                             unsigned long long* n_fallback, int grid, cudaStream_t st);

@@ -577,8 +577,13 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
                                                          const double* __restrict__ chi_in, const double* __restrict__ r_in,
                                                          const double* __restrict__ s_in, int64_t n, double tol,
                                                          int flags, float* __restrict__ out4, uint8_t* __restrict__ fell,
-                                                         float* __restrict__ err_out, unsigned long long* n_fallback) {
+                                                         float* __restrict__ err_out, unsigned long long* n_fallback,
+                                                         const unsigned long long* __restrict__ n_dev = nullptr) {
     __shared__ TcShared S;
+    if (n_dev) {  // a count the previous kernel of the stream left on the device
+        const int64_t nd = (int64_t)*n_dev;
+        if (nd < n) n = nd;
+    }
     if (threadIdx.x == 0) S.queued = 0;
     tc_setup(S, P);
     unsigned long long nf = 0;  // thread 0: fallbacks of this block
@@ -883,5 +888,19 @@ extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* 
     const int blocks = tc_blocks(n, (const void*)mlp_sample_kernel);
     mlp_sample_kernel<<<blocks, kTR, 0, (cudaStream_t)stream>>>(
         m->P, tab_params<double>(t), t->bes64, chi, r, s, n, tol, flags, out4, fell_back, err_out, n_fallback);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+// ---- the sampler inside the batched step (qed_batch.cu) ------------------------------------------------
+
+bool mlp_valid(qed_mlp_t m) { return valid_mlp(m); }
+
+int mlp_listed_grid(int64_t n_max) { return tc_blocks(n_max, (const void*)mlp_sample_kernel); }
+
+qed_status mlp_sample_listed(qed_mlp_t m, const qed_tables_s* t, const double* chi, const double* r, const double* s,
+                             int64_t n_max, const unsigned long long* n_dev, double tol, float* out4,
+                             unsigned long long* n_fallback, int grid, cudaStream_t st) {
+    mlp_sample_kernel<<<grid, kTR, 0, st>>>(m->P, tab_params<double>(t), t->bes64, chi, r, s, n_max, tol, 0, out4,
+                                            nullptr, nullptr, n_fallback, n_dev);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }

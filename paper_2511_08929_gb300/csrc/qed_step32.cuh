@@ -593,7 +593,8 @@ __device__ __forceinline__ bool reject_nbw(const Ctx& C, const uint4& w0, float 
 // the FP32 pass's decision.  Outputs: the lepton's x, p, s and the photon's k and P, rounded to float.
 static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X, const FieldP<double>& F64,
                                                   const float4& a, const float4& b, const float4& cc, bool down,
-                                                  const uint4& w0, const uint4& w1, const uint4& w2, F3& x_out,
+                                                  bool net, float lnu, const uint4& w0, const uint4& w1,
+                                                  const uint4& w2, F3& x_out,
                                                   F3& p_out, F3& s_out, F3& k_out, F3& P_out) {
     using V = V3<double>;
     const uint32_t fl = C.S.flags;
@@ -621,6 +622,10 @@ static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X,
         lam = r1 * r1 * r1;
         one_m = 1.0 - lam;
         up = 2.0 * lam / (3.0 * chi * one_m);
+    } else if (net) {  // ln u' as the learned sampler drew it from the same uniform r2
+        up = exp((double)lnu);
+        lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up);
+        one_m = 1.0 - lam;
     } else {
         up = exp(icdf_lookup(X.T, false, down ? 1 : 0, log(chi), log(r2) - log(1.0 - r2)));
         lam = 3.0 * chi * up / (2.0 + 3.0 * chi * up);
@@ -669,12 +674,14 @@ static __device__ __noinline__ void lepton_event64(const Ctx& C, const Tab64& X,
 
 // Events to be taken again in FP64, queued per warp so that the FP64 code runs with all 32 lanes busy
 // (one ill-conditioned lane would otherwise make its whole warp run it).  An entry names the lepton, the
-// photon's reserved slot (-1: no photon stored) and the caller's context key with the branch in bit 30.
+// photon's reserved slot (-1: no photon stored), the caller's context key with the branch in bit 30 and
+// the learned sampler's ln u' (when the caller uses it).
 constexpr int kExactQ = 64;  // entries per warp; drained 32 at a time
 struct ExactQ {
     int64_t j[kExactQ];
     int64_t slot[kExactQ];
     int key[kExactQ];
+    float lnu[kExactQ];
     int n;
 };
 
@@ -682,7 +689,7 @@ struct ExactQ {
 // the step began with; its event outcome and its photon (in the reserved slot) are written here.
 static __device__ __noinline__ void lepton_exact_one(const Ctx& C, const Tab64& X, const FieldP<double>& F64,
                                                     const PartDev& L, const PartDev& G, int64_t j, int64_t slot,
-                                                    bool down) {
+                                                    bool down, bool net = false, float lnu = 0.0f) {
     const uint32_t fl = C.S.flags;
     const float4 a = __ldcg(L.q0 + j), b = __ldcg(L.q1 + j), cc = __ldcg(L.q2 + j);
     const uint64_t id = L.id[j];
@@ -690,7 +697,7 @@ static __device__ __noinline__ void lepton_exact_one(const Ctx& C, const Tab64& 
     const uint4 w1 = draw(id, C.S.seed, C.S.step, kSlotLambdaSpin);
     const uint4 w2 = draw(id, C.S.seed, C.S.step, kSlotStokes);
     F3 x, pf, sf, k, P;
-    lepton_event64(C, X, F64, a, b, cc, down, w0, w1, w2, x, pf, sf, k, P);
+    lepton_event64(C, X, F64, a, b, cc, down, net, lnu, w0, w1, w2, x, pf, sf, k, P);
     const double tau_new = ((fl & QED_F_TAU) && !(fl & QED_F_REJECT)) ? exp_draw(w0.x, w0.y) : tau_join(cc.z, cc.w);
     store32(L, j, x, pf, sf, cc.y, tau_new);
     if (slot >= 0) {
@@ -704,11 +711,13 @@ static __device__ __noinline__ void lepton_exact_one(const Ctx& C, const Tab64& 
 // the event pass of one warp (all 32 lanes call it): a lane with j >= 0 takes particle j of buffer L,
 // whose step context is C and whose photons go to G through the reservation A (lanes may differ in all
 // three; A is NULL when the caller keeps no photons).  q (may be NULL): the warp's queue for the events
-// taken again in FP64, with the lane's context key; without it they are taken here.
+// taken again in FP64, with the lane's context key; without it they are taken here.  net: the energy
+// fraction is u' = exp(lnu), drawn by the learned sampler from the same uniform (Sec. 5.1), instead of
+// the branch's ICDF row.
 static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, const FieldP<double>& F64, int64_t j,
                                                  const PartDev& L, const PartDev& G, AppendState* A,
                                                  qed_counters* ctr, unsigned long long* c, ExactQ* q = nullptr,
-                                                 int key = 0) {
+                                                 int key = 0, bool net = false, float lnu = 0.0f) {
     // The lepton's outcome (energy fraction, recoil, spin) and the photon's polarization for every event,
     // then the photon's slot reservation: an event whose photon does not fit is not applied.
     const uint32_t fl = C.S.flags;
@@ -746,6 +755,12 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
             lam64 = r1 * r1 * r1;
             om64 = 1.0 - lam64;
             up = 2.0 * lam64 / (3.0 * (double)st.chi * om64);
+        } else if (net) {
+            const double chi = (double)st.chi;
+            up = exp((double)lnu);
+            const double den = 2.0 + 3.0 * chi * up;
+            lam64 = 3.0 * chi * up / den;
+            om64 = 2.0 / den;
         } else if (nlc_up_ff(C.T, down ? 1 : 0, logf(st.chi), w1.x, w1.y, up32)) {
             const float den = fmaf(3.0f * st.chi, up32, 2.0f);
             const float iden = rcp_(den);
@@ -808,7 +823,8 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
                 }
             }
         }
-        if (exact && q == nullptr) lepton_event64(C, X, F64, a, b, cc, down, w0, w1, w2, st.x, pf, sf, k, P);
+        if (exact && q == nullptr)
+            lepton_event64(C, X, F64, a, b, cc, down, net, lnu, w0, w1, w2, st.x, pf, sf, k, P);
         else if (!exact) P = stokes_to_P(xi, st.eps, st.beta, st.khat);
         if ((fl & QED_F_TAU) && !rej) tau_new = exp_draw(w0.x, w0.y);
         want = sqrt_(dot(k, k)) >= C.S.store_min_f;
@@ -846,6 +862,7 @@ static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, 
             q->j[e] = j;
             q->slot[e] = keep ? A->base[0] + ev : -1;
             q->key[e] = key | (down ? (1 << 30) : 0);
+            q->lnu[e] = lnu;
         }
         __syncwarp();
         if ((threadIdx.x & 31) == 0) q->n += __popc(m);

@@ -24,7 +24,10 @@ import oracle as O
 from oracle import mlp as OM
 from paper_2511_08929_gb300 import binding as B
 from paper_2511_08929_gb300 import buffers as Q
+from paper_2511_08929_gb300 import inputs as I
 from paper_2511_08929_gb300 import mlp as GM
+
+from parity_util import as_oracle_field, by_id
 
 pytestmark = pytest.mark.gpu
 
@@ -234,3 +237,122 @@ def test_network_against_the_step_sampler(gpu_tables, trained):
     n = chi.shape[0]
     print(f"network {n / t_net:.3e}/s, bisection {n / t_bis:.3e}/s, step sampler {n / t_br:.3e}/s")
     assert t_net < t_bis and t_br < t_net
+
+
+
+def _event_batch(gt, b, ph, f, seed, smp=None, tol=1e-4):
+    """One instance: the leptons b and photons ph with a spent optical depth, so that every particle
+    with a non-zero rate takes an event in the first step; every photon is stored."""
+    n = len(b["id"])
+    bt = Q.Batch(gt, [f], [seed], [(2 * n, 2 * n, 4 * n)], 0.1, t0=10.0, step0=0)
+    e, _, g = bt.buffers()[0]
+    e.load(b["pos"], b["mom"], b["spin"], b["w"], b["id"], tau=np.full(n, 1e-6))
+    g.load(ph["pos"], ph["mom"], ph["spin"], ph["w"], ph["id"], tau=np.full(len(ph["id"]), 1e-6))
+    if smp is not None:
+        bt.set_sampler(smp, tol)
+    return bt
+
+
+def _lambdas(bt, parents, seed):
+    """lambda = |k| / (|k| + |p_f|) of each parent's event, from its photon and its final momentum."""
+    e, _, g = bt.buffers()[0]
+    er, gr = e.read(), g.read()
+    pmap = {int(i): k for k, i in enumerate(er["id"])}
+    gmap = {int(i): k for k, i in enumerate(gr["id"])}
+    out = np.zeros(len(parents))
+    for m, pid in enumerate(parents):
+        kk = np.linalg.norm(gr["mom"][gmap[O.child_ids(int(pid), seed, 0)[0]]])
+        pf = np.linalg.norm(er["mom"][pmap[int(pid)]])
+        out[m] = kk / (kk + pf)
+    return out
+
+
+def test_network_on_the_event_path(gpu_tables, ora_tables, trained):
+    """The sampler inside the batched step (qed_batch_set_mlp): one step of leptons and photons that all
+    take events.  The event list, and so the event count, is the one the tables give; every lepton event's
+    inputs are its chi, its own uniform r2 (the oracle's Philox draw for its id) and s.beta in [-1, 1];
+    its ln u' meets the exact mixture CDF within the bound (network) or the tables' accuracy (fallback);
+    the event applied exactly that u' (lambda from the photon and the recoiled lepton equals
+    3 chi u'/(2 + 3 chi u')); pair events carry the placeholders.  Against the oracle's mixture-quantile
+    mode (the exact quantile at the same r2, from the oracle's own classical step) on a subset: the same
+    events, and each ln u' within the CDF bound mapped through the mixture's density there.  Setting the
+    network back to NULL restores the table step bit for bit, and the captured graph runs the sampler
+    too."""
+    smp, _ = trained
+    tol, seed = 1e-4, 23
+    n = 6000
+    b = I.random_states(n, seed=61, gamma_range=(200.0, 5000.0), field_region=(-35.0, 5.0))
+    ph = I.random_states(1500, seed=62, gamma_range=(2000.0, 8000.0), field_region=(-35.0, 5.0))
+    ph["id"] = ph["id"] + np.uint64(10 ** 12)
+    f = Q.field(B.QED_FIELD_LP, a0=120.0, n_cycles=5.0, eta0=I.eta0_for_wavelength(0.8))
+    A = _event_batch(gpu_tables, b, ph, f, seed)
+    Bn = _event_batch(gpu_tables, b, ph, f, seed, smp, tol)
+    Cr = _event_batch(gpu_tables, b, ph, f, seed, smp, tol)
+    Cr.set_sampler(None)
+    pre = A.buffers()[0][0].read()
+    for bt in (A, Bn, Cr):
+        bt.step(1)
+    torch.cuda.synchronize()
+    ca, cb = A.ctr.read(), Bn.ctr.read()
+    assert ca.status == 0 and cb.status == 0 and ca.dropped_capacity == 0
+    assert cb.events == ca.events
+    n_ev, fb, d = Bn.sampler_last(8 * n)
+    lep = d["is_lepton"]
+    assert n_ev == len(lep) and lep.sum() > 1000 and (~lep).sum() > 100, (n_ev, lep.sum())
+    assert fb < 0.5 * n_ev
+    np.testing.assert_array_equal(d["chi"][~lep], 1.0)
+    np.testing.assert_array_equal(d["r"][~lep], 0.5)
+    np.testing.assert_array_equal(d["s_beta"][~lep], 0.0)
+    assert np.all(d["chi"][lep] > 0) and np.all(np.abs(d["s_beta"][lep]) <= 1.0)
+    # each lepton event's r2 is its own draw: it names the parent
+    r2 = {O.uniform_pair(int(i), seed, 0, 1)[0]: int(i) for i in b["id"]}
+    parents = np.array([r2[x] for x in d["r"][lep]], dtype=np.uint64)
+    assert len(set(parents.tolist())) == len(parents)
+    chi, r, s, L = d["chi"][lep], d["r"][lep], d["s_beta"][lep], d["out4"][lep, 0].astype(np.float64)
+    rng = np.random.default_rng(3)
+    for i in rng.choice(len(r), 200, replace=False):
+        c = O.mlp_cdf(chi[i], s[i], L[i])
+        assert abs(c - r[i]) < tol + TABLE_ERR + 1e-6 * abs(L[i]), (i, chi[i], s[i], L[i], c, r[i])
+    up = np.exp(L)
+    lam_pred = 3 * chi * up / (2 + 3 * chi * up)
+    lam_net = _lambdas(Bn, parents, seed)
+    np.testing.assert_allclose(lam_net, lam_pred, rtol=3e-5)
+    # the oracle's exact mixture quantile on the first m electrons
+    m = 1500
+    oL = O.Particles.from_arrays(m, pre["pos"][:m], pre["mom"][:m], pre["spin"][:m], pre["w"][:m], pre["id"][:m],
+                                 tau=pre["tau"][:m])
+    oG = O.Particles(2 * m)
+    octr = O.lepton_step(ora_tables, as_oracle_field(f), O.step_desc(0.1, 10.0, 0, seed, O.F_FULL | O.F_MIX_QUANTILE),
+                         -1, oL, oG)
+    in_sub = np.isin(parents, pre["id"][:m])
+    assert octr.events == int(in_sub.sum()) > 500
+    og, ol = oG.view(), oL.view()
+    gmap = {int(i): k for k, i in enumerate(og["id"])}
+    lmap = {int(i): k for k, i in enumerate(ol["id"])}
+    worst = 0.0
+    for i in rng.choice(np.flatnonzero(in_sub), 150, replace=False):
+        pid = int(parents[i])
+        kk = np.linalg.norm(og["mom"][gmap[O.child_ids(pid, seed, 0)[0]]])
+        lo = kk / (kk + np.linalg.norm(ol["mom"][lmap[pid]]))
+        L_o = math.log(2 * lo / (3 * chi[i] * (1 - lo)))
+        h = 1e-3
+        dF = (O.mlp_cdf(chi[i], s[i], L_o + h) - O.mlp_cdf(chi[i], s[i], L_o - h)) / (2 * h)
+        bound = 1.5 * (tol + TABLE_ERR) / max(dF, 1e-300) + 1e-5 * (1 + abs(L_o))
+        worst = max(worst, abs(L[i] - L_o) / bound)
+    assert worst <= 1.0, worst
+    lam_tab = _lambdas(A, parents, seed)
+    moved = np.abs(lam_net / lam_tab - 1) > 1e-5
+    assert moved.mean() > 0.05, moved.mean()  # the network's samples, not the ICDF rows, were applied
+    # NULL restores the tables exactly (by id: daughters are appended in the order their warps reserve)
+    for x, y in zip(A.buffers()[0], Cr.buffers()[0]):
+        ra, rc = by_id(x.read()), by_id(y.read())
+        for k in ra:
+            np.testing.assert_array_equal(ra[k], rc[k])
+    # a captured graph of 8 steps runs the sampler too
+    Bn.set_tuning(graph_steps=8)
+    Bn.step(8)
+    torch.cuda.synchronize()
+    n2, fb2, _ = Bn.sampler_last(0)
+    assert Bn.ctr.read().status == 0 and n2 >= 0 and fb2 >= fb
+    for bt in (A, Bn, Cr):
+        bt.close()

@@ -16,6 +16,8 @@ module's own (nothing is taken from the oracle's tables or integrals):
 * The per-step probability decision (Sec. 4.1, 5.1, 5.2: event if r1 < W dt, branch by the same r1):
   event frequency W dt within binomial statistics, with W from the closed-form rate, and the sampled
   spectrum the spin (polarization) mixture, so the branch share W_down (1 - s.beta) / (2 W_s) holds.
+* The oracle's mixture-quantile mode (the learned sampler's target on the step): its fractions follow
+  the same w(lambda; s.beta), and each inverts the exact mixture CDF at the lepton's own r2.
 * T-BMT (Sec. 8.3): in a Wien filter (E = v B, E perpendicular to B and v) the momentum is constant and
   the spin precesses about B at (1 + a) B / gamma^2 (the textbook Wien-filter rotation) in the standard
   form; the form as printed gives (a + 1/gamma) B / gamma^2.
@@ -225,6 +227,33 @@ def test_nlc_photon_fraction_follows_w(chi, tb):
         if chi >= 1.0:
             # the opposite spin's spectrum is rejected: the s.beta term of w is resolved
             assert ks_p(lam, Spectrum(lambda l: nlc_density(l, chi, -sbeta), cube=True)) < 1e-6
+
+
+@pytest.mark.parametrize("chi,sbeta", [(1.0, 0.6), (10.0, -0.8)])
+def test_mixture_quantile_mode(chi, sbeta, tb):
+    """The oracle mode F_MIX_QUANTILE (the learned sampler's target on the step, Sec. 5.1): every
+    emission's u' is the exact quantile of the mixture w(lambda; s.beta) at the lepton's own r2, so the
+    oracle's mixture CDF there returns r2 (1e-9), and the fractions follow the closed-form w(lambda; s.beta)
+    (KS); with the sign of s.beta flipped the CDF misses r2 by more than 1e-3."""
+    n = 1500
+    L, f, pm = _electrons(chi, sbeta * BETA, n=n, seed=9)
+    G = O.Particles(n)
+    ctr = O.lepton_step(tb, f, O.step_desc(0.01, 0.0, 0, 13, FL_EMIT | O.F_MIX_QUANTILE), -1, L, G)
+    assert ctr.events == n and G.n == n
+    g, l = G.view(), L.view()
+    lam = g["mom"][:, 0] / pm
+    assert ks_p(lam, Spectrum(lambda x: nlc_density(x, chi, sbeta), cube=True)) > P_MIN
+    parent = {O.child_ids(int(i), 13, 0)[0]: k for k, i in enumerate(l["id"])}
+    worst, worst_flip = 0.0, 0.0
+    for m in range(0, n, 15):
+        k = parent[int(g["id"][m])]
+        lm = g["mom"][m, 0] / (g["mom"][m, 0] + l["mom"][k, 0])
+        ln_up = math.log(2.0 * lm / (3.0 * chi * (1.0 - lm)))
+        r2 = O.uniform_pair(int(l["id"][k]), 13, 0, 1)[0]
+        worst = max(worst, abs(O.mlp_cdf(chi, sbeta, ln_up) - r2))
+        worst_flip = max(worst_flip, abs(O.mlp_cdf(chi, -sbeta, ln_up) - r2))
+    assert worst < 1e-9, worst
+    assert worst_flip > 1e-3, worst_flip
 
 
 @pytest.mark.parametrize("chi", [0.1, 1.0, 10.0, 99.0])
