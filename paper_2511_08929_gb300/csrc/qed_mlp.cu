@@ -55,32 +55,60 @@ __device__ inline MixPoint mix_point(const TabP<double>& T, double chi, double r
     return m;
 }
 
-// CDF of one spin branch at ln u' = L: the logit y at which the interpolated ICDF equals L (bisection on
-// the monotone interpolant; the linear asymptote below the grid is inverted directly), mapped to r
+// Root of a monotone increasing g on the bracket [a, c] (g(a) < 0 < g(c)) by regula falsi with the
+// Illinois weight (the end that stays put has its value halved, so neither end stalls), started at the
+// guess x0; a step outside the bracket falls back to its midpoint.  Stops when the bracket is below
+// dx or |g| below dg, after at most ITERS evaluations.
+template <int ITERS, class G>
+__device__ inline double illinois(G g, double a, double ga, double c, double gc, double x0, double dx, double dg) {
+    double x = fmin(fmax(x0, a), c);
+    if (!(x > a && x < c)) x = 0.5 * (a + c);
+    int side = 0;
+    for (int it = 0; it < ITERS; ++it) {
+        const double f = g(x);
+        if (fabs(f) <= dg) return x;
+        if (f < 0.0) {
+            a = x;
+            ga = f;
+            if (side == -1) gc *= 0.5;
+            side = -1;
+        } else {
+            c = x;
+            gc = f;
+            if (side == 1) ga *= 0.5;
+            side = 1;
+        }
+        if (c - a <= dx) break;
+        x = (a * gc - c * ga) / (gc - ga);
+        if (!(x > a && x < c)) x = 0.5 * (a + c);
+    }
+    return 0.5 * (a + c);
+}
+
+// CDF of one spin branch at ln u' = L: the logit y at which the interpolated ICDF equals L (the
+// monotone interpolant solved from the guess yg; the linear asymptote below the grid is inverted
+// directly), mapped to r.  The logit to 1e-10, so the CDF to 3e-11.
 template <int ITERS>
-__device__ inline double branch_cdf(const TabP<double>& T, int b, double lnchi, double L) {
-    const double top = icdf_lookup(T, false, b, lnchi, T.y_lo + (T.n_r - 1) / T.inv_dy);
+__device__ inline double branch_cdf(const TabP<double>& T, int b, double lnchi, double L, double yg) {
+    const double yhi = T.y_lo + (T.n_r - 1) / T.inv_dy;
+    const double top = icdf_lookup(T, false, b, lnchi, yhi);
     if (L >= top) return 1.0;
     const double bot = icdf_lookup(T, false, b, lnchi, T.y_lo);
     double y;
     if (L <= bot) {
         y = T.y_lo + (L - bot) / 3.0;  // slope 3 of ln u' in y below the grid (u' ~ r^3)
     } else {
-        double lo = T.y_lo, hi = T.y_lo + (T.n_r - 1) / T.inv_dy;
-        for (int it = 0; it < ITERS; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (icdf_lookup(T, false, b, lnchi, mid) < L) lo = mid;
-            else hi = mid;
-        }
-        y = 0.5 * (lo + hi);
+        auto g = [&](double yy) { return icdf_lookup(T, false, b, lnchi, yy) - L; };
+        y = illinois<ITERS>(g, T.y_lo, bot - L, yhi, top - L, yg, 1e-10, 1e-13 * fmax(1.0, fabs(L)));
     }
     return 1.0 / (1.0 + exp(-y));
 }
 
-// ITERS bisection steps on y in [-20, 20]: 30 leave the CDF within 1e-8, 48 within 1e-13
+// the mixture's CDF at L: each branch solved from the mixture point's own logit, near which its root
+// lies (at most ITERS evaluations each)
 template <int ITERS>
 __device__ inline double mix_cdf(const TabP<double>& T, const MixPoint& m, double L) {
-    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L) + (1.0 - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L);
+    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L, m.y) + (1.0 - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L, m.y);
 }
 
 // the blend of the two branch quantiles (the baseline the network corrects)
@@ -89,17 +117,17 @@ __device__ inline double mix_baseline(const TabP<double>& T, const MixPoint& m) 
 }
 
 // the exact mixture quantile: the mixture CDF lies between the branch CDFs, so its quantile lies between
-// the branch quantiles; bisection there
+// the branch quantiles; the same solver there, from the blend of the two, until the mixture CDF is
+// within 2e-11 of r (the inner solves' own accuracy) or the bracket below 1e-12 in ln u'
 template <int OUTER, int INNER>
 __device__ inline double mix_quantile(const TabP<double>& T, const MixPoint& m, double r) {
     const double qu = icdf_lookup(T, false, 0, m.lnchi, m.y), qd = icdf_lookup(T, false, 1, m.lnchi, m.y);
-    double lo = fmin(qu, qd) - 1e-9, hi = fmax(qu, qd) + 1e-9;
-    for (int it = 0; it < OUTER; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mix_cdf<INNER>(T, m, mid) < r) lo = mid;
-        else hi = mid;
-    }
-    return 0.5 * (lo + hi);
+    const double lo = fmin(qu, qd) - 1e-9, hi = fmax(qu, qd) + 1e-9;
+    auto g = [&](double L) { return mix_cdf<INNER>(T, m, L) - r; };
+    const double glo = g(lo), ghi = g(hi);
+    if (!(glo < 0.0)) return lo;
+    if (!(ghi > 0.0)) return hi;
+    return illinois<OUTER>(g, lo, glo, hi, ghi, m.a * qu + (1.0 - m.a) * qd, 1e-12, 2e-11);
 }
 
 // xi3 = F3 / F0 at u' for s_i = s beta_hat, s_f = 0 (App. A.1)

@@ -12,6 +12,14 @@
 #include "qed_internal.h"
 #include "qed_steps.h"
 
+// How the event passes (lepton_events, photon_events) are compiled into their caller: out of line in
+// the single-buffer kernels, whose streaming loop stays free of their registers; the batched event
+// kernel, which runs nothing else, defines it as __forceinline__ (one block of 256 threads per SM then
+// holds the whole pass in registers without the call frames' local-memory traffic).
+#ifndef QED_EVENT_PASS
+#define QED_EVENT_PASS __noinline__
+#endif
+
 namespace qed {
 
 using F3 = V3<float>;
@@ -714,7 +722,7 @@ static __device__ __noinline__ void lepton_exact_one(const Ctx& C, const Tab64& 
 // taken again in FP64, with the lane's context key; without it they are taken here.  net: the energy
 // fraction is u' = exp(lnu), drawn by the learned sampler from the same uniform (Sec. 5.1), instead of
 // the branch's ICDF row.
-static __device__ __noinline__ void lepton_events(const Ctx& C, const Tab64& X, const FieldP<double>& F64, int64_t j,
+static __device__ QED_EVENT_PASS void lepton_events(const Ctx& C, const Tab64& X, const FieldP<double>& F64, int64_t j,
                                                  const PartDev& L, const PartDev& G, AppendState* A,
                                                  qed_counters* ctr, unsigned long long* c, ExactQ* q = nullptr,
                                                  int key = 0, bool net = false, float lnu = 0.0f) {
@@ -971,7 +979,7 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
 // the pair pass of one warp: a lane with j >= 0 takes photon j of G; the pair goes to El and Po through
 // the reservation A (NULL: the caller keeps no pairs, and photons do not convert).  Everything after the
 // decision is FP64 (pairs are rare; their spin coefficients cancel).
-static __device__ __noinline__ void photon_events(const Ctx& C, const Tab64& X, int64_t j, const PartDev& G,
+static __device__ QED_EVENT_PASS void photon_events(const Ctx& C, const Tab64& X, int64_t j, const PartDev& G,
                                                  const PartDev& El, const PartDev& Po, AppendState* A,
                                                  qed_counters* ctr, unsigned long long* c) {
     const uint32_t fl = C.S.flags;
