@@ -1031,7 +1031,7 @@ def mlp_leg(args, tables, torch, bt=None, stream=0):
             "eval_events": total, "samples_per_s": net_rate, "fallback_fraction": n_fb / total,
             "network_cdf_error_hist": {k: float(v / total) for k, v in zip(labels, hist)},
             "table_path_samples_per_s": tab_rate, "table_path_events": n_tab,
-            "table_path": "the checked sampler's own fallback: the mixture quantile by bisection of its CDF",
+            "table_path": "the checked sampler's own fallback: the exact mixture quantile, regula falsi on the tables' mixture CDF",
             "gain_over_table_path": net_rate / tab_rate,
             "branch_table_samples_per_s": br_rate,
             "branch_table": "the step's sampler: spin branch by W_down(1-s)/(2W_s), one float-float ICDF row",

@@ -425,7 +425,7 @@ qed_status qed_mlp_get_params(qed_mlp_t m, float *host_out);
 qed_status qed_mlp_set_params(qed_mlp_t m, const float *host_in);
 /* Training samples from the FP64 tables: sample first_index + i draws chi (log-uniform over [1e-3, 1e2]),
  * r and s_beta (uniform) from Philox(id = first_index + i, seed, step 2^64 - 2, slots 0 and 1); x_dev gets
- * its n x 3 features, y_dev its n x 4 targets (the exact mixture quantile, found by bisection between
+ * its n x 3 features, y_dev its n x 4 targets (the exact mixture quantile, found by regula falsi between
  * the branch quantiles on the mixture CDF of the interpolated branch rows, and xi3 there, minus the
  * blend baseline, times 100), raw_dev (may be NULL) n x 3 doubles (chi, r, s_beta). */
 qed_status qed_mlp_targets(qed_tables_t t, int64_t n, uint64_t seed, int64_t first_index, float *x_dev, float *y_dev,
@@ -445,7 +445,7 @@ qed_status qed_mlp_forward(qed_mlp_t m, const float *x_dev, int64_t n, float *ou
 /* The sampler: for device arrays chi, r, s_beta (n doubles each), out4 (n x 4 floats) = (ln u', xi1,
  * xi2, xi3) from the network, checked: the exact mixture CDF of the tables at ln u' must be within tol of
  * r and the Stokes vector within tol of its closed form there, else (or with QED_MLP_ALWAYS_TABLE) the
- * table path (the mixture quantile by bisection, the closed-form Stokes vector).  fell_back (n bytes,
+ * table path (the exact mixture quantile, the closed-form Stokes vector).  fell_back (n bytes,
  * may be NULL) marks the samples that took the table path; err_out (n floats, may be NULL) gets the
  * network's CDF error |C(ln u') - r| (-1 where the network was skipped); *n_fallback (device, may be
  * NULL) is incremented by the number of fallbacks. */

@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(kTR) mlp_forward_kernel(const float* __restric
     tc_teardown(S.tmem);
 }
 
-// the table path for sample i (the exact mixture quantile by bisection, and xi3 there)
+// the table path for sample i (the exact mixture quantile, and xi3 there)
 __device__ void table_path(const TabP<double>& T, const double* __restrict__ bes_tab, const double* __restrict__ chi_in,
                            const double* __restrict__ r_in, const double* __restrict__ s_in, int64_t i,
                            float* __restrict__ out4) {

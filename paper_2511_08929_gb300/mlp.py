@@ -82,7 +82,7 @@ class Sampler:
                with_error: bool = False, branch_table: bool = False):
         """(out4 = (ln u', xi1, xi2, xi3), fell_back mask, number of fallbacks[, network CDF errors]) for
         device double arrays chi, r, s.  table_only: the checked sampler's own fallback (the mixture
-        quantile by bisection) for every sample; branch_table: the step's sampler (branch, then one ICDF
+        quantile from the tables) for every sample; branch_table: the step's sampler (branch, then one ICDF
         row) instead of the network."""
         n = chi.shape[0]
         out = torch.empty((n, 4), dtype=torch.float32, device=self.device)

@@ -220,7 +220,7 @@ def test_branch_table_sampler_follows_the_mixture(gpu_tables, trained, chi, s):
 def test_network_against_the_step_sampler(gpu_tables, trained):
     """The honest comparison: per sample, the step's sampler (branch + one float-float ICDF row, 2-D
     tables) is faster than the network with its check, which needs those same tables; the network's gain
-    is only over the exact continuous-spin quantile by bisection.  Both relations are asserted, so the
+    is only over the exact continuous-spin quantile solved on the tables.  Both relations are asserted, so the
     figures quoted for them stay true."""
     smp, _ = trained
     chi, r, s = _query(1 << 22, 43)
@@ -235,7 +235,7 @@ def test_network_against_the_step_sampler(gpu_tables, trained):
 
     t_net, t_bis, t_br = timed(), timed(table_only=True), timed(branch_table=True)
     n = chi.shape[0]
-    print(f"network {n / t_net:.3e}/s, bisection {n / t_bis:.3e}/s, step sampler {n / t_br:.3e}/s")
+    print(f"network {n / t_net:.3e}/s, exact quantile {n / t_bis:.3e}/s, step sampler {n / t_br:.3e}/s")
     assert t_net < t_bis and t_br < t_net
 
 
