@@ -150,6 +150,20 @@ def measured_traffic():
     return d if d.get("source_sha256") == kernel_source_hash() else None
 
 
+# Algorithmic bytes of the FP32 particle traffic, the roofline's numerator.  The per-unit figures the
+# roofline is quoted on: a lepton-step moves 96 B (read x, p, s 36 + tau 8 + id 8; write x, p, s, tau 44),
+# a photon-step 84 B (read x, k, P 36 + tau 8 + id 8; write x, P, tau 32), a stored daughter 52 B.  The
+# smaller figures this layout needs (reported beside them): 88 B per lepton-step (the id only at events,
+# 8 B per event), 56 B per photon-step (read 44, write x 12) + 20 B (P, tau) for a photon with a pair
+# rate; 52 B per stored daughter.
+def unit_bytes(lepton_steps, photon_steps, stored):
+    return 96.0 * lepton_steps + 84.0 * photon_steps + 52.0 * stored
+
+
+def design_bytes(lepton_steps, photon_steps, rate_steps, events, stored):
+    return 88.0 * lepton_steps + 56.0 * photon_steps + 20.0 * rate_steps + 8.0 * events + 52.0 * stored
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -322,14 +336,12 @@ def native(args):
         tmax, psteps_all = reduce_over_ranks(ms, psteps, dist, device)
     value = psteps_all / (tmax / 1e3)
 
-    # roofline of the dominant kernel: algorithmic bytes per launch / its event-timed duration
-    # electron step: 88 B per lepton-step (read x, p, s, tau 44 B; write x, p, s, tau 44 B)
-    #                + 8 B id per emission + 52 B per stored photon (x, k, P 36 + tau 8 + id 8)
-    # photon step:   56 B per photon-step (read x, k, P, tau 44 B; write x 12 B) + 20 B (write P, tau)
-    #                per photon-step with a pair rate, + 8 B id per conversion + 104 B per stored pair
+    # roofline of the dominant kernel: algorithmic bytes per launch / its event-timed duration (the
+    # per-unit figures of unit_bytes; the stored daughters of all species are counted with both kernels,
+    # an upper bound)
     peak, peak_kind = measured_peaks()
-    push_bytes = 88.0 * (n_el + n_po) + 60.0 * (ctr.events)  # events of all species counted together (upper bound)
-    pair_bytes = 56.0 * n_ph + 20.0 * ctr.rate_steps
+    push_bytes = unit_bytes(n_el + n_po, 0.0, ctr.stored)
+    pair_bytes = unit_bytes(0.0, n_ph, ctr.stored)
     bw_push = push_bytes / (t_push / 1e3) / 1e9 if t_push > 0 else 0.0
     bw_pair = pair_bytes / (t_pair / 1e3) / 1e9 if t_pair > 0 else 0.0
     dominant = "photon_step" if t_pair >= t_push else "electron_step"
@@ -586,14 +598,9 @@ def native_batch(args):
     value = psteps_all / (tmax / 1e3)
 
     # roofline of the persistent kernel: algorithmic bytes per launch / its event-timed duration
-    # lepton-step 88 B (read x, p, s, tau 44 B; write them 44 B); photon-step 56 B (read x, k, P, tau 44 B;
-    # write x 12 B) + 20 B (write P, tau) when the photon has a pair rate; 8 B (id) per event; 52 B per
-    # stored daughter
     peak, peak_kind = measured_peaks()
-    alg = 88.0 * (d_sp[0] + d_sp[1]) + 56.0 * d_sp[2] + 20.0 * ctr.rate_steps + 8.0 * ctr.events + 52.0 * ctr.stored
-    # the same with the survey's per-unit figures (the id read every step): 96 B per lepton-step, 64 B per
-    # photon-step + 20 B with a pair rate
-    alg_survey = 96.0 * (d_sp[0] + d_sp[1]) + 64.0 * d_sp[2] + 20.0 * ctr.rate_steps + 52.0 * ctr.stored
+    alg = unit_bytes(d_sp[0] + d_sp[1], d_sp[2], ctr.stored)
+    alg_design = design_bytes(d_sp[0] + d_sp[1], d_sp[2], ctr.rate_steps, ctr.events, ctr.stored)
     tr = measured_traffic()
     traffic = None
     if tr is not None:  # ncu DRAM bytes per particle-step of a smaller capture, scaled to this launch
@@ -601,14 +608,14 @@ def native_batch(args):
     # the timed span of a step: the persistent streaming kernel and the event kernel that follows it
     roof = {"kernel": "batch_step_kernel+batch_event_kernel", "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
             "frac": None, "traffic": traffic, "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": alg / K}
+            "algorithmic_bytes_per_launch": alg / K, "design_bytes_per_launch": alg_design / K}
     if tr is not None:
         roof["traffic_source"] = tr["source"]
     if t_kern:
         tk = sum(t_kern)
         achieved = alg / (tk / 1e3) / 1e9
         roof.update({"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
-                     "frac_survey_bytes": round(alg_survey / (tk / 1e3) / 1e9 / peak, 4),
+                     "frac_design_bytes": round(alg_design / (tk / 1e3) / 1e9 / peak, 4),
                      "ms_per_launch": round(tk / K, 4), "share_of_step": round(tk / ms, 4)})
     clocks = summarize_clocks(clock_lines)
     if extras_on:
@@ -768,15 +775,16 @@ def native_cascade(args):
         tmax, psteps_all = reduce_over_ranks(ms, psteps, dist, device)
     value = psteps_all / (tmax / 1e3)
     peak, peak_kind = measured_peaks()
-    alg = 88.0 * (d_sp[0] + d_sp[1]) + 56.0 * d_sp[2] + 20.0 * tot["rate_steps"] + 8.0 * tot["events"] + \
-        52.0 * tot["stored"]
+    alg = unit_bytes(d_sp[0] + d_sp[1], d_sp[2], tot["stored"])
+    alg_design = design_bytes(d_sp[0] + d_sp[1], d_sp[2], tot["rate_steps"], tot["events"], tot["stored"])
     full = steps // SEG * SEG  # steps whose kernels were event-timed (whole graph launches)
     roof = {"kernel": "batch_step_kernel+batch_event_kernel", "bound": "hbm", "peak": peak, "unit": "GB/s",
             "peak_source": peak_kind, "traffic": None,
-            "algorithmic_bytes_per_launch": alg / steps}
+            "algorithmic_bytes_per_launch": alg / steps, "design_bytes_per_launch": alg_design / steps}
     if tk > 0:
         achieved = alg * (full / steps) / (tk / 1e3) / 1e9
         roof.update({"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+                     "frac_design_bytes": round(alg_design * (full / steps) / (tk / 1e3) / 1e9 / peak, 4),
                      "ms_per_launch": round(tk / full, 4), "share_of_step": round(tk / (ms * full / steps), 4)})
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": 0,

@@ -455,15 +455,15 @@ qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double *chi, const 
 
 /* The learned sampler on the batched step's event path: with m set, the energy fraction of every
  * emission (NLC event) of each step comes from the network instead of the branch choice and ICDF row
- * (Sec. 5.1), checked as qed_mlp_sample checks it (mixture CDF within tol of the uniform r2, else the
- * tables' mixture quantile).  Each step then runs, between the streaming pass and the event pass, a
- * kernel that gathers (chi, r2, s.beta) of the listed events and the sampler over them; the network's
- * Stokes outputs are not used (the event computes the photon's Stokes vector from the spectra at the
- * sampled u' with the collapsed final spin, which the network cannot know).  m = NULL restores the
- * tables.  The batch keeps the pointer, not the network: m must outlive its use.  Discards a captured
- * graph.  Scratch: 41 B per particle slot of the batch,
- * allocated by the first call with a network.  Errors: QED_ERR_STATE, QED_ERR_ARG
- * (tol not in (0, 1), or the batch's flags hold QED_F_REJECT), QED_ERR_NOMEM. */
+ * (Sec. 5.1), checked on its quantile as qed_mlp_sample checks it (mixture CDF within tol of the
+ * uniform r2, else the tables' mixture quantile).  Each step then runs, between the streaming pass and
+ * the event pass, a kernel that gathers (chi, r2, s.beta) of the listed events and the sampler over
+ * them.  The network's Stokes outputs are neither used nor checked (out4[1..3] are 0): the event
+ * computes the photon's Stokes vector from the spectra at the sampled u' with the collapsed final spin,
+ * which the network cannot know.  m = NULL restores the tables.  The batch keeps the pointer, not the
+ * network: m must outlive its use.  Discards a captured graph.  Scratch: 41 B per particle slot of the
+ * batch, allocated by the first call with a network.  Errors: QED_ERR_STATE, QED_ERR_ARG (tol not in
+ * (0, 1), or the batch's flags hold QED_F_REJECT), QED_ERR_NOMEM. */
 qed_status qed_batch_set_mlp(qed_batch_t b, qed_mlp_t m, double tol);
 /* For tests of the sampler on the event path: the last step's gathered inputs and samples, the first
  * n_max events (host arrays of n_max doubles each for chi, r, s_beta, n_max x 4 floats for out4, n_max

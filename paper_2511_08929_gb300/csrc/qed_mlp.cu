@@ -584,17 +584,21 @@ __global__ void __launch_bounds__(kTR) mlp_forward_kernel(const float* __restric
     tc_teardown(S.tmem);
 }
 
-// the table path for sample i (the exact mixture quantile, and xi3 there)
+// flags bit of the sampling kernel for callers that use ln u' only (the batched step's event pass):
+// no Stokes outputs, so neither their check nor xi3 on the table path
+constexpr int kLnUpOnly = 4;
+
+// the table path for sample i (the exact mixture quantile, and xi3 there unless ln_up_only)
 __device__ void table_path(const TabP<double>& T, const double* __restrict__ bes_tab, const double* __restrict__ chi_in,
                            const double* __restrict__ r_in, const double* __restrict__ s_in, int64_t i,
-                           float* __restrict__ out4) {
+                           float* __restrict__ out4, bool ln_up_only) {
     const double chi = chi_in[i], r = r_in[i], s = s_in[i];
     const MixPoint m = mix_point(T, chi, r, s);
     const double L = mix_quantile<44, 32>(T, m, r);
     out4[4 * i] = (float)L;
     out4[4 * i + 1] = 0.0f;
     out4[4 * i + 2] = 0.0f;
-    out4[4 * i + 3] = (float)xi3_at(bes_tab, chi, L, s);
+    out4[4 * i + 3] = ln_up_only ? 0.0f : (float)xi3_at(bes_tab, chi, L, s);
 }
 
 // the sampler: network, CDF check; samples that fail it (or all, flags bit 0) wait in a block-wide queue
@@ -618,6 +622,7 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
     uint32_t phase = 0;
     bool broken = false;  // a wait gave up: the remaining tiles take the table path (the same in every thread)
     const bool table_only = (flags & 1) != 0;
+    const bool ln_up_only = (flags & kLnUpOnly) != 0;
     for (int64_t base = (int64_t)blockIdx.x * kTR; base < n; base += (int64_t)gridDim.x * kTR) {
         const int64_t i = base + threadIdx.x;
         float x[3] = {0.0f, 0.0f, 0.0f}, o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -634,10 +639,14 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
                 const MixPoint m = mix_point(T, chi, r, s);
                 const double Lb = mix_baseline(T, m);
                 const double L = Lb + (double)o[0] / kOutScale;
-                const double xi1 = (double)o[1] / kOutScale, xi2 = (double)o[2] / kOutScale;
-                const double xi3 = xi3_at(bes_tab, chi, Lb, s) + (double)o[3] / kOutScale;
+                double xi1 = 0.0, xi2 = 0.0, xi3 = 0.0, xi3x = 0.0;
+                if (!ln_up_only) {
+                    xi1 = (double)o[1] / kOutScale;
+                    xi2 = (double)o[2] / kOutScale;
+                    xi3 = xi3_at(bes_tab, chi, Lb, s) + (double)o[3] / kOutScale;
+                    xi3x = xi3_at(bes_tab, chi, L, s);
+                }
                 const double err_q = fabs(mix_cdf<30>(T, m, L) - r);  // the CDF check
-                const double xi3x = xi3_at(bes_tab, chi, L, s);
                 if (err_out) err_out[i] = (float)err_q;
                 fb = !(err_q <= tol) || !(fabs(xi3 - xi3x) <= tol) || !(fabs(xi1) <= tol) || !(fabs(xi2) <= tol);
                 if (!fb) {
@@ -655,7 +664,7 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
         __syncthreads();
         const int qn = S.queued;  // the same in every thread
         if (qn >= kTR) {
-            table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[qn - kTR + threadIdx.x], out4);
+            table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[qn - kTR + threadIdx.x], out4, ln_up_only);
             __syncthreads();
             if (threadIdx.x == 0) {
                 S.queued = qn - kTR;
@@ -666,7 +675,7 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
     }
     __syncthreads();
     const int qn = S.queued;
-    if ((int)threadIdx.x < qn) table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[threadIdx.x], out4);
+    if ((int)threadIdx.x < qn) table_path(T, bes_tab, chi_in, r_in, s_in, S.queue[threadIdx.x], out4, ln_up_only);
     if (threadIdx.x == 0 && n_fallback && nf + (unsigned long long)qn) atomicAdd(n_fallback, nf + (unsigned long long)qn);
     tc_teardown(S.tmem);
 }
@@ -928,7 +937,7 @@ int mlp_listed_grid(int64_t n_max) { return tc_blocks(n_max, (const void*)mlp_sa
 qed_status mlp_sample_listed(qed_mlp_t m, const qed_tables_s* t, const double* chi, const double* r, const double* s,
                              int64_t n_max, const unsigned long long* n_dev, double tol, float* out4,
                              unsigned long long* n_fallback, int grid, cudaStream_t st) {
-    mlp_sample_kernel<<<grid, kTR, 0, st>>>(m->P, tab_params<double>(t), t->bes64, chi, r, s, n_max, tol, 0, out4,
-                                            nullptr, nullptr, n_fallback, n_dev);
+    mlp_sample_kernel<<<grid, kTR, 0, st>>>(m->P, tab_params<double>(t), t->bes64, chi, r, s, n_max, tol, kLnUpOnly,
+                                            out4, nullptr, nullptr, n_fallback, n_dev);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }

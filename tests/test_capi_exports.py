@@ -47,3 +47,7 @@ def test_argument_errors_need_no_device():
     assert lib.qed_push_step(None, None, None, None, None, None, None) == B.QED_ERR_STATE
     assert lib.qed_counters_read(None, None, None) == B.QED_ERR_ARG
     assert lib.qed_compact_workspace_bytes(1000) >= 1000 * 17
+    # the learned sampler on the batched step: a null batch is refused before any device work
+    assert lib.qed_batch_set_mlp(None, None, 1e-4) == B.QED_ERR_STATE
+    assert lib.qed_batch_mlp_last(None, 0, None, None, None, None, None, None, None) == B.QED_ERR_STATE
+    assert lib.qed_mlp_sample(None, None, None, None, None, 0, 1e-4, 0, None, None, None, None, None) == B.QED_ERR_STATE
