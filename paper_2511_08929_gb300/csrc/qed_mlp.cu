@@ -40,9 +40,11 @@ __device__ __forceinline__ float dsilu_f(float z) {
 }
 
 // ---- the map from (chi, r, s) to the target, FP64 tables -------------------------------------------
-struct MixPoint {
-    double lnchi, y, s, a;  // a = (1 + s) I_up / ((1 + s) I_up + (1 - s) I_down)
+template <class R>
+struct MixPointT {
+    R lnchi, y, s, a;  // a = (1 + s) I_up / ((1 + s) I_up + (1 - s) I_down)
 };
+using MixPoint = MixPointT<double>;
 
 __device__ inline MixPoint mix_point(const TabP<double>& T, double chi, double r, double s) {
     MixPoint m;
@@ -55,65 +57,85 @@ __device__ inline MixPoint mix_point(const TabP<double>& T, double chi, double r
     return m;
 }
 
+// the same point on the float tables; the logit from r and 1 - r, each rounded to float once, so that
+// neither end of (0, 1) loses its precision
+__device__ inline MixPointT<float> mix_point32(const TabP<float>& T, double chi, double r, double s) {
+    MixPointT<float> m;
+    const float c = (float)chi, sf = (float)s;
+    m.lnchi = logf(c);
+    m.y = logf((float)r) - logf((float)(1.0 - r));
+    m.s = sf;
+    float Iu, Id;
+    nlc_rates(T, c, m.lnchi, Iu, Id);
+    m.a = (1.0f + sf) * Iu / ((1.0f + sf) * Iu + (1.0f - sf) * Id);
+    return m;
+}
+
 // Root of a monotone increasing g on the bracket [a, c] (g(a) < 0 < g(c)) by regula falsi with the
 // Illinois weight (the end that stays put has its value halved, so neither end stalls), started at the
 // guess x0; a step outside the bracket falls back to its midpoint.  Stops when the bracket is below
 // dx or |g| below dg, after at most ITERS evaluations.
-template <int ITERS, class G>
-__device__ inline double illinois(G g, double a, double ga, double c, double gc, double x0, double dx, double dg) {
-    double x = fmin(fmax(x0, a), c);
-    if (!(x > a && x < c)) x = 0.5 * (a + c);
+template <int ITERS, class R, class G>
+__device__ inline R illinois(G g, R a, R ga, R c, R gc, R x0, R dx, R dg) {
+    R x = x0 < a ? a : (x0 > c ? c : x0);
+    if (!(x > a && x < c)) x = R(0.5) * (a + c);
     int side = 0;
     for (int it = 0; it < ITERS; ++it) {
-        const double f = g(x);
-        if (fabs(f) <= dg) return x;
-        if (f < 0.0) {
+        const R f = g(x);
+        if ((f < R(0) ? -f : f) <= dg) return x;
+        if (f < R(0)) {
             a = x;
             ga = f;
-            if (side == -1) gc *= 0.5;
+            if (side == -1) gc *= R(0.5);
             side = -1;
         } else {
             c = x;
             gc = f;
-            if (side == 1) ga *= 0.5;
+            if (side == 1) ga *= R(0.5);
             side = 1;
         }
         if (c - a <= dx) break;
         x = (a * gc - c * ga) / (gc - ga);
-        if (!(x > a && x < c)) x = 0.5 * (a + c);
+        if (!(x > a && x < c)) x = R(0.5) * (a + c);
     }
-    return 0.5 * (a + c);
+    return R(0.5) * (a + c);
 }
 
 // CDF of one spin branch at ln u' = L: the logit y at which the interpolated ICDF equals L (the
 // monotone interpolant solved from the guess yg; the linear asymptote below the grid is inverted
 // directly), mapped to r.  The logit to 1e-10, so the CDF to 3e-11.
-template <int ITERS>
-__device__ inline double branch_cdf(const TabP<double>& T, int b, double lnchi, double L, double yg) {
-    const double yhi = T.y_lo + (T.n_r - 1) / T.inv_dy;
-    const double top = icdf_lookup(T, false, b, lnchi, yhi);
-    if (L >= top) return 1.0;
-    const double bot = icdf_lookup(T, false, b, lnchi, T.y_lo);
-    double y;
+// In FP64 (R = double) the logit to 1e-10, so the CDF to 3e-11; on the float tables the logit to 1e-6
+// and the CDF to ~3e-7 (the float entries' own rounding, ~6e-8 of ln u', adds no more than that).
+template <int ITERS, class R>
+__device__ inline R branch_cdf(const TabP<R>& T, int b, R lnchi, R L, R yg) {
+    constexpr bool F64 = sizeof(R) == 8;
+    const R yhi = T.y_lo + R(T.n_r - 1) / T.inv_dy;
+    const R top = icdf_lookup(T, false, b, lnchi, yhi);
+    if (L >= top) return R(1);
+    const R bot = icdf_lookup(T, false, b, lnchi, T.y_lo);
+    R y;
     if (L <= bot) {
-        y = T.y_lo + (L - bot) / 3.0;  // slope 3 of ln u' in y below the grid (u' ~ r^3)
+        y = T.y_lo + (L - bot) / R(3);  // slope 3 of ln u' in y below the grid (u' ~ r^3)
     } else {
-        auto g = [&](double yy) { return icdf_lookup(T, false, b, lnchi, yy) - L; };
-        y = illinois<ITERS>(g, T.y_lo, bot - L, yhi, top - L, yg, 1e-10, 1e-13 * fmax(1.0, fabs(L)));
+        auto g = [&](R yy) { return icdf_lookup(T, false, b, lnchi, yy) - L; };
+        const R aL = L < R(0) ? -L : L;
+        y = illinois<ITERS>(g, T.y_lo, bot - L, yhi, top - L, yg, R(F64 ? 1e-10 : 1e-6),
+                            R(F64 ? 1e-13 : 1e-7) * (aL > R(1) ? aL : R(1)));
     }
-    return 1.0 / (1.0 + exp(-y));
+    return R(1) / (R(1) + exp_(-y));
 }
 
 // the mixture's CDF at L: each branch solved from the mixture point's own logit, near which its root
 // lies (at most ITERS evaluations each)
-template <int ITERS>
-__device__ inline double mix_cdf(const TabP<double>& T, const MixPoint& m, double L) {
-    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L, m.y) + (1.0 - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L, m.y);
+template <int ITERS, class R>
+__device__ inline R mix_cdf(const TabP<R>& T, const MixPointT<R>& m, R L) {
+    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L, m.y) + (R(1) - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L, m.y);
 }
 
 // the blend of the two branch quantiles (the baseline the network corrects)
-__device__ inline double mix_baseline(const TabP<double>& T, const MixPoint& m) {
-    return m.a * icdf_lookup(T, false, 0, m.lnchi, m.y) + (1.0 - m.a) * icdf_lookup(T, false, 1, m.lnchi, m.y);
+template <class R>
+__device__ inline R mix_baseline(const TabP<R>& T, const MixPointT<R>& m) {
+    return m.a * icdf_lookup(T, false, 0, m.lnchi, m.y) + (R(1) - m.a) * icdf_lookup(T, false, 1, m.lnchi, m.y);
 }
 
 // the exact mixture quantile: the mixture CDF lies between the branch CDFs, so its quantile lies between
@@ -139,6 +161,17 @@ __device__ inline double xi3_at(const double* __restrict__ bes_tab, double chi, 
     double b[3];
     bessel64(bes_tab, up, b);
     const double u = lam / one_m, kappa = 1.0 / one_m + one_m;
+    return (b[1] + u * s * b[0]) / (-b[2] + kappa * b[1] + lam * s * b[0]);
+}
+
+// the same from the float Bessel table
+__device__ inline float xi3_at32(const float* __restrict__ bes32, float chi, float L, float s) {
+    if (!(L > -85.0f && L < 50.0f)) return __int_as_float(0x7FC00000);  // u' outside the float range
+    const float up = expf(L);
+    const float den = fmaf(3.0f * chi, up, 2.0f), lam = 3.0f * chi * up / den, one_m = 2.0f / den;
+    float b[3];
+    bessel32(bes32, up, b);
+    const float u = lam / one_m, kappa = 1.0f / one_m + one_m;
     return (b[1] + u * s * b[0]) / (-b[2] + kappa * b[1] + lam * s * b[0]);
 }
 
@@ -601,10 +634,17 @@ __device__ void table_path(const TabP<double>& T, const double* __restrict__ bes
     out4[4 * i + 3] = ln_up_only ? 0.0f : (float)xi3_at(bes_tab, chi, L, s);
 }
 
+// The check of a network sample, first on the float tables: the FP32 CDF and xi3 errors are within ~1e-6
+// of the FP64 ones, so a sample whose FP32 errors are below tol - kMargin32 passes and one with an error
+// above tol + kMargin32 fails without FP64 work; only samples in the band between are checked again on
+// the FP64 tables (the FP64 pipe of this GPU runs at 1/64 of the FP32 rate).
+constexpr float kMargin32 = 1e-5f;
+
 // the sampler: network, CDF check; samples that fail it (or all, flags bit 0) wait in a block-wide queue
 // and take the table path 128 at a time, one per thread, so that the block never waits on a few slow
 // threads (the tiles of the network keep the block in step)
 __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict__ P, TabP<double> T,
+                                                         TabP<float> T32, const float* __restrict__ bes32,
                                                          const double* __restrict__ bes_tab,
                                                          const double* __restrict__ chi_in, const double* __restrict__ r_in,
                                                          const double* __restrict__ s_in, int64_t n, double tol,
@@ -636,24 +676,39 @@ __global__ void __launch_bounds__(kTR) mlp_sample_kernel(const float* __restrict
             bool fb = !net;
             if (!fb) {
                 const double chi = chi_in[i], r = r_in[i], s = s_in[i];
-                const MixPoint m = mix_point(T, chi, r, s);
-                const double Lb = mix_baseline(T, m);
-                const double L = Lb + (double)o[0] / kOutScale;
-                double xi1 = 0.0, xi2 = 0.0, xi3 = 0.0, xi3x = 0.0;
+                // the sample on the float tables: baseline, correction, CDF error (and xi3's)
+                const MixPointT<float> m32 = mix_point32(T32, chi, r, s);
+                const float Lb = mix_baseline(T32, m32);
+                const float L = Lb + o[0] / (float)kOutScale;
+                float xi1 = 0.0f, xi2 = 0.0f, xi3 = 0.0f, dxi3 = 0.0f;
                 if (!ln_up_only) {
-                    xi1 = (double)o[1] / kOutScale;
-                    xi2 = (double)o[2] / kOutScale;
-                    xi3 = xi3_at(bes_tab, chi, Lb, s) + (double)o[3] / kOutScale;
-                    xi3x = xi3_at(bes_tab, chi, L, s);
+                    xi1 = o[1] / (float)kOutScale;
+                    xi2 = o[2] / (float)kOutScale;
+                    xi3 = xi3_at32(bes32, (float)chi, Lb, (float)s) + o[3] / (float)kOutScale;
+                    dxi3 = fabsf(xi3 - xi3_at32(bes32, (float)chi, L, (float)s));
                 }
-                const double err_q = fabs(mix_cdf<30>(T, m, L) - r);  // the CDF check
-                if (err_out) err_out[i] = (float)err_q;
-                fb = !(err_q <= tol) || !(fabs(xi3 - xi3x) <= tol) || !(fabs(xi1) <= tol) || !(fabs(xi2) <= tol);
+                const float ftol = (float)tol;
+                float err_q = fabsf(mix_cdf<30>(T32, m32, L) - (float)r);  // the CDF check
+                const bool stokes_ok = fabsf(xi1) <= ftol && fabsf(xi2) <= ftol;
+                const bool pass32 = err_q <= ftol - kMargin32 && dxi3 <= ftol - kMargin32 && stokes_ok;
+                const bool fail32 = !(err_q <= ftol + kMargin32) || !(dxi3 <= ftol + kMargin32) || !stokes_ok;
+                fb = !pass32;
+                if (!pass32 && !fail32) {  // the band around tol: the FP64 check decides
+                    const MixPoint m = mix_point(T, chi, r, s);
+                    const double e64 = fabs(mix_cdf<30>(T, m, (double)L) - r);
+                    double d64 = 0.0;
+                    if (!ln_up_only)
+                        d64 = fabs(xi3_at(bes_tab, chi, mix_baseline(T, m), s) + (double)o[3] / kOutScale -
+                                   xi3_at(bes_tab, chi, (double)L, s));
+                    err_q = (float)e64;
+                    fb = !(e64 <= tol) || !(d64 <= tol);
+                }
+                if (err_out) err_out[i] = err_q;
                 if (!fb) {
-                    out4[4 * i] = (float)L;
-                    out4[4 * i + 1] = (float)xi1;
-                    out4[4 * i + 2] = (float)xi2;
-                    out4[4 * i + 3] = (float)xi3;
+                    out4[4 * i] = L;
+                    out4[4 * i + 1] = xi1;
+                    out4[4 * i + 2] = xi2;
+                    out4[4 * i + 3] = xi3;
                 }
             } else if (err_out) {
                 err_out[i] = -1.0f;
@@ -923,8 +978,9 @@ extern "C" qed_status qed_mlp_sample(qed_mlp_t m, qed_tables_t t, const double* 
     // persistent grid (one resident wave): each warp streams many 32-sample rows, so its fallback queue
     // drains full
     const int blocks = tc_blocks(n, (const void*)mlp_sample_kernel);
-    mlp_sample_kernel<<<blocks, kTR, 0, (cudaStream_t)stream>>>(
-        m->P, tab_params<double>(t), t->bes64, chi, r, s, n, tol, flags, out4, fell_back, err_out, n_fallback);
+    mlp_sample_kernel<<<blocks, kTR, 0, (cudaStream_t)stream>>>(m->P, tab_params<double>(t), tab_params<float>(t),
+                                                                t->bes32, t->bes64, chi, r, s, n, tol, flags, out4,
+                                                                fell_back, err_out, n_fallback);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
@@ -937,7 +993,8 @@ int mlp_listed_grid(int64_t n_max) { return tc_blocks(n_max, (const void*)mlp_sa
 qed_status mlp_sample_listed(qed_mlp_t m, const qed_tables_s* t, const double* chi, const double* r, const double* s,
                              int64_t n_max, const unsigned long long* n_dev, double tol, float* out4,
                              unsigned long long* n_fallback, int grid, cudaStream_t st) {
-    mlp_sample_kernel<<<grid, kTR, 0, st>>>(m->P, tab_params<double>(t), t->bes64, chi, r, s, n_max, tol, kLnUpOnly,
-                                            out4, nullptr, nullptr, n_fallback, n_dev);
+    mlp_sample_kernel<<<grid, kTR, 0, st>>>(m->P, tab_params<double>(t), tab_params<float>(t), t->bes32, t->bes64,
+                                            chi, r, s, n_max, tol, kLnUpOnly, out4, nullptr, nullptr, n_fallback,
+                                            n_dev);
     return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
