@@ -468,8 +468,8 @@ qed_status qed_batch_set_mlp(qed_batch_t b, qed_mlp_t m, double tol);
 /* For tests of the sampler on the event path: the last step's gathered inputs and samples, the first
  * n_max events (host arrays of n_max doubles each for chi, r, s_beta, n_max x 4 floats for out4, n_max
  * bytes for is_lepton; any may be NULL); *n_out = the number of events of that step; pair events carry
- * placeholder inputs (chi 1, r 1/2, s_beta 0) and is_lepton 0; *n_fallback_total = the samples that took
- * the tables since the network was set.  Synchronous. */
+ * placeholder inputs (chi 1, r 1/2, s_beta 0) and is_lepton 0; *n_fallback_total = the samples (pair
+ * placeholders included) that took the tables since the network was last set.  Synchronous. */
 qed_status qed_batch_mlp_last(qed_batch_t b, int64_t n_max, double *chi, double *r, double *s_beta, float *out4,
                               uint8_t *is_lepton, int64_t *n_out, unsigned long long *n_fallback_total);
 
