@@ -43,6 +43,7 @@ __device__ __forceinline__ float dsilu_f(float z) {
 template <class R>
 struct MixPointT {
     R lnchi, y, s, a;  // a = (1 + s) I_up / ((1 + s) I_up + (1 - s) I_down)
+    R qu, qd;          // the two branch quantiles at the logit y
 };
 using MixPoint = MixPointT<double>;
 
@@ -54,6 +55,8 @@ __device__ inline MixPoint mix_point(const TabP<double>& T, double chi, double r
     double Iu, Id;
     nlc_rates(T, chi, m.lnchi, Iu, Id);
     m.a = (1.0 + s) * Iu / ((1.0 + s) * Iu + (1.0 - s) * Id);
+    m.qu = icdf_lookup(T, false, 0, m.lnchi, m.y);
+    m.qd = icdf_lookup(T, false, 1, m.lnchi, m.y);
     return m;
 }
 
@@ -68,6 +71,8 @@ __device__ inline MixPointT<float> mix_point32(const TabP<float>& T, double chi,
     float Iu, Id;
     nlc_rates(T, c, m.lnchi, Iu, Id);
     m.a = (1.0f + sf) * Iu / ((1.0f + sf) * Iu + (1.0f - sf) * Id);
+    m.qu = icdf_lookup(T, false, 0, m.lnchi, m.y);
+    m.qd = icdf_lookup(T, false, 1, m.lnchi, m.y);
     return m;
 }
 
@@ -101,27 +106,52 @@ __device__ inline R illinois(G g, R a, R ga, R c, R gc, R x0, R dx, R dg) {
     return R(0.5) * (a + c);
 }
 
-// CDF of one spin branch at ln u' = L: the logit y at which the interpolated ICDF equals L (the
-// monotone interpolant solved from the guess yg; the linear asymptote below the grid is inverted
-// directly), mapped to r.  The logit to 1e-10, so the CDF to 3e-11.
-// In FP64 (R = double) the logit to 1e-10, so the CDF to 3e-11; on the float tables the logit to 1e-6
-// and the CDF to ~3e-7 (the float entries' own rounding, ~6e-8 of ln u', adds no more than that).
+// CDF of one spin branch at ln u' = L: the logit y at which the interpolated ICDF row equals L, mapped
+// to r.  The search starts at the mixture point's logit yg, whose quantile qg is known: steps of
+// (L - qg)/3 (the slope of ln u' in the logit below the grid; it is smaller above), doubled until the
+// sign of ICDF(y) - L changes, bracket the root, and the solver finishes inside the bracket.  A step
+// that reaches an end of the grid without the change means L lies beyond the tabulated range: above it
+// the CDF is 1, below it the linear asymptote is inverted directly.  In FP64 (R = double) the logit to
+// 1e-10, so the CDF to 3e-11; on the float tables the logit to 1e-6 and the CDF to ~3e-7 (the float
+// entries' own rounding, ~6e-8 of ln u', adds no more than that).
 template <int ITERS, class R>
-__device__ inline R branch_cdf(const TabP<R>& T, int b, R lnchi, R L, R yg) {
+__device__ inline R branch_cdf(const TabP<R>& T, int b, R lnchi, R L, R yg, R qg) {
     constexpr bool F64 = sizeof(R) == 8;
     const R yhi = T.y_lo + R(T.n_r - 1) / T.inv_dy;
-    const R top = icdf_lookup(T, false, b, lnchi, yhi);
-    if (L >= top) return R(1);
-    const R bot = icdf_lookup(T, false, b, lnchi, T.y_lo);
-    R y;
-    if (L <= bot) {
-        y = T.y_lo + (L - bot) / R(3);  // slope 3 of ln u' in y below the grid (u' ~ r^3)
-    } else {
-        auto g = [&](R yy) { return icdf_lookup(T, false, b, lnchi, yy) - L; };
-        const R aL = L < R(0) ? -L : L;
-        y = illinois<ITERS>(g, T.y_lo, bot - L, yhi, top - L, yg, R(F64 ? 1e-10 : 1e-6),
-                            R(F64 ? 1e-13 : 1e-7) * (aL > R(1) ? aL : R(1)));
+    auto g = [&](R yy) { return icdf_lookup(T, false, b, lnchi, yy) - L; };
+    const R g0 = qg - L;
+    if (g0 == R(0)) return R(1) / (R(1) + exp_(-yg));
+    const bool up = g0 < R(0);  // the root lies above yg
+    R x = yg, gx = g0;
+    R step = (L - qg) / R(3);
+    step = step < R(0) ? -step : step;
+    if (step < R(F64 ? 1e-9 : 1e-5)) step = R(F64 ? 1e-9 : 1e-5);
+    R a = x, ga = gx, c = x, gc = gx;
+    bool found = false;
+    for (int k = 0; k < 26 && !found; ++k) {
+        R xn = up ? x + step : x - step;
+        const bool edge = up ? xn >= yhi : xn <= T.y_lo;
+        if (edge) xn = up ? yhi : T.y_lo;
+        const R gn = g(xn);
+        if (up ? gn >= R(0) : gn <= R(0)) {
+            a = up ? x : xn;
+            ga = up ? gx : gn;
+            c = up ? xn : x;
+            gc = up ? gn : gx;
+            found = true;
+        } else if (edge) {
+            if (up) return R(1);                                   // L above the row's last entry
+            return R(1) / (R(1) + exp_(-(T.y_lo + (-gn) / R(3))));  // below: y_lo + (L - bottom)/3
+        } else {
+            x = xn;
+            gx = gn;
+            step *= R(2);
+        }
     }
+    if (!found) return R(1) / (R(1) + exp_(-x));  // not reached: 26 doublings span the grid
+    const R aL = L < R(0) ? -L : L;
+    const R x0 = a - ga * (c - a) / (gc - ga);
+    const R y = illinois<ITERS>(g, a, ga, c, gc, x0, R(F64 ? 1e-10 : 1e-6), R(F64 ? 1e-13 : 1e-7) * (aL > R(1) ? aL : R(1)));
     return R(1) / (R(1) + exp_(-y));
 }
 
@@ -129,13 +159,14 @@ __device__ inline R branch_cdf(const TabP<R>& T, int b, R lnchi, R L, R yg) {
 // lies (at most ITERS evaluations each)
 template <int ITERS, class R>
 __device__ inline R mix_cdf(const TabP<R>& T, const MixPointT<R>& m, R L) {
-    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L, m.y) + (R(1) - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L, m.y);
+    return m.a * branch_cdf<ITERS>(T, 0, m.lnchi, L, m.y, m.qu) +
+           (R(1) - m.a) * branch_cdf<ITERS>(T, 1, m.lnchi, L, m.y, m.qd);
 }
 
 // the blend of the two branch quantiles (the baseline the network corrects)
 template <class R>
 __device__ inline R mix_baseline(const TabP<R>& T, const MixPointT<R>& m) {
-    return m.a * icdf_lookup(T, false, 0, m.lnchi, m.y) + (R(1) - m.a) * icdf_lookup(T, false, 1, m.lnchi, m.y);
+    return m.a * m.qu + (R(1) - m.a) * m.qd;
 }
 
 // the exact mixture quantile: the mixture CDF lies between the branch CDFs, so its quantile lies between
@@ -143,7 +174,7 @@ __device__ inline R mix_baseline(const TabP<R>& T, const MixPointT<R>& m) {
 // within 2e-11 of r (the inner solves' own accuracy) or the bracket below 1e-12 in ln u'
 template <int OUTER, int INNER>
 __device__ inline double mix_quantile(const TabP<double>& T, const MixPoint& m, double r) {
-    const double qu = icdf_lookup(T, false, 0, m.lnchi, m.y), qd = icdf_lookup(T, false, 1, m.lnchi, m.y);
+    const double qu = m.qu, qd = m.qd;
     const double lo = fmin(qu, qd) - 1e-9, hi = fmax(qu, qd) + 1e-9;
     auto g = [&](double L) { return mix_cdf<INNER>(T, m, L) - r; };
     const double glo = g(lo), ghi = g(hi);
