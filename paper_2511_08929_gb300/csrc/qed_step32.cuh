@@ -949,9 +949,19 @@ __device__ __forceinline__ void photon_classical(const Ctx& C, const float4& a, 
     st.w = cc.w;
     constexpr bool PW = plane_waves_only<FIX>();
     field_eval<float, ACC, PW>(C.F, C.S.ph_hi_f, C.S.ph_lo_f, xold, st.E, st.B);
-    const float en2 = dot(st.k, st.k);
-    st.en = sqrt_(en2);
-    st.khat = en2 > 0.0f ? rsqrtf(en2) * st.k : F3{0, 0, 0};
+    float en2 = dot(st.k, st.k);
+    if (en2 < 0x1.0p-100f) {
+        // |k|^2 near or below the float range (photons of ~1e-15 mc^2 and softer, a few per 1e8 emissions
+        // in the NLC spectrum's lambda^(1/3) tail): the components scaled by 2^100 keep k-hat's precision
+        const F3 ks = 0x1.0p+100f * st.k;
+        const float e2s = dot(ks, ks);
+        st.en = sqrt_(e2s) * 0x1.0p-100f;
+        st.khat = e2s > 0.0f ? rsqrtf(e2s) * ks : F3{0, 0, 0};
+        en2 = e2s > 0.0f ? fmaxf(en2, 0x1.0p-149f) : 0.0f;  // nonzero exactly when k is
+    } else {
+        st.en = sqrt_(en2);
+        st.khat = rsqrtf(en2) * st.k;
+    }
     st.x = xold;
     if (flags_of<FIX>(C) & QED_F_MOVE) st.x = axpy(C.S.dt_f, st.khat, xold);
     st.qed = false;

@@ -203,6 +203,38 @@ def test_photon_pairs_and_compaction(gpu_tables, ora_tables, flags):
     assert f1 + f2 + f3 <= max(1, 1e-5 * 4000 * steps), (f1, f2, f3)
 
 
+def test_soft_photons_move_along_k(gpu_tables, ora_tables):
+    """Photons down to 1e-30 mc^2 (the NLC spectrum's lambda^(1/3) tail stores a few per 1e8 emissions
+    below 1e-15): |k|^2 leaves the float range, yet each moves by dt k-hat like the oracle's, to 1e-6 of
+    the position (and keeps its k, P and optical depth); the FULL-flag step, in and out of the pulse."""
+    n = 400
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    e = 10.0 ** rng.uniform(-30.0, 2.0, n)
+    pos = np.column_stack([rng.uniform(-3, 3, n), rng.uniform(-3, 3, n), rng.uniform(-40, 10, n)])
+    b = {"pos": pos, "mom": d * e[:, None], "spin": np.zeros((n, 3)), "w": np.ones(n),
+         "id": np.arange(n, dtype=np.uint64) * 7 + 3}
+    f = Q.field(B.QED_FIELD_LP, a0=150.0, n_cycles=4.0, eta0=ETA0)
+    gG, oG = _pair(b, B.QED_PHOTON, seed=9, photons=True)
+    gE, gP = Q.ParticleBuffer(64, FP32, B.QED_ELECTRON), Q.ParticleBuffer(64, FP32, B.QED_POSITRON)
+    oE, oP = O.Particles(64), O.Particles(64)
+    ctr, octr = Q.Counters(), O.Counters()
+    st = Q.step_desc(0.2, 6.0, 0, 9)
+    B.qed_pair_step(gpu_tables.handle, f, st, gG.s, gE.s, gP.s, ctr.ptr)
+    O.photon_step(ora_tables, as_oracle_field(f), as_oracle_step(st), oG, oE, oP, octr)
+    torch.cuda.synchronize()
+    g, o = gG.read(), oG.view()
+    assert ctr.read().events == 0 and octr.events == 0 and len(g["id"]) == n
+    go, oo = np.argsort(g["id"]), np.argsort(o["id"])
+    dx = np.linalg.norm(g["pos"][go] - o["pos"][oo], axis=1) / np.maximum(np.linalg.norm(o["pos"][oo], axis=1), 1.0)
+    assert dx.max() < 1e-6, (dx.max(), e[go][np.argmax(dx)])
+    np.testing.assert_array_equal(g["mom"][go], o["mom"][oo].astype(np.float32).astype(np.float64))
+    # every photon moved by dt (the soft ones too)
+    moved = np.linalg.norm(g["pos"][go] - b["pos"][go].astype(np.float32), axis=1)
+    assert np.all(np.abs(moved - 0.2) < 1e-5)
+
+
 def test_constant_field_general_forms(gpu_tables, ora_tables):
     """A constant field with every component nonzero: the FP32 path takes the general forms of chi, the
     basis vector, the Boris push and the T-BMT vector here (the plane-wave forms do not apply)."""
